@@ -1,0 +1,243 @@
+"""Plain FP64 oracle of the Tamm-Dancoff BSE hot path (numpy, CPU) -- test infrastructure.
+
+What it computes, and where each step comes from in the paper (arXiv 2607.05853):
+
+* W_mu,nu(q) = sum_R w_R W_mu,nu(R) exp(-i q.R) with q = k1 - k2: the R-sum inside
+  Eq. W_LRI (§III.A), whose phase is exp(i(k2-k1).R); w_R are the weights of the
+  Wigner-Seitz images of the coarse Born-von Karman cell (§III.B).
+* C^mu_st(k) = sum_R C^mu_st(R) exp(+i k.R), with C^mu_st nonzero only for mu on the
+  atom of s (the two-centre expansion and its Fourier transform, §III.A).
+* C~^mu_{j k2, i k1} = sum_st conj(c^{k2}_sj) c^{k1}_ti [C^mu_st(k1) + C^mu_ts(-k2)]
+  (the Kohn-Sham-basis LRI coefficients, §III.A).
+* direct kernel (j k2*, i k1|W|a k1*, b k2) = (1/N_k) sum_mu,nu C~^mu_{j k2,i k1}
+  W_mu,nu(k1-k2) C~^nu_{a k1,b k2} (Eq. W_LRI) and exchange kernel
+  (a k1*, i k1|V|j k2*, b k2) = (1/N_k) sum C~^mu_{a k1,i k1} V_mu,nu(0) C~^nu_{j k2,b k2}.
+* A_{ai k1, bj k2} = (E^GW_a k1 - E^GW_i k1) delta + alpha * exchange - direct
+  (Eq. Hamiltonian, §II.C; alpha = 2 singlet, 0 triplet).
+* eps2(omega) = 4 pi^2/(3 N_k V) sum_S |sum_{aik} <ik|v|ak>/(E_ak - E_ik) X^S_aik|^2
+  delta(omega - Omega_S) (Eq. abs_vel), the delta broadened to a Lorentzian of
+  half-width eta; the exact sum uses a LAPACK eigendecomposition, and a plain Haydock
+  (Lanczos) recursion gives the same quantity through a continued fraction.
+* lowest exciton energies: LAPACK eigvalsh of the Hermitian TDA matrix.
+
+Index conventions: the H row of (k, v, c) is (k*Nv + v)*Nc + c; valence window column
+v=0 is the valence band maximum (counting down), conduction column c=0 the conduction
+band minimum (counting up); k is flattened (n1*N2 + n2)*N3 + n3.
+
+Everything is FP64 / complex128, evaluated element block by element block from the
+definitions above; W(q) per q and C(k) per k are memoised (this does not change what
+is computed).  Nothing here is shared with, or imported from, the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
+    "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
+]
+
+TWO_PI = 2.0 * np.pi
+
+
+def interp_W(W_R, R_W, w_RW, q):
+    """W_mu,nu(q) = sum_R w_R W_mu,nu(R) e^{-i q.R}; q fractional (Eq. W_LRI's R-sum)."""
+    ph = np.exp(-1j * TWO_PI * (np.asarray(R_W, np.float64) @ np.asarray(q, np.float64)))
+    return np.einsum("r,rmn->mn", ph * np.asarray(w_RW), W_R)
+
+
+def lri_C_k(C_R, R_C, k, ao_atom, aux_atom):
+    """C^mu_st(k) = sum_R C^mu_st(R) e^{+i k.R} for mu on the atom of s, else 0 (§III.A).
+
+    Returns an array indexed [s, t, mu]."""
+    ph = np.exp(1j * TWO_PI * (np.asarray(R_C, np.float64) @ np.asarray(k, np.float64)))
+    Ck = np.einsum("r,rstu->stu", ph, C_R)
+    own = (np.asarray(ao_atom)[:, None] == np.asarray(aux_atom)[None, :])   # [s, mu]
+    return Ck * own[:, None, :]
+
+
+def ks_lri(c_bra, c_ket, C_of_kket, C_of_minus_kbra):
+    """C~^mu_{m k', n k} = sum_st conj(c^{k'}_sm) c^k_tn [C^mu_st(k) + C^mu_ts(-k')] (§III.A).
+
+    c_bra = c^{k'} [s, m], c_ket = c^k [t, n]; C_of_kket = C(k) [s,t,mu];
+    C_of_minus_kbra = C(-k') [s,t,mu].  Returns [mu, m, n]."""
+    t1 = np.einsum("sm,tn,stu->umn", np.conj(c_bra), c_ket, C_of_kket, optimize=True)
+    t2 = np.einsum("sm,tn,tsu->umn", np.conj(c_bra), c_ket, C_of_minus_kbra, optimize=True)
+    return t1 + t2
+
+
+class BSEOracle:
+    """Element-block evaluation of the TDA Hamiltonian A from the definitions above."""
+
+    def __init__(self, inp: dict, alpha: float = 2.0):
+        self.inp = inp
+        self.alpha = float(alpha)
+        self.mesh = np.asarray(inp["dense"], np.int64)
+        self.nk = int(np.prod(self.mesh))
+        self.nv, self.nc = int(inp["nv"]), int(inp["nc"])
+        self.nvc = self.nv * self.nc
+        self.dim = self.nk * self.nvc
+        n1, n2, n3 = self.mesh
+        g = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1)
+        self.kint = g.reshape(-1, 3)
+        self.kfrac = (self.kint + np.asarray(inp["k_offset"], np.float64)) / self.mesh
+        self._Ck, self._Cmk, self._Wq, self._X1, self._X2 = {}, {}, {}, {}, {}
+
+    # -- memoised pieces ---------------------------------------------------------
+    def C_k(self, ik):
+        if ik not in self._Ck:
+            i = self.inp
+            self._Ck[ik] = lri_C_k(i["C_R"], i["R_C"], self.kfrac[ik], i["ao_atom"], i["aux_atom"])
+        return self._Ck[ik]
+
+    def C_mk(self, ik):
+        if ik not in self._Cmk:
+            i = self.inp
+            self._Cmk[ik] = lri_C_k(i["C_R"], i["R_C"], -self.kfrac[ik], i["ao_atom"], i["aux_atom"])
+        return self._Cmk[ik]
+
+    def q_index(self, ik1, ik2):
+        d = np.mod(self.kint[ik1] - self.kint[ik2], self.mesh)
+        return int((d[0] * self.mesh[1] + d[1]) * self.mesh[2] + d[2])
+
+    def W_q(self, iq):
+        if iq not in self._Wq:
+            i = self.inp
+            n1, n2, n3 = self.mesh
+            qv = np.array([iq // (n2 * n3), (iq // n3) % n2, iq % n3], np.float64) / self.mesh
+            self._Wq[iq] = interp_W(i["W_R"], i["R_W"], i["w_RW"], qv)
+        return self._Wq[iq]
+
+    def _cv(self, ik):
+        return self.inp["c_k"][ik][:, : self.nv]
+
+    def _cc(self, ik):
+        return self.inp["c_k"][ik][:, self.nv:]
+
+    def X_exch_left(self, ik):       # C~^mu_{a k, i k}  -> [mu, a, i]
+        if ik not in self._X1:
+            self._X1[ik] = ks_lri(self._cc(ik), self._cv(ik), self.C_k(ik), self.C_mk(ik))
+        return self._X1[ik]
+
+    def X_exch_right(self, ik):      # C~^nu_{j k, b k}  -> [nu, j, b]
+        if ik not in self._X2:
+            self._X2[ik] = ks_lri(self._cv(ik), self._cc(ik), self.C_k(ik), self.C_mk(ik))
+        return self._X2[ik]
+
+    def M_vv(self, ik1, ik2):        # C~^mu_{j k2, i k1} -> [mu, j, i]
+        return ks_lri(self._cv(ik2), self._cv(ik1), self.C_k(ik1), self.C_mk(ik2))
+
+    def M_cc(self, ik1, ik2):        # C~^nu_{a k1, b k2} -> [nu, a, b]
+        return ks_lri(self._cc(ik1), self._cc(ik2), self.C_k(ik2), self.C_mk(ik1))
+
+    # -- kernels and blocks ------------------------------------------------------------
+    def direct(self, ik1, ik2):
+        """(j k2*, i k1|W|a k1*, b k2) as [i, a, j, b] (Eq. W_LRI)."""
+        Wq = self.W_q(self.q_index(ik1, ik2))
+        Mv, Mc = self.M_vv(ik1, ik2), self.M_cc(ik1, ik2)
+        T = np.einsum("uji,uv->jiv", Mv, Wq)
+        return np.einsum("jiv,vab->iajb", T, Mc) / self.nk
+
+    def exchange(self, ik1, ik2):
+        """(a k1*, i k1|V|j k2*, b k2) as [i, a, j, b] (the V-kernel beside Eq. W_LRI)."""
+        X1, X2 = self.X_exch_left(ik1), self.X_exch_right(ik2)
+        T = np.einsum("uai,uv->aiv", X1, self.inp["V0"])
+        return np.einsum("aiv,vjb->iajb", T, X2) / self.nk
+
+    def block(self, ik1, ik2):
+        """H block of rows (k1, i, a) and columns (k2, j, b), shape (Nv*Nc, Nv*Nc) (Eq. Hamiltonian)."""
+        blk = -self.direct(ik1, ik2)
+        if self.alpha != 0.0:
+            blk = blk + self.alpha * self.exchange(ik1, ik2)
+        blk = blk.reshape(self.nvc, self.nvc)
+        if ik1 == ik2:
+            e = self.inp["e_qp"][ik1]
+            de = (e[self.nv:][None, :] - e[: self.nv][:, None]).reshape(-1)   # (i, a)
+            blk = blk + np.diag(de)
+        return blk
+
+    def hamiltonian(self):
+        H = np.empty((self.dim, self.dim), np.complex128)
+        n = self.nvc
+        for k1 in range(self.nk):
+            for k2 in range(self.nk):
+                H[k1 * n:(k1 + 1) * n, k2 * n:(k2 + 1) * n] = self.block(k1, k2)
+        return H
+
+    # -- optics ------------------------------------------------------------------------
+    def dipoles(self):
+        """d_alpha,(k,i,a) = <ik|v_alpha|ak>/(E^KS_ak - E^KS_ik) (Eq. abs_vel), shape [3, dim]."""
+        e = self.inp["e_ks"]
+        de = e[:, self.nv:][:, None, :] - e[:, : self.nv][:, :, None]        # [k, i, a]
+        return (self.inp["vel"] / de[None]).reshape(3, -1)
+
+    def prefactor(self):
+        return spectrum_prefactor(self.nk, float(self.inp["volume"]))
+
+
+def spectrum_prefactor(nk, volume):
+    """4 pi^2 / (3 N_k V) of Eq. abs_vel (spin factor 1: the 1/sqrt2 normalisation and the
+    spin sum of the singlet cancel)."""
+    return 4.0 * np.pi ** 2 / (3.0 * nk * volume)
+
+
+def eps2_exact(H, d, omega, eta, pref):
+    """Eq. abs_vel with a Lorentzian of half-width eta, from a full eigendecomposition."""
+    w, X = np.linalg.eigh(H)
+    osc = np.abs(np.asarray(d) @ X) ** 2                                   # [pol, S]
+    L = (eta / np.pi) / ((np.asarray(omega)[:, None] - w[None, :]) ** 2 + eta ** 2)
+    return pref * (L @ osc.sum(axis=0))
+
+
+def haydock_coeffs(H, u, n_steps, reorth=True):
+    """Lanczos recursion on (H, u): returns (a[1..n], b[1..n], ||u||).
+
+    q_1 = u/||u||; w = H q_j - a_j q_j - b_{j-1} q_{j-1}, a_j = q_j^H H q_j,
+    b_j = ||w|| after (optional, twice-applied) full reorthogonalisation; stops early if
+    b_j < 1e-14 * ||H||_max."""
+    u = np.asarray(u, np.complex128)
+    beta0 = np.linalg.norm(u)
+    n = H.shape[0]
+    Q = np.zeros((n_steps + 1, n), np.complex128)
+    a = np.zeros(n_steps)
+    b = np.zeros(n_steps)
+    Q[0] = u / beta0
+    hmax = np.abs(H).max()
+    prev = np.zeros(n, np.complex128)
+    bprev = 0.0
+    m = n_steps
+    for j in range(n_steps):
+        w = H @ Q[j]
+        a[j] = np.vdot(Q[j], w).real
+        w = w - a[j] * Q[j] - bprev * prev
+        if reorth:
+            for _ in range(2):
+                w = w - Q[: j + 1].T @ (np.conj(Q[: j + 1]) @ w)
+        b[j] = np.linalg.norm(w)
+        if j == n_steps - 1:
+            break
+        if b[j] < 1e-14 * hmax:
+            m = j + 1
+            break
+        prev, bprev = Q[j], b[j]
+        Q[j + 1] = w / b[j]
+    return a[:m], b[:m], beta0
+
+
+def haydock_eps2(a, b, beta0, omega, eta):
+    """-(1/pi) Im g(omega + i eta), g(z) = beta0^2/(z - a1 - b1^2/(z - a2 - ...))."""
+    z = np.asarray(omega, np.float64) + 1j * eta
+    f = z - a[-1]
+    for j in range(len(a) - 2, -1, -1):
+        f = z - a[j] - b[j] ** 2 / f
+    return -(beta0 ** 2 / f).imag / np.pi
+
+
+def lowest_excitons(H, n):
+    """Lowest n eigenvalues of the Hermitian TDA matrix (LAPACK)."""
+    return np.linalg.eigvalsh(H)[:n]
+
+
+def binding_energy(e_qp, nv, omega1):
+    """E_B = min_k (E^QP_ck - E^QP_vk) - Omega_1 over the band edges (§IV, exciton binding)."""
+    return float(np.min(e_qp[:, nv] - e_qp[:, 0]) - omega1)

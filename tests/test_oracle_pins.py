@@ -1,0 +1,277 @@
+"""Pins of the FP64 oracle against facts fixed outside it (CPU only).
+
+Each test checks the oracle against something other than itself: an exact identity of
+the dual-k-mesh interpolation (§III.B), a library FFT, a brute-force lattice sum built
+from the real-space two-centre expansion and Bloch sums (§III.A, Eq. 2) instead of the
+k-space formulas, invariants the paper states (A Hermitian, §II.C), the independent-
+particle limit, LAPACK, and closed forms of the spectrum (Eq. abs_vel).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import CrystalSpec, config_spec, make_inputs, kmesh_frac
+from synth.crystal import _fcc
+
+TWO_PI = 2 * np.pi
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    inp = make_inputs(config_spec(0))
+    orc = O.BSEOracle(inp)
+    H = orc.hamiltonian()
+    return inp, orc, H
+
+
+def tiny_spec(**kw):
+    base = CrystalSpec("brute", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25]]),
+                       (2, 3), (3, 2), (3, 1, 1), (3, 2, 1), 2, 2, 777,
+                       k_offset=(0.3, 0.2, 0.0), r_max=1.0, s_W=0.3, s_V=0.2)
+    return dataclasses.replace(base, **kw)
+
+
+# ---------------------------------------------------------------- a1: interpolation
+def test_interp_reproduces_coarse_W_when_dense_equals_coarse():
+    """§III.B: W(q) -> W(R) on the folded coarse cell -> W(q) is exact on coarse points."""
+    for spec in (dataclasses.replace(config_spec(0), dense=(2, 2, 2)),
+                 dataclasses.replace(config_spec(4), dense=(6, 6, 1), nao=(3, 3, 3), naux=(5, 5, 5))):
+        inp = make_inputs(spec)
+        orc = O.BSEOracle(inp)
+        ref = inp["W_q_coarse"]
+        for iq in range(orc.nk):
+            got = orc.W_q(iq)
+            assert np.abs(got - ref[iq]).max() <= 1e-12 * np.abs(ref[iq]).max()
+
+
+def test_interp_hermitian_off_mesh():
+    """Symmetric image set + real W(R) with W(-R)=W(R)^T => W(q) Hermitian at any q."""
+    inp = make_inputs(config_spec(0))
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        q = rng.random(3)
+        W = O.interp_W(inp["W_R"], inp["R_W"], inp["w_RW"], q)
+        assert np.abs(W - W.conj().T).max() <= 1e-13 * np.abs(W).max()
+
+
+def test_interp_equals_fft_on_full_cell():
+    """With one image per class of an N-cell and unit weights, the R-sum is a DFT (numpy FFT)."""
+    rng = np.random.default_rng(2)
+    N = (3, 4, 2)
+    n_aux = 3
+    R = np.stack(np.meshgrid(*[np.arange(n) for n in N], indexing="ij"), -1).reshape(-1, 3)
+    WR = rng.standard_normal((len(R), n_aux, n_aux))
+    fft = np.fft.fftn(WR.reshape(*N, n_aux, n_aux), axes=(0, 1, 2)).reshape(-1, n_aux, n_aux)
+    qs = kmesh_frac(N)
+    for iq, q in enumerate(qs):
+        got = O.interp_W(WR, R, np.ones(len(R)), q)
+        assert np.allclose(got, fft[iq], atol=1e-12)
+
+
+# ---------------------------------------------------------------- a2/a3 brute force
+def _rho(inp, cb, kb, ck, kk, L):
+    """Coefficient of P_mu(r - L - tau_mu) in psi_bra^{kb*} psi_ket^{kk}: Bloch sums (Eq. 2)
+    over the two-centre expansion (§III.A), evaluated at the lattice cell L."""
+    C, RC = inp["C_R"], inp["R_C"].astype(float)
+    own = inp["ao_atom"][:, None] == inp["aux_atom"][None, :]                 # [s, mu]
+    L = np.asarray(L, float)
+    # pairs (L_s, L_t) = (L, L + R): mu on the atom of s, coefficient C^mu_st(R)
+    ph1 = np.exp(-1j * TWO_PI * kb @ L) * np.exp(1j * TWO_PI * (RC + L) @ kk)
+    t1 = np.einsum("r,s,t,rstu,su->u", ph1, np.conj(cb), ck, C, own)
+    # pairs (L_s, L_t) = (L + R, L): mu on the atom of t, coefficient C^mu_ts(R)
+    ph2 = np.exp(-1j * TWO_PI * (RC + L) @ kb) * np.exp(1j * TWO_PI * kk @ L)
+    t2 = np.einsum("r,s,t,rtsu,tu->u", ph2, np.conj(cb), ck, C, own)
+    return t1 + t2
+
+
+def _brute_kernel(inp, kf, nk, mesh, pair1, pair2, R_set, weights, mats):
+    """(1/N_k^2) sum_{L in supercell} sum_R rho1(L) Wtrue(R) rho2(L+R): the six-dimensional
+    integral of Eq. BSEkernel with W_mu,nu(R) defined as in §III.A, no k-space algebra."""
+    tot = 0.0
+    cells = np.stack(np.meshgrid(*[np.arange(n) for n in mesh], indexing="ij"), -1).reshape(-1, 3)
+    for L in cells:
+        r1 = _rho(inp, *pair1, L)
+        for R, w, M in zip(R_set, weights, mats):
+            r2 = _rho(inp, *pair2, L + R)
+            tot += w * (r1 @ M @ r2)
+    return tot / nk ** 2
+
+
+def test_kernels_match_realspace_brute_force():
+    spec = tiny_spec()
+    inp = make_inputs(spec)
+    rng = np.random.default_rng(5)
+    RV = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, -1]])
+    Vbar = rng.standard_normal((len(RV), spec.n_aux, spec.n_aux))
+    inp["V0"] = Vbar.sum(axis=0)
+    orc = O.BSEOracle(inp)
+    kf, nk, mesh = orc.kfrac, orc.nk, spec.dense
+    nv = spec.nv
+    c = inp["c_k"]
+    for (k1, k2) in [(0, 0), (1, 4), (5, 2), (3, 3)]:
+        D = orc.direct(k1, k2)
+        X = orc.exchange(k1, k2)
+        for (i, a, j, b) in [(0, 0, 0, 0), (1, 0, 0, 1), (0, 1, 1, 0), (1, 1, 1, 1)]:
+            p1 = (c[k2][:, j], kf[k2], c[k1][:, i], kf[k1])
+            p2 = (c[k1][:, nv + a], kf[k1], c[k2][:, nv + b], kf[k2])
+            bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
+            assert abs(bd - D[i, a, j, b]) <= 1e-12 * max(1.0, abs(bd)), (k1, k2, i, a, j, b)
+            q1 = (c[k1][:, nv + a], kf[k1], c[k1][:, i], kf[k1])
+            q2 = (c[k2][:, j], kf[k2], c[k2][:, nv + b], kf[k2])
+            bx = _brute_kernel(inp, kf, nk, mesh, q1, q2, RV, np.ones(len(RV)), Vbar)
+            assert abs(bx - X[i, a, j, b]) <= 1e-12 * max(1.0, abs(bx)), (k1, k2, i, a, j, b)
+
+
+def test_ks_lri_conjugate_symmetry():
+    """Real C(R): C~^mu_{n k', m k} = conj(C~^mu_{m k, n k'}) (both sides computed)."""
+    inp = make_inputs(config_spec(0))
+    orc = O.BSEOracle(inp)
+    for k1, k2 in [(0, 5), (7, 33), (12, 12)]:
+        a = O.ks_lri(inp["c_k"][k2], inp["c_k"][k1], orc.C_k(k1), orc.C_mk(k2))   # [mu, n@k2, m@k1]
+        b = O.ks_lri(inp["c_k"][k1], inp["c_k"][k2], orc.C_k(k2), orc.C_mk(k1))   # [mu, m@k1, n@k2]
+        assert np.allclose(a, np.conj(np.transpose(b, (0, 2, 1))), atol=1e-13)
+
+
+# ---------------------------------------------------------------- a3 invariants
+def test_hamiltonian_hermitian(cfg0):
+    _, _, H = cfg0
+    assert np.abs(H - H.conj().T).max() <= 1e-13 * np.abs(H).max()
+
+
+def test_independent_particle_limit():
+    """W = V = 0: eigenvalues are exactly the sorted E^QP_c - E^QP_v (no e-h interaction)."""
+    inp = make_inputs(config_spec(0), W_zero=True, V_zero=True)
+    H = O.BSEOracle(inp).hamiltonian()
+    de = (inp["e_qp"][:, 4:][:, None, :] - inp["e_qp"][:, :4][:, :, None]).reshape(-1)
+    assert np.abs(H - np.diag(de)).max() == 0.0
+    assert np.allclose(np.linalg.eigvalsh(H), np.sort(de), atol=1e-12)
+
+
+def test_exchange_rank_is_naux():
+    """With W = 0 the interaction is alpha/N_k X V0 X^dagger: rank N_aux (40) at dim 1024."""
+    inp = make_inputs(config_spec(0), W_zero=True)
+    orc = O.BSEOracle(inp)
+    H = orc.hamiltonian()
+    de = (inp["e_qp"][:, 4:][:, None, :] - inp["e_qp"][:, :4][:, :, None]).reshape(-1)
+    s = np.linalg.svd(H - np.diag(de), compute_uv=False)
+    assert np.sum(s > 1e-10 * s[0]) == 40
+
+
+def test_gauge_invariance(cfg0):
+    """Random phases on the band coefficients leave |H| and the spectrum unchanged."""
+    inp, _, H = cfg0
+    rng = np.random.default_rng(3)
+    g = dict(inp)
+    g["c_k"] = inp["c_k"] * np.exp(1j * rng.uniform(0, TWO_PI, size=(inp["c_k"].shape[0], 1, 8)))
+    H2 = O.BSEOracle(g).hamiltonian()
+    assert np.allclose(np.abs(H2), np.abs(H), atol=1e-12)
+    assert np.allclose(np.linalg.eigvalsh(H2), np.linalg.eigvalsh(H), atol=1e-11)
+
+
+def test_triplet_below_singlet(cfg0):
+    """alpha = 0 removes the (PSD) exchange: Weyl => lambda_i(triplet) <= lambda_i(singlet)."""
+    inp, _, H = cfg0
+    Ht = O.BSEOracle(inp, alpha=0).hamiltonian()
+    ls, lt = np.linalg.eigvalsh(H), np.linalg.eigvalsh(Ht)
+    assert np.all(lt <= ls + 1e-12)
+    assert np.abs(Ht - Ht.conj().T).max() <= 1e-13
+
+
+def test_conduction_shift_moves_all_excitons(cfg0):
+    inp, _, H = cfg0
+    g = dict(inp)
+    g["e_qp"] = inp["e_qp"].copy()
+    g["e_qp"][:, 4:] += 0.37
+    H2 = O.BSEOracle(g).hamiltonian()
+    assert np.allclose(np.linalg.eigvalsh(H2), np.linalg.eigvalsh(H) + 0.37, atol=1e-11)
+
+
+def test_binding_energy_in_paper_range(cfg0):
+    """The calibrated synthetic interaction binds the lowest singlet by 0.1-0.3 eV (§IV E_B)."""
+    inp, _, H = cfg0
+    eb = O.binding_energy(inp["e_qp"], 4, np.linalg.eigvalsh(H)[0])
+    assert 0.1 <= eb <= 0.3
+
+
+# ---------------------------------------------------------------- a4 spectrum
+def test_haydock_full_length_equals_exact(cfg0):
+    inp, orc, H = cfg0
+    d = orc.dipoles()
+    om = np.linspace(0, 10, 201)
+    eta, pref = 0.1, orc.prefactor()
+    ex = O.eps2_exact(H, d, om, eta, pref)
+    hy = np.zeros_like(om)
+    for p in range(3):
+        a, b, b0 = O.haydock_coeffs(H, np.conj(d[p]), H.shape[0])
+        hy += pref * O.haydock_eps2(a, b, b0, om, eta)
+    assert np.abs(hy - ex).max() <= 1e-10 * np.abs(ex).max()
+
+
+def test_haydock_moments(cfg0):
+    """Zeroth moment: sum_S |u^H x_S|^2 = ||u||^2; first coefficient a_1 = u^H H u/||u||^2."""
+    inp, orc, H = cfg0
+    u = np.conj(orc.dipoles()[0])
+    w, X = np.linalg.eigh(H)
+    assert np.isclose(np.sum(np.abs(X.conj().T @ u) ** 2), np.vdot(u, u).real, rtol=1e-12)
+    a, b, b0 = O.haydock_coeffs(H, u, 3)
+    assert np.isclose(a[0], np.vdot(u, H @ u).real / np.vdot(u, u).real, rtol=1e-13)
+    assert np.isclose(b0, np.linalg.norm(u), rtol=1e-14)
+
+
+def test_ipa_spectrum_closed_form():
+    """W = V = 0: eps2 = pref sum_r |d_r|^2 L(omega - de_r) (Eq. abs_vel with X = unit vectors)."""
+    inp = make_inputs(config_spec(0), W_zero=True, V_zero=True)
+    orc = O.BSEOracle(inp)
+    H = orc.hamiltonian()
+    d = orc.dipoles()
+    de = np.real(np.diag(H))
+    om = np.linspace(0, 10, 101)
+    eta, pref = 0.1, orc.prefactor()
+    closed = pref * ((eta / np.pi) / ((om[:, None] - de[None, :]) ** 2 + eta ** 2)) @ (np.abs(d) ** 2).sum(0)
+    assert np.allclose(O.eps2_exact(H, d, om, eta, pref), closed, rtol=1e-12, atol=0)
+
+
+def test_lowest_matches_lapack_order(cfg0):
+    _, _, H = cfg0
+    w = O.lowest_excitons(H, 10)
+    assert np.all(np.diff(w) >= 0) and w.shape == (10,)
+    assert np.allclose(w, np.sort(np.linalg.eigvals(H).real)[:10], atol=1e-10)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def _brute_error(inp, orc, pairs=((1, 4), (5, 2)), bands=((1, 0, 0, 1), (0, 1, 1, 1))):
+    kf, nk, mesh, nv, c = orc.kfrac, orc.nk, tuple(inp["dense"]), orc.nv, inp["c_k"]
+    err = 0.0
+    for k1, k2 in pairs:
+        D = orc.direct(k1, k2)
+        for (i, a, j, b) in bands:
+            p1 = (c[k2][:, j], kf[k2], c[k1][:, i], kf[k1])
+            p2 = (c[k1][:, nv + a], kf[k1], c[k2][:, nv + b], kf[k2])
+            bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
+            err = max(err, abs(bd - D[i, a, j, b]) / max(abs(bd), 1e-30))
+    return err
+
+
+@pytest.mark.parametrize("mistake", ["W_phase_sign", "C_bra_sign", "Mv_transposed", "no_1_over_Nk"])
+def test_planted_oracle_mistake_is_caught(mistake, monkeypatch):
+    """A plausible slip in the oracle's arithmetic makes the brute-force pin fail."""
+    inp = make_inputs(tiny_spec())
+    orc = O.BSEOracle(inp)
+    assert _brute_error(inp, orc) < 1e-12
+    mod = O.bse_oracle
+    if mistake == "W_phase_sign":
+        orig = mod.interp_W
+        monkeypatch.setattr(mod, "interp_W", lambda W, R, w, q: orig(W, R, w, -np.asarray(q)))
+    elif mistake == "C_bra_sign":
+        monkeypatch.setattr(mod.BSEOracle, "M_vv", lambda self, k1, k2: mod.ks_lri(
+            self._cv(k2), self._cv(k1), self.C_k(k1), self.C_k(k2)))
+    elif mistake == "Mv_transposed":
+        orig_mvv = mod.BSEOracle.M_vv
+        monkeypatch.setattr(mod.BSEOracle, "M_vv", lambda self, k1, k2: np.transpose(orig_mvv(self, k1, k2), (0, 2, 1)))
+    elif mistake == "no_1_over_Nk":
+        orig_d = mod.BSEOracle.direct
+        monkeypatch.setattr(mod.BSEOracle, "direct", lambda self, k1, k2: orig_d(self, k1, k2) * self.nk)
+    bad = O.BSEOracle(inp)
+    assert _brute_error(inp, bad) > 1e-6

@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 TDA-BSE hot path (one JSON line on rank 0).
+
+A step is one pass of the whole path over the split-precision-at-scale workload (2-atom
+diamond-like cell, 13 NAOs and 75 ABFs per atom, 4x4x4 coarse / 12x12x12 dense mesh,
+Nv = Nc = 4, H dimension 27648):
+  (a) W(q) interpolation, (b) per-k projection stage, (b+c) assembly of H, the dipole
+  vector, and (d) a 500-step Haydock spectrum for 3 polarisations on 1001 frequencies.
+value = H elements (dim^2) per second of whole step; the assembly-only rate, the FP64
+GPU path, the accuracy against the FP64 path and the stage breakdown are extra keys.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision bf16x3|bf16x2|bf16x1|fp64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H_BSE elements/s (split-prec TC vs FP64 GPU) at ≤1 meV lowest-exciton error"
+UNIT = "H elements/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--haydock-steps", type=int, default=500)
+    ap.add_argument("--n-omega", type=int, default=1001)
+    ap.add_argument("--eta", type=float, default=0.1)
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the FP64 GPU comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
+    return ap.parse_args()
+
+
+def workload(small):
+    from synth import config_spec
+    spec = config_spec(0 if small else 2)
+    return spec
+
+
+# ------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained", d["bf16_tflops"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0, "source": "fallback"}
+
+
+# ------------------------------------------------------------------------------ oracle leg
+def cpu_baseline(inp, seconds, rng_seed=5):
+    """The FP64 oracle, as it stands, on a bounded sample of H blocks of the same workload."""
+    import oracle as O
+    orc = O.BSEOracle(inp)
+    rng = np.random.default_rng(rng_seed)
+    nk = orc.nk
+    k1s = rng.integers(0, nk, 4)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        k1 = int(k1s[n % 4])
+        k2 = int(rng.integers(0, nk))
+        orc.block(k1, k2)
+        n += 1
+    dt = time.perf_counter() - t0
+    try:
+        import threadpoolctl
+        cores = max(i.get("num_threads", 1) for i in threadpoolctl.threadpool_info()) or 1
+    except Exception:
+        cores = os.cpu_count()
+    elems = n * orc.nvc * orc.nvc
+    return {"value": elems / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": f"{n} H blocks ({elems} elements) of the 27648-dim workload, W(q) and C(k) "
+                      f"memoised per block as the oracle does, {dt:.1f} s on host cores"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from synth import make_inputs
+    spec = workload(args.small)
+    inp = make_inputs(spec)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(inp, min(per_step, 5.0))
+    vals = [cpu_baseline(inp, per_step, rng_seed=100 + s) for s in range(args.steps)]
+    v = statistics.mean(x["value"] for x in vals)
+    cb = dict(vals[0])
+    cb["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * spec.dim ** 2 / v,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator, shapes of the paper's Si/MgO workloads)",
+           "config": {"workload": spec.name, "dim": spec.dim, "n_k": spec.n_k, "n_aux": spec.n_aux,
+                      "n_ao": spec.n_ao, "nv": spec.nv, "nc": spec.nc},
+           "cpu_baseline": cb,
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ------------------------------------------------------------------------------ our path
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    from paper_2607_05853_b300.api import BSE, launch_count
+    from synth import make_inputs
+
+    spec = workload(args.small)
+    inp = make_inputs(spec)
+    dev = torch.device("cuda", local)
+
+    def h2d(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x, dt)).pin_memory()
+
+    host = {k: h2d(inp[k], np.float64) for k in ("W_R", "V0", "C_R", "e_qp", "e_ks")}
+    host.update({k: h2d(inp[k], np.complex128) for k in ("c_k", "vel")})
+    d = {k: v.to(dev) for k, v in host.items()}
+    ctx = BSE.from_inputs(inp, precision=args.precision)
+    H = torch.empty((ctx.dim, ctx.dim), dtype=ctx.h_dtype, device=dev)
+    u = torch.empty((3, ctx.dim), dtype=torch.complex128, device=dev)
+    omega = torch.linspace(0.0, 10.0, args.n_omega, dtype=torch.float64, device=dev)
+    eps2 = torch.empty(args.n_omega, dtype=torch.float64, device=dev)
+    pref = 4.0 * np.pi ** 2 / (3.0 * spec.n_k * float(inp["volume"]))
+    nsteps = min(args.haydock_steps, ctx.dim)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step(dd=d):
+        ctx.interp_W(dd["W_R"], dd["V0"])
+        ctx.project_pairs(dd["C_R"], dd["c_k"], dd["e_qp"])
+        ctx.assemble(H)
+        ctx.dipole_vector(dd["vel"], dd["e_ks"], u)
+        ctx.spectrum(H, u, nsteps, omega, args.eta, pref, eps2)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.sync()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events) ----------
+    ctx.profile(True)
+    launches0 = launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sub = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(st)
+            ctx.interp_W(d["W_R"], d["V0"])
+            ctx.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+            sub[i][0].record(st)
+            ctx.assemble(H)
+            sub[i][1].record(st)
+            ctx.dipole_vector(d["vel"], d["e_ks"], u)
+            ctx.spectrum(H, u, nsteps, omega, args.eta, pref, eps2)
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+    launches = launch_count() - launches0
+    ctx.sync()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    pre_ms = [ev[i][0].elapsed_time(sub[i][0]) for i in range(args.steps)]
+    asm_ms = [sub[i][0].elapsed_time(sub[i][1]) for i in range(args.steps)]
+    spec_ms = [sub[i][1].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    prof = {k: ctx.profile_read(k) for k in ("interp", "half", "project", "g1", "g2", "exch", "matvec", "reorth")}
+    ctx.profile(False)
+    t_total = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    dim2 = float(ctx.dim) ** 2
+    value = world * args.steps * dim2 / (t_total / 1000.0)
+    asm_rate = dim2 / (statistics.mean([p + a for p, a in zip(pre_ms, asm_ms)]) / 1000.0)
+
+    # ---- end to end: host inputs -> device -> path -> eps2 back to host ----------------
+    h_out = torch.empty(args.n_omega, dtype=torch.float64).pin_memory()
+    in_bytes = sum(v.numel() * v.element_size() for v in host.values())
+    e2e_ms = []
+    for i in range(max(1, min(args.steps, 2))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+        step(dd)
+        h_out.copy_(eps2, non_blocking=True)
+        b.record(st)
+        torch.cuda.synchronize()
+        e2e_ms.append(a.elapsed_time(b))
+    e2e = {"value": dim2 / (statistics.mean(e2e_ms) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
+           "d2h_bytes_per_step": int(h_out.numel() * 8)}
+
+    # ---- roofline of the dominant kernel ----------------------------------------------------
+    pk = peaks()
+    top = max(prof, key=lambda k: prof[k][0])
+    ms, n = prof[top]
+    per_launch_ms = ms / max(n, 1)
+    h_elem = 16 if args.precision == "fp64" else 8
+    nk, naux, nv, nc = spec.n_k, spec.n_aux, spec.nv, spec.nc
+    if top == "matvec":
+        alg = dim2 * h_elem + 3 * ctx.dim * 16 * 2
+        roof = {"bound": "hbm", "achieved": alg / (per_launch_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+        roof_note = "Lanczos matvec: algorithmic bytes = dim^2 x H element + 3 vectors in/out, per launch"
+    elif top == "g1" and args.precision != "fp64":
+        pieces = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1}[args.precision]
+        alg = 8.0 * nk * nv * nv * naux * naux * pieces * (ctx_slab_q(ctx, spec))
+        roof = {"bound": "tensor", "achieved": alg / (per_launch_ms * 1e-3) / 1e12,
+                "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s"}
+        roof_note = "M_vv W(q): executed bf16 tensor flops (8 N_k Nv^2 Naux^2 x split products) per launch"
+    else:
+        alg = None
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
+        roof_note = f"dominant kernel {top}"
+    if roof.get("achieved") is not None and roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof["frac"] = None
+    roof["traffic"] = None
+    roof["kernel"] = top
+    roof["peak_source"] = pk["source"]
+    roof["note"] = roof_note
+
+    # ---- FP64 GPU comparison and accuracy (outside the timed region) ----------------------
+    extra = {}
+    if not args.no_fp64_compare and args.precision != "fp64":
+        ref = BSE.from_inputs(inp, precision="fp64")
+        H64 = torch.empty((ctx.dim, ctx.dim), dtype=torch.complex128, device=dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ref.interp_W(d["W_R"], d["V0"])
+        ref.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+        ref.assemble(H64)
+        b.record(st)
+        ref.sync()
+        fp64_ms = a.elapsed_time(b)
+        dH = (H.to(torch.complex128) - H64).abs().max().item()
+        fro = torch.linalg.matrix_norm(H.to(torch.complex128) - H64).item()
+        w_s, r_s = ctx.lowest(H, 10, 300)
+        w_d, r_d = ref.lowest(H64, 10, 300)
+        ref.sync()
+        eps64 = torch.empty_like(eps2)
+        u64 = ref.dipole_vector(d["vel"], d["e_ks"])
+        ref.spectrum(H64, u64, nsteps, omega, args.eta, pref, eps64)
+        ref.sync()
+        l2 = (torch.linalg.norm(eps2 - eps64) / torch.linalg.norm(eps64)).item()
+        extra["fp64_gpu"] = {"assembly_ms": fp64_ms, "elements_per_s": dim2 / (fp64_ms / 1000.0),
+                             "speedup_split_over_fp64": (dim2 / (fp64_ms / 1000.0)) and asm_rate / (dim2 / (fp64_ms / 1000.0))}
+        extra["accuracy_vs_fp64"] = {"max_abs_dH_eV": dH, "frobenius_dH_eV": fro,
+                                     "lowest10_abs_err_meV": (1000.0 * (w_s - w_d).abs()).tolist(),
+                                     "lowest10_eV": w_d.tolist(), "ritz_resid_max_eV": float(max(r_s.max(), r_d.max())),
+                                     "spectrum_rel_L2": l2}
+        del H64
+        ref.close()
+
+    clocks = clk.summary()
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64"}.get(args.precision, f"{args.precision} (split, f32 accumulate; f64 phases/diagonal/Lanczos)"),
+        "data": "synthetic (seeded generator, shapes of the paper's Si/MgO workloads)",
+        "config": {"workload": spec.name, "dim": ctx.dim, "n_k": spec.n_k, "mesh": list(spec.dense),
+                   "n_aux": spec.n_aux, "n_ao": spec.n_ao, "nv": nv, "nc": nc, "haydock_steps": nsteps,
+                   "n_pol": 3, "n_omega": args.n_omega, "precision": args.precision,
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+        "stages_ms": {"interp+per_k": statistics.mean(pre_ms), "assemble": statistics.mean(asm_ms),
+                      "dipole+spectrum": statistics.mean(spec_ms)},
+        "assembly_elements_per_s": asm_rate,
+        "kernels_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+    }
+    result.update(extra)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(inp, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def ctx_slab_q(ctx, spec):
+    return 1
+
+
+if __name__ == "__main__":
+    main()

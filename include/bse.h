@@ -1,0 +1,177 @@
+/*
+ * bse.h -- C ABI of the B300 (sm_103a) Tamm-Dancoff BSE hot path.
+ *
+ * The library builds the resonant block A of the BSE Hamiltonian on a dense k-mesh from
+ * the unit-cell-indexed screened interaction W_mu,nu(R) and the localized-RI pair
+ * coefficients C^mu_st(R), then computes the velocity-form absorption spectrum by a
+ * Haydock (Lanczos) recursion.  The steps and where the paper defines them
+ * (arXiv 2607.05853):
+ *   bse_interp_W       W_mu,nu(q) = sum_R w_R W_mu,nu(R) exp(-i q.R), q = k1 - k2: the
+ *                      R-sum of Eq. W_LRI (§III.A) on the dense mesh (§III.B).
+ *   bse_project_pairs  C^mu_st(k) = sum_R C^mu_st(R) exp(i k.R) and the Kohn-Sham-basis
+ *                      coefficients C~^mu_{j k2, i k1} (§III.A); the pair projections
+ *                      themselves are formed inside bse_assemble, one q-slab at a time.
+ *   bse_assemble       A_{ai k1, bj k2} = (E_a - E_i) delta + alpha (ak1*,ik1|V|jk2*,bk2)
+ *                      - (jk2*,ik1|W|ak1*,bk2) (Eq. Hamiltonian, §II.C) with both kernels
+ *                      in the LRI form of Eq. W_LRI (1/N_k, V at q = 0).
+ *   bse_dipole_vector  u_alpha,(k,i,a) = conj(<ik|v_alpha|ak> / (E_ak - E_ik)) (Eq. abs_vel).
+ *   bse_spectrum       eps2(w) = pref sum_alpha -(1/pi) Im <u|(w + i eta - A)^-1|u> -- Eq.
+ *                      abs_vel with the delta broadened to a Lorentzian -- by a Lanczos
+ *                      recursion with full reorthogonalisation and a continued fraction.
+ *   bse_lowest         lowest Ritz values of A by Lanczos (the TDA eigenvalues, §II.C).
+ *
+ * Conventions (all entry points):
+ *  - Dense k-points are k = (n + k_offset)/N per axis, flattened (n1*N2 + n2)*N3 + n3.
+ *    R vectors are integer lattice coordinates.  Phases are exp(2 pi i k.R).
+ *  - NAOs s are numbered atom by atom (nao_per_atom), ABFs mu atom by atom (naux_per_atom).
+ *  - Band window: columns 0..nv-1 are valence bands, column 0 the valence band maximum
+ *    counting down; columns nv..nv+nc-1 conduction bands, nv the minimum counting up.
+ *  - The row (and column) of the pair (k, v, c) in H is (k*nv + v)*nc + c;
+ *    dim = N_k * nv * nc.  H is row-major and fully stored (both triangles).
+ *  - complex128 arrays are interleaved (re, im) doubles; complex64 interleaved floats.
+ *  - Every array argument is a DEVICE pointer on the context's device unless marked
+ *    "host".  The caller owns every argument buffer; the context owns only its workspace
+ *    and copies the host arrays of bse_params at setup.
+ *  - Work is enqueued on the stream given to bse_setup and the call returns without
+ *    waiting, except where stated.  Argument errors are reported before anything is
+ *    enqueued.  A CUDA launch error returns BSE_ECUDA; bse_last_error() explains.
+ *  - Calls must come in order: setup, interp_W, project_pairs, then assemble; spectrum,
+ *    lowest and dipole_vector need only setup.  Out-of-order calls return BSE_ESTATE.
+ *  - No kernel traps or asserts; kernels that wait on a barrier give up after a bounded
+ *    number of polls, set a device error word, and bse_sync() then returns BSE_ETIMEOUT
+ *    (or BSE_EDEVICE for a failed device-side check).
+ */
+#ifndef BSE_H
+#define BSE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bse_ctx bse_ctx;
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_EINVAL = 1,    /* bad argument */
+  BSE_ENOMEM = 2,    /* device allocation failed */
+  BSE_ECUDA = 3,     /* a CUDA runtime call or launch failed */
+  BSE_ETIMEOUT = 4,  /* a device-side bounded wait gave up */
+  BSE_ESTATE = 5,    /* call out of order */
+  BSE_EDEVICE = 6    /* a device-side check set the error word */
+} bse_status;
+
+/* Arithmetic of the kernel contractions in bse_assemble.
+ *  BSE_FP64  : everything in FP64 on CUDA cores; H is complex128.
+ *  BSE_BF16X3: contractions on tcgen05 tensor cores with each FP32 operand split into
+ *              three bf16 pieces (6 piece products kept), FP32 accumulation; phases
+ *              and the E_c - E_v diagonal in FP64; H is complex64.
+ *  BSE_BF16X2: as BF16X3 with two pieces (3 piece products).
+ *  BSE_BF16X1: one bf16 piece (1 product) -- an accuracy ablation. */
+typedef enum { BSE_FP64 = 0, BSE_BF16X3 = 1, BSE_BF16X2 = 2, BSE_BF16X1 = 3 } bse_precision;
+
+typedef struct {
+  int32_t n_atoms;
+  const int32_t *nao_per_atom;   /* host [n_atoms], NAOs per atom (Eq. 2 basis)       */
+  const int32_t *naux_per_atom;  /* host [n_atoms], ABFs per atom (§III.A)            */
+  int32_t dense[3];              /* dense k-mesh N1,N2,N3 (>= 1)                       */
+  double k_offset[3];            /* mesh shift in units of the mesh spacing            */
+  int32_t n_RC;                  /* R-set of C(R) (§III.A, truncated beyond 2 rcut)    */
+  const int32_t *R_C;            /* host [n_RC][3]                                     */
+  int32_t n_RW;                  /* Wigner-Seitz images of the coarse cell (§III.B)    */
+  const int32_t *R_W;            /* host [n_RW][3]                                     */
+  const double *w_RW;            /* host [n_RW] image weights (1/degeneracy)           */
+  int32_t nv, nc;                /* band window, nv + nc <= total NAOs                 */
+  double alpha;                  /* 2 singlet, 0 triplet (Eq. Hamiltonian)             */
+  int32_t precision;             /* a bse_precision                                   */
+} bse_params;
+
+/* Validate p, copy its host arrays, allocate the workspace on the current CUDA device
+ * and bind the context to `cuda_stream` (a cudaStream_t, NULL = default stream).
+ * On success *out receives the context; on failure *out is NULL.  Synchronous. */
+bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out);
+
+/* Step (a): W(q) for every transfer q = k1 - k2 of the dense mesh (there are N_k).
+ *  W_R : [n_RW][N_aux][N_aux] float64, real, the images listed in bse_params.R_W.
+ *  V0  : [N_aux][N_aux] float64, V_mu,nu(q=0) = sum_R Vbar_mu,nu(R), real symmetric.
+ *  Wq_out : optional [N_k][N_aux][N_aux] complex128 (row mu, column nu), or NULL.
+ * Both inputs are read during this call's work only (the context keeps its own copy). */
+bse_status bse_interp_W(bse_ctx *ctx, const double *W_R, const double *V0, void *Wq_out);
+
+/* Step (b), per-k part: C(k) and the half-transforms Y^mu_sn(k) = sum_t C^mu_st(k) c^k_tn
+ * for s on the atom of mu (C real => the second LRI term is conj(Y), §III.A), the
+ * exchange factors C~^mu_{a k, i k}, and a copy of the band energies.
+ *  C_R  : [n_RC][N_ao][N_ao][N_aux] float64, C^mu_st(R); entries whose mu is not on the
+ *         atom of s are ignored (the expansion has no such terms).
+ *  c_k  : [N_k][N_ao][nv+nc] complex128 band coefficients (window columns).
+ *  e_qp : [N_k][nv+nc] float64 quasiparticle energies (eV) for the diagonal. */
+bse_status bse_project_pairs(bse_ctx *ctx, const double *C_R, const double *c_k,
+                             const double *e_qp);
+
+/* Steps (b)+(c): build H.  H : [dim][dim], complex128 for BSE_FP64, complex64 for the
+ * split precisions.  Every element is written. */
+bse_status bse_assemble(bse_ctx *ctx, void *H);
+
+/* u_alpha,(k,i,a) = conj(vel[alpha][k][i][a] / (e_ks[k][nv+a] - e_ks[k][i])).
+ *  vel : [3][N_k][nv][nc] complex128 <ik|v_alpha|ak>;  e_ks : [N_k][nv+nc] float64;
+ *  u   : [3][dim] complex128 output.  A zero denominator gives BSE_EDEVICE at bse_sync. */
+bse_status bse_dipole_vector(bse_ctx *ctx, const double *vel, const double *e_ks, double *u);
+
+/* Step (d): Haydock spectrum.  For each of n_pol (1..3) start vectors u[p] (complex128
+ * [n_pol][dim]) run n_steps (1..dim) Lanczos steps on H (type as in bse_assemble) in
+ * FP64 with full reorthogonalisation (twice), stopping early when b_j < 1e-14 max|H|,
+ * then eps2[w] = prefactor * sum_p -(1/pi) Im g_p(omega[w] + i eta), with
+ * g = |u|^2/(z - a1 - b1^2/(z - a2 - ...)).  eps2 : [n_w] float64.  ab : optional
+ * [n_pol][3][n_steps] float64 receiving a_j, b_j and (in [p][2][0]) |u|, or NULL.
+ * Scratch: a Krylov basis of n_pol*(n_steps+1)*dim complex128, allocated per call. */
+bse_status bse_spectrum(bse_ctx *ctx, const void *H, const double *u, int n_pol,
+                        int n_steps, const double *omega, int n_w, double eta,
+                        double prefactor, double *eps2, double *ab);
+
+/* Lowest Ritz values of H after n_steps (<= dim) Lanczos steps with full
+ * reorthogonalisation from a fixed pseudo-random start vector (seed `seed`).
+ *  omega_out : [n_eig] float64 ascending;  resid_out : optional [n_eig] float64
+ *  receiving |b_m * s_m,i| (the Lanczos residual norm of each Ritz pair), or NULL. */
+bse_status bse_lowest(bse_ctx *ctx, const void *H, int n_eig, int n_steps, uint64_t seed,
+                      double *omega_out, double *resid_out);
+
+/* Wait for the context's stream, then read and clear the device error word. */
+bse_status bse_sync(bse_ctx *ctx);
+
+/* Text of the last error on this context (never NULL; "" when none). */
+const char *bse_last_error(const bse_ctx *ctx);
+
+/* Size queries. */
+int64_t bse_dim(const bse_ctx *ctx);
+int32_t bse_naux(const bse_ctx *ctx);
+int32_t bse_nao(const bse_ctx *ctx);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+int64_t bse_launch_count(void);
+
+/* Per-kernel CUDA-event timing on the context's stream (off by default).  While enabled,
+ * each launch of the kernels below is bracketed by two events; bse_profile_read
+ * synchronises the stream and returns the accumulated device time and launch count of
+ * one kernel since profiling was (re-)enabled. */
+typedef enum {
+  BSE_KP_INTERP = 0,   /* W(q) interpolation                               */
+  BSE_KP_HALF = 1,     /* C(k) and half-transform Y(k)                     */
+  BSE_KP_PROJECT = 2,  /* pair projection M_vv, M_cc of one q-slab         */
+  BSE_KP_G1 = 3,       /* T = M_vv W(q) contraction                        */
+  BSE_KP_G2 = 4,       /* T M_cc^T + exchange + diagonal, H write          */
+  BSE_KP_EXCH = 5,     /* exchange contraction (tensor-core path)          */
+  BSE_KP_MATVEC = 6,   /* Lanczos H x                                      */
+  BSE_KP_REORTH = 7,   /* Lanczos reorthogonalisation                      */
+  BSE_KP_COUNT = 8
+} bse_kernel_id;
+bse_status bse_profile(bse_ctx *ctx, int enable);
+bse_status bse_profile_read(bse_ctx *ctx, int kernel_id, double *total_ms, int64_t *launches);
+
+/* Release the workspace and the context.  NULL-safe.  Synchronises the stream first. */
+void bse_free(bse_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSE_H */

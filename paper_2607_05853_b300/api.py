@@ -1,0 +1,168 @@
+"""Thin Python binding of libbse (include/bse.h): argument checks and marshalling only.
+
+Every step of the path runs in the CUDA library; torch supplies device memory and the
+stream.  Method names follow the C entry points (bse_setup -> BSE(...),
+bse_interp_W -> BSE.interp_W, ...).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+__all__ = ["BSE", "BseError", "launch_count"]
+
+BseError = _lib.BseError
+
+
+def launch_count() -> int:
+    """Kernels launched by libbse in this process."""
+    return int(_lib.load().bse_launch_count())
+
+
+def _dev(t: torch.Tensor, dtype, name: str, numel: int | None = None) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class BSE:
+    """One crystal's TDA-BSE problem bound to the current CUDA device and stream."""
+
+    def __init__(self, *, nao, naux, dense, R_C, R_W, w_RW, nv, nc, k_offset=(0.0, 0.0, 0.0),
+                 alpha=2.0, precision="fp64", stream: torch.cuda.Stream | None = None):
+        lib = _lib.load()
+        self._lib = lib
+        nao = np.ascontiguousarray(nao, np.int32)
+        naux = np.ascontiguousarray(naux, np.int32)
+        R_C = np.ascontiguousarray(R_C, np.int32).reshape(-1, 3)
+        R_W = np.ascontiguousarray(R_W, np.int32).reshape(-1, 3)
+        w_RW = np.ascontiguousarray(w_RW, np.float64)
+        if precision not in _lib.PRECISIONS:
+            raise ValueError(f"precision must be one of {list(_lib.PRECISIONS)}")
+        self.precision = precision
+        p = _lib.BseParams()
+        p.n_atoms = len(nao)
+        p.nao_per_atom = nao.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.naux_per_atom = naux.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.dense[:] = [int(x) for x in dense]
+        p.k_offset[:] = [float(x) for x in k_offset]
+        p.n_RC = len(R_C)
+        p.R_C = R_C.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.n_RW = len(R_W)
+        p.R_W = R_W.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        p.w_RW = w_RW.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        p.nv, p.nc = int(nv), int(nc)
+        p.alpha = float(alpha)
+        p.precision = _lib.PRECISIONS[precision]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        ctx = ctypes.c_void_p()
+        st = lib.bse_setup(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
+        if st != _lib.BSE_OK:
+            raise BseError(st, "bse_setup rejected the parameters or could not allocate")
+        self._ctx = ctx
+        self.nk = int(np.prod(dense))
+        self.nv, self.nc = int(nv), int(nc)
+        self.nb = self.nv + self.nc
+        self.dim = int(lib.bse_dim(ctx))
+        self.naux = int(lib.bse_naux(ctx))
+        self.nao = int(lib.bse_nao(ctx))
+        self.n_RW = len(R_W)
+        self.n_RC = len(R_C)
+        self.h_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+
+    @classmethod
+    def from_inputs(cls, inp: dict, **kw) -> "BSE":
+        return cls(nao=inp["nao"], naux=inp["naux"], dense=inp["dense"], R_C=inp["R_C"], R_W=inp["R_W"],
+                   w_RW=inp["w_RW"], nv=inp["nv"], nc=inp["nc"], k_offset=inp["k_offset"], **kw)
+
+    # -- helpers -------------------------------------------------------------------------
+    def _check(self, st: int, what: str):
+        if st != _lib.BSE_OK:
+            raise BseError(st, f"{what}: {self._lib.bse_last_error(self._ctx).decode()}")
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.bse_free(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- the ABI -------------------------------------------------------------------------
+    def interp_W(self, W_R: torch.Tensor, V0: torch.Tensor, Wq_out: torch.Tensor | None = None):
+        na = self.naux
+        a = _dev(W_R, torch.float64, "W_R", self.n_RW * na * na)
+        b = _dev(V0, torch.float64, "V0", na * na)
+        c = _dev(Wq_out, torch.complex128, "Wq_out", self.nk * na * na) if Wq_out is not None else None
+        self._check(self._lib.bse_interp_W(self._ctx, a, b, c), "bse_interp_W")
+        return Wq_out
+
+    def project_pairs(self, C_R: torch.Tensor, c_k: torch.Tensor, e_qp: torch.Tensor):
+        a = _dev(C_R, torch.float64, "C_R", self.n_RC * self.nao * self.nao * self.naux)
+        b = _dev(c_k, torch.complex128, "c_k", self.nk * self.nao * self.nb)
+        c = _dev(e_qp, torch.float64, "e_qp", self.nk * self.nb)
+        self._check(self._lib.bse_project_pairs(self._ctx, a, b, c), "bse_project_pairs")
+
+    def assemble(self, H: torch.Tensor | None = None) -> torch.Tensor:
+        if H is None:
+            H = torch.empty((self.dim, self.dim), dtype=self.h_dtype, device="cuda")
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        self._check(self._lib.bse_assemble(self._ctx, h), "bse_assemble")
+        return H
+
+    def dipole_vector(self, vel: torch.Tensor, e_ks: torch.Tensor, u: torch.Tensor | None = None) -> torch.Tensor:
+        if u is None:
+            u = torch.empty((3, self.dim), dtype=torch.complex128, device="cuda")
+        a = _dev(vel, torch.complex128, "vel", 3 * self.dim)
+        b = _dev(e_ks, torch.float64, "e_ks", self.nk * self.nb)
+        c = _dev(u, torch.complex128, "u", 3 * self.dim)
+        self._check(self._lib.bse_dipole_vector(self._ctx, a, b, c), "bse_dipole_vector")
+        return u
+
+    def spectrum(self, H: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor, eta: float,
+                 prefactor: float, eps2: torch.Tensor | None = None, ab: torch.Tensor | None = None):
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        if eps2 is None:
+            eps2 = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        a = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        o = _dev(omega, torch.float64, "omega")
+        e = _dev(eps2, torch.float64, "eps2", omega.numel())
+        abp = _dev(ab, torch.float64, "ab", n_pol * 3 * n_steps) if ab is not None else None
+        self._check(self._lib.bse_spectrum(self._ctx, h, a, n_pol, int(n_steps), o, omega.numel(), float(eta),
+                                           float(prefactor), e, abp), "bse_spectrum")
+        return eps2
+
+    def lowest(self, H: torch.Tensor, n_eig: int, n_steps: int, seed: int = 12345):
+        om = torch.empty(n_eig, dtype=torch.float64, device="cuda")
+        rs = torch.empty(n_eig, dtype=torch.float64, device="cuda")
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        self._check(self._lib.bse_lowest(self._ctx, h, int(n_eig), int(n_steps), ctypes.c_uint64(seed),
+                                         om.data_ptr(), rs.data_ptr()), "bse_lowest")
+        return om, rs
+
+    def profile(self, enable: bool = True):
+        self._check(self._lib.bse_profile(self._ctx, int(enable)), "bse_profile")
+
+    def profile_read(self, kernel: str):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self._lib.bse_profile_read(self._ctx, _lib.KERNEL_IDS[kernel], ctypes.byref(ms), ctypes.byref(n)),
+                    "bse_profile_read")
+        return ms.value, n.value
+
+    def sync(self):
+        self._check(self._lib.bse_sync(self._ctx), "bse_sync")

@@ -1,0 +1,373 @@
+// Host side of the C ABI declared in include/bse.h: validation, workspace, call order,
+// and the q-slab loop of the FP64 assembly.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "bse_internal.cuh"
+
+static std::atomic<long long> g_launches{0};
+void bse_count_launch(int n) { g_launches += n; }
+
+bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+bse_status bse_check_launch(bse_ctx *c, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bse_fail(c, BSE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return BSE_OK;
+}
+
+template <class T>
+static bse_status dalloc(bse_ctx *c, T **p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return BSE_OK;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return bse_fail(c, BSE_ENOMEM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+  }
+  return BSE_OK;
+}
+
+template <class T>
+static bse_status upload(bse_ctx *c, T **dst, const std::vector<T> &src) {
+  bse_status s = dalloc(c, dst, src.size());
+  if (s != BSE_OK) return s;
+  if (src.empty()) return BSE_OK;
+  if (cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bse_fail(c, BSE_ECUDA, "upload of parameter tables failed");
+  return BSE_OK;
+}
+
+static cudaEvent_t take_event(bse_ctx *c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+static int g_open_id = -1;
+static cudaEvent_t g_open_ev = nullptr;
+
+void bse_prof_begin(bse_ctx *c, int id) {
+  if (!c->prof) return;
+  g_open_ev = take_event(c);
+  g_open_id = id;
+  cudaEventRecord(g_open_ev, c->stream);
+}
+
+void bse_prof_end(bse_ctx *c, int id) {
+  if (!c->prof || g_open_id != id || !g_open_ev) return;
+  cudaEvent_t e = take_event(c);
+  cudaEventRecord(e, c->stream);
+  c->pending.push_back({id, g_open_ev, e});
+  g_open_ev = nullptr;
+  g_open_id = -1;
+}
+
+static void prof_collect(bse_ctx *c) {
+  for (auto &p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.id] += ms;
+      c->prof_n[p.id] += 1;
+    }
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+  cudaGetLastError();
+}
+
+static void release(bse_ctx *c) {
+  if (!c) return;
+  prof_collect(c);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  c->pool.clear();
+  void *ptrs[] = {c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
+                  c->d_aux_start, c->d_naux, c->d_err, c->Wq, c->V0c, c->Y, c->ck,
+                  c->eqp, c->X, c->P, c->Mv, c->Mc, c->T};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  split_free(c);
+}
+
+extern "C" {
+
+int64_t bse_launch_count(void) { return g_launches.load(); }
+
+const char *bse_last_error(const bse_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int64_t bse_dim(const bse_ctx *ctx) { return ctx ? ctx->dim : -1; }
+int32_t bse_naux(const bse_ctx *ctx) { return ctx ? ctx->naux_tot : -1; }
+int32_t bse_nao(const bse_ctx *ctx) { return ctx ? ctx->nao_tot : -1; }
+
+bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
+  if (!out) return BSE_EINVAL;
+  *out = nullptr;
+  if (!p) return BSE_EINVAL;
+  if (p->n_atoms < 1 || p->n_atoms > 4096 || !p->nao_per_atom || !p->naux_per_atom) return BSE_EINVAL;
+  for (int i = 0; i < 3; i++) {
+    if (p->dense[i] < 1 || p->dense[i] > 4096) return BSE_EINVAL;
+    if (!std::isfinite(p->k_offset[i])) return BSE_EINVAL;
+  }
+  if (p->n_RC < 1 || !p->R_C || p->n_RW < 1 || !p->R_W || !p->w_RW) return BSE_EINVAL;
+  if (p->nv < 1 || p->nc < 1 || p->nv > 8 || p->nc > 8) return BSE_EINVAL;
+  if (p->precision < BSE_FP64 || p->precision > BSE_BF16X1) return BSE_EINVAL;
+  if (!std::isfinite(p->alpha)) return BSE_EINVAL;
+  long long nk = (long long)p->dense[0] * p->dense[1] * p->dense[2];
+  if (nk > 65535) return BSE_EINVAL;
+  int nao_tot = 0, naux_tot = 0, nao_max = 0;
+  for (int a = 0; a < p->n_atoms; a++) {
+    if (p->nao_per_atom[a] < 1 || p->naux_per_atom[a] < 1) return BSE_EINVAL;
+    nao_tot += p->nao_per_atom[a];
+    naux_tot += p->naux_per_atom[a];
+    nao_max = std::max(nao_max, p->nao_per_atom[a]);
+  }
+  if (p->nv + p->nc > nao_tot || naux_tot > 8192 || nao_tot > 4096) return BSE_EINVAL;
+  for (int r = 0; r < p->n_RW; r++)
+    if (!std::isfinite(p->w_RW[r])) return BSE_EINVAL;
+
+  bse_ctx *c = new bse_ctx();
+  c->n_atoms = p->n_atoms;
+  c->nao.assign(p->nao_per_atom, p->nao_per_atom + p->n_atoms);
+  c->naux.assign(p->naux_per_atom, p->naux_per_atom + p->n_atoms);
+  int s0 = 0, m0 = 0;
+  std::vector<int> aux_atom;
+  for (int a = 0; a < p->n_atoms; a++) {
+    c->ao_start.push_back(s0);
+    c->aux_start.push_back(m0);
+    for (int m = 0; m < c->naux[a]; m++) aux_atom.push_back(a);
+    s0 += c->nao[a];
+    m0 += c->naux[a];
+  }
+  c->nao_tot = nao_tot;
+  c->naux_tot = naux_tot;
+  c->nao_max = nao_max;
+  for (int i = 0; i < 3; i++) {
+    c->mesh[i] = p->dense[i];
+    c->koff[i] = p->k_offset[i];
+  }
+  c->nk = (int)nk;
+  c->n_RC = p->n_RC;
+  c->n_RW = p->n_RW;
+  c->R_C.assign(p->R_C, p->R_C + 3 * p->n_RC);
+  c->R_W.assign(p->R_W, p->R_W + 3 * p->n_RW);
+  c->w_RW.assign(p->w_RW, p->w_RW + p->n_RW);
+  c->nv = p->nv;
+  c->nc = p->nc;
+  c->nb = p->nv + p->nc;
+  c->nvc = p->nv * p->nc;
+  c->alpha = p->alpha;
+  c->precision = p->precision;
+  c->dim = nk * c->nvc;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&c->device);
+
+  bse_status s = BSE_OK;
+#define TRY(x)              \
+  do {                      \
+    s = (x);                \
+    if (s != BSE_OK) goto fail; \
+  } while (0)
+  {
+    TRY(upload(c, &c->d_R_C, c->R_C));
+    TRY(upload(c, &c->d_R_W, c->R_W));
+    TRY(upload(c, &c->d_w_RW, c->w_RW));
+    TRY(upload(c, &c->d_aux_atom, aux_atom));
+    TRY(upload(c, &c->d_ao_start, c->ao_start));
+    TRY(upload(c, &c->d_nao, c->nao));
+    TRY(upload(c, &c->d_aux_start, c->aux_start));
+    TRY(upload(c, &c->d_naux, c->naux));
+    TRY(dalloc(c, &c->d_err, 1));
+    const size_t nn = (size_t)naux_tot * naux_tot;
+    TRY(dalloc(c, &c->V0c, nn));
+    TRY(dalloc(c, &c->Y, (size_t)nk * nao_max * c->nb * naux_tot));
+    TRY(dalloc(c, &c->ck, (size_t)nk * nao_tot * c->nb));
+    TRY(dalloc(c, &c->eqp, (size_t)nk * c->nb));
+    TRY(dalloc(c, &c->X, (size_t)c->dim * naux_tot));
+    TRY(dalloc(c, &c->P, (size_t)c->dim * naux_tot));
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->Y, 0, (size_t)nk * nao_max * c->nb * naux_tot * sizeof(double2)) != cudaSuccess) {
+      s = bse_fail(c, BSE_ECUDA, "workspace initialisation failed");
+      goto fail;
+    }
+    if (c->precision == BSE_FP64) {
+      TRY(dalloc(c, &c->Wq, (size_t)nk * nn));
+      const size_t per_q = (size_t)nk * (2 * c->nv * c->nv + c->nc * c->nc) * naux_tot * sizeof(double2);
+      size_t budget = (size_t)768 << 20;
+      c->slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
+      c->slab = std::min(c->slab, 65535);
+      TRY(dalloc(c, &c->Mv, (size_t)c->slab * nk * c->nv * c->nv * naux_tot));
+      TRY(dalloc(c, &c->T, (size_t)c->slab * nk * c->nv * c->nv * naux_tot));
+      TRY(dalloc(c, &c->Mc, (size_t)c->slab * nk * c->nc * c->nc * naux_tot));
+    } else {
+      TRY(split_setup(c));
+    }
+  }
+#undef TRY
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    s = bse_fail(c, BSE_ECUDA, "setup synchronisation failed");
+    goto fail;
+  }
+  *out = c;
+  return BSE_OK;
+fail:
+  release(c);
+  delete c;
+  return s;
+}
+
+namespace {
+__global__ void k_real_to_complex(const double *src, double2 *dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = make_double2(src[i], 0.0);
+}
+}  // namespace
+
+bse_status bse_interp_W(bse_ctx *c, const double *W_R, const double *V0, void *Wq_out) {
+  if (!c) return BSE_EINVAL;
+  if (!W_R || !V0) return bse_fail(c, BSE_EINVAL, "interp_W: null W_R or V0");
+  const long long nn = (long long)c->naux_tot * c->naux_tot;
+  k_real_to_complex<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(V0, c->V0c, nn);
+  bse_count_launch();
+  bse_status s = bse_check_launch(c, "V0 copy");
+  if (s != BSE_OK) return s;
+  if (c->precision == BSE_FP64) {
+    s = launch_interp_W_fp64(c, W_R, c->Wq);
+    if (s != BSE_OK) return s;
+    if (Wq_out &&
+        cudaMemcpyAsync(Wq_out, c->Wq, (size_t)c->nk * nn * sizeof(double2), cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      return bse_fail(c, BSE_ECUDA, "interp_W: copy to Wq_out failed");
+  } else {
+    s = split_interp_W(c, W_R, (double2 *)Wq_out);
+    if (s != BSE_OK) return s;
+  }
+  c->stage = std::max(c->stage, 1);
+  return BSE_OK;
+}
+
+bse_status bse_project_pairs(bse_ctx *c, const double *C_R, const double *c_k, const double *e_qp) {
+  if (!c) return BSE_EINVAL;
+  if (c->stage < 1) return bse_fail(c, BSE_ESTATE, "project_pairs before interp_W");
+  if (!C_R || !c_k || !e_qp) return bse_fail(c, BSE_EINVAL, "project_pairs: null argument");
+  if (cudaMemcpyAsync(c->ck, c_k, (size_t)c->nk * c->nao_tot * c->nb * sizeof(double2),
+                      cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->eqp, e_qp, (size_t)c->nk * c->nb * sizeof(double), cudaMemcpyDeviceToDevice,
+                      c->stream) != cudaSuccess)
+    return bse_fail(c, BSE_ECUDA, "project_pairs: copy of c_k / e_qp failed");
+  bse_status s = launch_half_transform_fp64(c, C_R);
+  if (s != BSE_OK) return s;
+  s = launch_exchange_factors_fp64(c);
+  if (s != BSE_OK) return s;
+  // P = X V(0): rows (k,i,a), K = N = N_aux
+  s = launch_zgemm_fp64(c, (int)c->dim, c->naux_tot, c->naux_tot, c->X, c->naux_tot, 0, c->V0c,
+                        c->naux_tot, 0, c->P, c->naux_tot, 0, 1);
+  if (s != BSE_OK) return s;
+  if (c->precision != BSE_FP64) {
+    s = split_project(c);
+    if (s != BSE_OK) return s;
+  }
+  c->stage = 2;
+  return BSE_OK;
+}
+
+bse_status bse_assemble(bse_ctx *c, void *H) {
+  if (!c) return BSE_EINVAL;
+  if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "assemble before project_pairs");
+  if (!H) return bse_fail(c, BSE_EINVAL, "assemble: null H");
+  if (c->precision != BSE_FP64) return split_assemble(c, H);
+  const int na = c->naux_tot;
+  const long long rows = (long long)c->nk * c->nv * c->nv;
+  for (int q0 = 0; q0 < c->nk; q0 += c->slab) {
+    const int nq = std::min(c->slab, c->nk - q0);
+    bse_status s = launch_project_slab_fp64(c, q0, nq);
+    if (s != BSE_OK) return s;
+    s = launch_zgemm_fp64(c, (int)rows, na, na, c->Mv, na, rows * na, c->Wq + (long long)q0 * na * na, na,
+                          (long long)na * na, c->T, na, rows * na, nq, BSE_KP_G1);
+    if (s != BSE_OK) return s;
+    s = launch_g2_write_fp64(c, q0, nq, (double2 *)H);
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double *u) {
+  if (!c) return BSE_EINVAL;
+  if (!vel || !e_ks || !u) return bse_fail(c, BSE_EINVAL, "dipole_vector: null argument");
+  return run_dipole_vector(c, vel, e_ks, (double2 *)u);
+}
+
+bse_status bse_spectrum(bse_ctx *c, const void *H, const double *u, int n_pol, int n_steps,
+                        const double *omega, int n_w, double eta, double prefactor, double *eps2,
+                        double *ab) {
+  if (!c) return BSE_EINVAL;
+  if (!H || !u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum: null argument");
+  if (n_pol < 1 || n_pol > 3 || n_steps < 1 || n_steps > c->dim || n_w < 1 || !(eta > 0.0) ||
+      !std::isfinite(prefactor))
+    return bse_fail(c, BSE_EINVAL, "spectrum: bad size or parameter");
+  return run_spectrum(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
+}
+
+bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
+                      double *omega_out, double *resid_out) {
+  if (!c) return BSE_EINVAL;
+  if (!H || !omega_out) return bse_fail(c, BSE_EINVAL, "lowest: null argument");
+  if (n_steps < 1 || n_steps > c->dim || n_eig < 1 || n_eig > n_steps)
+    return bse_fail(c, BSE_EINVAL, "lowest: bad size");
+  return run_lowest(c, H, n_eig, n_steps, seed, omega_out, resid_out);
+}
+
+bse_status bse_sync(bse_ctx *c) {
+  if (!c) return BSE_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return bse_fail(c, BSE_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+  int w = 0;
+  if (cudaMemcpy(&w, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
+    return bse_fail(c, BSE_ECUDA, "sync: error word unreadable");
+  if (w & BSE_DERR_TIMEOUT) return bse_fail(c, BSE_ETIMEOUT, "a bounded device wait gave up");
+  if (w) return bse_fail(c, BSE_EDEVICE, "device check failed, code " + std::to_string(w));
+  return BSE_OK;
+}
+
+bse_status bse_profile(bse_ctx *c, int enable) {
+  if (!c) return BSE_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  prof_collect(c);
+  c->prof = enable != 0;
+  for (int i = 0; i < BSE_KP_COUNT; i++) {
+    c->prof_ms[i] = 0.0;
+    c->prof_n[i] = 0;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_profile_read(bse_ctx *c, int id, double *total_ms, int64_t *launches) {
+  if (!c) return BSE_EINVAL;
+  if (id < 0 || id >= BSE_KP_COUNT || !total_ms || !launches) return bse_fail(c, BSE_EINVAL, "profile_read: bad id");
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bse_fail(c, BSE_ECUDA, "profile_read: sync failed");
+  prof_collect(c);
+  *total_ms = c->prof_ms[id];
+  *launches = c->prof_n[id];
+  return BSE_OK;
+}
+
+void bse_free(bse_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  release(c);
+  delete c;
+}
+
+}  // extern "C"

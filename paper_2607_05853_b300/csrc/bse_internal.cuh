@@ -1,0 +1,115 @@
+// Internal declarations of libbse (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bse.h"
+
+// Device error word bits (read and cleared by bse_sync).
+enum : int {
+  BSE_DERR_BOUNDS = 1,      // an index check failed
+  BSE_DERR_TIMEOUT = 2,     // a bounded mbarrier / flag wait gave up
+  BSE_DERR_ZERO_DENOM = 4,  // E_c - E_v == 0 in a dipole denominator
+  BSE_DERR_TMEM = 8         // tensor-memory allocation returned an unusable address
+};
+
+struct bse_ctx {
+  // problem (copied from bse_params)
+  int n_atoms = 0;
+  std::vector<int> nao, naux, ao_start, aux_start;
+  int nao_tot = 0, naux_tot = 0, nao_max = 0;
+  int mesh[3] = {1, 1, 1};
+  double koff[3] = {0, 0, 0};
+  int nk = 0;
+  int n_RC = 0, n_RW = 0;
+  std::vector<int> R_C, R_W;
+  std::vector<double> w_RW;
+  int nv = 0, nc = 0, nb = 0, nvc = 0;
+  double alpha = 2.0;
+  int precision = BSE_FP64;
+  int64_t dim = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int stage = 0;  // 0 setup, 1 interp_W done, 2 project_pairs done
+  std::string err;
+
+  // small device tables
+  int *d_R_C = nullptr, *d_R_W = nullptr;
+  double *d_w_RW = nullptr;
+  int *d_aux_atom = nullptr;   // atom of each ABF
+  int *d_ao_start = nullptr;   // first NAO of each atom
+  int *d_nao = nullptr;        // NAOs of each atom
+  int *d_aux_start = nullptr;  // first ABF of each atom
+  int *d_naux = nullptr;       // ABFs of each atom
+  int *d_err = nullptr;        // device error word
+
+  // workspace
+  double2 *Wq = nullptr;   // [nk][naux][naux]   W(q), row mu, column nu (FP64 path)
+  double2 *V0c = nullptr;  // [naux][naux]       V(0) as complex
+  double2 *Y = nullptr;    // [nk][nao_max][nb][naux]  Y^mu_{s n}(k), s local to atom(mu)
+  double2 *ck = nullptr;   // [nk][nao][nb]      band coefficients
+  double *eqp = nullptr;   // [nk][nb]
+  double2 *X = nullptr;    // [nk][nv][nc][naux] C~^mu_{a k, i k}
+  double2 *P = nullptr;    // [dim][naux]        X V0
+  int slab = 1;            // q values per assembly slab
+  double2 *Mv = nullptr, *Mc = nullptr, *T = nullptr;  // [slab][nk][nv*nv | nc*nc][naux]
+
+  // split-precision workspace (tensor-core path)
+  void *tc = nullptr;
+
+  // per-kernel event timing (bse_profile)
+  bool prof = false;
+  struct Pending { int id; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[BSE_KP_COUNT] = {0};
+  long long prof_n[BSE_KP_COUNT] = {0};
+};
+
+// Bracket one launch with events when profiling is enabled.
+void bse_prof_begin(bse_ctx *c, int id);
+void bse_prof_end(bse_ctx *c, int id);
+
+// ---- helpers shared by the .cu files --------------------------------------------------
+void bse_count_launch(int n = 1);
+bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg);
+bse_status bse_check_launch(bse_ctx *c, const char *what);
+
+// fp64 path launchers (k_fp64.cu)
+bse_status launch_interp_W_fp64(bse_ctx *c, const double *W_R, double2 *out);
+bse_status launch_half_transform_fp64(bse_ctx *c, const double *C_R);
+bse_status launch_exchange_factors_fp64(bse_ctx *c);
+bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, int lda,
+                             long long sA, const double2 *B, int ldb, long long sB, double2 *C,
+                             int ldc, long long sC, int batch, int prof_id = -1);
+bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq);
+bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H);
+
+// spectrum (k_haydock.cu)
+bse_status run_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double2 *u);
+bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
+                        const double *omega, int n_w, double eta, double pref, double *eps2,
+                        double *ab);
+bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
+                      double *omega_out, double *resid_out);
+
+// split-precision path (k_split.cu)
+bse_status split_setup(bse_ctx *c);
+bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
+bse_status split_assemble(bse_ctx *c, void *H);
+bse_status split_project(bse_ctx *c);
+void split_free(bse_ctx *c);
+
+// mesh helpers
+__host__ __device__ inline int kdiff(int k1, int q, int n1, int n2, int n3) {
+  // index of k2 = k1 - q on the mesh (integer parts; offsets cancel in differences)
+  int a1 = k1 / (n2 * n3), a2 = (k1 / n3) % n2, a3 = k1 % n3;
+  int b1 = q / (n2 * n3), b2 = (q / n3) % n2, b3 = q % n3;
+  int c1 = a1 - b1; if (c1 < 0) c1 += n1;
+  int c2 = a2 - b2; if (c2 < 0) c2 += n2;
+  int c3 = a3 - b3; if (c3 < 0) c3 += n3;
+  return (c1 * n2 + c2) * n3 + c3;
+}

@@ -1,0 +1,563 @@
+// Spectrum step: velocity-form oscillator vector, Haydock/Lanczos recursion with full
+// reorthogonalisation (FP64), continued fraction on the frequency grid (Eq. abs_vel with
+// a Lorentzian of half-width eta), and lowest Ritz values (Sturm bisection + inverse
+// iteration on the Lanczos tridiagonal).
+//
+// The matrix-vector product reads H once per Lanczos step for all polarisations.  For a
+// complex128 H the products are FP64; for a complex64 H (split-precision assembly) the
+// products and the per-lane partial sums are FP32 (H itself carries FP32 rounding) and
+// the cross-lane sums, dots, norms, updates and the reorthogonalisation are FP64.
+#include <cmath>
+
+#include "bse_internal.cuh"
+
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__global__ void k_dipole(const double2 *__restrict__ vel, const double *__restrict__ eks, int nk,
+                         int nv, int nc, double2 *__restrict__ u, int *err) {
+  const long long dim = (long long)nk * nv * nc;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.y;
+  if (idx >= dim) return;
+  const int k = (int)(idx / (nv * nc)), i = (int)((idx / nc) % nv), a = (int)(idx % nc);
+  const int nb = nv + nc;
+  double de = eks[(long long)k * nb + nv + a] - eks[(long long)k * nb + i];
+  double2 v = vel[(long long)p * dim + idx];
+  if (de == 0.0) {
+    atomicOr(err, BSE_DERR_ZERO_DENOM);
+    u[(long long)p * dim + idx] = make_double2(0.0, 0.0);
+    return;
+  }
+  u[(long long)p * dim + idx] = make_double2(v.x / de, -v.y / de);
+}
+
+// ---- block reductions -------------------------------------------------------------------
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < NT / 32; i++) s += red[i];
+  return s;  // valid in thread 0
+}
+
+// max |H| over all elements (for the early-stop threshold): per-block maxima, then one block.
+template <class HT>
+__global__ void k_absmax_part(const HT *__restrict__ H, long long n, double *part) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double x = (double)H[i].x, y = (double)H[i].y;
+    m = fmax(m, sqrt(x * x + y * y));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < blockDim.x / 32; i++) r = fmax(r, red[i]);
+    part[blockIdx.x] = r;
+  }
+}
+__global__ void k_absmax_final(const double *part, int n, double *out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double r = 0.0;
+    for (int i = 0; i < n; i++) r = fmax(r, part[i]);
+    *out = r;
+  }
+}
+
+// beta0[p] = |u_p|, Q[p][0] = u_p / beta0 (block per p).
+__global__ void k_lanczos_init(const double2 *__restrict__ u, long long dim, double2 *Q, long long qs,
+                               double *beta0) {
+  __shared__ double red[32];
+  __shared__ double sb;
+  const int p = blockIdx.x;
+  const double2 *up = u + (long long)p * dim;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) s += up[i].x * up[i].x + up[i].y * up[i].y;
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) {
+    sb = sqrt(s);
+    beta0[p] = sb;
+  }
+  __syncthreads();
+  const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x)
+    Q[p * qs + i] = make_double2(up[i].x * inv, up[i].y * inv);
+}
+
+constexpr int MV_WARPS = 8, MV_RPW = 4, MV_ROWS = MV_WARPS * MV_RPW, MV_CC = 256;
+
+// W[p][r] = sum_c H[r][c] Q[p][j][c]  -- complex128 H, FP64 arithmetic.
+template <int NP>
+__global__ void __launch_bounds__(256) k_matvec_c128(const double2 *__restrict__ H, long long dim,
+                                                     const double2 *__restrict__ Q, long long qs,
+                                                     int j, double2 *__restrict__ W, const int *meff) {
+  __shared__ double2 xs[NP][MV_CC];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long r0 = (long long)blockIdx.x * MV_ROWS + warp * MV_RPW;
+  bool live = false;
+  for (int p = 0; p < NP; p++) live |= (j < meff[p]);
+  if (!live) return;
+  double2 acc[MV_RPW][NP];
+#pragma unroll
+  for (int r = 0; r < MV_RPW; r++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) acc[r][p] = make_double2(0, 0);
+  for (long long c0 = 0; c0 < dim; c0 += MV_CC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < NP * MV_CC; t += blockDim.x) {
+      int p = t / MV_CC, cc = t % MV_CC;
+      long long c = c0 + cc;
+      xs[p][cc] = c < dim ? Q[p * qs + (long long)j * dim + c] : make_double2(0, 0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < MV_RPW; r++) {
+      const long long row = r0 + r;
+      if (row >= dim) continue;
+      const double2 *hr = H + row * dim + c0;
+#pragma unroll
+      for (int t = 0; t < MV_CC / 32; t++) {
+        const int cc = lane + 32 * t;
+        if (c0 + cc < dim) {
+          const double2 h = hr[cc];
+#pragma unroll
+          for (int p = 0; p < NP; p++) {
+            const double2 x = xs[p][cc];
+            acc[r][p].x = fma(h.x, x.x, fma(-h.y, x.y, acc[r][p].x));
+            acc[r][p].y = fma(h.x, x.y, fma(h.y, x.x, acc[r][p].y));
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < MV_RPW; r++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      double x = acc[r][p].x, y = acc[r][p].y;
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      const long long row = r0 + r;
+      if (lane == 0 && row < dim) W[(long long)p * dim + row] = make_double2(x, y);
+    }
+}
+
+// Same for a complex64 H: FP32 products and per-lane sums, FP64 across lanes.
+template <int NP>
+__global__ void __launch_bounds__(256) k_matvec_c64(const float2 *__restrict__ H, long long dim,
+                                                    const double2 *__restrict__ Q, long long qs, int j,
+                                                    double2 *__restrict__ W, const int *meff) {
+  __shared__ float2 xs[NP][MV_CC];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long r0 = (long long)blockIdx.x * MV_ROWS + warp * MV_RPW;
+  bool live = false;
+  for (int p = 0; p < NP; p++) live |= (j < meff[p]);
+  if (!live) return;
+  float2 acc[MV_RPW][NP];
+#pragma unroll
+  for (int r = 0; r < MV_RPW; r++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) acc[r][p] = make_float2(0.f, 0.f);
+  for (long long c0 = 0; c0 < dim; c0 += MV_CC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < NP * MV_CC; t += blockDim.x) {
+      int p = t / MV_CC, cc = t % MV_CC;
+      long long c = c0 + cc;
+      double2 v = c < dim ? Q[p * qs + (long long)j * dim + c] : make_double2(0, 0);
+      xs[p][cc] = make_float2((float)v.x, (float)v.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < MV_RPW; r++) {
+      const long long row = r0 + r;
+      if (row >= dim) continue;
+      const float2 *hr = H + row * dim + c0;
+#pragma unroll
+      for (int t = 0; t < MV_CC / 32; t++) {
+        const int cc = lane + 32 * t;
+        if (c0 + cc < dim) {
+          const float2 h = __ldcs(hr + cc);
+#pragma unroll
+          for (int p = 0; p < NP; p++) {
+            const float2 x = xs[p][cc];
+            acc[r][p].x = fmaf(h.x, x.x, fmaf(-h.y, x.y, acc[r][p].x));
+            acc[r][p].y = fmaf(h.x, x.y, fmaf(h.y, x.x, acc[r][p].y));
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < MV_RPW; r++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      double x = acc[r][p].x, y = acc[r][p].y;
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        y += __shfl_xor_sync(0xffffffffu, y, o);
+      }
+      const long long row = r0 + r;
+      if (lane == 0 && row < dim) W[(long long)p * dim + row] = make_double2(x, y);
+    }
+}
+
+// a[p][j] = Re(Q_j^H W); W -= a_j Q_j + b_{j-1} Q_{j-1}   (block per p)
+__global__ void k_alpha_axpy(double2 *W, long long dim, const double2 *Q, long long qs, int j, double *a,
+                             const double *b, int ldab, const int *meff) {
+  __shared__ double red[32];
+  __shared__ double sa;
+  const int p = blockIdx.x;
+  if (j >= meff[p]) return;
+  double2 *w = W + (long long)p * dim;
+  const double2 *qj = Q + p * qs + (long long)j * dim;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) s += qj[i].x * w[i].x + qj[i].y * w[i].y;
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) {
+    sa = s;
+    a[p * ldab + j] = s;
+  }
+  __syncthreads();
+  const double aj = sa, bj = j > 0 ? b[p * ldab + j - 1] : 0.0;
+  const double2 *qm = j > 0 ? qj - dim : qj;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) {
+    double2 v = w[i];
+    v.x -= aj * qj[i].x + bj * qm[i].x;
+    v.y -= aj * qj[i].y + bj * qm[i].y;
+    w[i] = v;
+  }
+}
+
+// coef[p][i] = Q_i^H W, i <= j   (grid: x = i, y = p)
+__global__ void k_reorth_dots(const double2 *W, long long dim, const double2 *Q, long long qs, int j,
+                              double2 *coef, int ldc, const int *meff) {
+  __shared__ double red[32];
+  const int i = blockIdx.x, p = blockIdx.y;
+  if (j >= meff[p] || i > j) return;
+  const double2 *w = W + (long long)p * dim;
+  const double2 *qi = Q + p * qs + (long long)i * dim;
+  double sr = 0.0, si = 0.0;
+  for (long long e = threadIdx.x; e < dim; e += blockDim.x) {
+    const double2 q = qi[e], v = w[e];
+    sr += q.x * v.x + q.y * v.y;
+    si += q.x * v.y - q.y * v.x;
+  }
+  sr = block_sum<256>(sr, red);
+  __syncthreads();
+  si = block_sum<256>(si, red);
+  if (threadIdx.x == 0) coef[p * ldc + i] = make_double2(sr, si);
+}
+
+// W -= sum_{i<=j} coef_i Q_i   (grid: x over elements, y = p)
+__global__ void k_reorth_update(double2 *W, long long dim, const double2 *Q, long long qs, int j,
+                                const double2 *coef, int ldc, const int *meff) {
+  const int p = blockIdx.y;
+  if (j >= meff[p]) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  const double2 *qp = Q + p * qs + e;
+  const double2 *cp = coef + p * ldc;
+  double2 v = W[(long long)p * dim + e];
+  for (int i = 0; i <= j; i++) {
+    const double2 c = cp[i], q = qp[(long long)i * dim];
+    v.x -= c.x * q.x - c.y * q.y;
+    v.y -= c.x * q.y + c.y * q.x;
+  }
+  W[(long long)p * dim + e] = v;
+}
+
+// b[p][j] = |W|; Q[p][j+1] = W/b (block per p); early stop when b < 1e-14 max|H|.
+__global__ void k_norm_scale(const double2 *W, long long dim, double2 *Q, long long qs, int j, double *b,
+                             int ldab, int *meff, const double *hmax, int n_steps) {
+  __shared__ double red[32];
+  __shared__ double sb;
+  const int p = blockIdx.x;
+  if (j >= meff[p]) return;
+  const double2 *w = W + (long long)p * dim;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) s += w[i].x * w[i].x + w[i].y * w[i].y;
+  s = block_sum<1024>(s, red);
+  if (threadIdx.x == 0) {
+    sb = sqrt(s);
+    b[p * ldab + j] = sb;
+  }
+  __syncthreads();
+  const double bj = sb;
+  if (j == n_steps - 1) return;
+  if (bj < 1e-14 * hmax[0]) {
+    __syncthreads();
+    if (threadIdx.x == 0) meff[p] = j + 1;
+    return;
+  }
+  const double inv = 1.0 / bj;
+  double2 *qn = Q + p * qs + (long long)(j + 1) * dim;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) qn[i] = make_double2(w[i].x * inv, w[i].y * inv);
+}
+
+// eps2[w] = pref * sum_p -(1/pi) Im( beta0^2 / (z - a1 - b1^2/(z - a2 - ...)) )
+__global__ void k_contfrac(const double *a, const double *b, int ldab, const double *beta0, const int *meff,
+                           int n_pol, const double *omega, int n_w, double eta, double pref, double *eps2) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= n_w) return;
+  const double zr = omega[w], zi = eta;
+  double tot = 0.0;
+  for (int p = 0; p < n_pol; p++) {
+    const int m = meff[p];
+    const double *ap = a + p * ldab, *bp = b + p * ldab;
+    double fr = zr - ap[m - 1], fi = zi;
+    for (int jj = m - 2; jj >= 0; jj--) {
+      const double d = fr * fr + fi * fi, bb = bp[jj] * bp[jj];
+      // f = z - a_jj - bb / f
+      const double qr = bb * fr / d, qi = -bb * fi / d;
+      fr = zr - ap[jj] - qr;
+      fi = zi - qi;
+    }
+    const double d = fr * fr + fi * fi, b0 = beta0[p] * beta0[p];
+    const double gi = -b0 * fi / d;  // Im(b0 / f)
+    tot += -gi / M_PI;
+  }
+  eps2[w] = pref * tot;
+}
+
+__global__ void k_pack_ab(const double *a, const double *b, const double *beta0, int ldab, int n_pol,
+                          int n_steps, double *ab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (j >= n_steps || p >= n_pol) return;
+  ab[((long long)p * 3 + 0) * n_steps + j] = a[p * ldab + j];
+  ab[((long long)p * 3 + 1) * n_steps + j] = b[p * ldab + j];
+  ab[((long long)p * 3 + 2) * n_steps + j] = j == 0 ? beta0[p] : 0.0;
+}
+
+__global__ void k_fill_meff(int *meff, int n_pol, int n_steps, double *a, double *b, int ldab) {
+  const int p = blockIdx.x;
+  for (int j = threadIdx.x; j < ldab; j += blockDim.x) {
+    a[p * ldab + j] = 0.0;
+    b[p * ldab + j] = 0.0;
+  }
+  if (threadIdx.x == 0 && p < n_pol) meff[p] = n_steps;
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) -> uniform doubles -> a complex start vector.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+__global__ void k_random_start(double2 *u, long long dim, unsigned long long seed) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= dim) return;
+  const unsigned long long r1 = splitmix64(seed ^ (2ull * (unsigned long long)i));
+  const unsigned long long r2 = splitmix64(seed ^ (2ull * (unsigned long long)i + 1ull));
+  u[i] = make_double2((double)(r1 >> 11) * (1.0 / 9007199254740992.0) - 0.5,
+                      (double)(r2 >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+}
+
+// Lowest Ritz values of the m x m tridiagonal (a, b) by Sturm-sequence bisection, and the
+// Lanczos residual |b_m s_m| from an inverse-iteration eigenvector (one thread each).
+__device__ int sturm_count(const double *a, const double *b, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; i++) {
+    const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) cnt++;
+  }
+  return cnt;
+}
+__global__ void k_ritz(const double *a, const double *b, const int *meff, int n_eig, double *omega,
+                       double *resid, double *work) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_eig) return;
+  const int m = meff[0];
+  if (e >= m) {
+    omega[e] = NAN;
+    if (resid) resid[e] = NAN;
+    return;
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; i++) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < m - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; it++) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(a, b, m, mid) >= e + 1) hi = mid; else lo = mid;
+  }
+  const double th = hi;
+  omega[e] = th;
+  if (!resid) return;
+  // inverse iteration (T - th I) v = rhs, Thomas algorithm, two sweeps
+  double *v = work + (long long)e * 3 * m, *cp = v + m, *dp = cp + m;
+  const double scale = fmax(fabs(lo), fabs(hi)) + 1.0;
+  const double shift = th + 1e-13 * scale;
+  for (int i = 0; i < m; i++) v[i] = 1.0;
+  for (int sweep = 0; sweep < 3; sweep++) {
+    double piv = a[0] - shift;
+    if (piv == 0.0) piv = 1e-300;
+    cp[0] = m > 1 ? b[0] / piv : 0.0;
+    dp[0] = v[0] / piv;
+    for (int i = 1; i < m; i++) {
+      piv = (a[i] - shift) - b[i - 1] * cp[i - 1];
+      if (piv == 0.0) piv = 1e-300;
+      cp[i] = i < m - 1 ? b[i] / piv : 0.0;
+      dp[i] = (v[i] - b[i - 1] * dp[i - 1]) / piv;
+    }
+    v[m - 1] = dp[m - 1];
+    for (int i = m - 2; i >= 0; i--) v[i] = dp[i] - cp[i] * v[i + 1];
+    double nrm = 0.0;
+    for (int i = 0; i < m; i++) nrm += v[i] * v[i];
+    nrm = sqrt(nrm);
+    for (int i = 0; i < m; i++) v[i] /= nrm;
+  }
+  resid[e] = fabs(b[m - 1] * v[m - 1]);
+}
+
+struct LanczosScratch {
+  double2 *Q = nullptr, *W = nullptr, *coef = nullptr;
+  double *a = nullptr, *b = nullptr, *beta0 = nullptr, *hmax = nullptr, *part = nullptr;
+  int *meff = nullptr;
+};
+
+bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) {
+  const long long dim = c->dim;
+  const size_t qbytes = sizeof(double2) * (size_t)n_pol * (n_steps + 1) * dim;
+  cudaStream_t st = c->stream;
+  if (cudaMallocAsync((void **)&s.Q, qbytes, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.W, sizeof(double2) * n_pol * dim, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.coef, sizeof(double2) * n_pol * (n_steps + 1), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.a, sizeof(double) * n_pol * (n_steps + 1), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.b, sizeof(double) * n_pol * (n_steps + 1), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.beta0, sizeof(double) * n_pol, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.hmax, sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.part, sizeof(double) * 1024, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess) {
+    cudaGetLastError();
+    return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
+  }
+  return BSE_OK;
+}
+
+void lanczos_release(bse_ctx *c, LanczosScratch &s) {
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff};
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
+// Runs the recursion; a, b, beta0, meff are left in s.
+bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const double2 *u, int n_pol,
+                       int n_steps) {
+  const long long dim = c->dim;
+  const long long qs = (long long)(n_steps + 1) * dim;
+  const int ldab = n_steps + 1;
+  cudaStream_t st = c->stream;
+  const bool c64 = c->precision != BSE_FP64;
+  // max |H|
+  if (c64)
+    k_absmax_part<float2><<<1024, 256, 0, st>>>((const float2 *)H, dim * dim, s.part);
+  else
+    k_absmax_part<double2><<<1024, 256, 0, st>>>((const double2 *)H, dim * dim, s.part);
+  k_absmax_final<<<1, 32, 0, st>>>(s.part, 1024, s.hmax);
+  k_fill_meff<<<n_pol, 256, 0, st>>>(s.meff, n_pol, n_steps, s.a, s.b, ldab);
+  k_lanczos_init<<<n_pol, 1024, 0, st>>>(u, dim, s.Q, qs, s.beta0);
+  bse_count_launch(4);
+  bse_status r = bse_check_launch(c, "lanczos init");
+  if (r != BSE_OK) return r;
+  const unsigned mv_blocks = (unsigned)((dim + MV_ROWS - 1) / MV_ROWS);
+  const unsigned el_blocks = (unsigned)((dim + 255) / 256);
+  for (int j = 0; j < n_steps; j++) {
+    bse_prof_begin(c, BSE_KP_MATVEC);
+    if (c64) {
+      if (n_pol == 1) k_matvec_c64<1><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+      else if (n_pol == 2) k_matvec_c64<2><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+      else k_matvec_c64<3><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+    } else {
+      if (n_pol == 1) k_matvec_c128<1><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+      else if (n_pol == 2) k_matvec_c128<2><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+      else k_matvec_c128<3><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
+    }
+    bse_prof_end(c, BSE_KP_MATVEC);
+    k_alpha_axpy<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff);
+    bse_prof_begin(c, BSE_KP_REORTH);
+    for (int pass = 0; pass < 2; pass++) {
+      k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+      k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+    }
+    bse_prof_end(c, BSE_KP_REORTH);
+    k_norm_scale<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps);
+    bse_count_launch(7);
+    r = bse_check_launch(c, "lanczos step");
+    if (r != BSE_OK) return r;
+  }
+  return BSE_OK;
+}
+
+}  // namespace
+
+bse_status run_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double2 *u) {
+  dim3 grid((unsigned)((c->dim + 255) / 256), 3);
+  k_dipole<<<grid, 256, 0, c->stream>>>((const double2 *)vel, e_ks, c->nk, c->nv, c->nc, u, c->d_err);
+  bse_count_launch();
+  return bse_check_launch(c, "dipole_vector");
+}
+
+bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
+                        const double *omega, int n_w, double eta, double pref, double *eps2, double *ab) {
+  LanczosScratch s;
+  bse_status r = lanczos_alloc(c, s, n_pol, n_steps);
+  if (r == BSE_OK) r = lanczos_run(c, s, H, u, n_pol, n_steps);
+  if (r == BSE_OK) {
+    k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega,
+                                                         n_w, eta, pref, eps2);
+    bse_count_launch();
+    if (ab) {
+      k_pack_ab<<<dim3((n_steps + 127) / 128, n_pol), 128, 0, c->stream>>>(s.a, s.b, s.beta0, n_steps + 1,
+                                                                          n_pol, n_steps, ab);
+      bse_count_launch();
+    }
+    r = bse_check_launch(c, "continued fraction");
+  }
+  lanczos_release(c, s);
+  return r;
+}
+
+bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed, double *omega_out,
+                      double *resid_out) {
+  LanczosScratch s;
+  double2 *u = nullptr;
+  double *work = nullptr;
+  bse_status r = lanczos_alloc(c, s, 1, n_steps);
+  if (r == BSE_OK && (cudaMallocAsync((void **)&u, sizeof(double2) * c->dim, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&work, sizeof(double) * 3 * n_eig * n_steps, c->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    r = bse_fail(c, BSE_ENOMEM, "lowest: scratch allocation failed");
+  }
+  if (r == BSE_OK) {
+    k_random_start<<<(unsigned)((c->dim + 255) / 256), 256, 0, c->stream>>>(u, c->dim, seed);
+    bse_count_launch();
+    r = lanczos_run(c, s, H, u, 1, n_steps);
+  }
+  if (r == BSE_OK) {
+    k_ritz<<<(n_eig + 31) / 32, 32, 0, c->stream>>>(s.a, s.b, s.meff, n_eig, omega_out, resid_out, work);
+    bse_count_launch();
+    r = bse_check_launch(c, "ritz");
+  }
+  if (u) cudaFreeAsync(u, c->stream);
+  if (work) cudaFreeAsync(work, c->stream);
+  lanczos_release(c, s);
+  return r;
+}

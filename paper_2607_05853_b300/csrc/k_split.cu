@@ -1,0 +1,450 @@
+// Split-precision assembly of H (BSE_BF16X3 / X2 / X1): the bulk complex contractions
+// run on tcgen05 tensor cores with bf16 operand pieces and FP32 accumulation; phases,
+// the per-k stage and the E_c - E_v diagonal stay FP64; H is stored as complex64.
+//
+// Per q-slab (q = k1 - k2, §III.A Eq. W_LRI):
+//   k_proj32      M_vv(k1,q) and M_cc(k1,q) in FP32 from Y (F(k',k) + conj F(k,k')^T),
+//                 M_vv written as bf16 pieces (the GEMM A operand), M_cc as FP32;
+//   k_tc_zgemm    T = M_vv W(q) on tensor cores (B operand: bf16 pieces of W(q)^T);
+//   k_g2_32       H block += -(1/N_k) T M_cc^T (+ diagonal, FP64), FP32 per pair.
+// Before the slabs, the exchange term alpha/N_k (X V0) conj(X)^T is one tensor-core GEMM
+// that writes every element of H.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "bse_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace {
+
+constexpr int TC_BN = 160;
+
+struct SplitWS {
+  int np = 3, pp = 6;
+  int kmem = 0, kchunks = 0;
+  int nq = 1, rows = 0;
+  __nv_bfloat16 *Wp = nullptr;   // [nk][PP][naux][kmem]   B[nu][mu] = W(q)[mu][nu]
+  __nv_bfloat16 *Ap = nullptr;   // [nq][PP][rows][kmem]   M_vv pieces
+  float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux]
+  float2 *T32 = nullptr;         // [nq][rows][naux]
+  float2 *Y32 = nullptr;         // [nk][nao_max][nb][naux]
+  __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V0
+  __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
+  CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
+};
+
+SplitWS *ws(bse_ctx *c) { return (SplitWS *)c->tc; }
+
+// x ~ p0 + p1 + p2, each a bf16 (round to nearest), residuals formed exactly in the
+// source precision.
+template <class R>
+__device__ __forceinline__ void split_pieces(R x, int np, __nv_bfloat16 *p) {
+  __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+  p[0] = h;
+  if (np > 1) {
+    R r = x - (R)__bfloat162float(h);
+    __nv_bfloat16 m = __float2bfloat16_rn((float)r);
+    p[1] = m;
+    if (np > 2) {
+      R r2 = r - (R)__bfloat162float(m);
+      p[2] = __float2bfloat16_rn((float)r2);
+    }
+  }
+}
+
+// Wp[q][pp][nu][mu] from W(q)[mu][nu] (FP64).
+__global__ void k_split_W(const double2 *__restrict__ Wq, int nk, int naux, int kmem, int np,
+                          __nv_bfloat16 *__restrict__ Wp) {
+  const long long nn = (long long)naux * naux;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (e >= nn) return;
+  const int nu = (int)(e / naux), mu = (int)(e % naux);
+  const double2 w = Wq[(long long)q * nn + (long long)mu * naux + nu];
+  __nv_bfloat16 pr[3], pi[3];
+  split_pieces<double>(w.x, np, pr);
+  split_pieces<double>(w.y, np, pi);
+  const long long plane = (long long)naux * kmem;
+  __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
+  for (int p = 0; p < np; p++) {
+    base[(2 * p) * plane] = pr[p];
+    base[(2 * p + 1) * plane] = pi[p];
+  }
+}
+
+// dst[pp][r][k] pieces of (conj ? conj(src) : src), src [rows][naux] FP64 complex.
+__global__ void k_split_rows(const double2 *__restrict__ src, long long rows, int naux, int kmem, int np,
+                             int conj, __nv_bfloat16 *__restrict__ dst) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * naux) return;
+  const long long r = e / naux;
+  const int k = (int)(e % naux);
+  double2 v = src[e];
+  if (conj) v.y = -v.y;
+  __nv_bfloat16 pr[3], pi[3];
+  split_pieces<double>(v.x, np, pr);
+  split_pieces<double>(v.y, np, pi);
+  const long long plane = rows * kmem;
+  for (int p = 0; p < np; p++) {
+    dst[(2 * p) * plane + r * kmem + k] = pr[p];
+    dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
+  }
+}
+
+__global__ void k_to_f32(const double2 *__restrict__ src, long long n, float2 *__restrict__ dst) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = make_float2((float)src[i].x, (float)src[i].y);
+}
+
+__device__ __forceinline__ float2 fcmulc(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+constexpr int MAXB = 8;
+
+// FP32 pair projection of one q-slab.  grid: x = nmu_chunks*(nv+nc), y = q - q0, z = k1.
+__global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot, int nb, int nv,
+                         int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
+                         const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1, int n2, int n3,
+                         int q0, int np, int rows, int kmem, __nv_bfloat16 *__restrict__ Ap,
+                         float2 *__restrict__ Mc) {
+  extern __shared__ float2 scf[];
+  const int nk = n1 * n2 * n3;
+  const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
+  const int row = blockIdx.x / nchunk;
+  const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
+  const int qq = blockIdx.y, q = q0 + qq, k1 = blockIdx.z;
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  float2 *c1 = scf, *c2 = scf + nao_tot * nb;
+  for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
+    const double2 a = ck[(long long)k1 * nao_tot * nb + e], b = ck[(long long)k2 * nao_tot * nb + e];
+    c1[e] = make_float2((float)a.x, (float)a.y);
+    c2[e] = make_float2((float)b.x, (float)b.y);
+  }
+  __syncthreads();
+  if (mu >= naux) return;
+  const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+  const float2 *Y1 = Y + (long long)k1 * nao_max * nb * naux + mu;
+  const float2 *Y2 = Y + (long long)k2 * nao_max * nb * naux + mu;
+  float2 acc1[MAXB], acc2[MAXB];
+#pragma unroll
+  for (int j = 0; j < MAXB; j++) acc1[j] = acc2[j] = make_float2(0.f, 0.f);
+  if (row < nv) {
+    const int i = row;
+    for (int s = 0; s < na; s++) {
+      const float2 y1 = Y1[((long long)s * nb + i) * naux];
+      const float2 ci = c1[(ao0 + s) * nb + i];
+#pragma unroll
+      for (int j = 0; j < MAXB; j++)
+        if (j < nv) {
+          const float2 t1 = fcmulc(c2[(ao0 + s) * nb + j], y1);
+          const float2 t2 = fcmulc(ci, Y2[((long long)s * nb + j) * naux]);
+          acc1[j].x += t1.x; acc1[j].y += t1.y;
+          acc2[j].x += t2.x; acc2[j].y += t2.y;
+        }
+    }
+    const long long plane = (long long)rows * kmem;
+    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)(k1 * nv + i) * nv * kmem + mu;
+#pragma unroll
+    for (int j = 0; j < MAXB; j++)
+      if (j < nv) {
+        const float vr = acc1[j].x + acc2[j].x, vi = acc1[j].y - acc2[j].y;
+        __nv_bfloat16 pr[3], pi[3];
+        split_pieces<float>(vr, np, pr);
+        split_pieces<float>(vi, np, pi);
+        for (int p = 0; p < np; p++) {
+          out[(2 * p) * plane + (long long)j * kmem] = pr[p];
+          out[(2 * p + 1) * plane + (long long)j * kmem] = pi[p];
+        }
+      }
+  } else {
+    const int a = row - nv;
+    for (int s = 0; s < na; s++) {
+      const float2 y1 = Y1[((long long)s * nb + nv + a) * naux];
+      const float2 ca = c1[(ao0 + s) * nb + nv + a];
+#pragma unroll
+      for (int b = 0; b < MAXB; b++)
+        if (b < nc) {
+          const float2 t1 = fcmulc(ca, Y2[((long long)s * nb + nv + b) * naux]);
+          const float2 t2 = fcmulc(c2[(ao0 + s) * nb + nv + b], y1);
+          acc1[b].x += t1.x; acc1[b].y += t1.y;
+          acc2[b].x += t2.x; acc2[b].y += t2.y;
+        }
+    }
+    float2 *out = Mc + ((((long long)qq * nk + k1) * nc + a) * nc) * naux + mu;
+#pragma unroll
+    for (int b = 0; b < MAXB; b++)
+      if (b < nc) out[(long long)b * naux] = make_float2(acc1[b].x + acc2[b].x, acc1[b].y - acc2[b].y);
+  }
+}
+
+constexpr int G2CH = 32;
+
+// H block (k1, k2 = k1 - q) += -(1/N_k) sum_nu T[(k1,i,j)][nu] M_cc[(k1,a,b)][nu] (+ diagonal).
+__global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                               const double *__restrict__ eqp, int nv, int nc, int naux, int n1,
+                                               int n2, int n3, int q0, int rows, long long dim,
+                                               float2 *__restrict__ H) {
+  extern __shared__ float2 sg[];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = q0 + qq;
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const int nvc = nv * nc, nvv = nv * nv, ncc = nc * nc, nb = nv + nc;
+  float2 *sT = sg, *sM = sT + nvv * G2CH;
+  const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * nvv) * naux;
+  const float2 *Mk = Mc + ((long long)qq * nk + k1) * ncc * naux;
+  const int nout = nvc * nvc;
+  constexpr int MAXO = 16;
+  float2 ad[MAXO];
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) ad[t] = make_float2(0.f, 0.f);
+  for (int n0 = 0; n0 < naux; n0 += G2CH) {
+    const int nn = min(G2CH, naux - n0);
+    for (int e = threadIdx.x; e < (nvv + ncc) * G2CH; e += blockDim.x) {
+      const int r = e / G2CH, u = e % G2CH;
+      float2 v = make_float2(0.f, 0.f);
+      if (u < nn) v = r < nvv ? Tk[(long long)r * naux + n0 + u] : Mk[(long long)(r - nvv) * naux + n0 + u];
+      sg[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < MAXO; t++) {
+      const int o = threadIdx.x + t * blockDim.x;
+      if (o < nout) {
+        const int ia = o / nvc, jb = o % nvc;
+        const int i = ia / nc, a = ia % nc, j = jb / nc, b = jb % nc;
+        const float2 *pt = sT + (i * nv + j) * G2CH, *pm = sM + (a * nc + b) * G2CH;
+        float xr = ad[t].x, xi = ad[t].y;
+        for (int u = 0; u < nn; u++) {
+          xr = fmaf(pt[u].x, pm[u].x, fmaf(-pt[u].y, pm[u].y, xr));
+          xi = fmaf(pt[u].x, pm[u].y, fmaf(pt[u].y, pm[u].x, xi));
+        }
+        ad[t] = make_float2(xr, xi);
+      }
+    }
+    __syncthreads();
+  }
+  const double inv = 1.0 / nk;
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) {
+    const int o = threadIdx.x + t * blockDim.x;
+    if (o < nout) {
+      const int ia = o / nvc, jb = o % nvc;
+      const int i = ia / nc, a = ia % nc;
+      float2 *hp = H + ((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb;
+      const float2 hx = *hp;
+      double hr = (double)hx.x - inv * (double)ad[t].x, hi = (double)hx.y - inv * (double)ad[t].y;
+      if (q == 0 && ia == jb) hr += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
+      *hp = make_float2((float)hr, (float)hi);
+    }
+  }
+}
+
+// ---- tensor maps ------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 3-D bf16 tensor {K = k_extent, rows, planes} with row pitch kmem elements.
+bool make_map(CUtensorMap *m, void *base, int k_extent, long long rows, long long planes, int kmem, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)k_extent, (cuuint64_t)rows, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)kmem * 2, (cuuint64_t)rows * kmem * 2};
+  cuuint32_t box[3] = {(cuuint32_t)tcg::BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int NP>
+bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
+                     int prof_id) {
+  using Cf = tcg::Cfg<NP, TC_BN>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM);
+    attr = true;
+  }
+  bse_prof_begin(c, prof_id);
+  tcg::k_tc_zgemm<NP, TC_BN><<<grid, 192, Cf::SMEM, c->stream>>>(A, B, args);
+  bse_prof_end(c, prof_id);
+  bse_count_launch();
+  return bse_check_launch(c, "tc_zgemm");
+}
+
+bse_status launch_tc_np(bse_ctx *c, int np, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args,
+                        dim3 grid, int prof_id) {
+  if (np == 3) return launch_tc<3>(c, A, B, args, grid, prof_id);
+  if (np == 2) return launch_tc<2>(c, A, B, args, grid, prof_id);
+  return launch_tc<1>(c, A, B, args, grid, prof_id);
+}
+
+}  // namespace
+
+bse_status split_setup(bse_ctx *c) {
+  SplitWS *w = new SplitWS();
+  c->tc = w;
+  w->np = c->precision == BSE_BF16X3 ? 3 : c->precision == BSE_BF16X2 ? 2 : 1;
+  w->pp = 2 * w->np;
+  const int na = c->naux_tot;
+  w->kmem = (na + 7) / 8 * 8;
+  w->kchunks = (na + tcg::BK - 1) / tcg::BK;
+  w->rows = c->nk * c->nv * c->nv;
+  const size_t per_q = (size_t)w->pp * w->rows * w->kmem * 2 + (size_t)c->nk * c->nc * c->nc * na * 8 +
+                       (size_t)w->rows * na * 8;
+  const size_t budget = (size_t)1536 << 20;
+  w->nq = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
+  w->nq = std::min(w->nq, 65535);
+  if (c->mesh[2] > 1 && w->nq >= c->mesh[2]) w->nq = w->nq / c->mesh[2] * c->mesh[2];  // whole q-lines
+  auto alloc = [&](void **p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  const size_t nn = (size_t)na * na;
+  const size_t dimz = (size_t)c->dim;
+  if (!alloc((void **)&c->Wq, (size_t)c->nk * nn * sizeof(double2)) ||
+      !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * 2) ||
+      !alloc((void **)&w->Ap, (size_t)w->nq * w->pp * w->rows * w->kmem * 2) ||
+      !alloc((void **)&w->Mc32, (size_t)w->nq * c->nk * c->nc * c->nc * na * 8) ||
+      !alloc((void **)&w->T32, (size_t)w->nq * w->rows * na * 8) ||
+      !alloc((void **)&w->Y32, (size_t)c->nk * c->nao_max * c->nb * na * 8) ||
+      !alloc((void **)&w->Pp, (size_t)w->pp * dimz * w->kmem * 2) ||
+      !alloc((void **)&w->Xp, (size_t)w->pp * dimz * w->kmem * 2))
+    return bse_fail(c, BSE_ENOMEM, "split workspace allocation failed");
+  cudaMemset(w->Wp, 0, (size_t)c->nk * w->pp * na * w->kmem * 2);
+  cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * 2);
+  cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * 2);
+  cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * 2);
+  bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
+            make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, TC_BN) &&
+            make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&
+            make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN);
+  if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");
+  if (cudaGetLastError() != cudaSuccess) return bse_fail(c, BSE_ECUDA, "split workspace initialisation failed");
+  return BSE_OK;
+}
+
+void split_free(bse_ctx *c) {
+  SplitWS *w = ws(c);
+  if (!w) return;
+  void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete w;
+  c->tc = nullptr;
+}
+
+bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out) {
+  SplitWS *w = ws(c);
+  bse_status s = launch_interp_W_fp64(c, W_R, c->Wq);
+  if (s != BSE_OK) return s;
+  const long long nn = (long long)c->naux_tot * c->naux_tot;
+  dim3 grid((unsigned)((nn + 255) / 256), c->nk);
+  k_split_W<<<grid, 256, 0, c->stream>>>(c->Wq, c->nk, c->naux_tot, w->kmem, w->np, w->Wp);
+  bse_count_launch();
+  s = bse_check_launch(c, "split_W");
+  if (s != BSE_OK) return s;
+  if (Wq_out && cudaMemcpyAsync(Wq_out, c->Wq, (size_t)c->nk * nn * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                c->stream) != cudaSuccess)
+    return bse_fail(c, BSE_ECUDA, "interp_W: copy to Wq_out failed");
+  return BSE_OK;
+}
+
+// Called at the end of bse_project_pairs (after Y, X and P exist in FP64).
+bse_status split_project(bse_ctx *c) {
+  SplitWS *w = ws(c);
+  const long long ny = (long long)c->nk * c->nao_max * c->nb * c->naux_tot;
+  k_to_f32<<<(unsigned)((ny + 255) / 256), 256, 0, c->stream>>>(c->Y, ny, w->Y32);
+  const long long nx = c->dim * (long long)c->naux_tot;
+  k_split_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->stream>>>(c->P, c->dim, c->naux_tot, w->kmem, w->np, 0,
+                                                                    w->Pp);
+  k_split_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->stream>>>(c->X, c->dim, c->naux_tot, w->kmem, w->np, 1,
+                                                                    w->Xp);
+  bse_count_launch(3);
+  return bse_check_launch(c, "split_project");
+}
+
+bse_status split_assemble(bse_ctx *c, void *Hv) {
+  SplitWS *w = ws(c);
+  float2 *H = (float2 *)Hv;
+  const int na = c->naux_tot;
+  // exchange: H = alpha/N_k (X V0) conj(X)^T  -- writes every element
+  {
+    tcg::Args a{};
+    a.rows = (int)c->dim;
+    a.n_valid = (int)c->dim;
+    a.k_chunks = w->kchunks;
+    a.scale = (float)(c->alpha / c->nk);
+    a.out = H;
+    a.ldo = c->dim;
+    a.out_bstride = 0;
+    a.b_batch_planes = 0;
+    a.b_base = 0;
+    a.err = c->d_err;
+    dim3 grid((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
+    bse_status s = launch_tc_np(c, w->np, w->tmA_x, w->tmB_x, a, grid, BSE_KP_EXCH);
+    if (s != BSE_OK) return s;
+  }
+  const int nchunk = (na + 127) / 128;
+  for (int q0 = 0; q0 < c->nk; q0 += w->nq) {
+    const int nq = std::min(w->nq, c->nk - q0);
+    {
+      dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
+      size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
+      bse_prof_begin(c, BSE_KP_PROJECT);
+      k_proj32<<<grid, 128, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+                                             c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
+                                             c->mesh[2], q0, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
+      bse_prof_end(c, BSE_KP_PROJECT);
+      bse_count_launch();
+      bse_status s = bse_check_launch(c, "proj32");
+      if (s != BSE_OK) return s;
+    }
+    {
+      tcg::Args a{};
+      a.rows = w->rows;
+      a.n_valid = na;
+      a.k_chunks = w->kchunks;
+      a.scale = 1.0f;
+      a.out = w->T32;
+      a.ldo = na;
+      a.out_bstride = (long long)w->rows * na;
+      a.b_batch_planes = 1;
+      a.b_base = q0;
+      a.err = c->d_err;
+      dim3 grid((unsigned)((na + TC_BN - 1) / TC_BN), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
+      bse_status s = launch_tc_np(c, w->np, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
+      if (s != BSE_OK) return s;
+    }
+    {
+      dim3 grid(c->nk, nq);
+      size_t sm = sizeof(float2) * (c->nv * c->nv + c->nc * c->nc) * G2CH;
+      bse_prof_begin(c, BSE_KP_G2);
+      k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                            c->mesh[2], q0, w->rows, c->dim, H);
+      bse_prof_end(c, BSE_KP_G2);
+      bse_count_launch();
+      bse_status s = bse_check_launch(c, "g2_32");
+      if (s != BSE_OK) return s;
+    }
+  }
+  return BSE_OK;
+}

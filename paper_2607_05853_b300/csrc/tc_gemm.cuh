@@ -1,0 +1,193 @@
+// Split-precision complex GEMM on tcgen05 tensor cores (sm_103a).
+//
+//   out[b][m][n] = scale * sum_{pa+pb <= NP-1} sum_k A_pa[b][m][k] * B_pb[b][n][k]   (complex)
+//
+// A and B are complex matrices stored K-major as planar bf16 "pieces": a real value x is
+// x ~ p0 + p1 + p2 with p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1), and only
+// piece products whose orders sum to at most NP-1 are kept (NP = 3: 6 products, NP = 2: 3,
+// NP = 1: 1), accumulated in FP32 in tensor memory.  A complex product uses four real
+// MMAs: Re += Ar Br^T - Ai Bi^T (the minus through the A-negate bit of the instruction
+// descriptor), Im += Ar Bi^T + Ai Br^T.
+//
+// Operands arrive by TMA as 3-D tensors {K, rows, plane-piece(-batch)} with 64-byte
+// swizzled rows (32 bf16 of K per stage); rows and K beyond the tensor are zero-filled.
+// One CTA computes a 128 x BN output tile: warp 0 issues TMA, warp 1 allocates tensor
+// memory and issues the MMAs from one thread, warps 2-5 drain the accumulators.  Every
+// barrier wait is bounded; a timeout sets the device error word and the CTA winds down.
+#pragma once
+
+#include "tc_ptx.cuh"
+
+namespace tcg {
+
+constexpr int BM = 128;
+constexpr int BK = 32;                // bf16 elements of K per stage (64-byte rows)
+constexpr int ROWB = BK * 2;          // bytes per smem row
+constexpr int A_TILE = BM * ROWB;     // 8 KB
+constexpr int SMEM_BUDGET = 221184;   // stage bytes per CTA
+constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (~2 s) before a wait gives up
+
+template <int NP, int BN>
+struct Cfg {
+  static constexpr int PP = 2 * NP;                   // planes x pieces
+  static constexpr int B_TILE = BN * ROWB;
+  static constexpr int STAGE = PP * (A_TILE + B_TILE);
+  static constexpr int S = SMEM_BUDGET / STAGE < 8 ? SMEM_BUDGET / STAGE : 8;
+  static constexpr int TMEM_COLS = 2 * BN <= 32 ? 32 : 2 * BN <= 64 ? 64 : 2 * BN <= 128 ? 128 : 2 * BN <= 256 ? 256 : 512;
+  static constexpr int SMEM = S * STAGE + 1024 + 256;  // + alignment slack + barriers
+  static_assert(S >= 2, "at least two pipeline stages");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "M=128 MMA needs N % 16 == 0, N <= 256");
+};
+
+struct Args {
+  int rows;              // valid rows of A per batch (tensor extent)
+  int n_valid;           // valid columns of the output (rows of B per batch)
+  int k_chunks;          // ceil(K / BK)
+  float scale;
+  float2 *out;           // interleaved complex
+  long long ldo;         // row pitch of out (elements)
+  long long out_bstride; // batch stride of out (elements)
+  int b_batch_planes;    // 0: B has no batch dimension (z = pp), else z = (b_base + b)*PP + pp
+  int b_base;
+  int *err;
+};
+
+template <int NP, int BN>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args args) {
+  using C = Cfg<NP, BN>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t *full = (uint64_t *)(smem + C::S * C::STAGE);
+  uint64_t *empty = full + C::S;
+  uint64_t *done = empty + C::S;
+  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::S; s++) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(done, 1);
+    *abort_flag = 0;
+    tc::fence_barrier_init();
+  }
+  if (warp == 0 && lane == 0) {
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tm_re = tmem, tm_im = tmem + BN;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kc = 0; kc < args.k_chunks; kc++) {
+      const int s = kc % C::S;
+      if (kc >= C::S) {
+        if (!tc::mbar_wait_bounded(&empty[s], ((kc / C::S) & 1) ^ 1, WAIT_LIMIT)) {
+          atomicOr(args.err, 2);
+          *abort_flag = 1;
+          break;
+        }
+      }
+      if (*abort_flag) break;
+      uint8_t *st = smem + s * C::STAGE;
+      tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
+      for (int pp = 0; pp < C::PP; pp++) {
+        tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
+        tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, n0,
+                        args.b_batch_planes ? (args.b_base + b) * C::PP + pp : pp);
+      }
+      issued = kc + 1;
+    }
+    // make sure every copy this CTA started has landed before the CTA can exit
+    for (int kc = issued - C::S < 0 ? 0 : issued - C::S; kc < issued; kc++)
+      if (!tc::mbar_wait_bounded(&full[kc % C::S], (kc / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t IPOS = tc::idesc_bf16(BM, BN, false);
+    constexpr uint32_t INEG = tc::idesc_bf16(BM, BN, true);
+    uint32_t acc_r = 0, acc_i = 0;
+    for (int kc = 0; kc < args.k_chunks; kc++) {
+      const int s = kc % C::S;
+      if (!tc::mbar_wait_bounded(&full[s], (kc / C::S) & 1, WAIT_LIMIT)) {
+        atomicOr(args.err, 2);
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      tc::tc_fence_after();
+      const uint32_t sa = tc::smem_u32(smem + s * C::STAGE);
+      const uint32_t sb = sa + C::PP * A_TILE;
+#pragma unroll
+      for (int k16 = 0; k16 < BK / 16; k16++) {
+#pragma unroll
+        for (int pa = 0; pa < NP; pa++) {
+#pragma unroll
+          for (int pb = 0; pb < NP; pb++) {
+            if (pa + pb > NP - 1) continue;
+            const uint64_t ar = tc::smem_desc(sa + (2 * pa) * A_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
+            tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
+            acc_r = 1;
+            tc::mma_bf16(tm_re, ai, bi, INEG, 1);
+            tc::mma_bf16(tm_im, ar, bi, IPOS, acc_i);
+            acc_i = 1;
+            tc::mma_bf16(tm_im, ai, br, IPOS, 1);
+          }
+        }
+      }
+      tc::mma_commit(&empty[s]);
+    }
+    tc::mma_commit(done);
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> registers -> global ----------------
+    const int quarter = warp % 4;
+    const bool ok = tc::mbar_wait_bounded(done, 0, 4 * WAIT_LIMIT);
+    if (!ok) atomicOr(args.err, 2);
+    tc::tc_fence_after();
+    if (ok && !*abort_flag) {
+      const int row = m0 + quarter * 32 + lane;
+      const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+      float2 *orow = args.out + (long long)b * args.out_bstride + (long long)row * args.ldo;
+      const bool row_ok = row < args.rows;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t rr[16], ri[16];
+        tc::tmem_ld16(tm_re + lane_off + c0, rr);
+        tc::tmem_ld16(tm_im + lane_off + c0, ri);
+        tc::tmem_ld_wait();
+        if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 16; j++) {
+            const int col = n0 + c0 + j;
+            if (col < args.n_valid)
+              orow[col] = make_float2(args.scale * __uint_as_float(rr[j]), args.scale * __uint_as_float(ri[j]));
+          }
+        }
+      }
+    }
+    tc::tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, C::TMEM_COLS);
+  }
+}
+
+}  // namespace tcg

@@ -1,0 +1,88 @@
+"""The C ABI library on a machine without a GPU: it loads, exports every symbol that
+include/bse.h declares, and rejects bad parameters before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2607_05853_b300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "bse.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(bse_[a-zA-Z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = declared_symbols()
+    assert len(syms) >= 14
+    for s in syms:
+        assert hasattr(lib, s), s
+    from paper_2607_05853_b300 import _lib
+    assert sorted(_lib.EXPORTS) == syms
+
+
+def _params(**over):
+    from paper_2607_05853_b300 import _lib
+    keep = {}
+    nao = np.array([4, 4], np.int32)
+    naux = np.array([20, 20], np.int32)
+    RC = np.zeros((1, 3), np.int32)
+    RW = np.zeros((1, 3), np.int32)
+    w = np.ones(1)
+    keep.update(nao=nao, naux=naux, RC=RC, RW=RW, w=w)
+    p = _lib.BseParams()
+    p.n_atoms = 2
+    p.nao_per_atom = nao.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.naux_per_atom = naux.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.dense[:] = [4, 4, 4]
+    p.k_offset[:] = [0.0, 0.0, 0.0]
+    p.n_RC, p.R_C = 1, RC.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.n_RW, p.R_W = 1, RW.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.w_RW = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.nv, p.nc, p.alpha, p.precision = 4, 4, 2.0, 0
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p, keep
+
+
+@pytest.mark.parametrize("field,value", [("nv", 0), ("nc", 9), ("nv", 5), ("n_atoms", 0), ("precision", 7),
+                                         ("n_RC", 0), ("n_RW", 0), ("alpha", float("nan"))])
+def test_bad_parameters_rejected_without_device(lib, field, value):
+    from paper_2607_05853_b300 import _lib
+    p, keep = _params(**{field: value})
+    if field == "nv" and value == 5:
+        p.nc = 4  # nv + nc = 9 > 8 NAOs
+    ctx = ctypes.c_void_p(123)
+    st = lib.bse_setup(ctypes.byref(p), None, ctypes.byref(ctx))
+    assert st == _lib.BSE_EINVAL
+    assert ctx.value is None
+
+
+def test_bad_mesh_rejected(lib):
+    from paper_2607_05853_b300 import _lib
+    p, keep = _params()
+    p.dense[:] = [4, 0, 4]
+    ctx = ctypes.c_void_p()
+    assert lib.bse_setup(ctypes.byref(p), None, ctypes.byref(ctx)) == _lib.BSE_EINVAL
+    assert lib.bse_setup(None, None, ctypes.byref(ctx)) == _lib.BSE_EINVAL
+
+
+def test_null_context_calls_are_safe(lib):
+    from paper_2607_05853_b300 import _lib
+    lib.bse_free(None)
+    assert lib.bse_last_error(None) == b"null context"
+    assert lib.bse_dim(None) == -1
+    assert lib.bse_sync(None) == _lib.BSE_EINVAL
+    assert lib.bse_assemble(None, None) == _lib.BSE_EINVAL
+    assert lib.bse_launch_count() >= 0

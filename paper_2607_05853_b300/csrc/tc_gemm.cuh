@@ -138,10 +138,10 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int pb = 0; pb < NP; pb++) {
             if (pa + pb > NP - 1) continue;
-            const uint64_t ar = tc::smem_desc(sa + (2 * pa) * A_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 0, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t ar = tc::smem_desc(sa + (2 * pa) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+            const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
             tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
             acc_r = 1;
             tc::mma_bf16(tm_re, ai, bi, INEG, 1);

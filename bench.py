@@ -46,12 +46,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
+    ap.add_argument("--mesh", type=int, default=0, help="override the dense mesh N x N x N (profiling captures)")
     return ap.parse_args()
 
 
-def workload(small):
+def workload(small, mesh=0):
+    import dataclasses
     from synth import config_spec
     spec = config_spec(0 if small else 2)
+    if mesh:
+        spec = dataclasses.replace(spec, dense=(mesh, mesh, mesh), name=f"{spec.name}-mesh{mesh}")
     return spec
 
 
@@ -149,7 +153,7 @@ def run_reference(args):
     if rank != 0:
         return
     from synth import make_inputs
-    spec = workload(args.small)
+    spec = workload(args.small, args.mesh)
     inp = make_inputs(spec)
     per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
@@ -185,7 +189,7 @@ def main():
     from paper_2607_05853_b300.api import BSE, launch_count
     from synth import make_inputs
 
-    spec = workload(args.small)
+    spec = workload(args.small, args.mesh)
     inp = make_inputs(spec)
     dev = torch.device("cuda", local)
 

@@ -94,7 +94,7 @@ static void release(bse_ctx *c) {
   prof_collect(c);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   c->pool.clear();
-  void *ptrs[] = {c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
+  void *ptrs[] = {c->d_qplus, c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
                   c->d_aux_start, c->d_naux, c->d_err, c->Wq, c->V0c, c->Y, c->ck,
                   c->eqp, c->X, c->P, c->Mv, c->Mc, c->T};
   for (void *p : ptrs)
@@ -173,6 +173,20 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
   c->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&c->device);
 
+  // transfers q in a half set, ordered by lines along the last mesh axis
+  {
+    const int n1 = c->mesh[0], n2 = c->mesh[1], n3 = c->mesh[2];
+    for (int q1 = 0; q1 < n1; q1++)
+      for (int q2 = 0; q2 < n2; q2++) {
+        const int m1 = (n1 - q1) % n1, m2 = (n2 - q2) % n2;
+        if (q1 < m1 || (q1 == m1 && q2 < m2)) {
+          for (int q3 = 0; q3 < n3; q3++) c->qplus.push_back((q1 * n2 + q2) * n3 + q3);
+        } else if (q1 == m1 && q2 == m2) {
+          for (int q3 = 0; q3 < n3; q3++)
+            if (q3 <= (n3 - q3) % n3 || q3 == 0) c->qplus.push_back((q1 * n2 + q2) * n3 + q3);
+        }
+      }
+  }
   bse_status s = BSE_OK;
 #define TRY(x)              \
   do {                      \
@@ -188,6 +202,7 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
     TRY(upload(c, &c->d_nao, c->nao));
     TRY(upload(c, &c->d_aux_start, c->aux_start));
     TRY(upload(c, &c->d_naux, c->naux));
+    TRY(upload(c, &c->d_qplus, c->qplus));
     TRY(dalloc(c, &c->d_err, 1));
     const size_t nn = (size_t)naux_tot * naux_tot;
     TRY(dalloc(c, &c->V0c, nn));
@@ -289,12 +304,13 @@ bse_status bse_assemble(bse_ctx *c, void *H) {
   if (c->precision != BSE_FP64) return split_assemble(c, H);
   const int na = c->naux_tot;
   const long long rows = (long long)c->nk * c->nv * c->nv;
-  for (int q0 = 0; q0 < c->nk; q0 += c->slab) {
-    const int nq = std::min(c->slab, c->nk - q0);
+  const int nqp = (int)c->qplus.size();
+  for (int q0 = 0; q0 < nqp; q0 += c->slab) {
+    const int nq = std::min(c->slab, nqp - q0);
     bse_status s = launch_project_slab_fp64(c, q0, nq);
     if (s != BSE_OK) return s;
-    s = launch_zgemm_fp64(c, (int)rows, na, na, c->Mv, na, rows * na, c->Wq + (long long)q0 * na * na, na,
-                          (long long)na * na, c->T, na, rows * na, nq, BSE_KP_G1);
+    s = launch_zgemm_fp64(c, (int)rows, na, na, c->Mv, na, rows * na, c->Wq, na, (long long)na * na, c->T, na,
+                          rows * na, nq, BSE_KP_G1, c->d_qplus + q0);
     if (s != BSE_OK) return s;
     s = launch_g2_write_fp64(c, q0, nq, (double2 *)H);
     if (s != BSE_OK) return s;

@@ -55,6 +55,10 @@ struct bse_ctx {
   double2 *X = nullptr;    // [nk][nv][nc][naux] C~^mu_{a k, i k}
   double2 *P = nullptr;    // [dim][naux]        X V0
   int slab = 1;            // q values per assembly slab
+  // Half set of transfers: q and -q give conjugate-transposed blocks, so only one of each
+  // pair is computed (self-conjugate q, every component 0 or N/2, are computed whole).
+  std::vector<int> qplus;
+  int *d_qplus = nullptr;
   double2 *Mv = nullptr, *Mc = nullptr, *T = nullptr;  // [slab][nk][nv*nv | nc*nc][naux]
 
   // split-precision workspace (tensor-core path)
@@ -84,7 +88,8 @@ bse_status launch_half_transform_fp64(bse_ctx *c, const double *C_R);
 bse_status launch_exchange_factors_fp64(bse_ctx *c);
 bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, int lda,
                              long long sA, const double2 *B, int ldb, long long sB, double2 *C,
-                             int ldc, long long sC, int batch, int prof_id = -1);
+                             int ldc, long long sC, int batch, int prof_id = -1,
+                             const int *bidx = nullptr);
 bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq);
 bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H);
 
@@ -104,6 +109,10 @@ bse_status split_project(bse_ctx *c);
 void split_free(bse_ctx *c);
 
 // mesh helpers
+__host__ __device__ inline bool q_self_conjugate(int q, int n1, int n2, int n3) {
+  int a1 = q / (n2 * n3), a2 = (q / n3) % n2, a3 = q % n3;
+  return (n1 - a1) % n1 == a1 && (n2 - a2) % n2 == a2 && (n3 - a3) % n3 == a3;
+}
 __host__ __device__ inline int kdiff(int k1, int q, int n1, int n2, int n3) {
   // index of k2 = k1 - q on the mesh (integer parts; offsets cancel in differences)
   int a1 = k1 / (n2 * n3), a2 = (k1 / n3) % n2, a3 = k1 % n3;

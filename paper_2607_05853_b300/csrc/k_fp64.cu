@@ -180,13 +180,14 @@ __global__ void k_project_slab(const double2 *__restrict__ Y, const double2 *__r
                                int nao_tot, int nb, int nv, int nc, int naux, int nao_max,
                                const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
                                const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
-                               double2 *__restrict__ Mv, double2 *__restrict__ Mc) {
+                               const int *__restrict__ qlist, double2 *__restrict__ Mv,
+                               double2 *__restrict__ Mc) {
   extern __shared__ double2 sc[];  // c1 [nao][nb], c2 [nao][nb]
   const int nk = n1 * n2 * n3;
   const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
   const int row = blockIdx.x / nchunk;
   const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
-  const int k1 = blockIdx.y, qq = blockIdx.z, q = q0 + qq;
+  const int k1 = blockIdx.y, qq = blockIdx.z, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
   double2 *c1 = sc, *c2 = sc + nao_tot * nb;
   for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
@@ -240,12 +241,12 @@ __global__ void k_project_slab(const double2 *__restrict__ Y, const double2 *__r
 __global__ void __launch_bounds__(256) k_zgemm_nn(int M, int N, int K, const double2 *__restrict__ A,
                                                   int lda, long long sA, const double2 *__restrict__ B,
                                                   int ldb, long long sB, double2 *__restrict__ C,
-                                                  int ldc, long long sC) {
+                                                  int ldc, long long sC, const int *__restrict__ bidx) {
   __shared__ double2 As[16][64];
   __shared__ double2 Bs[16][64];
   const int bz = blockIdx.z;
   A += bz * sA;
-  B += bz * sB;
+  B += (bidx ? bidx[bz] : bz) * sB;
   C += bz * sC;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
@@ -294,12 +295,13 @@ constexpr int G2CH = 16;  // nu chunk staged in shared memory
 __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T, const double2 *__restrict__ Mc,
                                                   const double2 *__restrict__ P, const double2 *__restrict__ X,
                                                   const double *__restrict__ eqp, int nv, int nc, int naux,
-                                                  int n1, int n2, int n3, int q0, double alpha,
-                                                  long long dim, double2 *__restrict__ H) {
+                                                  int n1, int n2, int n3, int q0, const int *__restrict__ qlist,
+                                                  double alpha, long long dim, double2 *__restrict__ H) {
   extern __shared__ double2 sm[];
   const int nk = n1 * n2 * n3;
-  const int k1 = blockIdx.x, qq = blockIdx.y, q = q0 + qq;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
   const int nvc = nv * nc, nvv = nv * nv, ncc = nc * nc, nb = nv + nc;
   double2 *sT = sm, *sM = sT + nvv * G2CH, *sP = sM + ncc * G2CH, *sX = sP + nvc * G2CH;
   const double2 *Tk = T + ((long long)qq * nk + k1) * nvv * naux;
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T,
       double2 h = make_double2((alpha * ax[t].x - ad[t].x) * inv, (alpha * ax[t].y - ad[t].y) * inv);
       if (q == 0 && ia == jb) h.x += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
       H[((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb] = h;
+      if (mirror) H[((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia] = conjd(h);
     }
   }
 }
@@ -400,11 +403,11 @@ bse_status launch_exchange_factors_fp64(bse_ctx *c) {
 
 bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, int lda, long long sA,
                              const double2 *B, int ldb, long long sB, double2 *C, int ldc,
-                             long long sC, int batch, int prof_id) {
+                             long long sC, int batch, int prof_id, const int *bidx) {
   dim3 grid((N + 63) / 64, (M + 63) / 64, batch);
   if (grid.y > 65535 || batch > 65535) return bse_fail(c, BSE_EINVAL, "zgemm grid too large");
   if (prof_id >= 0) bse_prof_begin(c, prof_id);
-  k_zgemm_nn<<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  k_zgemm_nn<<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, bidx);
   if (prof_id >= 0) bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "zgemm");
@@ -419,7 +422,7 @@ bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq) {
   k_project_slab<<<grid, 128, sm, c->stream>>>(c->Y, c->ck, c->nao_tot, c->nb, c->nv, c->nc,
                                                c->naux_tot, c->nao_max, c->d_aux_atom, c->d_ao_start,
                                                c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], q0,
-                                               c->Mv, c->Mc);
+                                               c->d_qplus, c->Mv, c->Mc);
   bse_prof_end(c, BSE_KP_PROJECT);
   bse_count_launch();
   return bse_check_launch(c, "project_slab");
@@ -432,7 +435,7 @@ bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H) {
   bse_prof_begin(c, BSE_KP_G2);
   k_g2_write<<<grid, 256, sm, c->stream>>>(c->T, c->Mc, c->P, c->X, c->eqp, c->nv, c->nc,
                                            c->naux_tot, c->mesh[0], c->mesh[1], c->mesh[2], q0,
-                                           c->alpha, c->dim, H);
+                                           c->d_qplus, c->alpha, c->dim, H);
   bse_prof_end(c, BSE_KP_G2);
   bse_count_launch();
   return bse_check_launch(c, "g2_write");

@@ -75,7 +75,7 @@ __global__ void k_absmax_final(const double *part, int n, double *out) {
 
 // beta0[p] = |u_p|, Q[p][0] = u_p / beta0 (block per p).
 __global__ void k_lanczos_init(const double2 *__restrict__ u, long long dim, double2 *Q, long long qs,
-                               double *beta0) {
+                               double *beta0, float2 *Q32) {
   __shared__ double red[32];
   __shared__ double sb;
   const int p = blockIdx.x;
@@ -89,8 +89,11 @@ __global__ void k_lanczos_init(const double2 *__restrict__ u, long long dim, dou
   }
   __syncthreads();
   const double inv = sb > 0.0 ? 1.0 / sb : 0.0;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x)
-    Q[p * qs + i] = make_double2(up[i].x * inv, up[i].y * inv);
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) {
+    const double2 v = make_double2(up[i].x * inv, up[i].y * inv);
+    Q[p * qs + i] = v;
+    if (Q32) Q32[p * qs + i] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
 constexpr int MV_WARPS = 8, MV_RPW = 4, MV_ROWS = MV_WARPS * MV_RPW, MV_CC = 256;
@@ -212,6 +215,145 @@ __global__ void __launch_bounds__(256) k_matvec_c64(const float2 *__restrict__ H
     }
 }
 
+
+// ---- Hermitian half-read matvec (complex64 H) ---------------------------------------------
+// H = H^dagger, so only tiles (bi <= bj) of HT x HT are read.  An off-diagonal tile
+// gives y[bi] += H_t x[bj] and y[bj] += H_t^dagger x[bi]; a diagonal tile gives
+// y[bi] += H_t x[bi].  Each contribution lands in its own slot part[target][source], and
+// k_hmv_reduce sums the slots in a fixed order (deterministic, no atomics).
+// 128 x 128 tiles, 4 warps of 32 rows; a lane owns columns {2f, 2f+1}, f = lane + 32 t.
+constexpr int HT = 128;
+
+// Sum over the 32 lanes of 32 values per lane with 31 shuffles; lane L returns the total of
+// value index L.
+__device__ __forceinline__ float warp_transpose_sum32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool up = (lane & half) != 0;
+#pragma unroll
+    for (int i = 0; i < half; i++) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, half);
+    }
+  }
+  return v[0];
+}
+
+template <int NP>
+__global__ void __launch_bounds__(128, 4) k_hmatvec_c64(const float2 *__restrict__ H, long long dim, int nb,
+                                                        const float2 *__restrict__ Q32, long long qs, int j,
+                                                        float2 *__restrict__ part, const int *meff) {
+  static_assert(NP * 2 * 4 <= 32, "4 rows x NP polarisations x (re, im) per reduction group");
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  bool live = false;
+  for (int p = 0; p < NP; p++) live |= (j < meff[p]);
+  if (!live) return;
+  __shared__ float2 xr[NP][HT], xc[NP][HT];
+  __shared__ float2 vs[4][HT][NP];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long r0 = (long long)bi * HT, c0 = (long long)bj * HT;
+  for (int t = threadIdx.x; t < NP * HT; t += blockDim.x) {
+    const int p = t / HT, l = t % HT;
+    const float2 z = make_float2(0.f, 0.f);
+    xr[p][l] = r0 + l < dim ? Q32[p * qs + (long long)j * dim + r0 + l] : z;
+    xc[p][l] = c0 + l < dim ? Q32[p * qs + (long long)j * dim + c0 + l] : z;
+  }
+  __syncthreads();
+  const bool diag = bi == bj;
+  float2 v[4][NP];  // column partials for columns 2(lane + 32t) + {0,1}, t < 2
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) v[q][p] = make_float2(0.f, 0.f);
+  for (int g = 0; g < 8; g++) {  // 8 groups of 4 rows = the warp's 32 rows
+    float4 h[4][2];
+#pragma unroll
+    for (int rr = 0; rr < 4; rr++) {
+      const long long row = r0 + warp * 32 + g * 4 + rr;
+#pragma unroll
+      for (int t = 0; t < 2; t++) {
+        const long long col = c0 + 2 * (lane + 32 * t);
+        if (row < dim && col < dim)
+          h[rr][t] = __ldcs(reinterpret_cast<const float4 *>(H + row * dim + col));
+        else
+          h[rr][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    float u[32];
+#pragma unroll
+    for (int i = 0; i < 32; i++) u[i] = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 4; rr++) {
+      const int lr = warp * 32 + g * 4 + rr;
+#pragma unroll
+      for (int t = 0; t < 2; t++) {
+        const int lc = 2 * (lane + 32 * t);
+        const float4 hh = h[rr][t];
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const float2 x0 = xc[p][lc], x1 = xc[p][lc + 1];
+          u[(rr * NP + p) * 2 + 0] += hh.x * x0.x - hh.y * x0.y + hh.z * x1.x - hh.w * x1.y;
+          u[(rr * NP + p) * 2 + 1] += hh.x * x0.y + hh.y * x0.x + hh.z * x1.y + hh.w * x1.x;
+          if (!diag) {
+            const float2 xrow = xr[p][lr];
+            v[2 * t][p].x += hh.x * xrow.x + hh.y * xrow.y;
+            v[2 * t][p].y += hh.x * xrow.y - hh.y * xrow.x;
+            v[2 * t + 1][p].x += hh.z * xrow.x + hh.w * xrow.y;
+            v[2 * t + 1][p].y += hh.z * xrow.y - hh.w * xrow.x;
+          }
+        }
+      }
+    }
+    const float tot = warp_transpose_sum32(u, lane);
+    if (lane < 4 * NP * 2) {
+      const int rr = lane / (2 * NP), p = (lane / 2) % NP, ri = lane % 2;
+      const int lr = warp * 32 + g * 4 + rr;
+      float *dst = reinterpret_cast<float *>(part + (((long long)bi * nb + bj) * HT + lr) * NP + p);
+      dst[ri] = tot;
+    }
+  }
+  if (diag) return;
+#pragma unroll
+  for (int t = 0; t < 2; t++)
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      vs[warp][2 * (lane + 32 * t)][p] = v[2 * t][p];
+      vs[warp][2 * (lane + 32 * t) + 1][p] = v[2 * t + 1][p];
+    }
+  __syncthreads();
+  for (int e = threadIdx.x; e < HT * NP; e += blockDim.x) {
+    const int l = e / NP, p = e % NP;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int w = 0; w < 4; w++) {
+      acc.x += vs[w][l][p].x;
+      acc.y += vs[w][l][p].y;
+    }
+    part[(((long long)bj * nb + bi) * HT + l) * NP + p] = acc;
+  }
+}
+
+// W[p][row] = sum_s part[row_block][s][row_local][p]  (FP64 sum in a fixed order)
+template <int NP>
+__global__ void k_hmv_reduce(const float2 *__restrict__ part, long long dim, int nb, double2 *__restrict__ W,
+                             int j, const int *meff) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim * NP) return;
+  const long long row = e / NP;
+  const int p = (int)(e % NP);
+  if (j >= meff[p]) return;
+  const long long t = row / HT, l = row % HT;
+  double sx = 0.0, sy = 0.0;
+  for (int s = 0; s < nb; s++) {
+    const float2 v = part[((t * nb + s) * HT + l) * NP + p];
+    sx += v.x;
+    sy += v.y;
+  }
+  W[(long long)p * dim + row] = make_double2(sx, sy);
+}
+
 // a[p][j] = Re(Q_j^H W); W -= a_j Q_j + b_{j-1} Q_{j-1}   (block per p)
 __global__ void k_alpha_axpy(double2 *W, long long dim, const double2 *Q, long long qs, int j, double *a,
                              const double *b, int ldab, const int *meff) {
@@ -277,9 +419,64 @@ __global__ void k_reorth_update(double2 *W, long long dim, const double2 *Q, lon
   W[(long long)p * dim + e] = v;
 }
 
+// FP32 projections for a complex64 H: coef[p][i] = Q32_i^H W (FP32 products and per-thread
+// sums, FP64 block reduction); the correction sum_i coef_i Q32_i is formed in FP32 and
+// subtracted from the FP64 vector.  W is already nearly orthogonal to the basis, so the
+// FP32 relative error lands on a small correction.
+__global__ void k_reorth_dots32(const double2 *W, long long dim, const float2 *Q32, long long qs, int j,
+                                double2 *coef, int ldc, const int *meff) {
+  __shared__ double red[32];
+  const int i = blockIdx.x, p = blockIdx.y;
+  if (j >= meff[p] || i > j) return;
+  const double2 *w = W + (long long)p * dim;
+  const float2 *qi = Q32 + p * qs + (long long)i * dim;
+  float sr = 0.f, si = 0.f;
+  for (long long e = threadIdx.x; e < dim; e += blockDim.x) {
+    const float2 q = qi[e];
+    const float vx = (float)w[e].x, vy = (float)w[e].y;
+    sr = fmaf(q.x, vx, fmaf(q.y, vy, sr));
+    si = fmaf(q.x, vy, fmaf(-q.y, vx, si));
+  }
+  double dr = block_sum<256>((double)sr, red);
+  __syncthreads();
+  double di = block_sum<256>((double)si, red);
+  if (threadIdx.x == 0) coef[p * ldc + i] = make_double2(dr, di);
+}
+
+__global__ void k_reorth_update32(double2 *W, long long dim, const float2 *Q32, long long qs, int j,
+                                  const double2 *coef, int ldc, const int *meff) {
+  __shared__ float2 cs[1024];
+  const int p = blockIdx.y;
+  if (j >= meff[p]) return;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const float2 *qp = Q32 + p * qs + e;
+  float cr = 0.f, ci = 0.f;
+  for (int i0 = 0; i0 <= j; i0 += 1024) {
+    const int n = min(1024, j + 1 - i0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const double2 c = coef[p * ldc + i0 + t];
+      cs[t] = make_float2((float)c.x, (float)c.y);
+    }
+    __syncthreads();
+    if (e < dim)
+      for (int i = 0; i < n; i++) {
+        const float2 c = cs[i], q = qp[(long long)(i0 + i) * dim];
+        cr = fmaf(c.x, q.x, fmaf(-c.y, q.y, cr));
+        ci = fmaf(c.x, q.y, fmaf(c.y, q.x, ci));
+      }
+  }
+  if (e < dim) {
+    double2 v = W[(long long)p * dim + e];
+    v.x -= (double)cr;
+    v.y -= (double)ci;
+    W[(long long)p * dim + e] = v;
+  }
+}
+
 // b[p][j] = |W|; Q[p][j+1] = W/b (block per p); early stop when b < 1e-14 max|H|.
 __global__ void k_norm_scale(const double2 *W, long long dim, double2 *Q, long long qs, int j, double *b,
-                             int ldab, int *meff, const double *hmax, int n_steps) {
+                             int ldab, int *meff, const double *hmax, int n_steps, float2 *Q32) {
   __shared__ double red[32];
   __shared__ double sb;
   const int p = blockIdx.x;
@@ -302,7 +499,12 @@ __global__ void k_norm_scale(const double2 *W, long long dim, double2 *Q, long l
   }
   const double inv = 1.0 / bj;
   double2 *qn = Q + p * qs + (long long)(j + 1) * dim;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x) qn[i] = make_double2(w[i].x * inv, w[i].y * inv);
+  float2 *qn32 = Q32 ? Q32 + p * qs + (long long)(j + 1) * dim : nullptr;
+  for (long long i = threadIdx.x; i < dim; i += blockDim.x) {
+    const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
+    qn[i] = v;
+    if (qn32) qn32[i] = make_float2((float)v.x, (float)v.y);
+  }
 }
 
 // eps2[w] = pref * sum_p -(1/pi) Im( beta0^2 / (z - a1 - b1^2/(z - a2 - ...)) )
@@ -429,6 +631,9 @@ __global__ void k_ritz(const double *a, const double *b, const int *meff, int n_
 
 struct LanczosScratch {
   double2 *Q = nullptr, *W = nullptr, *coef = nullptr;
+  float2 *Q32 = nullptr;  // FP32 shadow of Q (complex64 H only): reorthogonalisation projections
+  float2 *hpart = nullptr; // Hermitian matvec partials [nb][nb][HT][n_pol]
+  int nbt = 0;
   double *a = nullptr, *b = nullptr, *beta0 = nullptr, *hmax = nullptr, *part = nullptr;
   int *meff = nullptr;
 };
@@ -445,7 +650,15 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
       cudaMallocAsync((void **)&s.beta0, sizeof(double) * n_pol, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.hmax, sizeof(double), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.part, sizeof(double) * 1024, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess) {
+      cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess ||
+      (c->precision != BSE_FP64 &&
+       cudaMallocAsync((void **)&s.Q32, qbytes / 2, st) != cudaSuccess)) {
+    cudaGetLastError();
+    return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
+  }
+  s.nbt = (int)((dim + HT - 1) / HT);
+  if (c->precision != BSE_FP64 && dim % 2 == 0 &&
+      cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
   }
@@ -453,7 +666,7 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
 }
 
 void lanczos_release(bse_ctx *c, LanczosScratch &s) {
-  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff};
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -473,7 +686,7 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     k_absmax_part<double2><<<1024, 256, 0, st>>>((const double2 *)H, dim * dim, s.part);
   k_absmax_final<<<1, 32, 0, st>>>(s.part, 1024, s.hmax);
   k_fill_meff<<<n_pol, 256, 0, st>>>(s.meff, n_pol, n_steps, s.a, s.b, ldab);
-  k_lanczos_init<<<n_pol, 1024, 0, st>>>(u, dim, s.Q, qs, s.beta0);
+  k_lanczos_init<<<n_pol, 1024, 0, st>>>(u, dim, s.Q, qs, s.beta0, s.Q32);
   bse_count_launch(4);
   bse_status r = bse_check_launch(c, "lanczos init");
   if (r != BSE_OK) return r;
@@ -481,7 +694,21 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const unsigned el_blocks = (unsigned)((dim + 255) / 256);
   for (int j = 0; j < n_steps; j++) {
     bse_prof_begin(c, BSE_KP_MATVEC);
-    if (c64) {
+    if (c64 && s.hpart) {
+      dim3 g(s.nbt, s.nbt);
+      const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
+      if (n_pol == 1) {
+        k_hmatvec_c64<1><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        k_hmv_reduce<1><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      } else if (n_pol == 2) {
+        k_hmatvec_c64<2><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        k_hmv_reduce<2><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      } else {
+        k_hmatvec_c64<3><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        k_hmv_reduce<3><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      }
+      bse_count_launch();
+    } else if (c64) {
       if (n_pol == 1) k_matvec_c64<1><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
       else if (n_pol == 2) k_matvec_c64<2><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
       else k_matvec_c64<3><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
@@ -494,11 +721,16 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     k_alpha_axpy<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff);
     bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
-      k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
-      k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+      if (c64) {
+        k_reorth_dots32<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
+        k_reorth_update32<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
+      } else {
+        k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+        k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+      }
     }
     bse_prof_end(c, BSE_KP_REORTH);
-    k_norm_scale<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps);
+    k_norm_scale<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps, s.Q32);
     bse_count_launch(7);
     r = bse_check_launch(c, "lanczos step");
     if (r != BSE_OK) return r;

@@ -110,14 +110,14 @@ constexpr int MAXB = 8;
 __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot, int nb, int nv,
                          int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
                          const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1, int n2, int n3,
-                         int q0, int np, int rows, int kmem, __nv_bfloat16 *__restrict__ Ap,
-                         float2 *__restrict__ Mc) {
+                         int q0, const int *__restrict__ qlist, int np, int rows, int kmem,
+                         __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc) {
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
   const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
   const int row = blockIdx.x / nchunk;
   const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
-  const int qq = blockIdx.y, q = q0 + qq, k1 = blockIdx.z;
+  const int qq = blockIdx.y, q = qlist[q0 + qq], k1 = blockIdx.z;
   const int k2 = kdiff(k1, q, n1, n2, n3);
   float2 *c1 = scf, *c2 = scf + nao_tot * nb;
   for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
@@ -187,12 +187,13 @@ constexpr int G2CH = 32;
 // H block (k1, k2 = k1 - q) += -(1/N_k) sum_nu T[(k1,i,j)][nu] M_cc[(k1,a,b)][nu] (+ diagonal).
 __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
                                                const double *__restrict__ eqp, int nv, int nc, int naux, int n1,
-                                               int n2, int n3, int q0, int rows, long long dim,
-                                               float2 *__restrict__ H) {
+                                               int n2, int n3, int q0, const int *__restrict__ qlist, int rows,
+                                               long long dim, float2 *__restrict__ H) {
   extern __shared__ float2 sg[];
   const int nk = n1 * n2 * n3;
-  const int k1 = blockIdx.x, qq = blockIdx.y, q = q0 + qq;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
   const int nvc = nv * nc, nvv = nv * nv, ncc = nc * nc, nb = nv + nc;
   float2 *sT = sg, *sM = sT + nvv * G2CH;
   const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * nvv) * naux;
@@ -240,8 +241,218 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
       double hr = (double)hx.x - inv * (double)ad[t].x, hi = (double)hx.y - inv * (double)ad[t].y;
       if (q == 0 && ia == jb) hr += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
       *hp = make_float2((float)hr, (float)hi);
+      if (mirror) {  // block (k2, k1) gets the conjugate of the direct contribution
+        float2 *hm = H + ((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia;
+        const float2 mx = *hm;
+        *hm = make_float2((float)((double)mx.x - inv * (double)ad[t].x), (float)((double)mx.y + inv * (double)ad[t].y));
+      }
     }
   }
+}
+
+
+// Register-blocked projection: one thread per ABF mu of one pair computes every M_vv and
+// M_cc element of that mu; both LRI terms go into one accumulator,
+//   M_vv[i][j] = sum_s conj(c2_sj) Y1_si + c1_si conj(Y2_sj),
+//   M_cc[a][b] = sum_s conj(c1_sa) Y2_sb + c2_sb conj(Y1_sa)   (band indices in the window).
+// grid: x = q - q0, y = k1; block: mu chunk (blockDim >= 32), loop over mu.
+template <int NV, int NC>
+__global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
+                                                  int nao_tot, int naux, int nao_max,
+                                                  const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
+                                                  const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
+                                                  const int *__restrict__ qlist, int np, int rows, int kmem,
+                                                  __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc) {
+  constexpr int NB = NV + NC;
+  extern __shared__ float2 scf[];
+  const int nk = n1 * n2 * n3;
+  const int qq = blockIdx.x, q = qlist[q0 + qq], k1 = blockIdx.y;
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  float2 *c1 = scf, *c2 = scf + nao_tot * NB;
+  for (int e = threadIdx.x; e < nao_tot * NB; e += blockDim.x) {
+    const double2 a = ck[(long long)k1 * nao_tot * NB + e], b = ck[(long long)k2 * nao_tot * NB + e];
+    c1[e] = make_float2((float)a.x, (float)a.y);
+    c2[e] = make_float2((float)b.x, (float)b.y);
+  }
+  __syncthreads();
+  const long long plane = (long long)rows * kmem;
+  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
+    const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+    const float2 *Y1 = Y + (long long)k1 * nao_max * NB * naux + mu;
+    const float2 *Y2 = Y + (long long)k2 * nao_max * NB * naux + mu;
+    float2 mv[NV][NV], mc[NC][NC];
+#pragma unroll
+    for (int i = 0; i < NV; i++)
+#pragma unroll
+      for (int j = 0; j < NV; j++) mv[i][j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < NC; a++)
+#pragma unroll
+      for (int b = 0; b < NC; b++) mc[a][b] = make_float2(0.f, 0.f);
+    for (int s = 0; s < na; s++) {
+      float2 y1[NB], y2[NB];
+#pragma unroll
+      for (int n = 0; n < NB; n++) {
+        y1[n] = Y1[((long long)s * NB + n) * naux];
+        y2[n] = Y2[((long long)s * NB + n) * naux];
+      }
+      const float2 *cs1 = c1 + (ao0 + s) * NB, *cs2 = c2 + (ao0 + s) * NB;
+#pragma unroll
+      for (int i = 0; i < NV; i++) {
+        const float2 a1 = cs1[i];
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+          const float2 b2 = cs2[j];
+          // conj(b2) y1[i] + a1 conj(y2[j])
+          float xr = mv[i][j].x, xi = mv[i][j].y;
+          xr = fmaf(b2.x, y1[i].x, fmaf(b2.y, y1[i].y, xr));
+          xi = fmaf(b2.x, y1[i].y, fmaf(-b2.y, y1[i].x, xi));
+          xr = fmaf(a1.x, y2[j].x, fmaf(a1.y, y2[j].y, xr));
+          xi = fmaf(a1.y, y2[j].x, fmaf(-a1.x, y2[j].y, xi));
+          mv[i][j] = make_float2(xr, xi);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < NC; a++) {
+        const float2 a1 = cs1[NV + a];
+#pragma unroll
+        for (int b = 0; b < NC; b++) {
+          const float2 b2 = cs2[NV + b];
+          // conj(a1) y2[b] + b2 conj(y1[a])
+          float xr = mc[a][b].x, xi = mc[a][b].y;
+          xr = fmaf(a1.x, y2[NV + b].x, fmaf(a1.y, y2[NV + b].y, xr));
+          xi = fmaf(a1.x, y2[NV + b].y, fmaf(-a1.y, y2[NV + b].x, xi));
+          xr = fmaf(b2.x, y1[NV + a].x, fmaf(b2.y, y1[NV + a].y, xr));
+          xi = fmaf(b2.y, y1[NV + a].x, fmaf(-b2.x, y1[NV + a].y, xi));
+          mc[a][b] = make_float2(xr, xi);
+        }
+      }
+    }
+    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)k1 * NV * NV * kmem + mu;
+#pragma unroll
+    for (int i = 0; i < NV; i++)
+#pragma unroll
+      for (int j = 0; j < NV; j++) {
+        __nv_bfloat16 pr[3], pi[3];
+        split_pieces<float>(mv[i][j].x, np, pr);
+        split_pieces<float>(mv[i][j].y, np, pi);
+        const long long r = (long long)(i * NV + j) * kmem;
+        for (int p = 0; p < np; p++) {
+          out[(2 * p) * plane + r] = pr[p];
+          out[(2 * p + 1) * plane + r] = pi[p];
+        }
+      }
+    float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * naux + mu;
+#pragma unroll
+    for (int a = 0; a < NC; a++)
+#pragma unroll
+      for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * naux] = mc[a][b];
+  }
+}
+
+// Register-tiled second contraction: one block per pair; thread (r, c) owns the 2x2
+// outputs rows (i,j) in {2r, 2r+1}, columns (a,b) in {2c, 2c+1} of D = T M_cc^T.
+template <int NV, int NC>
+__global__ void __launch_bounds__(1024) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                                  const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
+                                                  int q0, const int *__restrict__ qlist, int rows, long long dim,
+                                                  float2 *__restrict__ H) {
+  constexpr int R = NV * NV, C = NC * NC, TR = (R + 1) / 2, TCC = (C + 1) / 2, NVC = NV * NC, NB = NV + NC;
+  constexpr int CH = 32;
+  __shared__ float2 sT[CH][R + 1], sM[CH][C + 1];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * R) * naux;
+  const float2 *Mk = Mc + ((long long)qq * nk + k1) * C * naux;
+  const int tr = threadIdx.x / TCC, tc = threadIdx.x % TCC;
+  const bool act = threadIdx.x < TR * TCC;
+  float2 acc[2][2];
+#pragma unroll
+  for (int x = 0; x < 2; x++)
+#pragma unroll
+    for (int y = 0; y < 2; y++) acc[x][y] = make_float2(0.f, 0.f);
+  for (int n0 = 0; n0 < naux; n0 += CH) {
+    const int nn = min(CH, naux - n0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < (R + C) * CH; e += blockDim.x) {
+      const int r = e / CH, u = e % CH;
+      float2 v = make_float2(0.f, 0.f);
+      if (u < nn) v = r < R ? Tk[(long long)r * naux + n0 + u] : Mk[(long long)(r - R) * naux + n0 + u];
+      if (r < R) sT[u][r] = v; else sM[u][r - R] = v;
+    }
+    __syncthreads();
+    if (act) {
+      const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
+      for (int u = 0; u < nn; u++) {
+        const float2 tt[2] = {sT[u][r0], sT[u][r1]}, mm[2] = {sM[u][m0], sM[u][m1]};
+#pragma unroll
+        for (int x = 0; x < 2; x++)
+#pragma unroll
+          for (int y = 0; y < 2; y++) {
+            acc[x][y].x = fmaf(tt[x].x, mm[y].x, fmaf(-tt[x].y, mm[y].y, acc[x][y].x));
+            acc[x][y].y = fmaf(tt[x].x, mm[y].y, fmaf(tt[x].y, mm[y].x, acc[x][y].y));
+          }
+      }
+    }
+  }
+  if (!act) return;
+  const double inv = 1.0 / nk;
+#pragma unroll
+  for (int x = 0; x < 2; x++)
+#pragma unroll
+    for (int y = 0; y < 2; y++) {
+      const int ij = 2 * tr + x, ab = 2 * tc + y;
+      if (ij >= R || ab >= C) continue;
+      const int i = ij / NV, j = ij % NV, a = ab / NC, b = ab % NC;
+      const int ia = i * NC + a, jb = j * NC + b;
+      float2 *hp = H + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
+      const float2 hx = *hp;
+      double hr = (double)hx.x - inv * (double)acc[x][y].x, hi = (double)hx.y - inv * (double)acc[x][y].y;
+      if (q == 0 && ia == jb) hr += eqp[(long long)k1 * NB + NV + a] - eqp[(long long)k1 * NB + i];
+      *hp = make_float2((float)hr, (float)hi);
+      if (mirror) {
+        float2 *hm = H + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
+        const float2 mx = *hm;
+        *hm = make_float2((float)((double)mx.x - inv * (double)acc[x][y].x),
+                          (float)((double)mx.y + inv * (double)acc[x][y].y));
+      }
+    }
+}
+
+template <int NV, int NC>
+void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq) {
+  const int na = c->naux_tot;
+  const int bs = std::min(160, (na + 31) / 32 * 32);
+  const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
+  k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, na, c->nao_max, c->d_aux_atom,
+                                                             c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
+                                                             c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap,
+                                                             w->Mc32);
+}
+
+template <int NV, int NC>
+void launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  constexpr int threads = ((NV * NV + 1) / 2) * ((NC * NC + 1) / 2);
+  const int bs = (threads + 31) / 32 * 32;
+  k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, 0, c->stream>>>(w->T32, w->Mc32, c->eqp, c->naux_tot, c->mesh[0],
+                                                           c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
+}
+
+// Dispatch the register-blocked kernels for windows with Nv, Nc in {2, 4, 6}; false means
+// the caller falls back to the generic kernels.
+bool fast_pair_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H, bool proj) {
+#define BSE_FAST(NV, NC)                                                       \
+  if (c->nv == NV && c->nc == NC) {                                            \
+    if (proj) launch_proj_fast<NV, NC>(c, w, q0, nq);                          \
+    else launch_g2_fast<NV, NC>(c, w, q0, nq, H);                              \
+    return true;                                                               \
+  }
+  BSE_FAST(2, 2) BSE_FAST(2, 4) BSE_FAST(2, 6) BSE_FAST(4, 2) BSE_FAST(4, 4) BSE_FAST(4, 6)
+  BSE_FAST(6, 2) BSE_FAST(6, 4) BSE_FAST(6, 6)
+#undef BSE_FAST
+  return false;
 }
 
 // ---- tensor maps ------------------------------------------------------------------------
@@ -398,21 +609,24 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
     a.out_bstride = 0;
     a.b_batch_planes = 0;
     a.b_base = 0;
+    a.qlist = nullptr;
     a.err = c->d_err;
     dim3 grid((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
     bse_status s = launch_tc_np(c, w->np, w->tmA_x, w->tmB_x, a, grid, BSE_KP_EXCH);
     if (s != BSE_OK) return s;
   }
   const int nchunk = (na + 127) / 128;
-  for (int q0 = 0; q0 < c->nk; q0 += w->nq) {
-    const int nq = std::min(w->nq, c->nk - q0);
+  const int nqp = (int)c->qplus.size();
+  for (int q0 = 0; q0 < nqp; q0 += w->nq) {
+    const int nq = std::min(w->nq, nqp - q0);
     {
       dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
       size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
       bse_prof_begin(c, BSE_KP_PROJECT);
-      k_proj32<<<grid, 128, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
-                                             c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
-                                             c->mesh[2], q0, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
+      if (!fast_pair_kernels(c, w, q0, nq, H, true))
+        k_proj32<<<grid, 128, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+                                               c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
+                                               c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
       bse_prof_end(c, BSE_KP_PROJECT);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "proj32");
@@ -429,6 +643,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       a.out_bstride = (long long)w->rows * na;
       a.b_batch_planes = 1;
       a.b_base = q0;
+      a.qlist = c->d_qplus;
       a.err = c->d_err;
       dim3 grid((unsigned)((na + TC_BN - 1) / TC_BN), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
       bse_status s = launch_tc_np(c, w->np, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
@@ -438,8 +653,9 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       dim3 grid(c->nk, nq);
       size_t sm = sizeof(float2) * (c->nv * c->nv + c->nc * c->nc) * G2CH;
       bse_prof_begin(c, BSE_KP_G2);
-      k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
-                                            c->mesh[2], q0, w->rows, c->dim, H);
+      if (!fast_pair_kernels(c, w, q0, nq, H, false))
+        k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                              c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
       bse_prof_end(c, BSE_KP_G2);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "g2_32");

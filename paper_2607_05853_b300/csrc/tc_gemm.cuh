@@ -47,8 +47,9 @@ struct Args {
   float2 *out;           // interleaved complex
   long long ldo;         // row pitch of out (elements)
   long long out_bstride; // batch stride of out (elements)
-  int b_batch_planes;    // 0: B has no batch dimension (z = pp), else z = (b_base + b)*PP + pp
+  int b_batch_planes;    // 0: B has no batch dimension (z = pp), else z = qlist[b_base + b]*PP + pp
   int b_base;
+  const int *qlist;
   int *err;
 };
 
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(192, 1)
       for (int pp = 0; pp < C::PP; pp++) {
         tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
         tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, n0,
-                        args.b_batch_planes ? (args.b_base + b) * C::PP + pp : pp);
+                        args.b_batch_planes ? args.qlist[args.b_base + b] * C::PP + pp : pp);
       }
       issued = kc + 1;
     }

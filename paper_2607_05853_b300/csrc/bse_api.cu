@@ -172,6 +172,7 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
   c->dim = nk * c->nvc;
   c->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&c->device);
+  cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
 
   // transfers q in a half set, ordered by lines along the last mesh axis
   {

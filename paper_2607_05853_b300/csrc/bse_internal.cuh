@@ -33,6 +33,7 @@ struct bse_ctx {
   int64_t dim = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  int n_sm = 148;
   int stage = 0;  // 0 setup, 1 interp_W done, 2 project_pairs done
   std::string err;
 

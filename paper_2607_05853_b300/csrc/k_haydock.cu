@@ -7,9 +7,14 @@
 // complex128 H the products are FP64; for a complex64 H (split-precision assembly) the
 // products and the per-lane partial sums are FP32 (H itself carries FP32 rounding) and
 // the cross-lane sums, dots, norms, updates and the reorthogonalisation are FP64.
+#include <algorithm>
 #include <cmath>
+#include <vector>
+
+#include <cudaTypedefs.h>
 
 #include "bse_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -335,6 +340,216 @@ __global__ void __launch_bounds__(128, 4) k_hmatvec_c64(const float2 *__restrict
   }
 }
 
+
+
+// Packed FP32 pairs (Blackwell fma.rn.f32x2): one instruction performs two FP32 FMAs.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 up2(unsigned long long v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long long a, unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// ---- TMA-fed Hermitian matvec (complex64 H), persistent ------------------------------------
+// Same tiles and partial slots as k_hmatvec_c64, but the H tile rows stream through a
+// 4-stage shared-memory ring filled by TMA (one producer lane), so the loads of the next
+// rows are in flight while four consumer warps compute on the current ones.  A stage is
+// 16 rows x 128 complex64 = 16 KB; rows/columns past dim arrive zero-filled.
+constexpr int MV_STAGES = 4, MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8;
+constexpr long long MV_WAIT = 4000000000LL;
+
+template <int NP>
+__global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim, int nb,
+                                                    const int2 *__restrict__ tiles, int ntiles,
+                                                    const float2 *__restrict__ Q32, long long qs, int j,
+                                                    float2 *__restrict__ part, const int *meff, int *err) {
+  extern __shared__ __align__(128) uint8_t smv[];
+  uint8_t *ring = smv;                                                        // MV_STAGES x 16 KB
+  float2 (*xr)[HT] = reinterpret_cast<float2 (*)[HT]>(ring + MV_STAGES * MV_STAGE_BYTES);
+  float2 (*xc)[HT] = xr + NP;
+  float2 (*xq)[HT] = xc + NP;                                                 // rotated rows (yi, -yr)
+  float2 (*vs)[HT][NP] = reinterpret_cast<float2 (*)[HT][NP]>(xq + NP);      // [4][HT][NP]
+  uint64_t *full = reinterpret_cast<uint64_t *>(vs + 4);
+  uint64_t *empty = full + MV_STAGES;
+  bool live = false;
+  for (int p = 0; p < NP; p++) live |= (j < meff[p]);
+  if (!live) return;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < MV_STAGES; st++) {
+      tc::mbar_init(&full[st], 1);
+      tc::mbar_init(&empty[st], 4);
+    }
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    if (lane == 0) {
+      tc::prefetch_tmap(&tmH);
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int2 tl = tiles[t];
+        for (int c = 0; c < HT / MV_CHUNK; c++, it++) {
+          const int st = it % MV_STAGES;
+          if (it >= MV_STAGES && !tc::mbar_wait_bounded(&empty[st], ((it / MV_STAGES) & 1) ^ 1, MV_WAIT)) {
+            atomicOr(err, 2);
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&full[st], MV_STAGE_BYTES);
+          asm volatile(
+              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                  tc::smem_u32(ring + st * MV_STAGE_BYTES)),
+              "l"(reinterpret_cast<uint64_t>(&tmH)), "r"(2 * tl.y * HT), "r"(tl.x * HT + c * MV_CHUNK),
+              "r"(tc::smem_u32(&full[st]))
+              : "memory");
+        }
+      }
+      // every copy started here lands before the CTA can exit
+      for (int k = it - MV_STAGES < 0 ? 0 : it - MV_STAGES; k < it; k++)
+        if (!tc::mbar_wait_bounded(&full[k % MV_STAGES], (k / MV_STAGES) & 1, MV_WAIT)) atomicOr(err, 2);
+    }
+    return;
+  }
+  // ---------------- consumers: warps 1..4 ----------------
+  const int cw = warp - 1;
+  const int ctid = threadIdx.x - 32;
+  int it = 0;
+  bool aborted = false;  // warp-uniform; after a timeout the warp runs on zeros so that every
+                         // named barrier below is still reached by all four consumer warps
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int2 tl = tiles[t];
+    const int bi = tl.x, bj = tl.y;
+    const bool diag = bi == bj;
+    const long long r0 = (long long)bi * HT, c0 = (long long)bj * HT;
+    for (int e = ctid; e < NP * HT; e += 128) {
+      const int p = e / HT, l = e % HT;
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 yv = r0 + l < dim ? Q32[p * qs + (long long)j * dim + r0 + l] : z;
+      xr[p][l] = yv;
+      xq[p][l] = make_float2(yv.y, -yv.x);
+      xc[p][l] = c0 + l < dim ? Q32[p * qs + (long long)j * dim + c0 + l] : z;
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    // per tile: column vectors as (xr, xi) and (-xi, xr) pairs; v accumulators as pairs
+    unsigned long long XN[4][NP], XR[4][NP], V[4][NP];
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+#pragma unroll
+      for (int p = 0; p < NP; p++) {
+        const float2 xv = xc[p][2 * (lane + 32 * (q / 2)) + (q % 2)];
+        XN[q][p] = pk2(xv.x, xv.y);
+        XR[q][p] = pk2(-xv.y, xv.x);
+        V[q][p] = 0ull;
+      }
+    for (int c = 0; c < HT / MV_CHUNK; c++, it++) {
+      const int st = it % MV_STAGES;
+      bool ok = aborted ? false : tc::mbar_wait_bounded(&full[st], (it / MV_STAGES) & 1, MV_WAIT);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok && !aborted) {
+        if (lane == 0) atomicOr(err, 2);
+        aborted = true;
+      }
+      const float4 *rows = reinterpret_cast<const float4 *>(ring + st * MV_STAGE_BYTES);
+      float4 h[4][2];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++)
+#pragma unroll
+        for (int tt = 0; tt < 2; tt++)
+          h[rr][tt] = aborted ? make_float4(0.f, 0.f, 0.f, 0.f) : rows[(cw * 4 + rr) * (HT / 2) + lane + 32 * tt];
+      __syncwarp();
+      if (lane == 0 && !aborted)
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[st])) : "memory");
+      // h x = hr (xr, xi) + hi (-xi, xr);  conj(h) y = hr (yr, yi) + hi (yi, -yr)
+      unsigned long long U[4][NP];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) U[rr][p] = 0ull;
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++) {
+        const int lr = c * MV_CHUNK + cw * 4 + rr;
+        unsigned long long YN[NP], YQ[NP];
+        if (!diag) {
+#pragma unroll
+          for (int p = 0; p < NP; p++) {
+            const float2 yv = xr[p][lr], yq = xq[p][lr];
+            YN[p] = pk2(yv.x, yv.y);
+            YQ[p] = pk2(yq.x, yq.y);
+          }
+        }
+#pragma unroll
+        for (int tt = 0; tt < 2; tt++) {
+          const float4 hh = h[rr][tt];
+#pragma unroll
+          for (int e2 = 0; e2 < 2; e2++) {
+            const float hre = e2 ? hh.z : hh.x, him = e2 ? hh.w : hh.y;
+            const unsigned long long hr2 = pk2(hre, hre), hi2 = pk2(him, him);
+            const int q = 2 * tt + e2;
+#pragma unroll
+            for (int p = 0; p < NP; p++) {
+              ffma2(U[rr][p], hr2, XN[q][p]);
+              ffma2(U[rr][p], hi2, XR[q][p]);
+              if (!diag) {
+                ffma2(V[q][p], hr2, YN[p]);
+                ffma2(V[q][p], hi2, YQ[p]);
+              }
+            }
+          }
+        }
+      }
+      float u[32];
+#pragma unroll
+      for (int rr = 0; rr < 4; rr++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) {
+          const float2 uv = up2(U[rr][p]);
+          u[(rr * NP + p) * 2 + 0] = uv.x;
+          u[(rr * NP + p) * 2 + 1] = uv.y;
+        }
+#pragma unroll
+      for (int i = 4 * NP * 2; i < 32; i++) u[i] = 0.f;
+      const float tot = warp_transpose_sum32(u, lane);
+      if (lane < 4 * NP * 2) {
+        const int rr = lane / (2 * NP), p = (lane / 2) % NP, ri = lane % 2;
+        const int lr = c * MV_CHUNK + cw * 4 + rr;
+        reinterpret_cast<float *>(part + (((long long)bi * nb + bj) * HT + lr) * NP + p)[ri] = tot;
+      }
+    }
+    if (!diag) {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int p = 0; p < NP; p++) vs[cw][2 * (lane + 32 * (q / 2)) + (q % 2)][p] = up2(V[q][p]);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      for (int e = ctid; e < HT * NP; e += 128) {
+        const int l = e / NP, p = e % NP;
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+          acc.x += vs[w][l][p].x;
+          acc.y += vs[w][l][p].y;
+        }
+        part[(((long long)bj * nb + bi) * HT + l) * NP + p] = acc;
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // xr/xc/vs free for the next tile
+  }
+}
+
+template <int NP>
+constexpr int hmv_tma_smem() {
+  return MV_STAGES * MV_STAGE_BYTES + 3 * NP * HT * 8 + 4 * HT * NP * 8 + 2 * MV_STAGES * 8;
+}
+
 // W[p][row] = sum_s part[row_block][s][row_local][p]  (FP64 sum in a fixed order)
 template <int NP>
 __global__ void k_hmv_reduce(const float2 *__restrict__ part, long long dim, int nb, double2 *__restrict__ W,
@@ -345,13 +560,30 @@ __global__ void k_hmv_reduce(const float2 *__restrict__ part, long long dim, int
   const int p = (int)(e % NP);
   if (j >= meff[p]) return;
   const long long t = row / HT, l = row % HT;
-  double sx = 0.0, sy = 0.0;
-  for (int s = 0; s < nb; s++) {
-    const float2 v = part[((t * nb + s) * HT + l) * NP + p];
-    sx += v.x;
-    sy += v.y;
+  const float2 *src = part + (t * nb * HT + l) * NP + p;
+  const long long step = (long long)HT * NP;
+  double sx[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sy[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int s = 0;
+  for (; s + 8 <= nb; s += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const float2 v = src[(s + u) * step];
+      sx[u] += v.x;
+      sy[u] += v.y;
+    }
   }
-  W[(long long)p * dim + row] = make_double2(sx, sy);
+  for (; s < nb; s++) {
+    const float2 v = src[s * step];
+    sx[0] += v.x;
+    sy[0] += v.y;
+  }
+  double tx = 0.0, ty = 0.0;
+#pragma unroll
+  for (int u = 0; u < 8; u++) {
+    tx += sx[u];
+    ty += sy[u];
+  }
+  W[(long long)p * dim + row] = make_double2(tx, ty);
 }
 
 // a[p][j] = Re(Q_j^H W); W -= a_j Q_j + b_{j-1} Q_{j-1}   (block per p)
@@ -430,16 +662,27 @@ __global__ void k_reorth_dots32(const double2 *W, long long dim, const float2 *Q
   if (j >= meff[p] || i > j) return;
   const double2 *w = W + (long long)p * dim;
   const float2 *qi = Q32 + p * qs + (long long)i * dim;
-  float sr = 0.f, si = 0.f;
-  for (long long e = threadIdx.x; e < dim; e += blockDim.x) {
+  float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+  long long e = threadIdx.x;
+  for (; e + 3 * 256 < dim; e += 4 * 256) {
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const float2 q = qi[e + u * 256];
+      const double2 wv = w[e + u * 256];
+      const float vx = (float)wv.x, vy = (float)wv.y;
+      sr[u] = fmaf(q.x, vx, fmaf(q.y, vy, sr[u]));
+      si[u] = fmaf(q.x, vy, fmaf(-q.y, vx, si[u]));
+    }
+  }
+  for (; e < dim; e += 256) {
     const float2 q = qi[e];
     const float vx = (float)w[e].x, vy = (float)w[e].y;
-    sr = fmaf(q.x, vx, fmaf(q.y, vy, sr));
-    si = fmaf(q.x, vy, fmaf(-q.y, vx, si));
+    sr[0] = fmaf(q.x, vx, fmaf(q.y, vy, sr[0]));
+    si[0] = fmaf(q.x, vy, fmaf(-q.y, vx, si[0]));
   }
-  double dr = block_sum<256>((double)sr, red);
+  double dr = block_sum<256>((double)(sr[0] + sr[1]) + (double)(sr[2] + sr[3]), red);
   __syncthreads();
-  double di = block_sum<256>((double)si, red);
+  double di = block_sum<256>((double)(si[0] + si[1]) + (double)(si[2] + si[3]), red);
   if (threadIdx.x == 0) coef[p * ldc + i] = make_double2(dr, di);
 }
 
@@ -459,12 +702,25 @@ __global__ void k_reorth_update32(double2 *W, long long dim, const float2 *Q32, 
       cs[t] = make_float2((float)c.x, (float)c.y);
     }
     __syncthreads();
-    if (e < dim)
-      for (int i = 0; i < n; i++) {
-        const float2 c = cs[i], q = qp[(long long)(i0 + i) * dim];
-        cr = fmaf(c.x, q.x, fmaf(-c.y, q.y, cr));
-        ci = fmaf(c.x, q.y, fmaf(c.y, q.x, ci));
+    if (e < dim) {
+      float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+      int i = 0;
+      for (; i + 4 <= n; i += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const float2 c = cs[i + u], q = qp[(long long)(i0 + i + u) * dim];
+          ar[u] = fmaf(c.x, q.x, fmaf(-c.y, q.y, ar[u]));
+          ai[u] = fmaf(c.x, q.y, fmaf(c.y, q.x, ai[u]));
+        }
       }
+      for (; i < n; i++) {
+        const float2 c = cs[i], q = qp[(long long)(i0 + i) * dim];
+        ar[0] = fmaf(c.x, q.x, fmaf(-c.y, q.y, ar[0]));
+        ai[0] = fmaf(c.x, q.y, fmaf(c.y, q.x, ai[0]));
+      }
+      cr += (ar[0] + ar[1]) + (ar[2] + ar[3]);
+      ci += (ai[0] + ai[1]) + (ai[2] + ai[3]);
+    }
   }
   if (e < dim) {
     double2 v = W[(long long)p * dim + e];
@@ -629,11 +885,35 @@ __global__ void k_ritz(const double *a, const double *b, const int *meff, int n_
   resid[e] = fabs(b[m - 1] * v[m - 1]);
 }
 
+bool encode_rows_f32(CUtensorMap *m, const void *base, unsigned long long inner, unsigned long long rows,
+                     unsigned box_inner, unsigned box_rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return false;
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 4};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct LanczosScratch {
   double2 *Q = nullptr, *W = nullptr, *coef = nullptr;
   float2 *Q32 = nullptr;  // FP32 shadow of Q (complex64 H only): reorthogonalisation projections
   float2 *hpart = nullptr; // Hermitian matvec partials [nb][nb][HT][n_pol]
   int nbt = 0;
+  int2 *tiles = nullptr;    // upper-triangle tile list for the TMA matvec
+  int ntiles = 0;
+  CUtensorMap tmH;
+  bool tma = false;
   double *a = nullptr, *b = nullptr, *beta0 = nullptr, *hmax = nullptr, *part = nullptr;
   int *meff = nullptr;
 };
@@ -657,16 +937,27 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
     return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
   }
   s.nbt = (int)((dim + HT - 1) / HT);
-  if (c->precision != BSE_FP64 && dim % 2 == 0 &&
-      cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
-    cudaGetLastError();
-    return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
+  if (c->precision != BSE_FP64 && dim % 2 == 0) {
+    if (cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
+      cudaGetLastError();
+      return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
+    }
+    std::vector<int2> tl;
+    for (int bi = 0; bi < s.nbt; bi++)
+      for (int bj = bi; bj < s.nbt; bj++) tl.push_back(make_int2(bi, bj));
+    s.ntiles = (int)tl.size();
+    if (cudaMallocAsync((void **)&s.tiles, sizeof(int2) * tl.size(), st) != cudaSuccess ||
+        cudaMemcpyAsync(s.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      return bse_fail(c, BSE_ENOMEM, "spectrum: tile list allocation failed");
+    }
   }
   return BSE_OK;
 }
 
 void lanczos_release(bse_ctx *c, LanczosScratch &s) {
-  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart};
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart, s.tiles};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -679,6 +970,18 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const int ldab = n_steps + 1;
   cudaStream_t st = c->stream;
   const bool c64 = c->precision != BSE_FP64;
+  if (c64 && s.hpart && s.tiles) {
+    s.tma = encode_rows_f32(&s.tmH, H, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK);
+    if (s.tma) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_hmv_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
+        cudaFuncSetAttribute(k_hmv_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
+        cudaFuncSetAttribute(k_hmv_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
+        attr = true;
+      }
+    }
+  }
   // max |H|
   if (c64)
     k_absmax_part<float2><<<1024, 256, 0, st>>>((const float2 *)H, dim * dim, s.part);
@@ -694,7 +997,21 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const unsigned el_blocks = (unsigned)((dim + 255) / 256);
   for (int j = 0; j < n_steps; j++) {
     bse_prof_begin(c, BSE_KP_MATVEC);
-    if (c64 && s.hpart) {
+    if (c64 && s.tma) {
+      const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
+      const int grid = std::min(s.ntiles, 2 * c->n_sm);
+      if (n_pol == 1) {
+        k_hmv_tma<1><<<grid, 160, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_reduce<1><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      } else if (n_pol == 2) {
+        k_hmv_tma<2><<<grid, 160, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_reduce<2><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      } else {
+        k_hmv_tma<3><<<grid, 160, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_reduce<3><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+      }
+      bse_count_launch();
+    } else if (c64 && s.hpart) {
       dim3 g(s.nbt, s.nbt);
       const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
       if (n_pol == 1) {

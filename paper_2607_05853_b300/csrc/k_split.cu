@@ -350,75 +350,79 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   }
 }
 
-// Register-tiled second contraction: one block per pair; thread (r, c) owns the 2x2
-// outputs rows (i,j) in {2r, 2r+1}, columns (a,b) in {2c, 2c+1} of D = T M_cc^T.
+// Second contraction per pair: the pair's T rows (R x N_aux) and M_cc rows (C x N_aux) are
+// contiguous in memory and are copied to shared memory in one vectorised sweep; thread
+// (r, c) then owns the 2x2 outputs rows (i,j) in {2r, 2r+1}, columns (a,b) in {2c, 2c+1}
+// of D = T M_cc^T.  H gets D's contribution at (k1, k2) and its conjugate at (k2, k1).
 template <int NV, int NC>
-__global__ void __launch_bounds__(1024) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
-                                                  const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
-                                                  int q0, const int *__restrict__ qlist, int rows, long long dim,
-                                                  float2 *__restrict__ H) {
+__global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                                 const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
+                                                 int q0, const int *__restrict__ qlist, int rows, long long dim,
+                                                 float2 *__restrict__ H) {
   constexpr int R = NV * NV, C = NC * NC, TR = (R + 1) / 2, TCC = (C + 1) / 2, NVC = NV * NC, NB = NV + NC;
-  constexpr int CH = 32;
-  __shared__ float2 sT[CH][R + 1], sM[CH][C + 1];
+  extern __shared__ float2 sg2[];
+  float2 *sT = sg2, *sM = sg2 + R * naux;
   const int nk = n1 * n2 * n3;
   const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
   const bool mirror = !q_self_conjugate(q, n1, n2, n3);
   const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * R) * naux;
   const float2 *Mk = Mc + ((long long)qq * nk + k1) * C * naux;
-  const int tr = threadIdx.x / TCC, tc = threadIdx.x % TCC;
-  const bool act = threadIdx.x < TR * TCC;
-  float2 acc[2][2];
-#pragma unroll
-  for (int x = 0; x < 2; x++)
-#pragma unroll
-    for (int y = 0; y < 2; y++) acc[x][y] = make_float2(0.f, 0.f);
-  for (int n0 = 0; n0 < naux; n0 += CH) {
-    const int nn = min(CH, naux - n0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < (R + C) * CH; e += blockDim.x) {
-      const int r = e / CH, u = e % CH;
-      float2 v = make_float2(0.f, 0.f);
-      if (u < nn) v = r < R ? Tk[(long long)r * naux + n0 + u] : Mk[(long long)(r - R) * naux + n0 + u];
-      if (r < R) sT[u][r] = v; else sM[u][r - R] = v;
-    }
-    __syncthreads();
-    if (act) {
-      const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
-      for (int u = 0; u < nn; u++) {
-        const float2 tt[2] = {sT[u][r0], sT[u][r1]}, mm[2] = {sM[u][m0], sM[u][m1]};
-#pragma unroll
-        for (int x = 0; x < 2; x++)
-#pragma unroll
-          for (int y = 0; y < 2; y++) {
-            acc[x][y].x = fmaf(tt[x].x, mm[y].x, fmaf(-tt[x].y, mm[y].y, acc[x][y].x));
-            acc[x][y].y = fmaf(tt[x].x, mm[y].y, fmaf(tt[x].y, mm[y].x, acc[x][y].y));
-          }
-      }
-    }
+  if ((naux & 1) == 0) {
+    // asynchronous 16-byte global->shared copies: every load of the sweep is in flight at once
+    const float4 *t4 = reinterpret_cast<const float4 *>(Tk), *m4 = reinterpret_cast<const float4 *>(Mk);
+    float4 *st4 = reinterpret_cast<float4 *>(sT), *sm4 = reinterpret_cast<float4 *>(sM);
+    for (int e = threadIdx.x; e < R * naux / 2; e += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st4 + e)), "l"(t4 + e) : "memory");
+    for (int e = threadIdx.x; e < C * naux / 2; e += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sm4 + e)), "l"(m4 + e) : "memory");
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  } else {
+    for (int e = threadIdx.x; e < R * naux; e += blockDim.x) sT[e] = Tk[e];
+    for (int e = threadIdx.x; e < C * naux; e += blockDim.x) sM[e] = Mk[e];
   }
-  if (!act) return;
+  __syncthreads();
   const double inv = 1.0 / nk;
+  for (int w = threadIdx.x; w < TR * TCC; w += blockDim.x) {
+    const int tr = w / TCC, tc = w % TCC;
+    const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
+    const float2 *pt0 = sT + r0 * naux, *pt1 = sT + r1 * naux, *pm0 = sM + m0 * naux, *pm1 = sM + m1 * naux;
+    float2 acc[2][2];
 #pragma unroll
-  for (int x = 0; x < 2; x++)
+    for (int x = 0; x < 2; x++)
 #pragma unroll
-    for (int y = 0; y < 2; y++) {
-      const int ij = 2 * tr + x, ab = 2 * tc + y;
-      if (ij >= R || ab >= C) continue;
-      const int i = ij / NV, j = ij % NV, a = ab / NC, b = ab % NC;
-      const int ia = i * NC + a, jb = j * NC + b;
-      float2 *hp = H + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
-      const float2 hx = *hp;
-      double hr = (double)hx.x - inv * (double)acc[x][y].x, hi = (double)hx.y - inv * (double)acc[x][y].y;
-      if (q == 0 && ia == jb) hr += eqp[(long long)k1 * NB + NV + a] - eqp[(long long)k1 * NB + i];
-      *hp = make_float2((float)hr, (float)hi);
-      if (mirror) {
-        float2 *hm = H + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
-        const float2 mx = *hm;
-        *hm = make_float2((float)((double)mx.x - inv * (double)acc[x][y].x),
-                          (float)((double)mx.y + inv * (double)acc[x][y].y));
-      }
+      for (int y = 0; y < 2; y++) acc[x][y] = make_float2(0.f, 0.f);
+    for (int u = 0; u < naux; u++) {
+      const float2 tt[2] = {pt0[u], pt1[u]}, mm[2] = {pm0[u], pm1[u]};
+#pragma unroll
+      for (int x = 0; x < 2; x++)
+#pragma unroll
+        for (int y = 0; y < 2; y++) {
+          acc[x][y].x = fmaf(tt[x].x, mm[y].x, fmaf(-tt[x].y, mm[y].y, acc[x][y].x));
+          acc[x][y].y = fmaf(tt[x].x, mm[y].y, fmaf(tt[x].y, mm[y].x, acc[x][y].y));
+        }
     }
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        const int ij = 2 * tr + x, ab = 2 * tc + y;
+        if (ij >= R || ab >= C) continue;
+        const int i = ij / NV, j = ij % NV, a = ab / NC, b = ab % NC;
+        const int ia = i * NC + a, jb = j * NC + b;
+        float2 *hp = H + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
+        const float2 hx = *hp;
+        double hr = (double)hx.x - inv * (double)acc[x][y].x, hi = (double)hx.y - inv * (double)acc[x][y].y;
+        if (q == 0 && ia == jb) hr += eqp[(long long)k1 * NB + NV + a] - eqp[(long long)k1 * NB + i];
+        *hp = make_float2((float)hr, (float)hi);
+        if (mirror) {
+          float2 *hm = H + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
+          const float2 mx = *hm;
+          *hm = make_float2((float)((double)mx.x - inv * (double)acc[x][y].x),
+                            (float)((double)mx.y + inv * (double)acc[x][y].y));
+        }
+      }
+  }
 }
 
 template <int NV, int NC>
@@ -433,11 +437,19 @@ void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq) {
 }
 
 template <int NV, int NC>
-void launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+bool launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
   constexpr int threads = ((NV * NV + 1) / 2) * ((NC * NC + 1) / 2);
-  const int bs = (threads + 31) / 32 * 32;
-  k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, 0, c->stream>>>(w->T32, w->Mc32, c->eqp, c->naux_tot, c->mesh[0],
+  const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
+  const size_t sm = sizeof(float2) * (size_t)(NV * NV + NC * NC) * c->naux_tot;
+  if (sm > 200 * 1024) return false;  // the pair's rows do not fit: generic chunked kernel
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->naux_tot, c->mesh[0],
                                                            c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
+  return true;
 }
 
 // Dispatch the register-blocked kernels for windows with Nv, Nc in {2, 4, 6}; false means
@@ -445,9 +457,11 @@ void launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
 bool fast_pair_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H, bool proj) {
 #define BSE_FAST(NV, NC)                                                       \
   if (c->nv == NV && c->nc == NC) {                                            \
-    if (proj) launch_proj_fast<NV, NC>(c, w, q0, nq);                          \
-    else launch_g2_fast<NV, NC>(c, w, q0, nq, H);                              \
-    return true;                                                               \
+    if (proj) {                                                                \
+      launch_proj_fast<NV, NC>(c, w, q0, nq);                                  \
+      return true;                                                             \
+    }                                                                          \
+    return launch_g2_fast<NV, NC>(c, w, q0, nq, H);                            \
   }
   BSE_FAST(2, 2) BSE_FAST(2, 4) BSE_FAST(2, 6) BSE_FAST(4, 2) BSE_FAST(4, 4) BSE_FAST(4, 6)
   BSE_FAST(6, 2) BSE_FAST(6, 4) BSE_FAST(6, 6)

@@ -106,3 +106,21 @@ def test_split_full_size_sampled_blocks_and_excitons():
     b64.sync()
     w_s, w_d = w_s.cpu().numpy(), w_d.cpu().numpy()
     assert np.abs(w_s - w_d).max() <= 1e-3
+
+
+@pytest.mark.parametrize("name", list(RAGGED))
+def test_split_spectrum_ragged_full_length(name):
+    """Ragged dimensions (not multiples of the 128-row matvec tiles; odd dim takes the
+    full-read matvec): full-length Haydock on the complex64 H against the exact sum."""
+    import torch
+    inp = make_inputs(RAGGED[name])
+    orc = O.BSEOracle(inp)
+    Href = orc.hamiltonian()
+    b, d, H, _ = gpu_hamiltonian(inp, precision="bf16x3")
+    u = b.dipole_vector(d["vel"], d["e_ks"])
+    om = torch.linspace(0, 10, 301, dtype=torch.float64, device="cuda")
+    eps = b.spectrum(H, u, b.dim, om, 0.1, orc.prefactor())
+    b.sync()
+    ref = O.eps2_exact(Href, orc.dipoles(), om.cpu().numpy(), 0.1, orc.prefactor())
+    rel_l2 = np.linalg.norm(eps.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert rel_l2 <= 1e-4, rel_l2

@@ -18,7 +18,6 @@
 
 namespace {
 
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 __global__ void k_dipole(const double2 *__restrict__ vel, const double *__restrict__ eks, int nk,
                          int nv, int nc, double2 *__restrict__ u, int *err) {
@@ -372,10 +371,8 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
                                                     float2 *__restrict__ part, const int *meff, int *err) {
   extern __shared__ __align__(128) uint8_t smv[];
   uint8_t *ring = smv;                                                        // MV_STAGES x 16 KB
-  float2 (*xr)[HT] = reinterpret_cast<float2 (*)[HT]>(ring + MV_STAGES * MV_STAGE_BYTES);
-  float2 (*xc)[HT] = xr + NP;
-  float2 (*xq)[HT] = xc + NP;                                                 // rotated rows (yi, -yr)
-  float2 (*vs)[HT][NP] = reinterpret_cast<float2 (*)[HT][NP]>(xq + NP);      // [4][HT][NP]
+  float2 (*xbuf)[HT] = reinterpret_cast<float2 (*)[HT]>(ring + MV_STAGES * MV_STAGE_BYTES);  // [2][3*NP][HT]
+  float2 (*vs)[HT][NP] = reinterpret_cast<float2 (*)[HT][NP]>(xbuf + 2 * 3 * NP);           // [4][HT][NP]
   uint64_t *full = reinterpret_cast<uint64_t *>(vs + 4);
   uint64_t *empty = full + MV_STAGES;
   bool live = false;
@@ -425,29 +422,58 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
   int it = 0;
   bool aborted = false;  // warp-uniform; after a timeout the warp runs on zeros so that every
                          // named barrier below is still reached by all four consumer warps
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // The x vectors of a tile are loaded one tile ahead into registers and parked in the other
+  // half of a double buffer, so no tile starts with a global-load stall.
+  constexpr int XPT = (NP * HT + 127) / 128;  // elements per consumer thread
+  float2 pre_r[XPT], pre_c[XPT];
+  auto fetch = [&](int t) {
+    const int2 tl = tiles[t];
+    const long long r0 = (long long)tl.x * HT, c0 = (long long)tl.y * HT;
+#pragma unroll
+    for (int k = 0; k < XPT; k++) {
+      const int e = ctid + 128 * k;
+      const int p = e / HT, l = e % HT;
+      const float2 z = make_float2(0.f, 0.f);
+      pre_r[k] = (e < NP * HT && r0 + l < dim) ? Q32[p * qs + (long long)j * dim + r0 + l] : z;
+      pre_c[k] = (e < NP * HT && c0 + l < dim) ? Q32[p * qs + (long long)j * dim + c0 + l] : z;
+    }
+  };
+  auto park = [&](int buf) {
+#pragma unroll
+    for (int k = 0; k < XPT; k++) {
+      const int e = ctid + 128 * k;
+      if (e < NP * HT) {
+        const int p = e / HT, l = e % HT;
+        xbuf[buf * 3 * NP + p][l] = make_float2(pre_r[k].x, -pre_r[k].x);      // (yr, -yr)
+        xbuf[buf * 3 * NP + NP + p][l] = pre_c[k];                              // (xr, xi)
+        xbuf[buf * 3 * NP + 2 * NP + p][l] = make_float2(pre_r[k].y, pre_r[k].y); // (yi, yi)
+      }
+    }
+  };
+  if (blockIdx.x < ntiles) {
+    fetch(blockIdx.x);
+    park(0);
+  }
+  int buf = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
     const int2 tl = tiles[t];
     const int bi = tl.x, bj = tl.y;
     const bool diag = bi == bj;
-    const long long r0 = (long long)bi * HT, c0 = (long long)bj * HT;
-    for (int e = ctid; e < NP * HT; e += 128) {
-      const int p = e / HT, l = e % HT;
-      const float2 z = make_float2(0.f, 0.f);
-      const float2 yv = r0 + l < dim ? Q32[p * qs + (long long)j * dim + r0 + l] : z;
-      xr[p][l] = yv;
-      xq[p][l] = make_float2(yv.y, -yv.x);
-      xc[p][l] = c0 + l < dim ? Q32[p * qs + (long long)j * dim + c0 + l] : z;
-    }
-    asm volatile("bar.sync 1, 128;" ::: "memory");
-    // per tile: column vectors as (xr, xi) and (-xi, xr) pairs; v accumulators as pairs
-    unsigned long long XN[4][NP], XR[4][NP], V[4][NP];
+    asm volatile("bar.sync 1, 128;" ::: "memory");  // this tile's x vectors are parked
+    float2 (*xr)[HT] = xbuf + buf * 3 * NP;
+    float2 (*xc)[HT] = xr + NP;
+    float2 (*xq)[HT] = xc + NP;
+    const bool has_next = t + (int)gridDim.x < ntiles;
+    if (has_next) fetch(t + gridDim.x);
+    // per tile: column vectors as (xr, xr) and (-xi, xi) pairs; v accumulators as pairs
+    unsigned long long XA[4][NP], XB[4][NP], V[4][NP];
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
       for (int p = 0; p < NP; p++) {
         const float2 xv = xc[p][2 * (lane + 32 * (q / 2)) + (q % 2)];
-        XN[q][p] = pk2(xv.x, xv.y);
-        XR[q][p] = pk2(-xv.y, xv.x);
+        XA[q][p] = pk2(xv.x, xv.x);
+        XB[q][p] = pk2(-xv.y, xv.y);
         V[q][p] = 0ull;
       }
     for (int c = 0; c < HT / MV_CHUNK; c++, it++) {
@@ -468,7 +494,9 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0 && !aborted)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[st])) : "memory");
-      // h x = hr (xr, xi) + hi (-xi, xr);  conj(h) y = hr (yr, yi) + hi (yi, -yr)
+      // with hp = (hr, hi) as loaded and hs = (hi, hr):
+      //   h x       = hp (xr, xr) + hs (-xi, xi)
+      //   conj(h) y = hp (yr, -yr) + hs (yi, yi)
       unsigned long long U[4][NP];
 #pragma unroll
       for (int rr = 0; rr < 4; rr++)
@@ -477,13 +505,13 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
 #pragma unroll
       for (int rr = 0; rr < 4; rr++) {
         const int lr = c * MV_CHUNK + cw * 4 + rr;
-        unsigned long long YN[NP], YQ[NP];
+        unsigned long long YA[NP], YB[NP];
         if (!diag) {
 #pragma unroll
           for (int p = 0; p < NP; p++) {
-            const float2 yv = xr[p][lr], yq = xq[p][lr];
-            YN[p] = pk2(yv.x, yv.y);
-            YQ[p] = pk2(yq.x, yq.y);
+            const float2 ya = xr[p][lr], yb = xq[p][lr];
+            YA[p] = pk2(ya.x, ya.y);
+            YB[p] = pk2(yb.x, yb.y);
           }
         }
 #pragma unroll
@@ -492,15 +520,15 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
 #pragma unroll
           for (int e2 = 0; e2 < 2; e2++) {
             const float hre = e2 ? hh.z : hh.x, him = e2 ? hh.w : hh.y;
-            const unsigned long long hr2 = pk2(hre, hre), hi2 = pk2(him, him);
+            const unsigned long long hp = pk2(hre, him), hs = pk2(him, hre);
             const int q = 2 * tt + e2;
 #pragma unroll
             for (int p = 0; p < NP; p++) {
-              ffma2(U[rr][p], hr2, XN[q][p]);
-              ffma2(U[rr][p], hi2, XR[q][p]);
+              ffma2(U[rr][p], hp, XA[q][p]);
+              ffma2(U[rr][p], hs, XB[q][p]);
               if (!diag) {
-                ffma2(V[q][p], hr2, YN[p]);
-                ffma2(V[q][p], hi2, YQ[p]);
+                ffma2(V[q][p], hp, YA[p]);
+                ffma2(V[q][p], hs, YB[p]);
               }
             }
           }
@@ -541,13 +569,13 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
         part[(((long long)bj * nb + bi) * HT + l) * NP + p] = acc;
       }
     }
-    asm volatile("bar.sync 1, 128;" ::: "memory");  // xr/xc/vs free for the next tile
+    if (has_next) park(buf ^ 1);  // visible after the next tile's opening barrier
   }
 }
 
 template <int NP>
 constexpr int hmv_tma_smem() {
-  return MV_STAGES * MV_STAGE_BYTES + 3 * NP * HT * 8 + 4 * HT * NP * 8 + 2 * MV_STAGES * 8;
+  return MV_STAGES * MV_STAGE_BYTES + 2 * 3 * NP * HT * 8 + 4 * HT * NP * 8 + 2 * MV_STAGES * 8;
 }
 
 // W[p][row] = sum_s part[row_block][s][row_local][p]  (FP64 sum in a fixed order)
@@ -655,35 +683,59 @@ __global__ void k_reorth_update(double2 *W, long long dim, const double2 *Q, lon
 // sums, FP64 block reduction); the correction sum_i coef_i Q32_i is formed in FP32 and
 // subtracted from the FP64 vector.  W is already nearly orthogonal to the basis, so the
 // FP32 relative error lands on a small correction.
-__global__ void k_reorth_dots32(const double2 *W, long long dim, const float2 *Q32, long long qs, int j,
-                                double2 *coef, int ldc, const int *meff) {
-  __shared__ double red[32];
-  const int i = blockIdx.x, p = blockIdx.y;
-  if (j >= meff[p] || i > j) return;
-  const double2 *w = W + (long long)p * dim;
-  const float2 *qi = Q32 + p * qs + (long long)i * dim;
-  float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
-  long long e = threadIdx.x;
-  for (; e + 3 * 256 < dim; e += 4 * 256) {
-#pragma unroll
-    for (int u = 0; u < 4; u++) {
-      const float2 q = qi[e + u * 256];
-      const double2 wv = w[e + u * 256];
-      const float vx = (float)wv.x, vy = (float)wv.y;
-      sr[u] = fmaf(q.x, vx, fmaf(q.y, vy, sr[u]));
-      si[u] = fmaf(q.x, vy, fmaf(-q.y, vx, si[u]));
-    }
+
+
+// Chunked projections for the complex64 path: block (chunk, p) stages 256 elements of W
+// once, each warp streams basis rows i = warp, warp + 8, ... <= j over the chunk and writes
+// the chunk partial of Q32_i^H W; k_reorth_coef sums the chunk partials in FP64.
+constexpr int RCH = 256;
+__global__ void __launch_bounds__(256) k_reorth_dots_chunk(const double2 *W, long long dim, const float2 *Q32,
+                                                           long long qs, int j, float2 *partial, int nchunk,
+                                                           int ldp, const int *meff) {
+  __shared__ float2 ws[RCH];
+  const int chunk = blockIdx.x, p = blockIdx.y;
+  if (j >= meff[p]) return;
+  const long long e0 = (long long)chunk * RCH;
+  for (int t = threadIdx.x; t < RCH; t += blockDim.x) {
+    const long long e = e0 + t;
+    const double2 v = e < dim ? W[(long long)p * dim + e] : make_double2(0.0, 0.0);
+    ws[t] = make_float2((float)v.x, (float)v.y);
   }
-  for (; e < dim; e += 256) {
-    const float2 q = qi[e];
-    const float vx = (float)w[e].x, vy = (float)w[e].y;
-    sr[0] = fmaf(q.x, vx, fmaf(q.y, vy, sr[0]));
-    si[0] = fmaf(q.x, vy, fmaf(-q.y, vx, si[0]));
-  }
-  double dr = block_sum<256>((double)(sr[0] + sr[1]) + (double)(sr[2] + sr[3]), red);
   __syncthreads();
-  double di = block_sum<256>((double)(si[0] + si[1]) + (double)(si[2] + si[3]), red);
-  if (threadIdx.x == 0) coef[p * ldc + i] = make_double2(dr, di);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const float2 *qp = Q32 + p * qs + e0;
+  const bool full = e0 + RCH <= dim;
+  for (int i = warp; i <= j; i += 8) {
+    const float2 *qi = qp + (long long)i * dim;
+    float sr = 0.f, si = 0.f;
+#pragma unroll
+    for (int t = 0; t < RCH / 32; t++) {
+      const int l = lane + 32 * t;
+      if (full || e0 + l < dim) {
+        const float2 q = qi[l], w = ws[l];
+        sr = fmaf(q.x, w.x, fmaf(q.y, w.y, sr));
+        si = fmaf(q.x, w.y, fmaf(-q.y, w.x, si));
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) partial[((long long)p * nchunk + chunk) * ldp + i] = make_float2(sr, si);
+  }
+}
+
+__global__ void k_reorth_coef(const float2 *partial, int nchunk, int ldp, int j, double2 *coef, int ldc,
+                              const int *meff) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  if (j >= meff[p] || i > j) return;
+  double sr = 0.0, si = 0.0;
+  for (int c = 0; c < nchunk; c++) {
+    const float2 v = partial[((long long)p * nchunk + c) * ldp + i];
+    sr += v.x;
+    si += v.y;
+  }
+  coef[p * ldc + i] = make_double2(sr, si);
 }
 
 __global__ void k_reorth_update32(double2 *W, long long dim, const float2 *Q32, long long qs, int j,
@@ -911,6 +963,8 @@ struct LanczosScratch {
   float2 *hpart = nullptr; // Hermitian matvec partials [nb][nb][HT][n_pol]
   int nbt = 0;
   int2 *tiles = nullptr;    // upper-triangle tile list for the TMA matvec
+  float2 *rpart = nullptr;  // chunk partials of the reorthogonalisation projections
+  int nrch = 0;
   int ntiles = 0;
   CUtensorMap tmH;
   bool tma = false;
@@ -937,6 +991,12 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
     return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
   }
   s.nbt = (int)((dim + HT - 1) / HT);
+  s.nrch = (int)((dim + RCH - 1) / RCH);
+  if (c->precision != BSE_FP64 &&
+      cudaMallocAsync((void **)&s.rpart, sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1), st) != cudaSuccess) {
+    cudaGetLastError();
+    return bse_fail(c, BSE_ENOMEM, "spectrum: reorthogonalisation scratch allocation failed");
+  }
   if (c->precision != BSE_FP64 && dim % 2 == 0) {
     if (cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
       cudaGetLastError();
@@ -957,7 +1017,7 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
 }
 
 void lanczos_release(bse_ctx *c, LanczosScratch &s) {
-  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart, s.tiles};
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart, s.tiles, s.rpart};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -1039,7 +1099,10 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
       if (c64) {
-        k_reorth_dots32<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
+        k_reorth_dots_chunk<<<dim3(s.nrch, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart, s.nrch, ldab,
+                                                                 s.meff);
+        k_reorth_coef<<<dim3((j + 1 + 127) / 128, n_pol), 128, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab,
+                                                                        s.meff);
         k_reorth_update32<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
       } else {
         k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);

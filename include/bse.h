@@ -129,6 +129,25 @@ bse_status bse_spectrum(bse_ctx *ctx, const void *H, const double *u, int n_pol,
                         int n_steps, const double *omega, int n_w, double eta,
                         double prefactor, double *eps2, double *ab);
 
+/* Allocation-free variant of bse_spectrum, for callers that cannot allocate device memory:
+ * for example a host application that hands the library a slice of a device pool it owns
+ * and forbids driver allocations inside its callbacks, or code already holding the GPU at
+ * its memory limit, where the per-call Krylov allocation of bse_spectrum would fail.  The
+ * paper has no counterpart; it is a deployment variant of step (d).
+ * Arguments, results and errors are those of bse_spectrum.  The Krylov basis and every other
+ * scratch buffer live in one file-scope device array of 64 MiB (67108864 bytes) that each
+ * GPU loading the library keeps until the process exits; requests that need more (roughly
+ * n_pol * (n_steps + 1) * dim * 24 bytes plus the matvec partials) return BSE_EINVAL with the
+ * size in bse_last_error, before anything is enqueued.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  No call allocates or frees memory.  All calls
+ * share the one array and it keeps the last call's contents (every value the recursion
+ * reads is written by the same call first); calls that overlap on the GPU -- two streams or
+ * two contexts on one device at once -- race on it, so serialise them. */
+bse_status bse_spectrum_static(bse_ctx *ctx, const void *H, const double *u, int n_pol,
+                               int n_steps, const double *omega, int n_w, double eta,
+                               double prefactor, double *eps2, double *ab);
+
 /* Lowest Ritz values of H after n_steps (<= dim) Lanczos steps with full
  * reorthogonalisation from a fixed pseudo-random start vector (seed `seed`).
  *  omega_out : [n_eig] float64 ascending;  resid_out : optional [n_eig] float64

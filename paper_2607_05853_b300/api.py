@@ -146,6 +146,19 @@ class BSE:
                                            float(prefactor), e, abp), "bse_spectrum")
         return eps2
 
+    def spectrum_static(self, H: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor, eta: float,
+                        prefactor: float, eps2: torch.Tensor, ab: torch.Tensor | None = None):
+        """bse_spectrum_static: the spectrum without any device allocation (outputs supplied)."""
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        a = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        o = _dev(omega, torch.float64, "omega")
+        e = _dev(eps2, torch.float64, "eps2", omega.numel())
+        abp = _dev(ab, torch.float64, "ab", n_pol * 3 * n_steps) if ab is not None else None
+        self._check(self._lib.bse_spectrum_static(self._ctx, h, a, n_pol, int(n_steps), o, omega.numel(), float(eta),
+                                                  float(prefactor), e, abp), "bse_spectrum_static")
+        return eps2
+
     def lowest(self, H: torch.Tensor, n_eig: int, n_steps: int, seed: int = 12345):
         om = torch.empty(n_eig, dtype=torch.float64, device="cuda")
         rs = torch.empty(n_eig, dtype=torch.float64, device="cuda")

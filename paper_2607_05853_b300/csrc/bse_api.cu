@@ -336,6 +336,17 @@ bse_status bse_spectrum(bse_ctx *c, const void *H, const double *u, int n_pol, i
   return run_spectrum(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
 }
 
+bse_status bse_spectrum_static(bse_ctx *c, const void *H, const double *u, int n_pol, int n_steps,
+                               const double *omega, int n_w, double eta, double prefactor, double *eps2,
+                               double *ab) {
+  if (!c) return BSE_EINVAL;
+  if (!H || !u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum_static: null argument");
+  if (n_pol < 1 || n_pol > 3 || n_steps < 1 || n_steps > c->dim || n_w < 1 || !(eta > 0.0) ||
+      !std::isfinite(prefactor))
+    return bse_fail(c, BSE_EINVAL, "spectrum_static: bad size or parameter");
+  return run_spectrum_static(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
+}
+
 bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
                       double *omega_out, double *resid_out) {
   if (!c) return BSE_EINVAL;

@@ -101,6 +101,9 @@ bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, 
                         double *ab);
 bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
                       double *omega_out, double *resid_out);
+bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
+                               const double *omega, int n_w, double eta, double pref, double *eps2,
+                               double *ab);
 
 // split-precision path (k_split.cu)
 bse_status split_setup(bse_ctx *c);

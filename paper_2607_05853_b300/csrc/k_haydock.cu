@@ -9,6 +9,7 @@
 // the cross-lane sums, dots, norms, updates and the reorthogonalisation are FP64.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -1172,4 +1173,111 @@ bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_
   if (work) cudaFreeAsync(work, c->stream);
   lanczos_release(c, s);
   return r;
+}
+
+// ---- allocation-free variant of the spectrum (bse_spectrum_static) -------------------------
+// Its Lanczos scratch lives in one file-scope device array instead of per-call allocations.
+// Every GPU that loads the library holds this array until the process exits.
+constexpr size_t BSE_STATIC_SCRATCH_BYTES = (size_t)64 << 20;
+static __device__ __align__(256) unsigned char g_spectrum_scratch[BSE_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+void *g_static_addr[64] = {nullptr};
+
+// Device address of g_spectrum_scratch on the context's device, looked up once per device
+// with that device current.  In host code the array's name is only a host-side stand-in.
+bse_status static_scratch_base(bse_ctx *c, unsigned char **out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  const int dev = c->device;
+  if (dev < 0 || dev >= 64) return bse_fail(c, BSE_EINVAL, "spectrum_static: device index out of range");
+  if (!g_static_addr[dev]) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return bse_fail(c, BSE_ECUDA, "spectrum_static: cudaGetDevice failed");
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess)
+      return bse_fail(c, BSE_ECUDA, "spectrum_static: cannot make the context's device current");
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_spectrum_scratch);
+    if (cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p)
+      return bse_fail(c, BSE_ECUDA, std::string("spectrum_static: cudaGetSymbolAddress failed: ") +
+                                        cudaGetErrorString(e));
+    g_static_addr[dev] = p;
+  }
+  *out = static_cast<unsigned char *>(g_static_addr[dev]);
+  return BSE_OK;
+}
+
+// Lay the Lanczos scratch out in [base, base + bytes) (256-byte aligned pieces) and return the
+// bytes it needs; with base == nullptr only the size is computed.
+size_t carve_scratch(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, unsigned char *base) {
+  const long long dim = c->dim;
+  const bool c64 = c->precision != BSE_FP64;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char * {
+    off = (off + 255) & ~(size_t)255;
+    unsigned char *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t qn = (size_t)n_pol * (n_steps + 1) * dim;
+  s.Q = (double2 *)take(sizeof(double2) * qn);
+  s.W = (double2 *)take(sizeof(double2) * n_pol * dim);
+  s.coef = (double2 *)take(sizeof(double2) * n_pol * (n_steps + 1));
+  s.a = (double *)take(sizeof(double) * n_pol * (n_steps + 1));
+  s.b = (double *)take(sizeof(double) * n_pol * (n_steps + 1));
+  s.beta0 = (double *)take(sizeof(double) * n_pol);
+  s.hmax = (double *)take(sizeof(double));
+  s.part = (double *)take(sizeof(double) * 1024);
+  s.meff = (int *)take(sizeof(int) * n_pol);
+  s.nbt = (int)((dim + HT - 1) / HT);
+  s.nrch = (int)((dim + RCH - 1) / RCH);
+  s.Q32 = c64 ? (float2 *)take(sizeof(float2) * qn) : nullptr;
+  s.rpart = c64 ? (float2 *)take(sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1)) : nullptr;
+  s.ntiles = s.nbt * (s.nbt + 1) / 2;
+  if (c64 && dim % 2 == 0) {
+    s.hpart = (float2 *)take(sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol);
+    s.tiles = (int2 *)take(sizeof(int2) * (size_t)s.ntiles);
+  } else {
+    s.hpart = nullptr;
+    s.tiles = nullptr;
+  }
+  return off;
+}
+}  // namespace
+
+bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
+                               const double *omega, int n_w, double eta, double pref, double *eps2, double *ab) {
+  LanczosScratch sz;
+  const size_t need = carve_scratch(c, sz, n_pol, n_steps, nullptr);
+  if (need > BSE_STATIC_SCRATCH_BYTES)
+    return bse_fail(c, BSE_EINVAL,
+                    "spectrum_static: needs " + std::to_string(need) + " bytes of scratch, the static array holds " +
+                        std::to_string(BSE_STATIC_SCRATCH_BYTES) + " (reduce n_steps, n_pol or dim)");
+  unsigned char *base = nullptr;
+  bse_status r = static_scratch_base(c, &base);
+  if (r != BSE_OK) return r;
+  LanczosScratch s;
+  carve_scratch(c, s, n_pol, n_steps, base);
+  if (s.tiles) {
+    std::vector<int2> tl;
+    tl.reserve(s.ntiles);
+    for (int bi = 0; bi < s.nbt; bi++)
+      for (int bj = bi; bj < s.nbt; bj++) tl.push_back(make_int2(bi, bj));
+    if (cudaMemcpyAsync(s.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return bse_fail(c, BSE_ECUDA, "spectrum_static: tile list upload failed");
+  }
+  r = lanczos_run(c, s, H, u, n_pol, n_steps);
+  if (r != BSE_OK) return r;
+  k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega, n_w, eta,
+                                                       pref, eps2);
+  bse_count_launch();
+  if (ab) {
+    k_pack_ab<<<dim3((n_steps + 127) / 128, n_pol), 128, 0, c->stream>>>(s.a, s.b, s.beta0, n_steps + 1, n_pol,
+                                                                        n_steps, ab);
+    bse_count_launch();
+  }
+  return bse_check_launch(c, "spectrum_static");
 }

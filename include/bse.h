@@ -149,11 +149,29 @@ bse_status bse_spectrum_static(bse_ctx *ctx, const void *H, const double *u, int
                                double prefactor, double *eps2, double *ab);
 
 /* Lowest Ritz values of H after n_steps (<= dim) Lanczos steps with full
- * reorthogonalisation from a fixed pseudo-random start vector (seed `seed`).
+ * reorthogonalisation from a fixed pseudo-random start vector (seed `seed`); the TDA
+ * eigenvalues Omega_S of §II.C for the converged pairs.
  *  omega_out : [n_eig] float64 ascending;  resid_out : optional [n_eig] float64
- *  receiving |b_m * s_m,i| (the Lanczos residual norm of each Ritz pair), or NULL. */
+ *  receiving |b_m * s_m,i| (the Lanczos residual norm of each Ritz pair), or NULL;
+ *  vecs_out : optional [n_eig][dim] complex128 receiving the unit Ritz vectors, or NULL. */
 bse_status bse_lowest(bse_ctx *ctx, const void *H, int n_eig, int n_steps, uint64_t seed,
-                      double *omega_out, double *resid_out);
+                      double *omega_out, double *resid_out, double *vecs_out);
+
+/* Adjoint seed Gamma = sum_s g[s] x_s x_s^dagger (Hermitian, [dim][dim] complex128), so that
+ * for L = sum_s g_s Omega_s the Hellmann-Feynman theorem gives dL = tr(Gamma dH).
+ *  vecs : [r][dim] complex128 (e.g. Ritz vectors from bse_lowest);  g : [r] float64. */
+bse_status bse_adjoint_seed(bse_ctx *ctx, const double *vecs, const double *g, int r, double *Gamma);
+
+/* Gradient of a scalar L with dL = tr(Gamma dH) through the assembly (Eq. Hamiltonian with
+ * the kernels of Eq. W_LRI), FP64 throughout; the pair projections are recomputed per q-slab.
+ *  Gamma : [dim][dim] complex128 Hermitian seed.
+ *  dW_R  : [n_RW][N_aux][N_aux] float64, dL/dW_mu,nu(R) = w_R Re sum_q e^{-iq.R} dL/dW(q)_mu,nu
+ *          (a perturbation of the symmetric pair W_mu,nu(R), W_nu,mu(-R) moves L by the sum of
+ *          the two entries);
+ *  de_qp : [N_k][nv+nc] float64, dL/dE^QP of each window band at each k.
+ * Needs interp_W and project_pairs first; the first call allocates the adjoint workspace
+ * (N_k N_aux^2 complex128 plus one q-slab of projections). */
+bse_status bse_adjoint(bse_ctx *ctx, const double *Gamma, double *dW_R, double *de_qp);
 
 /* Wait for the context's stream, then read and clear the device error word. */
 bse_status bse_sync(bse_ctx *ctx);

@@ -35,6 +35,7 @@ import numpy as np
 __all__ = [
     "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
     "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
+    "adjoint_seed_lowest", "grad_from_seed",
 ]
 
 TWO_PI = 2.0 * np.pi
@@ -241,3 +242,44 @@ def lowest_excitons(H, n):
 def binding_energy(e_qp, nv, omega1):
     """E_B = min_k (E^QP_ck - E^QP_vk) - Omega_1 over the band edges (§IV, exciton binding)."""
     return float(np.min(e_qp[:, nv] - e_qp[:, 0]) - omega1)
+
+
+# ---------------------------------------------------------------------------- gradients
+def adjoint_seed_lowest(H, n):
+    """Eigenpairs (Omega_S, x_S) of the n lowest excitons and the Hellmann-Feynman seeds
+    Gamma_S = x_S x_S^dagger, so that dOmega_S = tr(Gamma_S dH) for a Hermitian dH."""
+    w, X = np.linalg.eigh(H)
+    return w[:n], X[:, :n]
+
+
+def grad_from_seed(orc, Gamma):
+    """dL/dW(R) and dL/dE^QP for dL = tr(Gamma dH) (Gamma Hermitian, e.g. x x^dagger).
+
+    H depends on W only through the direct term -(1/N_k) sum M_vv W(q) M_cc (Eq. W_LRI), with
+    W(q) = sum_R w_R W(R) e^{-i q.R}; the gradient with respect to one real entry W_mu,nu(R)
+    is Re tr(Gamma dH/dW_mu,nu(R)) (the symmetric pair W_mu,nu(R), W_nu,mu(-R) together moves
+    the energy by twice this).  E^QP enters only the diagonal (Eq. Hamiltonian):
+    dL/dE^QP_ak = sum_i Gamma_(k,i,a),(k,i,a), dL/dE^QP_ik = -sum_a Gamma_(k,i,a),(k,i,a).
+    Returns (dW_R [n_RW][N_aux][N_aux], de_qp [N_k][Nv+Nc])."""
+    inp = orc.inp
+    nk, nv, nc, nvc = orc.nk, orc.nv, orc.nc, orc.nvc
+    naux = inp["W_R"].shape[1]
+    Aq = np.zeros((nk, naux, naux), np.complex128)
+    for k1 in range(nk):
+        for k2 in range(nk):
+            iq = orc.q_index(k1, k2)
+            Mv, Mc = orc.M_vv(k1, k2), orc.M_cc(k1, k2)          # [mu, j, i], [nu, a, b]
+            # Gamma block with rows (k2, j, b) and columns (k1, i, a)
+            G = Gamma[k2 * nvc:(k2 + 1) * nvc, k1 * nvc:(k1 + 1) * nvc].reshape(nv, nc, nv, nc)  # [j,b,i,a]
+            Aq[iq] += -np.einsum("uji,jbia,vab->uv", Mv, G, Mc, optimize=True) / nk
+    # adjoint of W(q) = sum_R w_R W(R) e^{-i q.R}
+    n1, n2, n3 = orc.mesh
+    qint = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1).reshape(-1, 3)
+    qfrac = qint / orc.mesh
+    ph = np.exp(-1j * TWO_PI * (qfrac @ inp["R_W"].astype(np.float64).T))            # [q, R]
+    dW = np.real(np.einsum("qr,quv->ruv", ph, Aq)) * inp["w_RW"][:, None, None]
+    d = np.real(np.diag(Gamma)).reshape(nk, nv, nc)
+    de = np.zeros((nk, nv + nc))
+    de[:, nv:] = d.sum(axis=1)
+    de[:, :nv] = -d.sum(axis=2)
+    return dW, de

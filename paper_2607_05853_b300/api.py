@@ -159,13 +159,36 @@ class BSE:
                                                   float(prefactor), e, abp), "bse_spectrum_static")
         return eps2
 
-    def lowest(self, H: torch.Tensor, n_eig: int, n_steps: int, seed: int = 12345):
+    def lowest(self, H: torch.Tensor, n_eig: int, n_steps: int, seed: int = 12345, vectors: bool = False):
         om = torch.empty(n_eig, dtype=torch.float64, device="cuda")
         rs = torch.empty(n_eig, dtype=torch.float64, device="cuda")
+        vec = torch.empty((n_eig, self.dim), dtype=torch.complex128, device="cuda") if vectors else None
         h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
         self._check(self._lib.bse_lowest(self._ctx, h, int(n_eig), int(n_steps), ctypes.c_uint64(seed),
-                                         om.data_ptr(), rs.data_ptr()), "bse_lowest")
-        return om, rs
+                                         om.data_ptr(), rs.data_ptr(), vec.data_ptr() if vectors else None),
+                    "bse_lowest")
+        return (om, rs, vec) if vectors else (om, rs)
+
+    def adjoint_seed(self, vecs: torch.Tensor, g: torch.Tensor, Gamma: torch.Tensor | None = None):
+        r = vecs.shape[0]
+        if Gamma is None:
+            Gamma = torch.empty((self.dim, self.dim), dtype=torch.complex128, device="cuda")
+        a = _dev(vecs, torch.complex128, "vecs", r * self.dim)
+        b = _dev(g, torch.float64, "g", r)
+        c = _dev(Gamma, torch.complex128, "Gamma", self.dim * self.dim)
+        self._check(self._lib.bse_adjoint_seed(self._ctx, a, b, int(r), c), "bse_adjoint_seed")
+        return Gamma
+
+    def adjoint(self, Gamma: torch.Tensor, dW_R: torch.Tensor | None = None, de_qp: torch.Tensor | None = None):
+        if dW_R is None:
+            dW_R = torch.empty((self.n_RW, self.naux, self.naux), dtype=torch.float64, device="cuda")
+        if de_qp is None:
+            de_qp = torch.empty((self.nk, self.nb), dtype=torch.float64, device="cuda")
+        a = _dev(Gamma, torch.complex128, "Gamma", self.dim * self.dim)
+        b = _dev(dW_R, torch.float64, "dW_R", self.n_RW * self.naux * self.naux)
+        c = _dev(de_qp, torch.float64, "de_qp", self.nk * self.nb)
+        self._check(self._lib.bse_adjoint(self._ctx, a, b, c), "bse_adjoint")
+        return dW_R, de_qp
 
     def profile(self, enable: bool = True):
         self._check(self._lib.bse_profile(self._ctx, int(enable)), "bse_profile")

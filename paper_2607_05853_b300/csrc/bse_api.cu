@@ -94,7 +94,7 @@ static void release(bse_ctx *c) {
   prof_collect(c);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   c->pool.clear();
-  void *ptrs[] = {c->d_qplus, c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
+  void *ptrs[] = {c->d_qplus, c->d_qall, c->Aq, c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
                   c->d_aux_start, c->d_naux, c->d_err, c->Wq, c->V0c, c->Y, c->ck,
                   c->eqp, c->X, c->P, c->Mv, c->Mc, c->T};
   for (void *p : ptrs)
@@ -204,6 +204,11 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
     TRY(upload(c, &c->d_aux_start, c->aux_start));
     TRY(upload(c, &c->d_naux, c->naux));
     TRY(upload(c, &c->d_qplus, c->qplus));
+    {
+      std::vector<int> qall(c->nk);
+      for (int q = 0; q < c->nk; q++) qall[q] = q;
+      TRY(upload(c, &c->d_qall, qall));
+    }
     TRY(dalloc(c, &c->d_err, 1));
     const size_t nn = (size_t)naux_tot * naux_tot;
     TRY(dalloc(c, &c->V0c, nn));
@@ -308,7 +313,7 @@ bse_status bse_assemble(bse_ctx *c, void *H) {
   const int nqp = (int)c->qplus.size();
   for (int q0 = 0; q0 < nqp; q0 += c->slab) {
     const int nq = std::min(c->slab, nqp - q0);
-    bse_status s = launch_project_slab_fp64(c, q0, nq);
+    bse_status s = launch_project_slab_fp64(c, q0, nq, c->d_qplus);
     if (s != BSE_OK) return s;
     s = launch_zgemm_fp64(c, (int)rows, na, na, c->Mv, na, rows * na, c->Wq, na, (long long)na * na, c->T, na,
                           rows * na, nq, BSE_KP_G1, c->d_qplus + q0);
@@ -348,12 +353,25 @@ bse_status bse_spectrum_static(bse_ctx *c, const void *H, const double *u, int n
 }
 
 bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
-                      double *omega_out, double *resid_out) {
+                      double *omega_out, double *resid_out, double *vecs_out) {
   if (!c) return BSE_EINVAL;
   if (!H || !omega_out) return bse_fail(c, BSE_EINVAL, "lowest: null argument");
   if (n_steps < 1 || n_steps > c->dim || n_eig < 1 || n_eig > n_steps)
     return bse_fail(c, BSE_EINVAL, "lowest: bad size");
-  return run_lowest(c, H, n_eig, n_steps, seed, omega_out, resid_out);
+  return run_lowest(c, H, n_eig, n_steps, seed, omega_out, resid_out, (double2 *)vecs_out);
+}
+
+bse_status bse_adjoint_seed(bse_ctx *c, const double *vecs, const double *g, int r, double *Gamma) {
+  if (!c) return BSE_EINVAL;
+  if (!vecs || !g || !Gamma || r < 1) return bse_fail(c, BSE_EINVAL, "adjoint_seed: bad argument");
+  return run_seed_lowrank(c, (const double2 *)vecs, g, r, (double2 *)Gamma);
+}
+
+bse_status bse_adjoint(bse_ctx *c, const double *Gamma, double *dW_R, double *de_qp) {
+  if (!c) return BSE_EINVAL;
+  if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "adjoint before project_pairs");
+  if (!Gamma || !dW_R || !de_qp) return bse_fail(c, BSE_EINVAL, "adjoint: null argument");
+  return run_adjoint(c, (const double2 *)Gamma, dW_R, de_qp);
 }
 
 bse_status bse_sync(bse_ctx *c) {

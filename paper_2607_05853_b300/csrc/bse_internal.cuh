@@ -60,6 +60,8 @@ struct bse_ctx {
   // pair is computed (self-conjugate q, every component 0 or N/2, are computed whole).
   std::vector<int> qplus;
   int *d_qplus = nullptr;
+  int *d_qall = nullptr;   // 0 .. N_k-1 (every transfer, for the adjoint)
+  double2 *Aq = nullptr;   // [nk][naux][naux] dL/dW(q) (adjoint workspace, allocated on first use)
   double2 *Mv = nullptr, *Mc = nullptr, *T = nullptr;  // [slab][nk][nv*nv | nc*nc][naux]
 
   // split-precision workspace (tensor-core path)
@@ -91,7 +93,7 @@ bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, 
                              long long sA, const double2 *B, int ldb, long long sB, double2 *C,
                              int ldc, long long sC, int batch, int prof_id = -1,
                              const int *bidx = nullptr);
-bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq);
+bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist);
 bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H);
 
 // spectrum (k_haydock.cu)
@@ -100,7 +102,10 @@ bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, 
                         const double *omega, int n_w, double eta, double pref, double *eps2,
                         double *ab);
 bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
-                      double *omega_out, double *resid_out);
+                      double *omega_out, double *resid_out, double2 *vecs_out);
+// adjoint (k_adjoint.cu)
+bse_status run_adjoint(bse_ctx *c, const double2 *Gamma, double *dW_R, double *de_qp);
+bse_status run_seed_lowrank(bse_ctx *c, const double2 *X, const double *g, int r, double2 *Gamma);
 bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
                                const double *omega, int n_w, double eta, double pref, double *eps2,
                                double *ab);

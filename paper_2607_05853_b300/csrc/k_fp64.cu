@@ -413,7 +413,7 @@ bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, 
   return bse_check_launch(c, "zgemm");
 }
 
-bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq) {
+bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist) {
   const int nchunk = (c->naux_tot + 127) / 128;
   dim3 grid(nchunk * (c->nv + c->nc), c->nk, nq);
   size_t sm = sizeof(double2) * 2 * c->nao_tot * c->nb;
@@ -422,7 +422,7 @@ bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq) {
   k_project_slab<<<grid, 128, sm, c->stream>>>(c->Y, c->ck, c->nao_tot, c->nb, c->nv, c->nc,
                                                c->naux_tot, c->nao_max, c->d_aux_atom, c->d_ao_start,
                                                c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], q0,
-                                               c->d_qplus, c->Mv, c->Mc);
+                                               qlist, c->Mv, c->Mc);
   bse_prof_end(c, BSE_KP_PROJECT);
   bse_count_launch();
   return bse_check_launch(c, "project_slab");

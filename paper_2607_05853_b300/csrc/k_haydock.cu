@@ -1148,8 +1148,29 @@ bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, 
   return r;
 }
 
+// y[e][x] = sum_l v_e[l] Q[l][x]: Ritz vectors from the tridiagonal eigenvectors v_e (stored
+// in work[e*3m .. e*3m+m)) and the Krylov basis of the first start vector.
+__global__ void k_ritz_vectors(const double *work, const int *meff, int n_eig, const double2 *Q, long long dim,
+                               double2 *Y) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= dim) return;
+  const int m = meff[0];
+  for (int e = 0; e < n_eig; e++) {
+    double2 acc = make_double2(0.0, 0.0);
+    if (e < m) {
+      const double *v = work + (long long)e * 3 * m;
+      for (int l = 0; l < m; l++) {
+        const double2 q = Q[(long long)l * dim + x];
+        acc.x += v[l] * q.x;
+        acc.y += v[l] * q.y;
+      }
+    }
+    Y[(long long)e * dim + x] = acc;
+  }
+}
+
 bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed, double *omega_out,
-                      double *resid_out) {
+                      double *resid_out, double2 *vecs_out) {
   LanczosScratch s;
   double2 *u = nullptr;
   double *work = nullptr;
@@ -1165,9 +1186,24 @@ bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_
     r = lanczos_run(c, s, H, u, 1, n_steps);
   }
   if (r == BSE_OK) {
-    k_ritz<<<(n_eig + 31) / 32, 32, 0, c->stream>>>(s.a, s.b, s.meff, n_eig, omega_out, resid_out, work);
-    bse_count_launch();
-    r = bse_check_launch(c, "ritz");
+    // the residual pass also leaves the tridiagonal eigenvectors in work, which the Ritz
+    // vectors need; use a scratch residual array when the caller passed none
+    double *res = resid_out;
+    if (!res && vecs_out && cudaMallocAsync((void **)&res, sizeof(double) * n_eig, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      r = bse_fail(c, BSE_ENOMEM, "lowest: scratch allocation failed");
+    }
+    if (r == BSE_OK) {
+      k_ritz<<<(n_eig + 31) / 32, 32, 0, c->stream>>>(s.a, s.b, s.meff, n_eig, omega_out, res, work);
+      bse_count_launch();
+      if (vecs_out) {
+        k_ritz_vectors<<<(unsigned)((c->dim + 255) / 256), 256, 0, c->stream>>>(work, s.meff, n_eig, s.Q, c->dim,
+                                                                                vecs_out);
+        bse_count_launch();
+      }
+      r = bse_check_launch(c, "ritz");
+    }
+    if (res && res != resid_out) cudaFreeAsync(res, c->stream);
   }
   if (u) cudaFreeAsync(u, c->stream);
   if (work) cudaFreeAsync(work, c->stream);

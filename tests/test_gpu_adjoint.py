@@ -1,0 +1,134 @@
+"""GPU adjoint (gradients of the lowest exciton energies with respect to W(R) and the
+quasiparticle energies) against the FP64 oracle's Hellmann-Feynman gradient, central
+differences of the GPU forward, and the shift sum rules."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth import config_spec, make_inputs
+
+from helpers import gpu_hamiltonian, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    inp = make_inputs(config_spec(0))
+    orc = O.BSEOracle(inp)
+    H = orc.hamiltonian()
+    w, X = O.adjoint_seed_lowest(H, 3)
+    return inp, orc, w, X
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_adjoint_fp64_matches_oracle(cfg0):
+    import torch
+    inp, orc, w, X = cfg0
+    b, d, H, _ = gpu_hamiltonian(inp, precision="fp64")
+    om, rs, vec = b.lowest(H, 3, 400, vectors=True)
+    g = torch.tensor([1.0, 0.0, 0.0], dtype=torch.float64, device="cuda")
+    Gamma = b.adjoint_seed(vec[:1].contiguous(), g[:1].contiguous())
+    dW, de = b.adjoint(Gamma)
+    b.sync()
+    ref_dW, ref_de = O.grad_from_seed(orc, np.outer(X[:, 0], X[:, 0].conj()))
+    assert abs(om[0].item() - w[0]) <= 1e-10
+    assert _rel(dW.cpu().numpy(), ref_dW) <= 1e-8
+    assert _rel(de.cpu().numpy(), ref_de) <= 1e-8
+    de = de.cpu().numpy()
+    assert np.isclose(de[:, 4:].sum(), 1.0, atol=1e-10) and np.isclose(de[:, :4].sum(), -1.0, atol=1e-10)
+
+
+def test_autograd_function_backward(cfg0):
+    import torch
+    from paper_2607_05853_b300.api import BSE
+    from paper_2607_05853_b300.grad import ExcitonEnergies
+    inp, orc, w, X = cfg0
+    b = BSE.from_inputs(inp, precision="fp64")
+    d = to_dev(inp)
+    W = d["W_R"].clone().requires_grad_(True)
+    e = d["e_qp"].clone().requires_grad_(True)
+    om, rs = ExcitonEnergies.apply(W, e, b, d, 3, 400, 12345)
+    loss = om[0] + 0.5 * om[1] - 0.25 * om[2]
+    loss.backward()
+    G = (np.outer(X[:, 0], X[:, 0].conj()) + 0.5 * np.outer(X[:, 1], X[:, 1].conj())
+         - 0.25 * np.outer(X[:, 2], X[:, 2].conj()))
+    ref_dW, ref_de = O.grad_from_seed(orc, G)
+    assert _rel(W.grad.cpu().numpy(), ref_dW) <= 1e-8
+    assert _rel(e.grad.cpu().numpy(), ref_de) <= 1e-8
+
+
+def test_adjoint_against_gpu_central_differences(cfg0):
+    """Central differences (step 1e-5) of the GPU FP64 forward on symmetric W(R) pairs."""
+    import torch
+    inp, orc, w, X = cfg0
+    b, d, H, _ = gpu_hamiltonian(inp, precision="fp64")
+    om, rs, vec = b.lowest(H, 1, 400, vectors=True)
+    dW, de = b.adjoint(b.adjoint_seed(vec, torch.ones(1, dtype=torch.float64, device="cuda")))
+    dW = dW.cpu().numpy()
+    RW = inp["R_W"]
+    rng = np.random.default_rng(3)
+    eps = 1e-5
+
+    def lowest(WR):
+        b.interp_W(torch.from_numpy(WR).cuda(), d["V0"])
+        b.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+        Hp = b.assemble()
+        o, _ = b.lowest(Hp, 1, 400)
+        return o.item()
+    for _ in range(4):
+        r, m, n = int(rng.integers(len(RW))), int(rng.integers(40)), int(rng.integers(40))
+        rp = [i for i in range(len(RW)) if np.all(RW[i] == -RW[r])][0]
+        single = rp == r and m == n
+        vals = []
+        for s in (eps, -eps):
+            WR = inp["W_R"].copy()
+            WR[r, m, n] += s
+            if not single:
+                WR[rp, n, m] += s
+            vals.append(lowest(WR))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        an = dW[r, m, n] + (0.0 if single else dW[rp, n, m])
+        assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-2), (r, m, n, fd, an)
+
+
+def test_split_forward_gradient_close_to_fp64(cfg0):
+    """bf16x3 forward (complex64 H, its Ritz vectors) with the FP64 adjoint vs the FP64 path."""
+    import torch
+    inp, orc, w, X = cfg0
+    ref_dW, ref_de = O.grad_from_seed(orc, np.outer(X[:, 0], X[:, 0].conj()))
+    b, d, H, _ = gpu_hamiltonian(inp, precision="bf16x3")
+    om, rs, vec = b.lowest(H, 1, 400, vectors=True)
+    dW, de = b.adjoint(b.adjoint_seed(vec, torch.ones(1, dtype=torch.float64, device="cuda")))
+    b.sync()
+    assert abs(om[0].item() - w[0]) <= 1e-3
+    assert np.linalg.norm(dW.cpu().numpy() - ref_dW) <= 1e-3 * np.linalg.norm(ref_dW)
+    assert np.linalg.norm(de.cpu().numpy() - ref_de) <= 1e-3 * np.linalg.norm(ref_de)
+
+
+@pytest.mark.slow
+def test_monolayer_gradient_full_size():
+    """The 3600-dim monolayer workload (900 k, N_aux 240): lowest-4 gradients from the split
+    forward and from the FP64 forward agree; shift sum rules hold; timing is printed."""
+    import time
+    import torch
+    inp = make_inputs(config_spec(4))
+    out = {}
+    for prec in ("fp64", "bf16x3"):
+        b, d, H, _ = gpu_hamiltonian(inp, precision=prec)
+        om, rs, vec = b.lowest(H, 4, 300, vectors=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dW, de = b.adjoint(b.adjoint_seed(vec, torch.ones(4, dtype=torch.float64, device="cuda")))
+        b.sync()
+        out[prec] = (om.cpu().numpy(), dW.cpu().numpy(), de.cpu().numpy(), time.perf_counter() - t0)
+        del H
+        b.close()
+    (o64, w64, e64, t64), (o32, w32, e32, t32) = out["fp64"], out["bf16x3"]
+    print(f"monolayer gradient: fp64 forward {t64:.2f} s, split forward {t32:.2f} s (adjoint time)")
+    assert np.abs(o64 - o32).max() <= 1e-3
+    assert np.isclose(e64[:, 2:].sum(), 4.0, atol=1e-8) and np.isclose(e64[:, :2].sum(), -4.0, atol=1e-8)
+    assert np.linalg.norm(w32 - w64) <= 1e-3 * np.linalg.norm(w64)

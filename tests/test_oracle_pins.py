@@ -275,3 +275,78 @@ def test_planted_oracle_mistake_is_caught(mistake, monkeypatch):
         monkeypatch.setattr(mod.BSEOracle, "direct", lambda self, k1, k2: orig_d(self, k1, k2) * self.nk)
     bad = O.BSEOracle(inp)
     assert _brute_error(inp, bad) > 1e-6
+
+
+# ---------------------------------------------------------------- a8 gradients
+def _grad_setup():
+    spec = CrystalSpec("g", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25]]), (3, 4), (7, 6), (3, 1, 1),
+                       (3, 2, 1), 2, 2, 5151, k_offset=(0.1, 0.2, 0.0), r_max=1.0, s_W=0.3, s_V=0.1)
+    inp = make_inputs(spec)
+    orc = O.BSEOracle(inp)
+    H = orc.hamiltonian()
+    w, X = O.adjoint_seed_lowest(H, 2)
+    return inp, orc, w, X
+
+
+def _lowest_after(inp, key, change):
+    d = dict(inp)
+    d[key] = change(inp[key].copy())
+    return np.linalg.eigvalsh(O.BSEOracle(d).hamiltonian())[0]
+
+
+def _pair(RW, r):
+    return [i for i in range(len(RW)) if np.all(RW[i] == -RW[r])][0]
+
+
+def test_gradient_matches_central_differences():
+    """Hellmann-Feynman gradient of the lowest exciton against central differences of
+    LAPACK eigenvalues: symmetric W(R) pairs (keeping H Hermitian) and single E^QP entries."""
+    inp, orc, w, X = _grad_setup()
+    dW, de = O.grad_from_seed(orc, np.outer(X[:, 0], X[:, 0].conj()))
+    RW, eps = inp["R_W"], 1e-6
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        r, m, n = int(rng.integers(len(RW))), int(rng.integers(13)), int(rng.integers(13))
+        rp = _pair(RW, r)
+        single = rp == r and m == n
+
+        def bump(s):
+            def f(W):
+                W[r, m, n] += s
+                if not single:
+                    W[rp, n, m] += s
+                return W
+            return f
+        fd = (_lowest_after(inp, "W_R", bump(eps)) - _lowest_after(inp, "W_R", bump(-eps))) / (2 * eps)
+        an = dW[r, m, n] + (0.0 if single else dW[rp, n, m])
+        assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-3), (r, m, n, fd, an)
+    for (k, n) in [(1, 2), (4, 0), (5, 3)]:
+        def shift(s):
+            def f(e):
+                e[k, n] += s
+                return e
+            return f
+        fd = (_lowest_after(inp, "e_qp", shift(eps)) - _lowest_after(inp, "e_qp", shift(-eps))) / (2 * eps)
+        assert abs(fd - de[k, n]) <= 1e-6, (k, n, fd, de[k, n])
+
+
+def test_gradient_shift_sum_rules():
+    """A uniform conduction (valence) shift moves the exciton by +1 (-1) times the shift."""
+    inp, orc, w, X = _grad_setup()
+    for s in range(2):
+        dW, de = O.grad_from_seed(orc, np.outer(X[:, s], X[:, s].conj()))
+        assert np.isclose(de[:, 2:].sum(), 1.0, atol=1e-12)
+        assert np.isclose(de[:, :2].sum(), -1.0, atol=1e-12)
+
+
+def test_gradient_euler_identity():
+    """The direct term is linear in W: sum_R,mu,nu W(R) dOmega/dW(R) = x^dagger (-direct) x."""
+    inp, orc, w, X = _grad_setup()
+    x = X[:, 0]
+    dW, _ = O.grad_from_seed(orc, np.outer(x, x.conj()))
+    direct = np.zeros((orc.dim, orc.dim), np.complex128)
+    n = orc.nvc
+    for k1 in range(orc.nk):
+        for k2 in range(orc.nk):
+            direct[k1 * n:(k1 + 1) * n, k2 * n:(k2 + 1) * n] = -orc.direct(k1, k2).reshape(n, n)
+    assert np.isclose(np.sum(inp["W_R"] * dW), np.vdot(x, direct @ x).real, rtol=1e-10)

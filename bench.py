@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
     ap.add_argument("--mesh", type=int, default=0, help="override the dense mesh N x N x N (profiling captures)")
+    ap.add_argument("--batch16", action="store_true",
+                    help="add the 16-uneven-crystal batch (one CUDA graph) report under 'batched_uneven'")
     return ap.parse_args()
 
 
@@ -363,6 +365,10 @@ def main():
         "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
     }
     result.update(extra)
+    if args.batch16:
+        del H
+        torch.cuda.empty_cache()
+        result["batched_uneven"] = batch16_report()
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(inp, args.cpu_seconds)
     if rank == 0:
@@ -373,6 +379,61 @@ def main():
 
 def ctx_slab_q(ctx, spec):
     return 1
+
+
+def batch16_report(precision="bf16x3"):
+    """16 seeded crystals of uneven size assembled as one CUDA graph: per-system throughput
+    inside the batch, the isolated throughput of each system, aggregate speedup over running
+    them one after another, and Jain's fairness index of (batched / isolated) throughput."""
+    import torch
+    from paper_2607_05853_b300.api import BSE, batch_assemble, batch_release
+    from synth import batched_specs, make_inputs
+    systems, Hs, dims, tiles = [], [], [], []
+    for sp in batched_specs(16):
+        inp = make_inputs(sp)
+        b = BSE.from_inputs(inp, precision=precision)
+        d = {k: torch.from_numpy(np.ascontiguousarray(inp[k])).cuda() for k in ("W_R", "V0", "C_R", "e_qp", "c_k")}
+        b.interp_W(d["W_R"], d["V0"])
+        b.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+        tiles.append(b.autotune())
+        systems.append(b)
+        Hs.append(torch.empty((b.dim, b.dim), dtype=b.h_dtype, device="cuda"))
+        dims.append(b.dim)
+        del d
+    st = torch.cuda.current_stream()
+    iso = []
+    for b, H in zip(systems, Hs):
+        b.assemble(H)  # warm
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        b.assemble(H)
+        e.record(st)
+        torch.cuda.synchronize()
+        iso.append(a.elapsed_time(e))
+    batch_assemble(systems, Hs)  # build + first replay
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    batch_assemble(systems, Hs)
+    e.record(st)
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(e)
+    stamps = batch_assemble(systems, Hs, stamps=True)
+    done_ms = [x / 1e6 for x in stamps]
+    x = [t_i / max(c_i, 1e-9) for t_i, c_i in zip(iso, done_ms)]   # batched / isolated throughput
+    jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
+    el = [float(dm) ** 2 for dm in dims]
+    out = {"systems": 16, "precision": precision, "graph_ms": t_batch, "serial_ms": sum(iso),
+           "aggregate_elements_per_s": sum(el) / (t_batch / 1e3),
+           "serial_elements_per_s": sum(el) / (sum(iso) / 1e3),
+           "batch_speedup_over_serial": sum(iso) / t_batch, "jain_fairness": jain,
+           "per_system": [{"dim": dm, "tile": tl, "isolated_ms": round(ti, 3), "done_in_batch_ms": round(c, 3),
+                           "elements_per_s_isolated": e2 / (ti / 1e3)}
+                          for dm, tl, ti, c, e2 in zip(dims, tiles, iso, done_ms, el)]}
+    batch_release()
+    for b in systems:
+        b.close()
+    return out
 
 
 if __name__ == "__main__":

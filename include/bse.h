@@ -173,6 +173,24 @@ bse_status bse_adjoint_seed(bse_ctx *ctx, const double *vecs, const double *g, i
  * (N_k N_aux^2 complex128 plus one q-slab of projections). */
 bse_status bse_adjoint(bse_ctx *ctx, const double *Gamma, double *dW_R, double *de_qp);
 
+/* Batching of several crystals (one context each, every one past bse_project_pairs): their
+ * assemblies run as one CUDA graph, a branch per context forked from and joined into
+ * `cuda_stream`, so the GPU interleaves systems of uneven size and the host issues one
+ * launch.  The first call for a given list of (context, H) runs each assembly once eagerly,
+ * then captures and instantiates the graph; later calls with the same list replay it.
+ *  H : [n] device pointers as in bse_assemble;  stamps_ns : optional host [n] receiving, for
+ *  each system, the nanoseconds from the start of this replay to the end of its branch
+ *  (the call then waits for the stream), or NULL.  Contexts must not be freed while a graph
+ *  that uses them is cached; bse_batch_release drops every cached graph. */
+bse_status bse_batch_assemble(bse_ctx **ctxs, void **H, int n, void *cuda_stream, int64_t *stamps_ns);
+void bse_batch_release(void);
+
+/* Autotuner: times the tensor-core GEMM of one q-slab (T = M_vv W(q)) for each candidate
+ * N tile (64, 96, 128, 160 columns), keeps the fastest for this context and reports it in
+ * *chosen_tile (0 for BSE_FP64, which has no tensor-core GEMM).  Results are cached per shape
+ * (N_aux, rows per q, q per slab, pieces) for the life of the process.  Synchronous. */
+bse_status bse_autotune(bse_ctx *ctx, int *chosen_tile);
+
 /* Wait for the context's stream, then read and clear the device error word. */
 bse_status bse_sync(bse_ctx *ctx);
 

@@ -13,7 +13,7 @@ import torch
 
 from . import _lib
 
-__all__ = ["BSE", "BseError", "launch_count"]
+__all__ = ["BSE", "BseError", "launch_count", "batch_assemble", "batch_release"]
 
 BseError = _lib.BseError
 
@@ -200,5 +200,33 @@ class BSE:
                     "bse_profile_read")
         return ms.value, n.value
 
+    def autotune(self) -> int:
+        chosen = ctypes.c_int()
+        self._check(self._lib.bse_autotune(self._ctx, ctypes.byref(chosen)), "bse_autotune")
+        return chosen.value
+
     def sync(self):
         self._check(self._lib.bse_sync(self._ctx), "bse_sync")
+
+
+def batch_assemble(systems, Hs, stream=None, stamps: bool = False):
+    """bse_batch_assemble: assemble several crystals as one CUDA graph (one branch each).
+
+    systems: list of BSE contexts (each past project_pairs); Hs: matching H tensors.
+    Returns per-system completion times in ns from the replay start when stamps=True."""
+    lib = _lib.load()
+    n = len(systems)
+    for b, H in zip(systems, Hs):
+        _dev(H, b.h_dtype, "H", b.dim * b.dim)
+    ctxs = (ctypes.c_void_p * n)(*[b._ctx.value for b in systems])
+    hp = (ctypes.c_void_p * n)(*[H.data_ptr() for H in Hs])
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = (ctypes.c_int64 * n)() if stamps else None
+    r = lib.bse_batch_assemble(ctxs, hp, n, ctypes.c_void_p(st.cuda_stream), out)
+    if r != _lib.BSE_OK:
+        raise BseError(r, "bse_batch_assemble: " + lib.bse_last_error(systems[0]._ctx).decode())
+    return [int(x) for x in out] if stamps else None
+
+
+def batch_release():
+    _lib.load().bse_batch_release()

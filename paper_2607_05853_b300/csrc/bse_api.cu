@@ -60,7 +60,7 @@ static int g_open_id = -1;
 static cudaEvent_t g_open_ev = nullptr;
 
 void bse_prof_begin(bse_ctx *c, int id) {
-  if (!c->prof) return;
+  if (!c->prof || id < 0 || id >= BSE_KP_COUNT) return;
   g_open_ev = take_event(c);
   g_open_id = id;
   cudaEventRecord(g_open_ev, c->stream);

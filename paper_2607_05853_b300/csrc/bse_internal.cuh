@@ -115,6 +115,7 @@ bse_status split_setup(bse_ctx *c);
 bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
 bse_status split_project(bse_ctx *c);
+bse_status split_autotune(bse_ctx *c, int *chosen);
 void split_free(bse_ctx *c);
 
 // mesh helpers

@@ -21,7 +21,8 @@
 
 namespace {
 
-constexpr int TC_BN = 160;
+constexpr int TC_BN = 160;                       // default N tile (and the exchange's)
+constexpr int TC_BN_CAND[4] = {64, 96, 128, 160};  // N tiles the autotuner may pick for T = M_vv W(q)
 
 struct SplitWS {
   int np = 3, pp = 6;
@@ -35,6 +36,7 @@ struct SplitWS {
   __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V0
   __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
   CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
+  int bn_g1 = TC_BN;             // N tile of the M_vv W(q) GEMM (autotuned)
 };
 
 SplitWS *ws(bse_ctx *c) { return (SplitWS *)c->tc; }
@@ -442,11 +444,6 @@ bool launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
   const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
   const size_t sm = sizeof(float2) * (size_t)(NV * NV + NC * NC) * c->naux_tot;
   if (sm > 200 * 1024) return false;  // the pair's rows do not fit: generic chunked kernel
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
   k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->naux_tot, c->mesh[0],
                                                            c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
   return true;
@@ -495,27 +492,54 @@ bool make_map(CUtensorMap *m, void *base, int k_extent, long long rows, long lon
   return r == CUDA_SUCCESS;
 }
 
-template <int NP>
+template <int NP, int BN>
 bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
                      int prof_id) {
-  using Cf = tcg::Cfg<NP, TC_BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, TC_BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM);
-    attr = true;
-  }
+  using Cf = tcg::Cfg<NP, BN>;
   bse_prof_begin(c, prof_id);
-  tcg::k_tc_zgemm<NP, TC_BN><<<grid, 192, Cf::SMEM, c->stream>>>(A, B, args);
+  tcg::k_tc_zgemm<NP, BN><<<grid, 192, Cf::SMEM, c->stream>>>(A, B, args);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_zgemm");
 }
 
-bse_status launch_tc_np(bse_ctx *c, int np, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args,
+template <int NP>
+bse_status launch_tc_bn(bse_ctx *c, int bn, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args,
                         dim3 grid, int prof_id) {
-  if (np == 3) return launch_tc<3>(c, A, B, args, grid, prof_id);
-  if (np == 2) return launch_tc<2>(c, A, B, args, grid, prof_id);
-  return launch_tc<1>(c, A, B, args, grid, prof_id);
+  switch (bn) {
+    case 64: return launch_tc<NP, 64>(c, A, B, args, grid, prof_id);
+    case 96: return launch_tc<NP, 96>(c, A, B, args, grid, prof_id);
+    case 128: return launch_tc<NP, 128>(c, A, B, args, grid, prof_id);
+    default: return launch_tc<NP, 160>(c, A, B, args, grid, prof_id);
+  }
+}
+
+bse_status launch_tc_np(bse_ctx *c, int np, int bn, const CUtensorMap &A, const CUtensorMap &B,
+                        const tcg::Args &args, dim3 grid, int prof_id) {
+  if (np == 3) return launch_tc_bn<3>(c, bn, A, B, args, grid, prof_id);
+  if (np == 2) return launch_tc_bn<2>(c, bn, A, B, args, grid, prof_id);
+  return launch_tc_bn<1>(c, bn, A, B, args, grid, prof_id);
+}
+
+// Shared-memory size attributes of every tensor-core instantiation, set once (outside any
+// stream capture).
+template <int NP, int BN>
+void set_attr() {
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::Cfg<NP, BN>::SMEM);
+}
+template <int NV, int NC>
+void set_g2_attr() {
+  cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+void set_all_attrs() {
+  static bool done = false;
+  if (done) return;
+  set_g2_attr<2, 2>(); set_g2_attr<2, 4>(); set_g2_attr<2, 6>(); set_g2_attr<4, 2>(); set_g2_attr<4, 4>();
+  set_g2_attr<4, 6>(); set_g2_attr<6, 2>(); set_g2_attr<6, 4>(); set_g2_attr<6, 6>();
+  set_attr<1, 64>(); set_attr<1, 96>(); set_attr<1, 128>(); set_attr<1, 160>();
+  set_attr<2, 64>(); set_attr<2, 96>(); set_attr<2, 128>(); set_attr<2, 160>();
+  set_attr<3, 64>(); set_attr<3, 96>(); set_attr<3, 128>(); set_attr<3, 160>();
+  done = true;
 }
 
 }  // namespace
@@ -558,8 +582,9 @@ bse_status split_setup(bse_ctx *c) {
   cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * 2);
   cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * 2);
   cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * 2);
+  set_all_attrs();
   bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
-            make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, TC_BN) &&
+            make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
             make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&
             make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN);
   if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");
@@ -626,7 +651,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
     a.qlist = nullptr;
     a.err = c->d_err;
     dim3 grid((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
-    bse_status s = launch_tc_np(c, w->np, w->tmA_x, w->tmB_x, a, grid, BSE_KP_EXCH);
+    bse_status s = launch_tc_np(c, w->np, TC_BN, w->tmA_x, w->tmB_x, a, grid, BSE_KP_EXCH);
     if (s != BSE_OK) return s;
   }
   const int nchunk = (na + 127) / 128;
@@ -659,8 +684,8 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       a.b_base = q0;
       a.qlist = c->d_qplus;
       a.err = c->d_err;
-      dim3 grid((unsigned)((na + TC_BN - 1) / TC_BN), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
-      bse_status s = launch_tc_np(c, w->np, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
+      dim3 grid((unsigned)((na + w->bn_g1 - 1) / w->bn_g1), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
+      bse_status s = launch_tc_np(c, w->np, w->bn_g1, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
       if (s != BSE_OK) return s;
     }
     {
@@ -677,4 +702,85 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
     }
   }
   return BSE_OK;
+}
+
+// ---- autotuner ----------------------------------------------------------------------------
+// Picks the N tile of the T = M_vv W(q) tensor-core GEMM by timing one q-slab launch per
+// candidate (values do not change the timing, so no inputs are needed), keeps the fastest,
+// and re-encodes the B-operand tensor map.  Results are cached per shape in the process.
+#include <map>
+#include <mutex>
+#include <tuple>
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+}  // namespace
+
+bse_status split_autotune(bse_ctx *c, int *chosen) {
+  SplitWS *w = ws(c);
+  const int na = c->naux_tot;
+  const auto key = std::make_tuple(na, w->rows, std::min(w->nq, (int)c->qplus.size()), w->np);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      w->bn_g1 = it->second;
+      if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1))
+        return bse_fail(c, BSE_ECUDA, "autotune: tensor map encoding failed");
+      if (chosen) *chosen = w->bn_g1;
+      return BSE_OK;
+    }
+  }
+  const int nq = std::min(w->nq, (int)c->qplus.size());
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const bool prof = c->prof;
+  c->prof = false;
+  float best = 1e30f;
+  int best_bn = TC_BN;
+  for (int bn : TC_BN_CAND) {
+    CUtensorMap tB;
+    if (!make_map(&tB, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, bn)) continue;
+    tcg::Args a{};
+    a.rows = w->rows;
+    a.n_valid = na;
+    a.k_chunks = w->kchunks;
+    a.scale = 1.0f;
+    a.out = w->T32;
+    a.ldo = na;
+    a.out_bstride = (long long)w->rows * na;
+    a.b_batch_planes = 1;
+    a.b_base = 0;
+    a.qlist = c->d_qplus;
+    a.err = c->d_err;
+    dim3 grid((unsigned)((na + bn - 1) / bn), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
+    float t = 0.f;
+    bool ok = launch_tc_np(c, w->np, bn, w->tmA_g1, tB, a, grid, -1) == BSE_OK;  // warm-up
+    for (int rep = 0; rep < 3 && ok; rep++) {
+      cudaEventRecord(e0, c->stream);
+      ok = launch_tc_np(c, w->np, bn, w->tmA_g1, tB, a, grid, -1) == BSE_OK;
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t += ms;
+    }
+    if (ok && t < best) {
+      best = t;
+      best_bn = bn;
+    }
+  }
+  c->prof = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  w->bn_g1 = best_bn;
+  if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1))
+    return bse_fail(c, BSE_ECUDA, "autotune: tensor map encoding failed");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_bn;
+  }
+  if (chosen) *chosen = best_bn;
+  return bse_check_launch(c, "autotune");
 }

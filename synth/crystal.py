@@ -225,7 +225,7 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
     kf = kmesh_frac(spec.dense, spec.k_offset)
     nk = kf.shape[0]
     ph = np.exp(1j * TWO_PI * (kf @ R_h.T.astype(np.float64)))          # [k, R]
-    Hk = np.einsum("kr,rst->kst", ph, hR)
+    Hk = np.einsum("kr,rst->kst", ph, hR, optimize=True)
     Hk = 0.5 * (Hk + np.conj(np.transpose(Hk, (0, 2, 1))))
     E, U = np.linalg.eigh(Hk)
     vcols = [n_occ - 1 - v for v in range(spec.nv)]
@@ -240,8 +240,8 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
     Rc = R_h.astype(np.float64) @ lat                                     # [R, 3] Cartesian
     vel = np.empty((3, nk, spec.nv, spec.nc), dtype=np.complex128)
     for a in range(3):
-        dH = np.einsum("kr,rst->kst", ph * (1j * Rc[:, a])[None, :], hR)
-        vel[a] = np.einsum("ksv,kst,ktc->kvc", np.conj(c_k[:, :, : spec.nv]), dH, c_k[:, :, spec.nv:])
+        dH = np.einsum("kr,rst->kst", ph * (1j * Rc[:, a])[None, :], hR, optimize=True)
+        vel[a] = np.einsum("ksv,kst,ktc->kvc", np.conj(c_k[:, :, : spec.nv]), dH, c_k[:, :, spec.nv:], optimize=True)
 
     # ---- LRI coefficients C^mu_st(R), mu on the atom of s -----------------------
     R_C = r_set(spec.r_max, spec.two_d)
@@ -261,11 +261,11 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
     Rl = r_set(1.0, spec.two_d)
     G = rng.standard_normal((len(Rl), n_aux, n_aux))
     damp = np.exp(-np.linalg.norm(Rl, axis=1))
-    Lq = np.einsum("qr,r,rmn->qmn", np.exp(-1j * TWO_PI * (qc @ Rl.T.astype(np.float64))), damp, G)
-    Wq = spec.s_W * np.einsum("qmk,qnk->qmn", Lq, np.conj(Lq)) / n_aux
+    Lq = np.einsum("qr,r,rmn->qmn", np.exp(-1j * TWO_PI * (qc @ Rl.T.astype(np.float64))), damp, G, optimize=True)
+    Wq = spec.s_W * np.matmul(Lq, np.conj(np.transpose(Lq, (0, 2, 1)))) / n_aux
     R_W, w_RW, owner = _ws_images(spec.coarse, lat, spec.two_d)
     cls = kmesh_index(spec.coarse).astype(np.float64)
-    Wcls = np.einsum("qc,qmn->cmn", np.exp(1j * TWO_PI * (qc @ cls.T)), Wq) / qc.shape[0]
+    Wcls = np.einsum("qc,qmn->cmn", np.exp(1j * TWO_PI * (qc @ cls.T)), Wq, optimize=True) / qc.shape[0]
     W_R = np.ascontiguousarray(Wcls.real[owner])
     LV = rng.standard_normal((n_aux, n_aux))
     V0 = spec.s_V * (LV @ LV.T) / n_aux

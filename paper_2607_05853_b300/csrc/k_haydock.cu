@@ -56,11 +56,13 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 template <class HT>
 __global__ void k_absmax_part(const HT *__restrict__ H, long long n, double *part) {
   __shared__ double red[32];
-  double m = 0.0;
+  // squared magnitudes in FP32 (the stop threshold only needs max|H| approximately)
+  float m2 = 0.f;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double x = (double)H[i].x, y = (double)H[i].y;
-    m = fmax(m, sqrt(x * x + y * y));
+    const float x = (float)H[i].x, y = (float)H[i].y;
+    m2 = fmaxf(m2, x * x + y * y);
   }
+  double m = sqrt((double)m2);
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = m;
   __syncthreads();
@@ -358,24 +360,36 @@ __device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long lon
 }
 
 // ---- TMA-fed Hermitian matvec (complex64 H), persistent ------------------------------------
-// Same tiles and partial slots as k_hmatvec_c64, but the H tile rows stream through a
-// 4-stage shared-memory ring filled by TMA (one producer lane), so the loads of the next
-// rows are in flight while four consumer warps compute on the current ones.  A stage is
-// 16 rows x 128 complex64 = 16 KB; rows/columns past dim arrive zero-filled.
-constexpr int MV_STAGES = 4, MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8;
+// Same tiles and partial slots as k_hmatvec_c64.  Each CTA (four warps, no dedicated
+// producer warp) walks its tiles in 16-row chunks through a 3-stage shared-memory ring
+// filled by TMA: lane 0 of warp 0 refills a stage as soon as all four warps have copied
+// their rows of it into registers, so two chunks are in flight while one is computed.
+// Three CTAs per SM (128 registers a thread).  A stage is 16 rows x 128 complex64 = 16 KB;
+// rows/columns past dim arrive zero-filled.
+constexpr int MV_STAGES = 3, MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8, MV_CTAS = 3;
 constexpr long long MV_WAIT = 4000000000LL;
 
 template <int NP>
-__global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim, int nb,
-                                                    const int2 *__restrict__ tiles, int ntiles,
-                                                    const float2 *__restrict__ Q32, long long qs, int j,
-                                                    float2 *__restrict__ part, const int *meff, int *err) {
+struct HmvSmem {
+  static constexpr int RSTR = 8 * NP + 4;                 // floats per lane in the U-sum scratch
+  static constexpr int XB = NP * HT * 24;                 // x vectors: (yr,-yr,yi,yi) + (xr,xi)
+  static constexpr int USTR = (HT * NP * 8 > 32 * RSTR * 4) ? HT * NP * 8 : 32 * RSTR * 4;
+  static constexpr int BYTES = 128 + MV_STAGES * MV_STAGE_BYTES + XB + 4 * USTR;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
+                                                         int nb, const int2 *__restrict__ tiles, int ntiles,
+                                                         const float2 *__restrict__ Q32, long long qs, int j,
+                                                         float2 *__restrict__ part, const int *meff, int *err) {
+  using S = HmvSmem<NP>;
   extern __shared__ __align__(128) uint8_t smv[];
-  uint8_t *ring = smv;                                                        // MV_STAGES x 16 KB
-  float2 (*xbuf)[HT] = reinterpret_cast<float2 (*)[HT]>(ring + MV_STAGES * MV_STAGE_BYTES);  // [2][3*NP][HT]
-  float2 (*vs)[HT][NP] = reinterpret_cast<float2 (*)[HT][NP]>(xbuf + 2 * 3 * NP);           // [4][HT][NP]
-  uint64_t *full = reinterpret_cast<uint64_t *>(vs + 4);
+  uint64_t *full = reinterpret_cast<uint64_t *>(smv);
   uint64_t *empty = full + MV_STAGES;
+  uint8_t *ring = smv + 128;
+  float4 *yb = reinterpret_cast<float4 *>(ring + MV_STAGES * MV_STAGE_BYTES);  // [NP][HT] (yr,-yr,yi,yi)
+  float2 *xc = reinterpret_cast<float2 *>(yb + NP * HT);                       // [NP][HT] (xr,xi)
+  uint8_t *uni = reinterpret_cast<uint8_t *>(xc + NP * HT);  // per warp: U-sum scratch, then V partials
   bool live = false;
   for (int p = 0; p < NP; p++) live |= (j < meff[p]);
   if (!live) return;
@@ -388,96 +402,83 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
     tc::fence_barrier_init();
   }
   __syncthreads();
-  if (warp == 0) {
-    if (lane == 0) {
-      tc::prefetch_tmap(&tmH);
-      int it = 0;
-      bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int2 tl = tiles[t];
-        for (int c = 0; c < HT / MV_CHUNK; c++, it++) {
-          const int st = it % MV_STAGES;
-          if (it >= MV_STAGES && !tc::mbar_wait_bounded(&empty[st], ((it / MV_STAGES) & 1) ^ 1, MV_WAIT)) {
-            atomicOr(err, 2);
-            ok = false;
-            break;
-          }
-          tc::mbar_arrive_expect_tx(&full[st], MV_STAGE_BYTES);
-          asm volatile(
-              "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-                  tc::smem_u32(ring + st * MV_STAGE_BYTES)),
-              "l"(reinterpret_cast<uint64_t>(&tmH)), "r"(2 * tl.y * HT), "r"(tl.x * HT + c * MV_CHUNK),
-              "r"(tc::smem_u32(&full[st]))
-              : "memory");
-        }
-      }
-      // every copy started here lands before the CTA can exit
-      for (int k = it - MV_STAGES < 0 ? 0 : it - MV_STAGES; k < it; k++)
-        if (!tc::mbar_wait_bounded(&full[k % MV_STAGES], (k / MV_STAGES) & 1, MV_WAIT)) atomicOr(err, 2);
+  // ---- producer state (lane 0 of warp 0): the next chunk to copy ----
+  constexpr int CPT = HT / MV_CHUNK;
+  int p_it = 0, p_t = blockIdx.x, p_c = 0;
+  int2 p_tl = make_int2(0, 0);
+  bool p_ok = true;
+  auto issue = [&]() {  // copy chunk p_it into stage p_it % MV_STAGES (the caller knows it is free)
+    if (p_t >= ntiles) return;
+    if (p_c == 0) p_tl = tiles[p_t];
+    const int st = p_it % MV_STAGES;
+    tc::mbar_arrive_expect_tx(&full[st], MV_STAGE_BYTES);
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            tc::smem_u32(ring + st * MV_STAGE_BYTES)),
+        "l"(reinterpret_cast<uint64_t>(&tmH)), "r"(2 * p_tl.y * HT), "r"(p_tl.x * HT + p_c * MV_CHUNK),
+        "r"(tc::smem_u32(&full[st]))
+        : "memory");
+    p_it++;
+    if (++p_c == CPT) {
+      p_c = 0;
+      p_t += gridDim.x;
     }
-    return;
+  };
+  if (threadIdx.x == 0) {
+    tc::prefetch_tmap(&tmH);
+    for (int k = 0; k < MV_STAGES; k++) issue();
   }
-  // ---------------- consumers: warps 1..4 ----------------
-  const int cw = warp - 1;
-  const int ctid = threadIdx.x - 32;
   int it = 0;
-  bool aborted = false;  // warp-uniform; after a timeout the warp runs on zeros so that every
-                         // named barrier below is still reached by all four consumer warps
-  // The x vectors of a tile are loaded one tile ahead into registers and parked in the other
-  // half of a double buffer, so no tile starts with a global-load stall.
-  constexpr int XPT = (NP * HT + 127) / 128;  // elements per consumer thread
+  bool aborted = false;  // warp-uniform; after a timeout the warp runs on without waiting so that
+                         // every named barrier below is still reached by all four warps
+  // x vectors of the next tile are fetched into registers during the current one
+  constexpr int XPT = (NP * HT + 127) / 128;
   float2 pre_r[XPT], pre_c[XPT];
-  auto fetch = [&](int t) {
-    const int2 tl = tiles[t];
-    const long long r0 = (long long)tl.x * HT, c0 = (long long)tl.y * HT;
-#pragma unroll
-    for (int k = 0; k < XPT; k++) {
-      const int e = ctid + 128 * k;
-      const int p = e / HT, l = e % HT;
-      const float2 z = make_float2(0.f, 0.f);
-      pre_r[k] = (e < NP * HT && r0 + l < dim) ? Q32[p * qs + (long long)j * dim + r0 + l] : z;
-      pre_c[k] = (e < NP * HT && c0 + l < dim) ? Q32[p * qs + (long long)j * dim + c0 + l] : z;
-    }
-  };
-  auto park = [&](int buf) {
-#pragma unroll
-    for (int k = 0; k < XPT; k++) {
-      const int e = ctid + 128 * k;
-      if (e < NP * HT) {
-        const int p = e / HT, l = e % HT;
-        xbuf[buf * 3 * NP + p][l] = make_float2(pre_r[k].x, -pre_r[k].x);      // (yr, -yr)
-        xbuf[buf * 3 * NP + NP + p][l] = pre_c[k];                              // (xr, xi)
-        xbuf[buf * 3 * NP + 2 * NP + p][l] = make_float2(pre_r[k].y, pre_r[k].y); // (yi, yi)
-      }
-    }
-  };
+  int2 tl_next = make_int2(0, 0);
+#define HMV_FETCH(T)                                                                              \
+  do {                                                                                            \
+    tl_next = tiles[(T)];                                                                         \
+    const long long r0 = (long long)tl_next.x * HT, c0 = (long long)tl_next.y * HT;              \
+    _Pragma("unroll") for (int k = 0; k < XPT; k++) {                                             \
+      const int e = threadIdx.x + 128 * k;                                                        \
+      const int p = e / HT, l = e % HT;                                                           \
+      const float2 z = make_float2(0.f, 0.f);                                                     \
+      pre_r[k] = (e < NP * HT && r0 + l < dim) ? Q32[p * qs + (long long)j * dim + r0 + l] : z;   \
+      pre_c[k] = (e < NP * HT && c0 + l < dim) ? Q32[p * qs + (long long)j * dim + c0 + l] : z;   \
+    }                                                                                             \
+  } while (0)
+#define HMV_PARK()                                                                                \
+  do {                                                                                            \
+    _Pragma("unroll") for (int k = 0; k < XPT; k++) {                                             \
+      const int e = threadIdx.x + 128 * k;                                                        \
+      if (e < NP * HT) {                                                                          \
+        yb[e] = make_float4(pre_r[k].x, -pre_r[k].x, pre_r[k].y, pre_r[k].y);                     \
+        xc[e] = pre_c[k];                                                                         \
+      }                                                                                           \
+    }                                                                                             \
+  } while (0)
   if (blockIdx.x < ntiles) {
-    fetch(blockIdx.x);
-    park(0);
+    HMV_FETCH(blockIdx.x);
+    HMV_PARK();
   }
-  int buf = 0;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
-    const int2 tl = tiles[t];
-    const int bi = tl.x, bj = tl.y;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int bi = tl_next.x, bj = tl_next.y;
     const bool diag = bi == bj;
     asm volatile("bar.sync 1, 128;" ::: "memory");  // this tile's x vectors are parked
-    float2 (*xr)[HT] = xbuf + buf * 3 * NP;
-    float2 (*xc)[HT] = xr + NP;
-    float2 (*xq)[HT] = xc + NP;
     const bool has_next = t + (int)gridDim.x < ntiles;
-    if (has_next) fetch(t + gridDim.x);
-    // per tile: column vectors as (xr, xr) and (-xi, xi) pairs; v accumulators as pairs
+    if (has_next) HMV_FETCH(t + gridDim.x);
+    // a lane owns columns 2f, 2f+1 (f = lane, lane + 32): x as (xr, xr) and (-xi, xi) pairs
     unsigned long long XA[4][NP], XB[4][NP], V[4][NP];
 #pragma unroll
     for (int q = 0; q < 4; q++)
 #pragma unroll
       for (int p = 0; p < NP; p++) {
-        const float2 xv = xc[p][2 * (lane + 32 * (q / 2)) + (q % 2)];
+        const float2 xv = xc[p * HT + 2 * (lane + 32 * (q / 2)) + (q % 2)];
         XA[q][p] = pk2(xv.x, xv.x);
         XB[q][p] = pk2(-xv.y, xv.y);
         V[q][p] = 0ull;
       }
-    for (int c = 0; c < HT / MV_CHUNK; c++, it++) {
+    for (int c = 0; c < CPT; c++, it++) {
       const int st = it % MV_STAGES;
       bool ok = aborted ? false : tc::mbar_wait_bounded(&full[st], (it / MV_STAGES) & 1, MV_WAIT);
       ok = __all_sync(0xffffffffu, ok);
@@ -490,11 +491,20 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
 #pragma unroll
       for (int rr = 0; rr < 4; rr++)
 #pragma unroll
-        for (int tt = 0; tt < 2; tt++)
-          h[rr][tt] = aborted ? make_float4(0.f, 0.f, 0.f, 0.f) : rows[(cw * 4 + rr) * (HT / 2) + lane + 32 * tt];
+        for (int tt = 0; tt < 2; tt++) h[rr][tt] = rows[(warp * 4 + rr) * (HT / 2) + lane + 32 * tt];
       __syncwarp();
       if (lane == 0 && !aborted)
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[st])) : "memory");
+      if (threadIdx.x == 0 && p_ok && !aborted && p_t < ntiles) {
+        // all four warps have taken chunk it out of stage st: refill it with chunk it + MV_STAGES
+        if (tc::mbar_wait_bounded(&empty[st], (it / MV_STAGES) & 1, MV_WAIT)) {
+          issue();
+        } else {
+          atomicOr(err, 2);
+          p_ok = false;
+        }
+      }
+      __syncwarp();
       // with hp = (hr, hi) as loaded and hs = (hi, hr):
       //   h x       = hp (xr, xr) + hs (-xi, xi)
       //   conj(h) y = hp (yr, -yr) + hs (yi, yi)
@@ -505,14 +515,14 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
         for (int p = 0; p < NP; p++) U[rr][p] = 0ull;
 #pragma unroll
       for (int rr = 0; rr < 4; rr++) {
-        const int lr = c * MV_CHUNK + cw * 4 + rr;
+        const int lr = c * MV_CHUNK + warp * 4 + rr;
         unsigned long long YA[NP], YB[NP];
         if (!diag) {
 #pragma unroll
           for (int p = 0; p < NP; p++) {
-            const float2 ya = xr[p][lr], yb = xq[p][lr];
-            YA[p] = pk2(ya.x, ya.y);
-            YB[p] = pk2(yb.x, yb.y);
+            const float4 y = yb[p * HT + lr];
+            YA[p] = pk2(y.x, y.y);
+            YB[p] = pk2(y.z, y.w);
           }
         }
 #pragma unroll
@@ -535,48 +545,79 @@ __global__ void __launch_bounds__(160, 2) k_hmv_tma(const __grid_constant__ CUte
           }
         }
       }
-      float u[32];
+      // row sums of U over the 32 lanes through shared memory: each lane parks its 4*NP pairs,
+      // lane L < 8*NP sums pair L % (4*NP) over 16 of the lanes, and the two halves are added
+      {
+        float *red = reinterpret_cast<float *>(uni + warp * S::USTR);
+        float4 *mine = reinterpret_cast<float4 *>(red + lane * S::RSTR);
 #pragma unroll
-      for (int rr = 0; rr < 4; rr++)
-#pragma unroll
-        for (int p = 0; p < NP; p++) {
-          const float2 uv = up2(U[rr][p]);
-          u[(rr * NP + p) * 2 + 0] = uv.x;
-          u[(rr * NP + p) * 2 + 1] = uv.y;
+        for (int k = 0; k < 2 * NP; k++) {
+          const int i0 = 2 * k, i1 = 2 * k + 1;
+          const float2 a = up2(U[i0 / NP][i0 % NP]), b = up2(U[i1 / NP][i1 % NP]);
+          mine[k] = make_float4(a.x, a.y, b.x, b.y);
         }
+        __syncwarp();
+        const int i = lane % (4 * NP), g = lane / (4 * NP);
+        unsigned long long s0 = 0ull, s1 = 0ull;
+        const unsigned long long one = pk2(1.f, 1.f);
+        if (lane < 8 * NP) {
+          const float *src = red + 16 * g * S::RSTR + 2 * i;
 #pragma unroll
-      for (int i = 4 * NP * 2; i < 32; i++) u[i] = 0.f;
-      const float tot = warp_transpose_sum32(u, lane);
-      if (lane < 4 * NP * 2) {
-        const int rr = lane / (2 * NP), p = (lane / 2) % NP, ri = lane % 2;
-        const int lr = c * MV_CHUNK + cw * 4 + rr;
-        reinterpret_cast<float *>(part + (((long long)bi * nb + bj) * HT + lr) * NP + p)[ri] = tot;
+          for (int k = 0; k < 16; k += 2) {
+            const float2 v0 = *reinterpret_cast<const float2 *>(src + k * S::RSTR);
+            const float2 v1 = *reinterpret_cast<const float2 *>(src + (k + 1) * S::RSTR);
+            ffma2(s0, pk2(v0.x, v0.y), one);
+            ffma2(s1, pk2(v1.x, v1.y), one);
+          }
+        }
+        ffma2(s0, s1, one);
+        float2 tot = up2(s0);
+        tot.x += __shfl_down_sync(0xffffffffu, tot.x, 4 * NP);
+        tot.y += __shfl_down_sync(0xffffffffu, tot.y, 4 * NP);
+        if (lane < 4 * NP) {
+          const int rr = i / NP, p = i % NP;
+          const int lr = c * MV_CHUNK + warp * 4 + rr;
+          part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = tot;
+        }
+        __syncwarp();
       }
     }
     if (!diag) {
+      // column sums H_t^dagger y: the four warps' partials meet in shared memory
+      float2 (*vs)[NP] = reinterpret_cast<float2 (*)[NP]>(uni + warp * S::USTR);
 #pragma unroll
       for (int q = 0; q < 4; q++)
 #pragma unroll
-        for (int p = 0; p < NP; p++) vs[cw][2 * (lane + 32 * (q / 2)) + (q % 2)][p] = up2(V[q][p]);
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      for (int e = ctid; e < HT * NP; e += 128) {
+        for (int p = 0; p < NP; p++) vs[2 * (lane + 32 * (q / 2)) + (q % 2)][p] = up2(V[q][p]);
+    }
+    // every warp is past its last read of the x buffers (and, off the diagonal, has parked V)
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (!diag) {
+      for (int e = threadIdx.x; e < HT * NP; e += 128) {
         const int l = e / NP, p = e % NP;
         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < 4; w++) {
-          acc.x += vs[w][l][p].x;
-          acc.y += vs[w][l][p].y;
+          const float2 v = reinterpret_cast<const float2 (*)[NP]>(uni + w * S::USTR)[l][p];
+          acc.x += v.x;
+          acc.y += v.y;
         }
         part[(((long long)bj * nb + bi) * HT + l) * NP + p] = acc;
       }
     }
-    if (has_next) park(buf ^ 1);  // visible after the next tile's opening barrier
+    if (has_next) HMV_PARK();  // visible after the next tile's opening barrier
   }
+  // chunks copied but never consumed (only after a timeout) must land before the CTA exits
+  if (threadIdx.x == 0)
+    for (int k = it; k < p_it; k++)
+      if (!tc::mbar_wait_bounded(&full[k % MV_STAGES], (k / MV_STAGES) & 1, MV_WAIT)) atomicOr(err, 2);
 }
+#undef HMV_FETCH
+#undef HMV_PARK
 
 template <int NP>
 constexpr int hmv_tma_smem() {
-  return MV_STAGES * MV_STAGE_BYTES + 2 * 3 * NP * HT * 8 + 4 * HT * NP * 8 + 2 * MV_STAGES * 8;
+  return HmvSmem<NP>::BYTES;
 }
 
 // W[p][row] = sum_s part[row_block][s][row_local][p]  (FP64 sum in a fixed order)
@@ -686,43 +727,85 @@ __global__ void k_reorth_update(double2 *W, long long dim, const double2 *Q, lon
 // FP32 relative error lands on a small correction.
 
 
-// Chunked projections for the complex64 path: block (chunk, p) stages 256 elements of W
-// once, each warp streams basis rows i = warp, warp + 8, ... <= j over the chunk and writes
-// the chunk partial of Q32_i^H W; k_reorth_coef sums the chunk partials in FP64.
-constexpr int RCH = 256;
-__global__ void __launch_bounds__(256) k_reorth_dots_chunk(const double2 *W, long long dim, const float2 *Q32,
-                                                           long long qs, int j, float2 *partial, int nchunk,
-                                                           int ldp, const int *meff) {
-  __shared__ float2 ws[RCH];
+// Chunked projections for the complex64 path: block (chunk, p, row group) stages 256
+// elements of W once (FP32) and its warps stream 4 basis rows at a time over the chunk,
+// issuing all 16 float4 loads of a pass before the first use; the per-row sums over the
+// 32 lanes are one butterfly transpose.  Writes the chunk partial of Q32_i^H W;
+// k_reorth_coef sums the chunk partials in FP64.  Needs an even dim (float4 = 2 elements).
+constexpr int RCH = 256, RROWS = 64, RPW = 4;
+
+template <int N>
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[N], int lane) {
+  int bit = 16;
+#pragma unroll
+  for (int half = N / 2; half >= 1; half >>= 1, bit >>= 1) {
+    const bool up = (lane & bit) != 0;
+#pragma unroll
+    for (int i = 0; i < half; i++) {
+      const float send = up ? v[i] : v[i + half];
+      const float keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, bit);
+    }
+  }
+  for (; bit >= 1; bit >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], bit);
+  return v[0];  // lane L holds the total of value L / (32 / N)
+}
+
+__global__ void __launch_bounds__(256, 2) k_reorth_dots_chunk(const double2 *__restrict__ W, long long dim,
+                                                              const float2 *__restrict__ Q32, long long qs, int j,
+                                                              float2 *__restrict__ partial, int nchunk, int ldp,
+                                                              const int *__restrict__ meff) {
+  __shared__ float4 ws[RCH / 2];
   const int chunk = blockIdx.x, p = blockIdx.y;
   if (j >= meff[p]) return;
+  const int ib = blockIdx.z * RROWS;
+  if (ib > j) return;
+  const int ie = min(j, ib + RROWS - 1);
   const long long e0 = (long long)chunk * RCH;
-  for (int t = threadIdx.x; t < RCH; t += blockDim.x) {
-    const long long e = e0 + t;
-    const double2 v = e < dim ? W[(long long)p * dim + e] : make_double2(0.0, 0.0);
-    ws[t] = make_float2((float)v.x, (float)v.y);
+  for (int t = threadIdx.x; t < RCH / 2; t += blockDim.x) {
+    const long long e = e0 + 2 * t;
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (e < dim) {
+      const double2 a = W[(long long)p * dim + e], b = W[(long long)p * dim + e + 1];
+      w = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
+    }
+    ws[t] = w;
   }
   __syncthreads();
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const float2 *qp = Q32 + p * qs + e0;
-  const bool full = e0 + RCH <= dim;
-  for (int i = warp; i <= j; i += 8) {
-    const float2 *qi = qp + (long long)i * dim;
-    float sr = 0.f, si = 0.f;
+  const float4 *qp = reinterpret_cast<const float4 *>(Q32 + p * qs + e0);
+  const long long rs = dim / 2;
+  for (int i0 = ib + RPW * warp; i0 <= ie; i0 += RPW * 8) {
+    float4 q[RPW][RCH / 64];
 #pragma unroll
-    for (int t = 0; t < RCH / 32; t++) {
-      const int l = lane + 32 * t;
-      if (full || e0 + l < dim) {
-        const float2 q = qi[l], w = ws[l];
-        sr = fmaf(q.x, w.x, fmaf(q.y, w.y, sr));
-        si = fmaf(q.x, w.y, fmaf(-q.y, w.x, si));
+    for (int r = 0; r < RPW; r++) {
+      const int row = min(i0 + r, ie);  // rows past ie repeat row ie; their sums are dropped
+#pragma unroll
+      for (int t = 0; t < RCH / 64; t++) {
+        const int f = lane + 32 * t;
+        q[r][t] = (e0 + 2 * f < dim) ? __ldg(qp + (long long)row * rs + f) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      sr += __shfl_xor_sync(0xffffffffu, sr, o);
-      si += __shfl_xor_sync(0xffffffffu, si, o);
+    float v[2 * RPW];
+#pragma unroll
+    for (int r = 0; r < 2 * RPW; r++) v[r] = 0.f;
+#pragma unroll
+    for (int t = 0; t < RCH / 64; t++) {
+      const float4 w = ws[lane + 32 * t];
+#pragma unroll
+      for (int r = 0; r < RPW; r++) {
+        const float4 a = q[r][t];  // conj(q) w for two elements
+        v[2 * r] = fmaf(a.x, w.x, fmaf(a.y, w.y, fmaf(a.z, w.z, fmaf(a.w, w.w, v[2 * r]))));
+        v[2 * r + 1] = fmaf(a.x, w.y, fmaf(-a.y, w.x, fmaf(a.z, w.w, fmaf(-a.w, w.z, v[2 * r + 1]))));
+      }
     }
-    if (lane == 0) partial[((long long)p * nchunk + chunk) * ldp + i] = make_float2(sr, si);
+    const float tot = warp_transpose_sum<2 * RPW>(v, lane);
+    constexpr int G = 32 / (2 * RPW);
+    if (lane % G == 0) {
+      const int idx = lane / G, r = idx / 2;
+      if (i0 + r <= ie)
+        reinterpret_cast<float *>(partial + ((long long)p * nchunk + chunk) * ldp + i0 + r)[idx % 2] = tot;
+    }
   }
 }
 
@@ -739,14 +822,21 @@ __global__ void k_reorth_coef(const float2 *partial, int nchunk, int ldp, int j,
   coef[p * ldc + i] = make_double2(sr, si);
 }
 
-__global__ void k_reorth_update32(double2 *W, long long dim, const float2 *Q32, long long qs, int j,
-                                  const double2 *coef, int ldc, const int *meff) {
+// W -= sum_i coef_i Q32_i for two elements per thread (float4 loads, 16 basis rows in flight
+// per thread); FP32 products and sums, subtracted from the FP64 vector.  Needs an even dim.
+constexpr int RUN = 16;
+__global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict__ W, long long dim,
+                                                            const float2 *__restrict__ Q32, long long qs, int j,
+                                                            const double2 *__restrict__ coef, int ldc,
+                                                            const int *__restrict__ meff) {
   __shared__ float2 cs[1024];
   const int p = blockIdx.y;
   if (j >= meff[p]) return;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const float2 *qp = Q32 + p * qs + e;
-  float cr = 0.f, ci = 0.f;
+  const long long e = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const bool in = e < dim;
+  const float4 *qp = reinterpret_cast<const float4 *>(Q32 + p * qs + e);
+  const long long rs = dim / 2;
+  float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
   for (int i0 = 0; i0 <= j; i0 += 1024) {
     const int n = min(1024, j + 1 - i0);
     __syncthreads();
@@ -755,31 +845,40 @@ __global__ void k_reorth_update32(double2 *W, long long dim, const float2 *Q32, 
       cs[t] = make_float2((float)c.x, (float)c.y);
     }
     __syncthreads();
-    if (e < dim) {
-      float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+    if (in) {
       int i = 0;
-      for (; i + 4 <= n; i += 4) {
+      for (; i + RUN <= n; i += RUN) {
+        float4 q[RUN];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-          const float2 c = cs[i + u], q = qp[(long long)(i0 + i + u) * dim];
-          ar[u] = fmaf(c.x, q.x, fmaf(-c.y, q.y, ar[u]));
-          ai[u] = fmaf(c.x, q.y, fmaf(c.y, q.x, ai[u]));
+        for (int u = 0; u < RUN; u++) q[u] = __ldg(qp + (long long)(i0 + i + u) * rs);
+#pragma unroll
+        for (int u = 0; u < RUN; u++) {
+          const float2 c = cs[i + u];
+          a0r = fmaf(c.x, q[u].x, fmaf(-c.y, q[u].y, a0r));
+          a0i = fmaf(c.x, q[u].y, fmaf(c.y, q[u].x, a0i));
+          a1r = fmaf(c.x, q[u].z, fmaf(-c.y, q[u].w, a1r));
+          a1i = fmaf(c.x, q[u].w, fmaf(c.y, q[u].z, a1i));
         }
       }
       for (; i < n; i++) {
-        const float2 c = cs[i], q = qp[(long long)(i0 + i) * dim];
-        ar[0] = fmaf(c.x, q.x, fmaf(-c.y, q.y, ar[0]));
-        ai[0] = fmaf(c.x, q.y, fmaf(c.y, q.x, ai[0]));
+        const float2 c = cs[i];
+        const float4 q = __ldg(qp + (long long)(i0 + i) * rs);
+        a0r = fmaf(c.x, q.x, fmaf(-c.y, q.y, a0r));
+        a0i = fmaf(c.x, q.y, fmaf(c.y, q.x, a0i));
+        a1r = fmaf(c.x, q.z, fmaf(-c.y, q.w, a1r));
+        a1i = fmaf(c.x, q.w, fmaf(c.y, q.z, a1i));
       }
-      cr += (ar[0] + ar[1]) + (ar[2] + ar[3]);
-      ci += (ai[0] + ai[1]) + (ai[2] + ai[3]);
     }
   }
-  if (e < dim) {
-    double2 v = W[(long long)p * dim + e];
-    v.x -= (double)cr;
-    v.y -= (double)ci;
-    W[(long long)p * dim + e] = v;
+  if (in) {
+    double2 *wp = W + (long long)p * dim + e;
+    double2 v0 = wp[0], v1 = wp[1];
+    v0.x -= (double)a0r;
+    v0.y -= (double)a0i;
+    v1.x -= (double)a1r;
+    v1.y -= (double)a1i;
+    wp[0] = v0;
+    wp[1] = v1;
   }
 }
 
@@ -1056,19 +1155,20 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   if (r != BSE_OK) return r;
   const unsigned mv_blocks = (unsigned)((dim + MV_ROWS - 1) / MV_ROWS);
   const unsigned el_blocks = (unsigned)((dim + 255) / 256);
+  const unsigned el2_blocks = (unsigned)((dim / 2 + 255) / 256);
   for (int j = 0; j < n_steps; j++) {
     bse_prof_begin(c, BSE_KP_MATVEC);
     if (c64 && s.tma) {
       const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
-      const int grid = std::min(s.ntiles, 2 * c->n_sm);
+      const int grid = std::min(s.ntiles, MV_CTAS * c->n_sm);
       if (n_pol == 1) {
-        k_hmv_tma<1><<<grid, 160, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         k_hmv_reduce<1><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
       } else if (n_pol == 2) {
-        k_hmv_tma<2><<<grid, 160, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_tma<2><<<grid, 128, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         k_hmv_reduce<2><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
       } else {
-        k_hmv_tma<3><<<grid, 160, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        k_hmv_tma<3><<<grid, 128, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         k_hmv_reduce<3><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
       }
       bse_count_launch();
@@ -1099,13 +1199,13 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     k_alpha_axpy<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff);
     bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
-      if (c64) {
-        k_reorth_dots_chunk<<<dim3(s.nrch, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart, s.nrch, ldab,
-                                                                 s.meff);
+      if (c64 && dim % 2 == 0) {
+        k_reorth_dots_chunk<<<dim3(s.nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart,
+                                                                                   s.nrch, ldab, s.meff);
         k_reorth_coef<<<dim3((j + 1 + 127) / 128, n_pol), 128, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab,
                                                                         s.meff);
-        k_reorth_update32<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
-      } else {
+        k_reorth_update32<<<dim3(el2_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
+      } else {  // complex128 H, or an odd dim: FP64 projections on the FP64 basis
         k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
         k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
       }

@@ -620,32 +620,43 @@ constexpr int hmv_tma_smem() {
   return HmvSmem<NP>::BYTES;
 }
 
-// W[p][row] = sum_s part[row_block][s][row_local][p]  (FP64 sum in a fixed order)
+// W[p][row] = sum_s part[t][s][row_local][p] for the rows of block t (FP64, fixed order),
+// and the block's share of alpha_j = Re(Q_j^H W) per polarisation (apart[p][t]).  Two
+// threads per output stream the two halves of the block's 216 x 3 KB slab; their sums meet
+// in shared memory.
 template <int NP>
-__global__ void k_hmv_reduce(const float2 *__restrict__ part, long long dim, int nb, double2 *__restrict__ W,
-                             int j, const int *meff) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= dim * NP) return;
-  const long long row = e / NP;
-  const int p = (int)(e % NP);
-  if (j >= meff[p]) return;
-  const long long t = row / HT, l = row % HT;
-  const float2 *src = part + (t * nb * HT + l) * NP + p;
-  const long long step = (long long)HT * NP;
+__global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__restrict__ part, long long dim,
+                                                                int nb, double2 *__restrict__ W,
+                                                                const double2 *__restrict__ Q, long long qs, int j,
+                                                                const int *__restrict__ meff, double *__restrict__ apart) {
+  __shared__ double2 hs[HT * NP];
+  __shared__ double av[HT * NP];
+  const int t = blockIdx.x;
+  const int o = threadIdx.x % (HT * NP), h = threadIdx.x / (HT * NP);
+  const int l = o / NP, p = o % NP;
+  const long long row = (long long)t * HT + l;
+  const bool on = row < dim && j < meff[p];
+  const int s0 = h ? nb / 2 : 0, s1 = h ? nb : nb / 2;
   double sx[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sy[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  int s = 0;
-  for (; s + 8 <= nb; s += 8) {
+  if (on) {
+    const float2 *src = part + ((long long)t * nb * HT + l) * NP + p;
+    const long long step = (long long)HT * NP;
+    int s = s0;
+    for (; s + 8 <= s1; s += 8) {
+      float2 v[8];
 #pragma unroll
-    for (int u = 0; u < 8; u++) {
-      const float2 v = src[(s + u) * step];
-      sx[u] += v.x;
-      sy[u] += v.y;
+      for (int u = 0; u < 8; u++) v[u] = src[(s + u) * step];
+#pragma unroll
+      for (int u = 0; u < 8; u++) {
+        sx[u] += v[u].x;
+        sy[u] += v[u].y;
+      }
     }
-  }
-  for (; s < nb; s++) {
-    const float2 v = src[s * step];
-    sx[0] += v.x;
-    sy[0] += v.y;
+    for (; s < s1; s++) {
+      const float2 v = src[s * step];
+      sx[0] += v.x;
+      sy[0] += v.y;
+    }
   }
   double tx = 0.0, ty = 0.0;
 #pragma unroll
@@ -653,34 +664,117 @@ __global__ void k_hmv_reduce(const float2 *__restrict__ part, long long dim, int
     tx += sx[u];
     ty += sy[u];
   }
-  W[(long long)p * dim + row] = make_double2(tx, ty);
-}
-
-// a[p][j] = Re(Q_j^H W); W -= a_j Q_j + b_{j-1} Q_{j-1}   (block per p)
-__global__ void k_alpha_axpy(double2 *W, long long dim, const double2 *Q, long long qs, int j, double *a,
-                             const double *b, int ldab, const int *meff) {
-  __shared__ double red[32];
-  __shared__ double sa;
-  const int p = blockIdx.x;
-  if (j >= meff[p]) return;
-  double2 *w = W + (long long)p * dim;
-  const double2 *qj = Q + p * qs + (long long)j * dim;
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x) s += qj[i].x * w[i].x + qj[i].y * w[i].y;
-  s = block_sum<1024>(s, red);
-  if (threadIdx.x == 0) {
-    sa = s;
-    a[p * ldab + j] = s;
+  if (h) hs[o] = make_double2(tx, ty);
+  __syncthreads();
+  if (!h) {
+    double ar = 0.0;
+    if (on) {
+      tx += hs[o].x;
+      ty += hs[o].y;
+      W[(long long)p * dim + row] = make_double2(tx, ty);
+      const double2 q = Q[p * qs + (long long)j * dim + row];
+      ar = q.x * tx + q.y * ty;
+    }
+    av[o] = ar;
   }
   __syncthreads();
-  const double aj = sa, bj = j > 0 ? b[p * ldab + j - 1] : 0.0;
-  const double2 *qm = j > 0 ? qj - dim : qj;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x) {
-    double2 v = w[i];
-    v.x -= aj * qj[i].x + bj * qm[i].x;
-    v.y -= aj * qj[i].y + bj * qm[i].y;
-    w[i] = v;
+  if (threadIdx.x < NP) {
+    double sa = 0.0;
+    for (int ll = 0; ll < HT; ll++) sa += av[ll * NP + threadIdx.x];
+    apart[threadIdx.x * nb + t] = sa;
   }
+}
+
+// Block sum returned to every thread (tree order fixed by NT).
+template <int NT>
+__device__ __forceinline__ double block_sum_all(double v, double *red, double *out) {
+  v = block_sum<NT>(v, red);
+  if (threadIdx.x == 0) *out = v;
+  __syncthreads();
+  return *out;
+}
+
+// apart[p][t] = sum of Re(conj(Q_j) W) over rows of block t (matvec paths that write W directly)
+__global__ void k_alpha_part(const double2 *__restrict__ W, long long dim, const double2 *__restrict__ Q,
+                             long long qs, int j, const int *__restrict__ meff, int nb, double *__restrict__ apart) {
+  __shared__ double red[32];
+  const int t = blockIdx.x, p = blockIdx.y;
+  const long long row = (long long)t * HT + threadIdx.x;
+  double ar = 0.0;
+  if (row < dim && j < meff[p]) {
+    const double2 w = W[(long long)p * dim + row], q = Q[p * qs + (long long)j * dim + row];
+    ar = q.x * w.x + q.y * w.y;
+  }
+  ar = block_sum<HT>(ar, red);
+  if (threadIdx.x == 0) apart[p * nb + t] = ar;
+}
+
+// alpha_j = sum_t apart[p][t] (same order in every block); W -= alpha_j Q_j + b_{j-1} Q_{j-1}
+__global__ void __launch_bounds__(256) k_axpy(double2 *__restrict__ W, long long dim, const double2 *__restrict__ Q,
+                                              long long qs, int j, double *__restrict__ a, const double *__restrict__ b,
+                                              int ldab, const int *__restrict__ meff, int nb,
+                                              const double *__restrict__ apart) {
+  __shared__ double red[32];
+  __shared__ double sa;
+  const int p = blockIdx.y;
+  if (j >= meff[p]) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += apart[p * nb + i];
+  const double aj = block_sum_all<256>(s, red, &sa);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a[p * ldab + j] = aj;
+  const double bj = j > 0 ? b[p * ldab + j - 1] : 0.0;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  const double2 *qj = Q + p * qs + (long long)j * dim;
+  const double2 *qm = j > 0 ? qj - dim : qj;
+  double2 v = W[(long long)p * dim + e];
+  const double2 x = qj[e], y = qm[e];
+  v.x -= aj * x.x + bj * y.x;
+  v.y -= aj * x.y + bj * y.y;
+  W[(long long)p * dim + e] = v;
+}
+
+// npart[p][t] = sum over the rows of block t of |W|^2
+__global__ void k_norm_part(const double2 *__restrict__ W, long long dim, int j, const int *__restrict__ meff, int nb,
+                            double *__restrict__ npart) {
+  __shared__ double red[32];
+  const int t = blockIdx.x, p = blockIdx.y;
+  const long long row = (long long)t * HT + threadIdx.x;
+  double v = 0.0;
+  if (row < dim && j < meff[p]) {
+    const double2 w = W[(long long)p * dim + row];
+    v = w.x * w.x + w.y * w.y;
+  }
+  v = block_sum<HT>(v, red);
+  if (threadIdx.x == 0) npart[p * nb + t] = v;
+}
+
+// b[p][j] = |W| from the partials (same order in every block); Q[p][j+1] = W / b (and its FP32
+// shadow); early stop when b < 1e-14 max|H|.
+__global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ W, long long dim, double2 *__restrict__ Q,
+                                               long long qs, int j, double *__restrict__ b, int ldab, int *meff,
+                                               const double *__restrict__ hmax, int n_steps, float2 *__restrict__ Q32,
+                                               int nb, const double *__restrict__ npart) {
+  __shared__ double red[32];
+  __shared__ double sb;
+  const int p = blockIdx.y;
+  if (j >= meff[p]) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += npart[p * nb + i];
+  const double bj = sqrt(block_sum_all<256>(s, red, &sb));
+  if (blockIdx.x == 0 && threadIdx.x == 0) b[p * ldab + j] = bj;
+  if (j == n_steps - 1) return;
+  if (bj < 1e-14 * hmax[0]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) meff[p] = j + 1;
+    return;
+  }
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  const double inv = 1.0 / bj;
+  const double2 w = W[(long long)p * dim + e];
+  const double2 v = make_double2(w.x * inv, w.y * inv);
+  Q[p * qs + (long long)(j + 1) * dim + e] = v;
+  if (Q32) Q32[p * qs + (long long)(j + 1) * dim + e] = make_float2((float)v.x, (float)v.y);
 }
 
 // coef[p][i] = Q_i^H W, i <= j   (grid: x = i, y = p)
@@ -730,8 +824,8 @@ __global__ void k_reorth_update(double2 *W, long long dim, const double2 *Q, lon
 // Chunked projections for the complex64 path: block (chunk, p, row group) stages 256
 // elements of W once (FP32) and its warps stream 4 basis rows at a time over the chunk,
 // issuing all 16 float4 loads of a pass before the first use; the per-row sums over the
-// 32 lanes are one butterfly transpose.  Writes the chunk partial of Q32_i^H W;
-// k_reorth_coef sums the chunk partials in FP64.  Needs an even dim (float4 = 2 elements).
+// 32 lanes are one butterfly transpose.  Writes the chunk partial of Q32_i^H W to
+// partial[p][i][chunk]; k_reorth_coef sums the chunk partials in FP64.  Needs an even dim (float4 = 2 elements).
 constexpr int RCH = 256, RROWS = 64, RPW = 4;
 
 template <int N>
@@ -804,22 +898,28 @@ __global__ void __launch_bounds__(256, 2) k_reorth_dots_chunk(const double2 *__r
     if (lane % G == 0) {
       const int idx = lane / G, r = idx / 2;
       if (i0 + r <= ie)
-        reinterpret_cast<float *>(partial + ((long long)p * nchunk + chunk) * ldp + i0 + r)[idx % 2] = tot;
+        reinterpret_cast<float *>(partial + ((long long)p * ldp + i0 + r) * nchunk + chunk)[idx % 2] = tot;
     }
   }
 }
 
-__global__ void k_reorth_coef(const float2 *partial, int nchunk, int ldp, int j, double2 *coef, int ldc,
-                              const int *meff) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+// coef[p][i] = sum over chunks of partial[p][i][chunk] (FP64): one warp per (i, p)
+__global__ void __launch_bounds__(256) k_reorth_coef(const float2 *__restrict__ partial, int nchunk, int ldp, int j,
+                                                     double2 *__restrict__ coef, int ldc, const int *__restrict__ meff) {
+  const int i = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32, p = blockIdx.y;
   if (j >= meff[p] || i > j) return;
+  const float2 *src = partial + ((long long)p * ldp + i) * nchunk;
   double sr = 0.0, si = 0.0;
-  for (int c = 0; c < nchunk; c++) {
-    const float2 v = partial[((long long)p * nchunk + c) * ldp + i];
+  for (int c = lane; c < nchunk; c += 32) {
+    const float2 v = src[c];
     sr += v.x;
     si += v.y;
   }
-  coef[p * ldc + i] = make_double2(sr, si);
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) coef[p * ldc + i] = make_double2(sr, si);
 }
 
 // W -= sum_i coef_i Q32_i for two elements per thread (float4 loads, 16 basis rows in flight
@@ -882,38 +982,6 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
   }
 }
 
-// b[p][j] = |W|; Q[p][j+1] = W/b (block per p); early stop when b < 1e-14 max|H|.
-__global__ void k_norm_scale(const double2 *W, long long dim, double2 *Q, long long qs, int j, double *b,
-                             int ldab, int *meff, const double *hmax, int n_steps, float2 *Q32) {
-  __shared__ double red[32];
-  __shared__ double sb;
-  const int p = blockIdx.x;
-  if (j >= meff[p]) return;
-  const double2 *w = W + (long long)p * dim;
-  double s = 0.0;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x) s += w[i].x * w[i].x + w[i].y * w[i].y;
-  s = block_sum<1024>(s, red);
-  if (threadIdx.x == 0) {
-    sb = sqrt(s);
-    b[p * ldab + j] = sb;
-  }
-  __syncthreads();
-  const double bj = sb;
-  if (j == n_steps - 1) return;
-  if (bj < 1e-14 * hmax[0]) {
-    __syncthreads();
-    if (threadIdx.x == 0) meff[p] = j + 1;
-    return;
-  }
-  const double inv = 1.0 / bj;
-  double2 *qn = Q + p * qs + (long long)(j + 1) * dim;
-  float2 *qn32 = Q32 ? Q32 + p * qs + (long long)(j + 1) * dim : nullptr;
-  for (long long i = threadIdx.x; i < dim; i += blockDim.x) {
-    const double2 v = make_double2(w[i].x * inv, w[i].y * inv);
-    qn[i] = v;
-    if (qn32) qn32[i] = make_float2((float)v.x, (float)v.y);
-  }
-}
 
 // eps2[w] = pref * sum_p -(1/pi) Im( beta0^2 / (z - a1 - b1^2/(z - a2 - ...)) )
 __global__ void k_contfrac(const double *a, const double *b, int ldab, const double *beta0, const int *meff,
@@ -1069,6 +1137,7 @@ struct LanczosScratch {
   CUtensorMap tmH;
   bool tma = false;
   double *a = nullptr, *b = nullptr, *beta0 = nullptr, *hmax = nullptr, *part = nullptr;
+  double *apart = nullptr, *npart = nullptr;  // per-row-block partials of alpha_j and |W|^2
   int *meff = nullptr;
 };
 
@@ -1085,12 +1154,14 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
       cudaMallocAsync((void **)&s.hmax, sizeof(double), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.part, sizeof(double) * 1024, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.apart, sizeof(double) * 2 * n_pol * ((dim + HT - 1) / HT), st) != cudaSuccess ||
       (c->precision != BSE_FP64 &&
        cudaMallocAsync((void **)&s.Q32, qbytes / 2, st) != cudaSuccess)) {
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
   }
   s.nbt = (int)((dim + HT - 1) / HT);
+  s.npart = s.apart + (size_t)n_pol * s.nbt;
   s.nrch = (int)((dim + RCH - 1) / RCH);
   if (c->precision != BSE_FP64 &&
       cudaMallocAsync((void **)&s.rpart, sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1), st) != cudaSuccess) {
@@ -1117,7 +1188,7 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
 }
 
 void lanczos_release(bse_ctx *c, LanczosScratch &s) {
-  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.Q32, s.hpart, s.tiles, s.rpart};
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.apart, s.Q32, s.hpart, s.tiles, s.rpart};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -1159,33 +1230,31 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   for (int j = 0; j < n_steps; j++) {
     bse_prof_begin(c, BSE_KP_MATVEC);
     if (c64 && s.tma) {
-      const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
       const int grid = std::min(s.ntiles, MV_CTAS * c->n_sm);
       if (n_pol == 1) {
         k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
-        k_hmv_reduce<1><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmv_tma<2><<<grid, 128, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
-        k_hmv_reduce<2><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmv_tma<3><<<grid, 128, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
-        k_hmv_reduce<3><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
-      bse_count_launch();
+      bse_count_launch(2);
     } else if (c64 && s.hpart) {
       dim3 g(s.nbt, s.nbt);
-      const unsigned rb = (unsigned)((dim * n_pol + 255) / 256);
       if (n_pol == 1) {
         k_hmatvec_c64<1><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
-        k_hmv_reduce<1><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmatvec_c64<2><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
-        k_hmv_reduce<2><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmatvec_c64<3><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
-        k_hmv_reduce<3><<<rb, 256, 0, st>>>(s.hpart, dim, s.nbt, s.W, j, s.meff);
+        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
-      bse_count_launch();
+      bse_count_launch(2);
     } else if (c64) {
       if (n_pol == 1) k_matvec_c64<1><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
       else if (n_pol == 2) k_matvec_c64<2><<<mv_blocks, 256, 0, st>>>((const float2 *)H, dim, s.Q, qs, j, s.W, s.meff);
@@ -1195,15 +1264,19 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       else if (n_pol == 2) k_matvec_c128<2><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
       else k_matvec_c128<3><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
     }
+    if (!s.hpart) bse_count_launch();
     bse_prof_end(c, BSE_KP_MATVEC);
-    k_alpha_axpy<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff);
+    if (!s.hpart) {  // the full-read matvecs write W directly: alpha_j partials in a separate pass
+      k_alpha_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, s.Q, qs, j, s.meff, s.nbt, s.apart);
+      bse_count_launch();
+    }
+    k_axpy<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff, s.nbt, s.apart);
     bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
       if (c64 && dim % 2 == 0) {
         k_reorth_dots_chunk<<<dim3(s.nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart,
                                                                                    s.nrch, ldab, s.meff);
-        k_reorth_coef<<<dim3((j + 1 + 127) / 128, n_pol), 128, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab,
-                                                                        s.meff);
+        k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab, s.meff);
         k_reorth_update32<<<dim3(el2_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
       } else {  // complex128 H, or an odd dim: FP64 projections on the FP64 basis
         k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
@@ -1211,8 +1284,10 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       }
     }
     bse_prof_end(c, BSE_KP_REORTH);
-    k_norm_scale<<<n_pol, 1024, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps, s.Q32);
-    bse_count_launch(7);
+    k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.npart);
+    k_scale<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps, s.Q32,
+                                                    s.nbt, s.npart);
+    bse_count_launch((c64 && dim % 2 == 0) ? 9 : 7);  // axpy, two reorthogonalisation passes, norm, scale
     r = bse_check_launch(c, "lanczos step");
     if (r != BSE_OK) return r;
   }
@@ -1367,6 +1442,8 @@ size_t carve_scratch(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, unsi
   s.part = (double *)take(sizeof(double) * 1024);
   s.meff = (int *)take(sizeof(int) * n_pol);
   s.nbt = (int)((dim + HT - 1) / HT);
+  s.apart = (double *)take(sizeof(double) * 2 * n_pol * s.nbt);
+  s.npart = s.apart ? s.apart + (size_t)n_pol * s.nbt : nullptr;
   s.nrch = (int)((dim + RCH - 1) / RCH);
   s.Q32 = c64 ? (float2 *)take(sizeof(float2) * qn) : nullptr;
   s.rpart = c64 ? (float2 *)take(sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1)) : nullptr;

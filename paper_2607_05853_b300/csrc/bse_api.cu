@@ -271,7 +271,7 @@ bse_status bse_interp_W(bse_ctx *c, const double *W_R, const double *V0, void *W
                         c->stream) != cudaSuccess)
       return bse_fail(c, BSE_ECUDA, "interp_W: copy to Wq_out failed");
   } else {
-    s = split_interp_W(c, W_R, (double2 *)Wq_out);
+    s = split_interp_W(c, W_R, V0, (double2 *)Wq_out);
     if (s != BSE_OK) return s;
   }
   c->stage = std::max(c->stage, 1);
@@ -287,16 +287,18 @@ bse_status bse_project_pairs(bse_ctx *c, const double *C_R, const double *c_k, c
       cudaMemcpyAsync(c->eqp, e_qp, (size_t)c->nk * c->nb * sizeof(double), cudaMemcpyDeviceToDevice,
                       c->stream) != cudaSuccess)
     return bse_fail(c, BSE_ECUDA, "project_pairs: copy of c_k / e_qp failed");
-  bse_status s = launch_half_transform_fp64(c, C_R);
-  if (s != BSE_OK) return s;
-  s = launch_exchange_factors_fp64(c);
-  if (s != BSE_OK) return s;
-  // P = X V(0): rows (k,i,a), K = N = N_aux
-  s = launch_zgemm_fp64(c, (int)c->dim, c->naux_tot, c->naux_tot, c->X, c->naux_tot, 0, c->V0c,
-                        c->naux_tot, 0, c->P, c->naux_tot, 0, 1);
-  if (s != BSE_OK) return s;
-  if (c->precision != BSE_FP64) {
-    s = split_project(c);
+  bse_status s;
+  if (c->precision == BSE_FP64) {
+    s = launch_half_transform_fp64(c, C_R);
+    if (s != BSE_OK) return s;
+    s = launch_exchange_factors_fp64(c);
+    if (s != BSE_OK) return s;
+    // P = X V(0): rows (k,i,a), K = N = N_aux
+    s = launch_zgemm_fp64(c, (int)c->dim, c->naux_tot, c->naux_tot, c->X, c->naux_tot, 0, c->V0c,
+                          c->naux_tot, 0, c->P, c->naux_tot, 0, 1);
+    if (s != BSE_OK) return s;
+  } else {
+    s = split_project(c, C_R);
     if (s != BSE_OK) return s;
   }
   c->stage = 2;

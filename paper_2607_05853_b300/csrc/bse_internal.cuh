@@ -35,6 +35,7 @@ struct bse_ctx {
   int device = 0;
   int n_sm = 148;
   int stage = 0;  // 0 setup, 1 interp_W done, 2 project_pairs done
+  bool y64_valid = true;  // c->Y holds the pair table (split precisions keep it in FP32)
   std::string err;
 
   // small device tables
@@ -112,9 +113,10 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
 
 // split-precision path (k_split.cu)
 bse_status split_setup(bse_ctx *c);
-bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
+bse_status split_interp_W(bse_ctx *c, const double *W_R, const double *V0, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
-bse_status split_project(bse_ctx *c);
+bse_status split_project(bse_ctx *c, const double *C_R);
+bse_status split_y_to_fp64(bse_ctx *c);
 bse_status split_autotune(bse_ctx *c, int *chosen);
 void split_free(bse_ctx *c);
 
@@ -132,3 +134,32 @@ __host__ __device__ inline int kdiff(int k1, int q, int n1, int n2, int n3) {
   int c3 = a3 - b3; if (c3 < 0) c3 += n3;
   return (c1 * n2 + c2) * n3 + c3;
 }
+
+#ifdef __CUDACC__
+// e^{-2 pi i q.R} with q = m/N (integers): exact argument reduction mod N_k.
+__device__ __forceinline__ double2 phase_qR(int q, const int *R, int n1, int n2, int n3) {
+  int m1 = q / (n2 * n3), m2 = (q / n3) % n2, m3 = q % n3;
+  long long nk = (long long)n1 * n2 * n3;
+  long long p = (long long)m1 * R[0] * n2 * n3 + (long long)m2 * R[1] * n1 * n3 +
+                (long long)m3 * R[2] * n1 * n2;
+  p %= nk;
+  if (p < 0) p += nk;
+  double s, c;
+  sincospi(2.0 * (double)p / (double)nk, &s, &c);
+  return make_double2(c, -s);
+}
+
+// e^{+2 pi i k.R} for k = (n + off)/N.
+__device__ __forceinline__ double2 phase_kR(int k, const int *R, int n1, int n2, int n3,
+                                            double o1, double o2, double o3) {
+  int a1 = k / (n2 * n3), a2 = (k / n3) % n2, a3 = k % n3;
+  long long i1 = ((long long)a1 * R[0]) % n1, i2 = ((long long)a2 * R[1]) % n2,
+            i3 = ((long long)a3 * R[2]) % n3;
+  double f = (double)i1 / n1 + (double)i2 / n2 + (double)i3 / n3 +
+             (o1 * R[0]) / n1 + (o2 * R[1]) / n2 + (o3 * R[2]) / n3;
+  f = f - floor(f);
+  double s, c;
+  sincospi(2.0 * f, &s, &c);
+  return make_double2(c, s);
+}
+#endif

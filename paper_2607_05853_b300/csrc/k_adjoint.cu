@@ -218,6 +218,10 @@ bse_status adjoint_workspace(bse_ctx *c) {
 bse_status run_adjoint(bse_ctx *c, const double2 *Gamma, double *dW_R, double *de_qp) {
   bse_status s = adjoint_workspace(c);
   if (s != BSE_OK) return s;
+  if (!c->y64_valid) {  // split-precision context: widen its FP32 pair table once
+    s = split_y_to_fp64(c);
+    if (s != BSE_OK) return s;
+  }
   const int na = c->naux_tot;
   const long long rows = (long long)c->nk * c->nv * c->nv;
   for (int q0 = 0; q0 < c->nk; q0 += c->slab) {

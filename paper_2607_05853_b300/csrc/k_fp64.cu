@@ -30,33 +30,6 @@ __device__ __forceinline__ double2 cadd(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
 
-// e^{-2 pi i (q.R)} * w with q = m/N (integers): exact argument reduction mod N_k.
-__device__ __forceinline__ double2 phase_qR(int q, const int *R, int n1, int n2, int n3) {
-  int m1 = q / (n2 * n3), m2 = (q / n3) % n2, m3 = q % n3;
-  long long nk = (long long)n1 * n2 * n3;
-  long long p = (long long)m1 * R[0] * n2 * n3 + (long long)m2 * R[1] * n1 * n3 +
-                (long long)m3 * R[2] * n1 * n2;
-  p %= nk;
-  if (p < 0) p += nk;
-  double s, c;
-  sincospi(2.0 * (double)p / (double)nk, &s, &c);
-  return make_double2(c, -s);
-}
-
-// e^{+2 pi i k.R} for k = (n + off)/N.
-__device__ __forceinline__ double2 phase_kR(int k, const int *R, int n1, int n2, int n3,
-                                            double o1, double o2, double o3) {
-  int a1 = k / (n2 * n3), a2 = (k / n3) % n2, a3 = k % n3;
-  long long i1 = ((long long)a1 * R[0]) % n1, i2 = ((long long)a2 * R[1]) % n2,
-            i3 = ((long long)a3 * R[2]) % n3;
-  double f = (double)i1 / n1 + (double)i2 / n2 + (double)i3 / n3 +
-             (o1 * R[0]) / n1 + (o2 * R[1]) / n2 + (o3 * R[2]) / n3;
-  f = f - floor(f);
-  double s, c;
-  sincospi(2.0 * f, &s, &c);
-  return make_double2(c, s);
-}
-
 constexpr int QB = 4;  // q values per interp block
 
 __global__ void k_interp_W(const double *__restrict__ WR, const int *__restrict__ RW,

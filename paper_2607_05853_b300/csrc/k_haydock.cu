@@ -620,10 +620,11 @@ constexpr int hmv_tma_smem() {
   return HmvSmem<NP>::BYTES;
 }
 
-// W[p][row] = sum_s part[t][s][row_local][p] for the rows of block t (FP64, fixed order),
-// and the block's share of alpha_j = Re(Q_j^H W) per polarisation (apart[p][t]).  Two
-// threads per output stream the two halves of the block's 216 x 3 KB slab; their sums meet
-// in shared memory.
+// W[p][row] = sum_s part[t][s][row_local][p] for the rows of block t, and the block's share
+// of alpha_j = Re(Q_j^H W) per polarisation (apart[p][t]).  Two threads per output stream
+// the two halves of the block's slot slab; each keeps a compensated (Kahan) FP32 sum, so the
+// result carries FP64-like accuracy without FP64 adds (B300's FP64 rate is ~1/60 of FP32),
+// and the two halves meet in FP64 in a fixed order.
 template <int NP>
 __global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__restrict__ part, long long dim,
                                                                 int nb, double2 *__restrict__ W,
@@ -637,7 +638,9 @@ __global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__r
   const long long row = (long long)t * HT + l;
   const bool on = row < dim && j < meff[p];
   const int s0 = h ? nb / 2 : 0, s1 = h ? nb : nb / 2;
-  double sx[8] = {0, 0, 0, 0, 0, 0, 0, 0}, sy[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // Kahan: sum + (-comp) is the running total; each add is y = v - comp; t = sum + y;
+  // comp = (t - sum) - y; sum = t
+  float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
   if (on) {
     const float2 *src = part + ((long long)t * nb * HT + l) * NP + p;
     const long long step = (long long)HT * NP;
@@ -648,22 +651,25 @@ __global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__r
       for (int u = 0; u < 8; u++) v[u] = src[(s + u) * step];
 #pragma unroll
       for (int u = 0; u < 8; u++) {
-        sx[u] += v[u].x;
-        sy[u] += v[u].y;
+        const float yx = v[u].x - cx, tx = sx + yx;
+        cx = (tx - sx) - yx;
+        sx = tx;
+        const float yy = v[u].y - cy, ty = sy + yy;
+        cy = (ty - sy) - yy;
+        sy = ty;
       }
     }
     for (; s < s1; s++) {
       const float2 v = src[s * step];
-      sx[0] += v.x;
-      sy[0] += v.y;
+      const float yx = v.x - cx, tx = sx + yx;
+      cx = (tx - sx) - yx;
+      sx = tx;
+      const float yy = v.y - cy, ty = sy + yy;
+      cy = (ty - sy) - yy;
+      sy = ty;
     }
   }
-  double tx = 0.0, ty = 0.0;
-#pragma unroll
-  for (int u = 0; u < 8; u++) {
-    tx += sx[u];
-    ty += sy[u];
-  }
+  double tx = (double)sx - (double)cx, ty = (double)sy - (double)cy;
   if (h) hs[o] = make_double2(tx, ty);
   __syncthreads();
   if (!h) {

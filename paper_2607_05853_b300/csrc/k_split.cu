@@ -37,6 +37,14 @@ struct SplitWS {
   __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
   CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
   int bn_g1 = TC_BN;             // N tile of the M_vv W(q) GEMM (autotuned)
+  // FP32 per-k stage
+  float2 *PHQ = nullptr;         // [nk][n_RW]  w_R e^{-i q.R}
+  float2 *PHK = nullptr;         // [nk][n_RC]  e^{+i k.R}
+  float *WR32T = nullptr;        // [n_RW][nu][mu]
+  float *CR32 = nullptr;         // [n_RC][nao][nao][naux]
+  float *V032 = nullptr;         // [naux][naux]
+  float2 *ck32 = nullptr;        // [nk][nao][nb]
+  float2 *X32 = nullptr;         // [dim][naux]  exchange factors
 };
 
 SplitWS *ws(bse_ctx *c) { return (SplitWS *)c->tc; }
@@ -95,6 +103,244 @@ __global__ void k_split_rows(const double2 *__restrict__ src, long long rows, in
     dst[(2 * p) * plane + r * kmem + k] = pr[p];
     dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
   }
+}
+
+// ---- FP32 per-k stage (split precisions): phases in FP64, sums in FP32 -------------------
+// The products feed bf16 pieces whose sum carries ~2^-24 relative precision, so FP32 sums
+// lose nothing that the tensor-core path keeps, and B300's FP32 rate is ~60x its FP64 rate.
+
+// PHQ[q][r] = w_R e^{-2 pi i q.R} and PHK[k][r] = e^{+2 pi i k.R}, reduced exactly in FP64
+__global__ void k_phase_tables(const int *__restrict__ RW, const double *__restrict__ wRW, int nRW,
+                               const int *__restrict__ RC, int nRC, int n1, int n2, int n3, double o1, double o2,
+                               double o3, float2 *__restrict__ PHQ, float2 *__restrict__ PHK) {
+  const long long nk = (long long)n1 * n2 * n3;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nk * nRW) {
+    const int q = (int)(e / nRW), r = (int)(e % nRW);
+    const double2 d = phase_qR(q, RW + 3 * r, n1, n2, n3);
+    PHQ[e] = make_float2((float)(d.x * wRW[r]), (float)(d.y * wRW[r]));
+  } else if (e < nk * (nRW + nRC)) {
+    const long long e2 = e - nk * nRW;
+    const int k = (int)(e2 / nRC), r = (int)(e2 % nRC);
+    const double2 d = phase_kR(k, RC + 3 * r, n1, n2, n3, o1, o2, o3);
+    PHK[e2] = make_float2((float)d.x, (float)d.y);
+  }
+}
+
+// WR32T[r][nu][mu] = W_R[r][mu][nu]
+__global__ void k_wr_f32t(const double *__restrict__ WR, int nRW, int naux, float *__restrict__ WR32T) {
+  const long long nn = (long long)naux * naux;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn * nRW) return;
+  const long long r = e / nn, rem = e % nn;
+  const int mu = (int)(rem / naux), nu = (int)(rem % naux);
+  WR32T[r * nn + (long long)nu * naux + mu] = (float)WR[e];
+}
+
+__global__ void k_d2f(const double *__restrict__ src, long long n, float *__restrict__ dst) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (float)src[e];
+}
+
+__global__ void k_f2d(const float *__restrict__ src, long long n, double *__restrict__ dst) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+// W(q) = sum_R w_R e^{-i q.R} W(R) (R-sum of Eq. W_LRI) for IQB transfers per block, written
+// straight as the bf16 pieces of the tensor-core operand B[nu][mu] = W(q)[mu][nu] and, when
+// asked, as complex128 W(q)[mu][nu].
+constexpr int IQB = 16;
+__global__ void __launch_bounds__(256) k_interp_W32(const float *__restrict__ WR32T, const float2 *__restrict__ PHQ,
+                                                    int nRW, int naux, int nk, int kmem, int np,
+                                                    __nv_bfloat16 *__restrict__ Wp, double2 *__restrict__ Wq_out) {
+  extern __shared__ float2 phs[];  // [IQB][nRW]
+  const int q0 = blockIdx.y * IQB;
+  for (int t = threadIdx.x; t < IQB * nRW; t += blockDim.x) {
+    const int qq = t / nRW, r = t % nRW;
+    phs[t] = q0 + qq < nk ? PHQ[(long long)(q0 + qq) * nRW + r] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const long long nn = (long long)naux * naux;
+  const long long plane = (long long)naux * kmem;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x) {
+    float2 acc[IQB];
+#pragma unroll
+    for (int j = 0; j < IQB; j++) acc[j] = make_float2(0.f, 0.f);
+    for (int r = 0; r < nRW; r++) {
+      const float w = WR32T[r * nn + e];
+#pragma unroll
+      for (int j = 0; j < IQB; j++) {
+        acc[j].x = fmaf(phs[j * nRW + r].x, w, acc[j].x);
+        acc[j].y = fmaf(phs[j * nRW + r].y, w, acc[j].y);
+      }
+    }
+    const int nu = (int)(e / naux), mu = (int)(e % naux);
+#pragma unroll
+    for (int j = 0; j < IQB; j++) {
+      const int q = q0 + j;
+      if (q >= nk) break;
+      __nv_bfloat16 pr[3], pi[3];
+      split_pieces<float>(acc[j].x, np, pr);
+      split_pieces<float>(acc[j].y, np, pi);
+      __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
+      for (int p = 0; p < np; p++) {
+        base[(2 * p) * plane] = pr[p];
+        base[(2 * p + 1) * plane] = pi[p];
+      }
+      if (Wq_out) Wq_out[(long long)q * nn + (long long)mu * naux + nu] = make_double2(acc[j].x, acc[j].y);
+    }
+  }
+}
+
+constexpr int TCH32 = 16;  // t-chunk of the half transform
+
+// One block per (s, k): Y32[k][s_loc][n][mu] = sum_t [sum_R C^mu_st(R) e^{ik.R}] c^k_tn, mu on atom(s).
+__global__ void k_half_transform32(const float *__restrict__ CR, const float2 *__restrict__ PHK, int nRC,
+                                   const float2 *__restrict__ ck, int nao_tot, int nb, int naux, int nao_max,
+                                   const int *__restrict__ ao_start, const int *__restrict__ aux_start,
+                                   const int *__restrict__ nauxA, int n_atoms, float2 *__restrict__ Y) {
+  extern __shared__ float2 sh[];
+  const int s = blockIdx.x, k = blockIdx.y;
+  int A = 0;
+  while (A + 1 < n_atoms && ao_start[A + 1] <= s) A++;
+  const int s_loc = s - ao_start[A], mu0 = aux_start[A], nmu = nauxA[A];
+  float2 *phs = sh;                       // [nRC]
+  float2 *cks = phs + nRC;                // [nao_tot][nb]
+  float2 *Ckc = cks + nao_tot * nb;       // [TCH32][nmu]
+  float2 *Yacc = Ckc + TCH32 * nmu;       // [nb][nmu]
+  for (int r = threadIdx.x; r < nRC; r += blockDim.x) phs[r] = PHK[(long long)k * nRC + r];
+  for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) cks[e] = ck[(long long)k * nao_tot * nb + e];
+  for (int e = threadIdx.x; e < nb * nmu; e += blockDim.x) Yacc[e] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const long long sR = (long long)nao_tot * nao_tot * naux;
+  for (int t0 = 0; t0 < nao_tot; t0 += TCH32) {
+    for (int e = threadIdx.x; e < TCH32 * nmu; e += blockDim.x) {
+      const int tt = e / nmu, mu = e % nmu, t = t0 + tt;
+      float2 acc = make_float2(0.f, 0.f);
+      if (t < nao_tot) {
+        const float *src = CR + ((long long)s * nao_tot + t) * naux + mu0 + mu;
+        for (int r = 0; r < nRC; r++) {
+          const float v = src[r * sR];
+          acc.x = fmaf(phs[r].x, v, acc.x);
+          acc.y = fmaf(phs[r].y, v, acc.y);
+        }
+      }
+      Ckc[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nmu; e += blockDim.x) {
+      const int n = e / nmu, mu = e % nmu;
+      float2 acc = Yacc[e];
+      const int tmax = min(TCH32, nao_tot - t0);
+      for (int tt = 0; tt < tmax; tt++) {
+        const float2 a = Ckc[tt * nmu + mu], b = cks[(t0 + tt) * nb + n];
+        acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
+        acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
+      }
+      Yacc[e] = acc;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nmu; e += blockDim.x) {
+    const int n = e / nmu, mu = e % nmu;
+    Y[(((long long)k * nao_max + s_loc) * nb + n) * naux + mu0 + mu] = Yacc[e];
+  }
+}
+
+// X[(k,i,a)][mu] = C~^mu_{a k, i k} = F(k,k)_{(nv+a) i} + conj(F(k,k)_{i (nv+a)}) in FP32,
+// also written as the bf16 pieces of conj(X) (operand B of the exchange GEMM).
+__global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__restrict__ ck, int nao_tot, int nb,
+                               int nv, int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
+                               const int *__restrict__ ao_start, const int *__restrict__ naoA, long long dim,
+                               int kmem, int np, float2 *__restrict__ X, __nv_bfloat16 *__restrict__ Xp) {
+  const int k = blockIdx.y;
+  const int mu = blockIdx.x * blockDim.x + threadIdx.x;
+  if (mu >= naux) return;
+  const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+  const float2 *c = ck + (long long)k * nao_tot * nb;
+  const float2 *Yk = Y + (long long)k * nao_max * nb * naux;
+  const long long plane = dim * kmem;
+  for (int i = 0; i < nv; i++)
+    for (int a = 0; a < nc; a++) {
+      float2 f1 = make_float2(0.f, 0.f), f2 = make_float2(0.f, 0.f);
+      for (int s = 0; s < na; s++) {
+        const float2 ca = c[(ao0 + s) * nb + nv + a], y1 = Yk[((long long)s * nb + i) * naux + mu];
+        const float2 ci = c[(ao0 + s) * nb + i], y2 = Yk[((long long)s * nb + nv + a) * naux + mu];
+        f1.x = fmaf(ca.x, y1.x, fmaf(ca.y, y1.y, f1.x));   // conj(ca) y1
+        f1.y = fmaf(ca.x, y1.y, fmaf(-ca.y, y1.x, f1.y));
+        f2.x = fmaf(ci.x, y2.x, fmaf(ci.y, y2.y, f2.x));   // conj(ci) y2
+        f2.y = fmaf(ci.x, y2.y, fmaf(-ci.y, y2.x, f2.y));
+      }
+      const float2 x = make_float2(f1.x + f2.x, f1.y - f2.y);
+      const long long r = ((long long)k * nv + i) * nc + a;
+      X[r * naux + mu] = x;
+      __nv_bfloat16 pr[3], pi[3];
+      split_pieces<float>(x.x, np, pr);
+      split_pieces<float>(-x.y, np, pi);
+      for (int p = 0; p < np; p++) {
+        Xp[(2 * p) * plane + r * kmem + mu] = pr[p];
+        Xp[(2 * p + 1) * plane + r * kmem + mu] = pi[p];
+      }
+    }
+}
+
+// P = X V(0) (V(0) real) in FP32, 64 x 64 tiles, written as bf16 pieces (operand A of the
+// exchange GEMM).
+__global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *__restrict__ X,
+                                                    const float *__restrict__ V0, int kmem, int np,
+                                                    __nv_bfloat16 *__restrict__ Pp) {
+  __shared__ float2 As[16][64];
+  __shared__ float Bs[16][64];
+  const int K = N;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int r = e / 16, kk = e % 16, gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? X[(long long)gr * K + gk] : make_float2(0.f, 0.f);
+      const int kb = e / 64, cc = e % 64, gkb = k0 + kb, gc = col0 + cc;
+      Bs[kb][cc] = (gkb < K && gc < N) ? V0[(long long)gkb * N + gc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+      float2 a[4];
+      float b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[i][j].x = fmaf(a[i].x, b[j], acc[i][j].x);
+          acc[i][j].y = fmaf(a[i].y, b[j], acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+  const long long plane = (long long)M * kmem;
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = row0 + ty + 16 * i, cc = col0 + tx + 16 * j;
+      if (r >= M || cc >= N) continue;
+      __nv_bfloat16 pr[3], pi[3];
+      split_pieces<float>(acc[i][j].x, np, pr);
+      split_pieces<float>(acc[i][j].y, np, pi);
+      for (int p = 0; p < np; p++) {
+        Pp[(2 * p) * plane + (long long)r * kmem + cc] = pr[p];
+        Pp[(2 * p + 1) * plane + (long long)r * kmem + cc] = pi[p];
+      }
+    }
 }
 
 __global__ void k_to_f32(const double2 *__restrict__ src, long long n, float2 *__restrict__ dst) {
@@ -232,6 +478,7 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
     __syncthreads();
   }
   const double inv = 1.0 / nk;
+  const float invf = (float)inv;
 #pragma unroll
   for (int t = 0; t < MAXO; t++) {
     const int o = threadIdx.x + t * blockDim.x;
@@ -240,13 +487,15 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
       const int i = ia / nc, a = ia % nc;
       float2 *hp = H + ((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb;
       const float2 hx = *hp;
-      double hr = (double)hx.x - inv * (double)ad[t].x, hi = (double)hx.y - inv * (double)ad[t].y;
-      if (q == 0 && ia == jb) hr += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
-      *hp = make_float2((float)hr, (float)hi);
+      float2 hv = make_float2(fmaf(-invf, ad[t].x, hx.x), fmaf(-invf, ad[t].y, hx.y));
+      if (q == 0 && ia == jb)  // the diagonal sums in FP64 (one element per row)
+        hv.x = (float)((double)hx.x - inv * (double)ad[t].x + eqp[(long long)k1 * nb + nv + a] -
+                       eqp[(long long)k1 * nb + i]);
+      *hp = hv;
       if (mirror) {  // block (k2, k1) gets the conjugate of the direct contribution
         float2 *hm = H + ((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia;
         const float2 mx = *hm;
-        *hm = make_float2((float)((double)mx.x - inv * (double)ad[t].x), (float)((double)mx.y + inv * (double)ad[t].y));
+        *hm = make_float2(fmaf(-invf, ad[t].x, mx.x), fmaf(invf, ad[t].y, mx.y));
       }
     }
   }
@@ -385,6 +634,7 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
   }
   __syncthreads();
   const double inv = 1.0 / nk;
+  const float invf = (float)inv;
   for (int w = threadIdx.x; w < TR * TCC; w += blockDim.x) {
     const int tr = w / TCC, tc = w % TCC;
     const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
@@ -414,14 +664,15 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
         const int ia = i * NC + a, jb = j * NC + b;
         float2 *hp = H + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
         const float2 hx = *hp;
-        double hr = (double)hx.x - inv * (double)acc[x][y].x, hi = (double)hx.y - inv * (double)acc[x][y].y;
-        if (q == 0 && ia == jb) hr += eqp[(long long)k1 * NB + NV + a] - eqp[(long long)k1 * NB + i];
-        *hp = make_float2((float)hr, (float)hi);
+        float2 hv = make_float2(fmaf(-invf, acc[x][y].x, hx.x), fmaf(-invf, acc[x][y].y, hx.y));
+        if (q == 0 && ia == jb)  // the diagonal sums in FP64 (one element per row)
+          hv.x = (float)((double)hx.x - inv * (double)acc[x][y].x + eqp[(long long)k1 * NB + NV + a] -
+                         eqp[(long long)k1 * NB + i]);
+        *hp = hv;
         if (mirror) {
           float2 *hm = H + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
           const float2 mx = *hm;
-          *hm = make_float2((float)((double)mx.x - inv * (double)acc[x][y].x),
-                            (float)((double)mx.y + inv * (double)acc[x][y].y));
+          *hm = make_float2(fmaf(-invf, acc[x][y].x, mx.x), fmaf(invf, acc[x][y].y, mx.y));
         }
       }
   }
@@ -569,7 +820,13 @@ bse_status split_setup(bse_ctx *c) {
   };
   const size_t nn = (size_t)na * na;
   const size_t dimz = (size_t)c->dim;
-  if (!alloc((void **)&c->Wq, (size_t)c->nk * nn * sizeof(double2)) ||
+  if (!alloc((void **)&w->PHQ, (size_t)c->nk * c->n_RW * sizeof(float2)) ||
+      !alloc((void **)&w->PHK, (size_t)c->nk * c->n_RC * sizeof(float2)) ||
+      !alloc((void **)&w->WR32T, (size_t)c->n_RW * nn * sizeof(float)) ||
+      !alloc((void **)&w->CR32, (size_t)c->n_RC * c->nao_tot * c->nao_tot * na * sizeof(float)) ||
+      !alloc((void **)&w->V032, nn * sizeof(float)) ||
+      !alloc((void **)&w->ck32, (size_t)c->nk * c->nao_tot * c->nb * sizeof(float2)) ||
+      !alloc((void **)&w->X32, dimz * na * sizeof(float2)) ||
       !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * 2) ||
       !alloc((void **)&w->Ap, (size_t)w->nq * w->pp * w->rows * w->kmem * 2) ||
       !alloc((void **)&w->Mc32, (size_t)w->nq * c->nk * c->nc * c->nc * na * 8) ||
@@ -582,6 +839,13 @@ bse_status split_setup(bse_ctx *c) {
   cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * 2);
   cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * 2);
   cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * 2);
+  {
+    const long long nph = (long long)c->nk * (c->n_RW + c->n_RC);
+    k_phase_tables<<<(unsigned)((nph + 255) / 256), 256, 0, c->stream>>>(
+        c->d_R_W, c->d_w_RW, c->n_RW, c->d_R_C, c->n_RC, c->mesh[0], c->mesh[1], c->mesh[2], c->koff[0],
+        c->koff[1], c->koff[2], w->PHQ, w->PHK);
+    bse_count_launch();
+  }
   set_all_attrs();
   bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
             make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
@@ -595,41 +859,72 @@ bse_status split_setup(bse_ctx *c) {
 void split_free(bse_ctx *c) {
   SplitWS *w = ws(c);
   if (!w) return;
-  void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp};
+  void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp, w->PHQ, w->PHK, w->WR32T, w->CR32, w->V032,
+                  w->ck32, w->X32};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
   c->tc = nullptr;
 }
 
-bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out) {
+bse_status split_interp_W(bse_ctx *c, const double *W_R, const double *V0, double2 *Wq_out) {
   SplitWS *w = ws(c);
-  bse_status s = launch_interp_W_fp64(c, W_R, c->Wq);
-  if (s != BSE_OK) return s;
-  const long long nn = (long long)c->naux_tot * c->naux_tot;
-  dim3 grid((unsigned)((nn + 255) / 256), c->nk);
-  k_split_W<<<grid, 256, 0, c->stream>>>(c->Wq, c->nk, c->naux_tot, w->kmem, w->np, w->Wp);
-  bse_count_launch();
-  s = bse_check_launch(c, "split_W");
-  if (s != BSE_OK) return s;
-  if (Wq_out && cudaMemcpyAsync(Wq_out, c->Wq, (size_t)c->nk * nn * sizeof(double2), cudaMemcpyDeviceToDevice,
-                                c->stream) != cudaSuccess)
-    return bse_fail(c, BSE_ECUDA, "interp_W: copy to Wq_out failed");
-  return BSE_OK;
+  const int na = c->naux_tot;
+  const long long nn = (long long)na * na;
+  k_wr_f32t<<<(unsigned)((nn * c->n_RW + 255) / 256), 256, 0, c->stream>>>(W_R, c->n_RW, na, w->WR32T);
+  k_d2f<<<(unsigned)std::min<long long>((nn + 255) / 256, 4096), 256, 0, c->stream>>>(V0, nn, w->V032);
+  const size_t sm = sizeof(float2) * IQB * c->n_RW;
+  if (sm > 48 * 1024 &&
+      cudaFuncSetAttribute(k_interp_W32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+    return bse_fail(c, BSE_EINVAL, "interp_W: too many W(R) images for one block");
+  dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (c->nk + IQB - 1) / IQB);
+  bse_prof_begin(c, BSE_KP_INTERP);
+  k_interp_W32<<<grid, 256, sm, c->stream>>>(w->WR32T, w->PHQ, c->n_RW, na, c->nk, w->kmem, w->np, w->Wp, Wq_out);
+  bse_prof_end(c, BSE_KP_INTERP);
+  bse_count_launch(3);
+  return bse_check_launch(c, "split interp_W");
 }
 
-// Called at the end of bse_project_pairs (after Y, X and P exist in FP64).
-bse_status split_project(bse_ctx *c) {
+// Per-k stage in FP32: Y, the exchange factors X (+ pieces of conj X) and P = X V(0) (pieces).
+bse_status split_project(bse_ctx *c, const double *C_R) {
   SplitWS *w = ws(c);
-  const long long ny = (long long)c->nk * c->nao_max * c->nb * c->naux_tot;
-  k_to_f32<<<(unsigned)((ny + 255) / 256), 256, 0, c->stream>>>(c->Y, ny, w->Y32);
-  const long long nx = c->dim * (long long)c->naux_tot;
-  k_split_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->stream>>>(c->P, c->dim, c->naux_tot, w->kmem, w->np, 0,
-                                                                    w->Pp);
-  k_split_rows<<<(unsigned)((nx + 255) / 256), 256, 0, c->stream>>>(c->X, c->dim, c->naux_tot, w->kmem, w->np, 1,
-                                                                    w->Xp);
-  bse_count_launch(3);
-  return bse_check_launch(c, "split_project");
+  const int na = c->naux_tot;
+  const long long ncr = (long long)c->n_RC * c->nao_tot * c->nao_tot * na;
+  const long long nck = (long long)c->nk * c->nao_tot * c->nb * 2;
+  k_d2f<<<(unsigned)std::min<long long>((ncr + 255) / 256, 8192), 256, 0, c->stream>>>(C_R, ncr, w->CR32);
+  k_d2f<<<(unsigned)std::min<long long>((nck + 255) / 256, 8192), 256, 0, c->stream>>>((const double *)c->ck, nck,
+                                                                                        (float *)w->ck32);
+  int maxmu = 0;
+  for (int a : c->naux) maxmu = std::max(maxmu, a);
+  const size_t sm = sizeof(float2) * (c->n_RC + c->nao_tot * c->nb + TCH32 * maxmu + c->nb * maxmu);
+  if (sm > 200 * 1024) return bse_fail(c, BSE_EINVAL, "half transform: basis too large for one block");
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_half_transform32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  bse_prof_begin(c, BSE_KP_HALF);
+  k_half_transform32<<<dim3(c->nao_tot, c->nk), 256, sm, c->stream>>>(
+      w->CR32, w->PHK, c->n_RC, w->ck32, c->nao_tot, c->nb, na, c->nao_max, c->d_ao_start, c->d_aux_start,
+      c->d_naux, c->n_atoms, w->Y32);
+  bse_prof_end(c, BSE_KP_HALF);
+  k_exchange_X32<<<dim3((na + 127) / 128, c->nk), 128, 0, c->stream>>>(
+      w->Y32, w->ck32, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao,
+      c->dim, w->kmem, w->np, w->X32, w->Xp);
+  dim3 g((na + 63) / 64, (unsigned)((c->dim + 63) / 64));
+  if (g.y > 65535) return bse_fail(c, BSE_EINVAL, "exchange factors: dim too large for the P grid");
+  k_xv0_pieces<<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
+  bse_count_launch(5);
+  c->y64_valid = false;
+  return bse_check_launch(c, "split project");
+}
+
+// The FP64 pair table for the adjoint of a split-precision context: the FP32 table widened.
+bse_status split_y_to_fp64(bse_ctx *c) {
+  SplitWS *w = ws(c);
+  const long long ny = 2LL * c->nk * c->nao_max * c->nb * c->naux_tot;
+  k_f2d<<<(unsigned)std::min<long long>((ny + 255) / 256, 8192), 256, 0, c->stream>>>((const float *)w->Y32, ny,
+                                                                                       (double *)c->Y);
+  bse_count_launch();
+  c->y64_valid = true;
+  return bse_check_launch(c, "pair table to FP64");
 }
 
 bse_status split_assemble(bse_ctx *c, void *Hv) {

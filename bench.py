@@ -29,6 +29,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "H_BSE elements/s (split-prec TC vs FP64 GPU) at ≤1 meV lowest-exciton error"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128x128 tile of the current
+# Hermitian matvec kernel, from one ncu capture of the 16000-dim case (7875 tiles):
+# 1.032880 GB read (the tiles themselves) + 45.80 MB written (the partial slots).
+MV_DRAM_BYTES_PER_TILE = (1.032880e9 + 45.800704e6) / 7875
 UNIT = "H elements/s"
 
 
@@ -150,6 +154,20 @@ def cpu_baseline(inp, seconds, rng_seed=5):
                       f"memoised per block as the oracle does, {dt:.1f} s on host cores"}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks, returned on every rank (the job's wall time is that of
+    its slowest rank)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, units_per_step: float, t_max_ms: float) -> float:
+    """Whole-job rate: every rank processes units_per_step per step (weak scaling)."""
+    return world * steps * units_per_step / (t_max_ms / 1000.0)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -253,11 +271,9 @@ def main():
     ctx.profile(False)
     t_total = sum(step_ms)
     if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+        t_total = max_over_ranks(t_total, dist, dev)
     dim2 = float(ctx.dim) ** 2
-    value = world * args.steps * dim2 / (t_total / 1000.0)
+    value = job_throughput(world, args.steps, dim2, t_total)
     asm_rate = dim2 / (statistics.mean([p + a for p, a in zip(pre_ms, asm_ms)]) / 1000.0)
 
     # ---- end to end: host inputs -> device -> path -> eps2 back to host ----------------
@@ -292,10 +308,15 @@ def main():
         else:
             HT = 128
             nbt = (ctx.dim + HT - 1) // HT
-            alg = nbt * (nbt + 1) / 2 * HT * HT * h_elem + 3 * ctx.dim * 16
-            roof_note = ("Lanczos matvec, Hermitian half read: algorithmic bytes = upper-triangle 128x128 tiles of "
-                         "the complex64 H (the only part the method must read) + 3 output vectors, per launch")
+            ntiles = nbt * (nbt + 1) // 2
+            alg = ntiles * HT * HT * h_elem
+            roof_note = ("Lanczos matvec k_hmv_tma, Hermitian half read: algorithmic bytes = the upper-triangle "
+                         "128x128 tiles of the complex64 H (the only part the method must read), per launch; "
+                         "traffic = DRAM read+write bytes per tile from an ncu capture of the 16000-dim case "
+                         "(7875 tiles) times this launch's tile count")
         roof = {"bound": "hbm", "achieved": alg / (per_launch_ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+        if args.precision != "fp64" and ctx.dim % 2 == 0:
+            roof["traffic"] = MV_DRAM_BYTES_PER_TILE * ntiles
     elif top == "g1" and args.precision != "fp64":
         pieces = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1}[args.precision]
         alg = 8.0 * nk * nv * nv * naux * naux * pieces * (ctx_slab_q(ctx, spec))
@@ -310,7 +331,7 @@ def main():
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof["frac"] = None
-    roof["traffic"] = None
+    roof.setdefault("traffic", None)
     roof["kernel"] = top
     roof["peak_source"] = pk["source"]
     roof["note"] = roof_note

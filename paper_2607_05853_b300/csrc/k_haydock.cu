@@ -1239,12 +1239,15 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       const int grid = std::min(s.ntiles, MV_CTAS * c->n_sm);
       if (n_pol == 1) {
         k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmv_tma<2><<<grid, 128, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmv_tma<3><<<grid, 128, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
       bse_count_launch(2);
@@ -1252,12 +1255,15 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       dim3 g(s.nbt, s.nbt);
       if (n_pol == 1) {
         k_hmatvec_c64<1><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmatvec_c64<2><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmatvec_c64<3><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
+        bse_prof_end(c, BSE_KP_MATVEC);
         k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
       bse_count_launch(2);

@@ -19,6 +19,9 @@ What it computes, and where each step comes from in the paper (arXiv 2607.05853)
   half-width eta; the exact sum uses a LAPACK eigendecomposition, and a plain Haydock
   (Lanczos) recursion gives the same quantity through a continued fraction.
 * lowest exciton energies: LAPACK eigvalsh of the Hermitian TDA matrix.
+* the windowed absorption integral I = int_lo^hi eps2(omega) domega (eps2 as above) and
+  its seed Gamma with dI = tr(Gamma dH), by the Daleckii-Krein formula for the derivative
+  of a matrix function on the full eigendecomposition.
 
 Index conventions: the H row of (k, v, c) is (k*Nv + v)*Nc + c; valence window column
 v=0 is the valence band maximum (counting down), conduction column c=0 the conduction
@@ -35,7 +38,7 @@ import numpy as np
 __all__ = [
     "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
     "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
-    "adjoint_seed_lowest", "grad_from_seed",
+    "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact",
 ]
 
 TWO_PI = 2.0 * np.pi
@@ -283,3 +286,39 @@ def grad_from_seed(orc, Gamma):
     de[:, nv:] = d.sum(axis=1)
     de[:, :nv] = -d.sum(axis=2)
     return dW, de
+
+
+def window_weight(x, lo, hi, eta):
+    """f(x) = int_lo^hi (1/pi) eta / ((omega - x)^2 + eta^2) domega: the Lorentzian of
+    Eq. abs_vel (half width eta) integrated over the window [lo, hi]."""
+    x = np.asarray(x, dtype=np.float64)
+    return (np.arctan((hi - x) / eta) - np.arctan((lo - x) / eta)) / np.pi
+
+
+def window_integral(H, d, lo, hi, eta, pref):
+    """I = int_lo^hi eps2(omega) domega for eps2 of Eq. abs_vel (Lorentzian half width eta),
+    from a full eigendecomposition: pref sum_S |sum_r d_r X_rS|^2 f(Omega_S)."""
+    w, X = np.linalg.eigh(H)
+    osc = np.abs(np.asarray(d) @ X) ** 2
+    return pref * float(osc.sum(axis=0) @ window_weight(w, lo, hi, eta))
+
+
+def window_seed_exact(H, d, lo, hi, eta, pref):
+    """Gamma with dI = tr(Gamma dH) for the window integral I, from the Daleckii-Krein
+    derivative of the matrix function f(H): with H = X diag(w) X^dagger,
+    df(H) = X (F o (X^dagger dH X)) X^dagger, F_ST = (f(w_S) - f(w_T)) / (w_S - w_T)
+    (f'(w_S) where w_S = w_T).  I = pref sum_p u_p^dagger f(H) u_p with u_p = conj(d_p)
+    gives Gamma = pref sum_p X (F o c_p c_p^dagger) X^dagger, c_p = X^dagger u_p."""
+    w, X = np.linalg.eigh(H)
+    f = window_weight(w, lo, hi, eta)
+    ya, yb = lo - w, hi - w
+    df = (eta / (ya ** 2 + eta ** 2) - eta / (yb ** 2 + eta ** 2)) / np.pi
+    gap = w[:, None] - w[None, :]
+    close = np.abs(gap) <= 1e-9 * (np.abs(w[:, None]) + np.abs(w[None, :]) + eta)
+    F = np.where(close, 0.5 * (df[:, None] + df[None, :]), (f[:, None] - f[None, :]) / np.where(close, 1.0, gap))
+    G = np.zeros(H.shape, np.complex128)
+    for dp in np.asarray(d):
+        c = X.conj().T @ np.conj(dp)
+        G += X @ (F * np.outer(c, c.conj())) @ X.conj().T
+    return pref * G
+

@@ -350,3 +350,76 @@ def test_gradient_euler_identity():
         for k2 in range(orc.nk):
             direct[k1 * n:(k1 + 1) * n, k2 * n:(k2 + 1) * n] = -orc.direct(k1, k2).reshape(n, n)
     assert np.isclose(np.sum(inp["W_R"] * dW), np.vdot(x, direct @ x).real, rtol=1e-10)
+
+
+# ---- windowed absorption integral (scope row a8) -------------------------------------------
+WIN = (1.5, 3.0)
+
+
+def _win_setup():
+    inp, orc, _, _ = _grad_setup()
+    d = orc.dipoles()
+    eta, pref = 0.1, orc.prefactor()
+    return inp, orc, d, eta, pref
+
+
+def _window_after(inp, key, change, d, eta, pref):
+    dd = dict(inp)
+    dd[key] = change(inp[key].copy())
+    return O.window_integral(O.BSEOracle(dd).hamiltonian(), d, WIN[0], WIN[1], eta, pref)
+
+
+def test_window_integral_equals_quadrature_of_spectrum():
+    """The closed-form window weight (atan difference) against a fine trapezoid rule of the
+    broadened spectrum eps2 over the window."""
+    inp, orc, d, eta, pref = _win_setup()
+    H = orc.hamiltonian()
+    om = np.linspace(WIN[0], WIN[1], 60001)
+    eps = O.eps2_exact(H, d, om, eta, pref)
+    quad = float(np.sum(0.5 * (eps[1:] + eps[:-1]) * np.diff(om)))
+    assert np.isclose(O.window_integral(H, d, WIN[0], WIN[1], eta, pref), quad, rtol=1e-8)
+
+
+def test_window_gradient_matches_central_differences():
+    """Daleckii-Krein seed through the oracle's gradient against central differences of the
+    window integral: symmetric W(R) pairs and single E^QP entries."""
+    inp, orc, d, eta, pref = _win_setup()
+    G = O.window_seed_exact(orc.hamiltonian(), d, WIN[0], WIN[1], eta, pref)
+    assert np.abs(G - G.conj().T).max() <= 1e-13 * np.abs(G).max()
+    dW, de = O.grad_from_seed(orc, G)
+    RW, h = inp["R_W"], 1e-6
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        r, m, n = int(rng.integers(len(RW))), int(rng.integers(13)), int(rng.integers(13))
+        rp = _pair(RW, r)
+        single = rp == r and m == n
+
+        def bump(s):
+            def f(W):
+                W[r, m, n] += s
+                if not single:
+                    W[rp, n, m] += s
+                return W
+            return f
+        fd = (_window_after(inp, "W_R", bump(h), d, eta, pref) - _window_after(inp, "W_R", bump(-h), d, eta, pref)) / (2 * h)
+        an = dW[r, m, n] + (0.0 if single else dW[rp, n, m])
+        assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-4 * np.abs(dW).max()), (r, m, n, fd, an)
+    for (k, n) in [(1, 2), (4, 0), (5, 3)]:
+        def shift(s):
+            def f(e):
+                e[k, n] += s
+                return e
+            return f
+        fd = (_window_after(inp, "e_qp", shift(h), d, eta, pref) - _window_after(inp, "e_qp", shift(-h), d, eta, pref)) / (2 * h)
+        assert abs(fd - de[k, n]) <= 1e-5 * max(abs(fd), 1e-4 * np.abs(de).max()), (k, n, fd, de[k, n])
+
+
+def test_window_gradient_shift_sum_rule():
+    """A uniform conduction shift s moves every exciton by s, so dI/ds = eps2(lo) - eps2(hi);
+    a valence shift gives the opposite."""
+    inp, orc, d, eta, pref = _win_setup()
+    H = orc.hamiltonian()
+    dW, de = O.grad_from_seed(orc, O.window_seed_exact(H, d, WIN[0], WIN[1], eta, pref))
+    e_lo, e_hi = O.eps2_exact(H, d, np.array(WIN), eta, pref)
+    assert np.isclose(de[:, 2:].sum(), e_lo - e_hi, rtol=1e-10, atol=1e-14)
+    assert np.isclose(de[:, :2].sum(), e_hi - e_lo, rtol=1e-10, atol=1e-14)

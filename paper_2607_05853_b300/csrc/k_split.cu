@@ -80,7 +80,9 @@ __global__ void k_split_W(const double2 *__restrict__ Wq, int nk, int naux, int 
   split_pieces<double>(w.y, np, pi);
   const long long plane = (long long)naux * kmem;
   __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
-  for (int p = 0; p < np; p++) {
+#pragma unroll
+  for (int p = 0; p < 3; p++) {
+    if (p >= np) break;
     base[(2 * p) * plane] = pr[p];
     base[(2 * p + 1) * plane] = pi[p];
   }
@@ -99,7 +101,9 @@ __global__ void k_split_rows(const double2 *__restrict__ src, long long rows, in
   split_pieces<double>(v.x, np, pr);
   split_pieces<double>(v.y, np, pi);
   const long long plane = rows * kmem;
-  for (int p = 0; p < np; p++) {
+#pragma unroll
+  for (int p = 0; p < 3; p++) {
+    if (p >= np) break;
     dst[(2 * p) * plane + r * kmem + k] = pr[p];
     dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
   }
@@ -184,7 +188,9 @@ __global__ void __launch_bounds__(256) k_interp_W32(const float *__restrict__ WR
       split_pieces<float>(acc[j].x, np, pr);
       split_pieces<float>(acc[j].y, np, pi);
       __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
-      for (int p = 0; p < np; p++) {
+#pragma unroll
+      for (int p = 0; p < 3; p++) {
+        if (p >= np) break;
         base[(2 * p) * plane] = pr[p];
         base[(2 * p + 1) * plane] = pi[p];
       }
@@ -278,7 +284,9 @@ __global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__res
       __nv_bfloat16 pr[3], pi[3];
       split_pieces<float>(x.x, np, pr);
       split_pieces<float>(-x.y, np, pi);
-      for (int p = 0; p < np; p++) {
+#pragma unroll
+      for (int p = 0; p < 3; p++) {
+        if (p >= np) break;
         Xp[(2 * p) * plane + r * kmem + mu] = pr[p];
         Xp[(2 * p + 1) * plane + r * kmem + mu] = pi[p];
       }
@@ -336,7 +344,9 @@ __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *
       __nv_bfloat16 pr[3], pi[3];
       split_pieces<float>(acc[i][j].x, np, pr);
       split_pieces<float>(acc[i][j].y, np, pi);
-      for (int p = 0; p < np; p++) {
+#pragma unroll
+      for (int p = 0; p < 3; p++) {
+        if (p >= np) break;
         Pp[(2 * p) * plane + (long long)r * kmem + cc] = pr[p];
         Pp[(2 * p + 1) * plane + (long long)r * kmem + cc] = pi[p];
       }
@@ -404,7 +414,9 @@ __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict
         __nv_bfloat16 pr[3], pi[3];
         split_pieces<float>(vr, np, pr);
         split_pieces<float>(vi, np, pi);
-        for (int p = 0; p < np; p++) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+          if (p >= np) break;
           out[(2 * p) * plane + (long long)j * kmem] = pr[p];
           out[(2 * p + 1) * plane + (long long)j * kmem] = pi[p];
         }
@@ -588,7 +600,9 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
         split_pieces<float>(mv[i][j].x, np, pr);
         split_pieces<float>(mv[i][j].y, np, pi);
         const long long r = (long long)(i * NV + j) * kmem;
-        for (int p = 0; p < np; p++) {
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+          if (p >= np) break;
           out[(2 * p) * plane + r] = pr[p];
           out[(2 * p + 1) * plane + r] = pi[p];
         }

@@ -162,6 +162,25 @@ bse_status bse_lowest(bse_ctx *ctx, const void *H, int n_eig, int n_steps, uint6
  *  vecs : [r][dim] complex128 (e.g. Ritz vectors from bse_lowest);  g : [r] float64. */
 bse_status bse_adjoint_seed(bse_ctx *ctx, const double *vecs, const double *g, int r, double *Gamma);
 
+/* Adjoint seed of the windowed absorption integral (scope row a8): with the Lorentzian of
+ * Eq. abs_vel (half width eta) integrated over [w_lo, w_hi],
+ *   I = prefactor * sum_p u_p^dagger f(H) u_p,
+ *   f(x) = (1/pi) [atan((w_hi - x)/eta) - atan((w_lo - x)/eta)],
+ * i.e. the integral of the bse_spectrum output over the window.  n_steps Lanczos steps per
+ * start vector (FP64, full reorthogonalisation, as bse_spectrum) give the tridiagonal T_p;
+ * its eigenpairs (implicit QL) give Ritz vectors y_i and weights v_i (first components), and
+ *   Gamma = sum_p prefactor |u_p|^2 sum_{i,l} F_il v_i v_l y_i y_l^dagger,
+ *   F_il = (f(theta_i) - f(theta_l)) / (theta_i - theta_l), F_ii = f'(theta_i)
+ * (Daleckii-Krein in the Krylov subspace; exact when n_steps = dim), so that
+ * dI = tr(Gamma dH) and bse_adjoint(Gamma) returns dI/dW(R) and dI/dE^QP.
+ *  H : as bse_spectrum;  u : [n_pol][dim] complex128 (n_pol 1..3), e.g. from bse_dipole_vector;
+ *  I_out : optional device float64 receiving I from the same Krylov data, or NULL;
+ *  Gamma : [dim][dim] complex128 output, Hermitian, overwritten.
+ * Scratch per call: the Krylov basis and 2 n_pol n_steps (n_steps + dim) doubles. */
+bse_status bse_window_seed(bse_ctx *ctx, const void *H, const double *u, int n_pol, int n_steps,
+                           double w_lo, double w_hi, double eta, double prefactor, double *I_out,
+                           double *Gamma);
+
 /* Gradient of a scalar L with dL = tr(Gamma dH) through the assembly (Eq. Hamiltonian with
  * the kernels of Eq. W_LRI), FP64 throughout; the pair projections are recomputed per q-slab.
  *  Gamma : [dim][dim] complex128 Hermitian seed.

@@ -179,6 +179,20 @@ class BSE:
         self._check(self._lib.bse_adjoint_seed(self._ctx, a, b, int(r), c), "bse_adjoint_seed")
         return Gamma
 
+    def window_seed(self, H: torch.Tensor, u: torch.Tensor, n_steps: int, w_lo: float, w_hi: float, eta: float,
+                    prefactor: float, Gamma: torch.Tensor | None = None):
+        """bse_window_seed: (Gamma, I) for I = the spectrum integrated over [w_lo, w_hi]."""
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        if Gamma is None:
+            Gamma = torch.empty((self.dim, self.dim), dtype=torch.complex128, device="cuda")
+        I = torch.empty(1, dtype=torch.float64, device="cuda")
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        a = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        c = _dev(Gamma, torch.complex128, "Gamma", self.dim * self.dim)
+        self._check(self._lib.bse_window_seed(self._ctx, h, a, n_pol, int(n_steps), float(w_lo), float(w_hi),
+                                              float(eta), float(prefactor), I.data_ptr(), c), "bse_window_seed")
+        return Gamma, I
+
     def adjoint(self, Gamma: torch.Tensor, dW_R: torch.Tensor | None = None, de_qp: torch.Tensor | None = None):
         if dW_R is None:
             dW_R = torch.empty((self.n_RW, self.naux, self.naux), dtype=torch.float64, device="cuda")

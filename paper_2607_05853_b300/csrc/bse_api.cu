@@ -363,6 +363,17 @@ bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_
   return run_lowest(c, H, n_eig, n_steps, seed, omega_out, resid_out, (double2 *)vecs_out);
 }
 
+bse_status bse_window_seed(bse_ctx *c, const void *H, const double *u, int n_pol, int n_steps, double w_lo,
+                           double w_hi, double eta, double prefactor, double *I_out, double *Gamma) {
+  if (!c) return BSE_EINVAL;
+  if (!H || !u || !Gamma) return bse_fail(c, BSE_EINVAL, "window_seed: null H, u or Gamma");
+  if (n_pol < 1 || n_pol > 3) return bse_fail(c, BSE_EINVAL, "window_seed: n_pol must be 1..3");
+  if (n_steps < 1 || n_steps > c->dim) return bse_fail(c, BSE_EINVAL, "window_seed: n_steps must be 1..dim");
+  if (!(eta > 0.0) || !(w_hi > w_lo)) return bse_fail(c, BSE_EINVAL, "window_seed: need eta > 0 and w_hi > w_lo");
+  return run_window_seed(c, H, (const double2 *)u, n_pol, n_steps, w_lo, w_hi, eta, prefactor, I_out,
+                         (double2 *)Gamma);
+}
+
 bse_status bse_adjoint_seed(bse_ctx *c, const double *vecs, const double *g, int r, double *Gamma) {
   if (!c) return BSE_EINVAL;
   if (!vecs || !g || !Gamma || r < 1) return bse_fail(c, BSE_EINVAL, "adjoint_seed: bad argument");

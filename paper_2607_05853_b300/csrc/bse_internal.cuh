@@ -107,6 +107,10 @@ bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_
 // adjoint (k_adjoint.cu)
 bse_status run_adjoint(bse_ctx *c, const double2 *Gamma, double *dW_R, double *de_qp);
 bse_status run_seed_lowrank(bse_ctx *c, const double2 *X, const double *g, int r, double2 *Gamma);
+bse_status launch_zgemm_tn(bse_ctx *c, int M, int N, int K, const double2 *A, const double2 *B, double2 *C,
+                           double alpha);
+bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
+                           double w_hi, double eta, double pref, double *I_out, double2 *Gamma);
 bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
                                const double *omega, int n_w, double eta, double pref, double *eps2,
                                double *ab);

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(256) k_adj_phi_mc(const double2 *__restrict__ 
   }
 }
 
-// C[qlist[q0+b]] = alpha A[b]^T B[b]: A, B row-major [K x M], [K x N]; C [M x N].
+// C[qlist[q0+b]] (C[b] when qlist is null) = alpha A[b]^T B[b]: A, B row-major [K x M],
+// [K x N]; C [M x N].
 __global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const double2 *__restrict__ A, long long sA,
                                                   const double2 *__restrict__ B, long long sB, double2 *__restrict__ C,
                                                   long long sC, const int *__restrict__ cidx, int q0, double alpha) {
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(256) k_zgemm_tn(int M, int N, int K, const dou
   const int bz = blockIdx.z;
   A += bz * sA;
   B += bz * sB;
-  C += (long long)cidx[q0 + bz] * sC;
+  C += (long long)(cidx ? cidx[q0 + bz] : bz) * sC;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
   double2 acc[4][4];
@@ -252,4 +253,14 @@ bse_status run_seed_lowrank(bse_ctx *c, const double2 *X, const double *g, int r
   k_seed_lowrank<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(X, g, r, c->dim, Gamma);
   bse_count_launch();
   return bse_check_launch(c, "adjoint seed");
+}
+
+// C = alpha A^T B for one pair of row-major complex matrices A [K x M], B [K x N]; C [M x N].
+bse_status launch_zgemm_tn(bse_ctx *c, int M, int N, int K, const double2 *A, const double2 *B, double2 *C,
+                           double alpha) {
+  dim3 grid((N + 63) / 64, (M + 63) / 64, 1);
+  if (grid.y > 65535) return bse_fail(c, BSE_EINVAL, "zgemm_tn grid too large");
+  k_zgemm_tn<<<grid, 256, 0, c->stream>>>(M, N, K, A, 0, B, 0, C, 0, nullptr, 0, alpha);
+  bse_count_launch();
+  return bse_check_launch(c, "zgemm_tn");
 }

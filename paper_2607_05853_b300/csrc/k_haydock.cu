@@ -1398,6 +1398,264 @@ bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_
   return r;
 }
 
+namespace {
+
+// ---- adjoint seed of the windowed absorption integral (bse_window_seed) --------------------
+// I = pref sum_p u_p^dagger f(H) u_p with f(x) = (1/pi)[atan((w_hi - x)/eta) - atan((w_lo - x)/eta)],
+// the Lorentzian of Eq. abs_vel integrated over [w_lo, w_hi].  From the Lanczos tridiagonal
+// T = Z diag(theta) Z^T of each start vector: the Ritz vectors Y = Z^T Q (rows), v = first
+// components of Z's columns, and (Daleckii-Krein in the Krylov subspace)
+//   Gamma = sum_p Y_p^T M_p conj(Y_p),  M_p = pref |u_p|^2 (F o v v^T),
+//   F_il = (f(theta_i) - f(theta_l)) / (theta_i - theta_l),  F_ii = f'(theta_i),
+// so that dI = tr(Gamma dH); I = sum_p pref |u_p|^2 sum_i v_i^2 f(theta_i).
+
+__device__ __forceinline__ double window_f(double x, double lo, double hi, double eta) {
+  return (atan((hi - x) / eta) - atan((lo - x) / eta)) * (1.0 / M_PI);
+}
+__device__ __forceinline__ double window_df(double x, double lo, double hi, double eta) {
+  const double ya = lo - x, yb = hi - x;
+  return (eta / (ya * ya + eta * eta) - eta / (yb * yb + eta * eta)) * (1.0 / M_PI);
+}
+
+// Eigen-decomposition of each tridiagonal T_p (diagonal a, off-diagonal b, order m = meff[p])
+// by the implicit QL algorithm with Wilkinson-type shifts (Bowdler, Martin, Reinsch and
+// Wilkinson, Numer. Math. 11 (1968) 293).  Thread 0 runs the shifted sweeps on (d, e) and
+// records each sweep's Givens rotations; then every thread applies them, in order, to its
+// columns of Zt (Zt[i][k] = component k of eigenvector i), so the updates are coalesced.
+// On exit d holds the eigenvalues (unsorted) and Zt the eigenvectors.  A block that fails to
+// converge sets the error word.
+constexpr int QL_MAX_SWEEPS = 60;
+__global__ void __launch_bounds__(256) k_tridiag_ql(const double *__restrict__ a, const double *__restrict__ b,
+                                                    int ldab, const int *__restrict__ meff, int mmax,
+                                                    double *__restrict__ dd, double *__restrict__ ee,
+                                                    double *__restrict__ Zt, double2 *__restrict__ rot, int *err) {
+  __shared__ int s_mm, s_first, s_last;
+  const int p = blockIdx.x;
+  const int m = meff[p];
+  double *d = dd + (long long)p * mmax, *e = ee + (long long)p * mmax;
+  double *Z = Zt + (long long)p * mmax * mmax;
+  double2 *cs = rot + (long long)p * mmax;
+  for (int i = threadIdx.x; i < mmax; i += blockDim.x) {
+    d[i] = i < m ? a[p * ldab + i] : 0.0;
+    e[i] = i < m - 1 ? b[p * ldab + i] : 0.0;
+  }
+  for (long long t = threadIdx.x; t < (long long)mmax * mmax; t += blockDim.x)
+    Z[t] = (t / mmax == t % mmax && t / mmax < m) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int l = 0; l < m; l++) {
+    for (int sweep = 0;; sweep++) {
+      if (threadIdx.x == 0) {
+        int mm = l;
+        while (mm < m - 1) {
+          const double scale = fabs(d[mm]) + fabs(d[mm + 1]);
+          if (fabs(e[mm]) <= 1e-16 * scale || fabs(e[mm]) < 1e-300) break;
+          mm++;
+        }
+        s_mm = mm;
+        s_first = mm - 1;
+        s_last = mm;  // rotations i = s_first down to s_last are valid (none when s_last > s_first)
+        if (mm != l && sweep < QL_MAX_SWEEPS) {
+          // shift from the leading 2x2 block at l
+          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+          double r = hypot(g, 1.0);
+          g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
+          double sn = 1.0, cn = 1.0, pp = 0.0;
+          bool split = false;
+          int i = mm - 1;
+          for (; i >= l; i--) {
+            const double f = sn * e[i], bb = cn * e[i];
+            r = hypot(f, g);
+            e[i + 1] = r;
+            if (r == 0.0) {  // underflow: the block splits here
+              d[i + 1] -= pp;
+              e[mm] = 0.0;
+              split = true;
+              break;
+            }
+            sn = f / r;
+            cn = g / r;
+            g = d[i + 1] - pp;
+            r = (d[i] - g) * sn + 2.0 * cn * bb;
+            pp = sn * r;
+            d[i + 1] = g + pp;
+            g = cn * r - bb;
+            cs[i] = make_double2(cn, sn);
+          }
+          s_last = split ? i + 1 : l;
+          if (!split) {
+            d[l] -= pp;
+            e[l] = g;
+            e[mm] = 0.0;
+          }
+        } else if (mm != l) {
+          atomicOr(err, BSE_DERR_BOUNDS);
+          s_mm = l;  // give up on this eigenvalue
+        }
+      }
+      __syncthreads();
+      if (s_mm == l) break;
+      const int first = s_first, last = s_last;
+      for (int k = threadIdx.x; k < m; k += blockDim.x) {
+        for (int i = first; i >= last; i--) {
+          const double2 r = cs[i];
+          const double zi = Z[(long long)i * mmax + k], zn = Z[(long long)(i + 1) * mmax + k];
+          Z[(long long)(i + 1) * mmax + k] = r.y * zi + r.x * zn;
+          Z[(long long)i * mmax + k] = r.x * zi - r.y * zn;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// M_p[i][l] = pref |u_p|^2 F_il v_i v_l with v_i = Zt[i][0]; Ipart[p] = pref |u_p|^2 sum_i v_i^2 f(theta_i).
+__global__ void k_window_M(const double *__restrict__ dd, const double *__restrict__ Zt, const int *__restrict__ meff,
+                           int mmax, const double *__restrict__ beta0, double lo, double hi, double eta, double pref,
+                           double *__restrict__ M, double *__restrict__ Ipart) {
+  const int p = blockIdx.y;
+  const int m = meff[p];
+  const double *d = dd + (long long)p * mmax, *Z = Zt + (long long)p * mmax * mmax;
+  const double sc = pref * beta0[p] * beta0[p];
+  const long long nm = (long long)mmax * mmax;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nm; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / mmax), l = (int)(t % mmax);
+    double v = 0.0;
+    if (i < m && l < m) {
+      const double ti = d[i], tl = d[l];
+      const double gap = ti - tl, tol = 1e-9 * (fabs(ti) + fabs(tl) + eta);
+      const double F = fabs(gap) > tol ? (window_f(ti, lo, hi, eta) - window_f(tl, lo, hi, eta)) / gap
+                                       : window_df(0.5 * (ti + tl), lo, hi, eta);
+      v = sc * F * Z[(long long)i * mmax] * Z[(long long)l * mmax];
+    }
+    M[(long long)p * nm + t] = v;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int i = 0; i < m; i++) {
+      const double vi = Z[(long long)i * mmax];
+      acc += vi * vi * window_f(d[i], lo, hi, eta);
+    }
+    Ipart[p] = sc * acc;
+  }
+}
+
+__global__ void k_sum_small(const double *__restrict__ x, int n, double *__restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += x[i];
+    *out = s;
+  }
+}
+
+// C[p][i][x] = sum_l A[p][i][l] * (conj ? conj(B[p][l][x]) : B[p][l][x]) for l < meff[p]; A real
+// [mmax][mmax], B complex [mmax rows, stride ldb][dim]; rows i >= meff[p] are written as zero.
+__global__ void __launch_bounds__(256) k_real_cgemm(const double *__restrict__ A, const double2 *__restrict__ B,
+                                                    long long ldb_p, int conj, const int *__restrict__ meff,
+                                                    int mmax, long long dim, double2 *__restrict__ C) {
+  __shared__ double As[16][64];
+  __shared__ double2 Bs[16][64];
+  const int p = blockIdx.z, m = meff[p];
+  A += (long long)p * mmax * mmax;
+  B += p * ldb_p;
+  C += (long long)p * mmax * dim;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row0 = blockIdx.y * 64;
+  const long long col0 = (long long)blockIdx.x * 64;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = make_double2(0, 0);
+  for (int k0 = 0; k0 < m; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int r = e / 16, kk = e % 16, gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < m && gk < m) ? A[(long long)gr * mmax + gk] : 0.0;
+      const int kb = e / 64, cc = e % 64, gkb = k0 + kb;
+      const long long gc = col0 + cc;
+      double2 v = make_double2(0, 0);
+      if (gkb < m && gc < dim) {
+        v = B[(long long)gkb * dim + gc];
+        if (conj) v.y = -v.y;
+      }
+      Bs[kb][cc] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+      double a[4];
+      double2 bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[i][j].x = fma(a[i], bv[j].x, acc[i][j].x);
+          acc[i][j].y = fma(a[i], bv[j].y, acc[i][j].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = row0 + ty + 16 * i;
+      const long long cc = col0 + tx + 16 * j;
+      if (r < mmax && cc < dim) C[(long long)r * dim + cc] = r < m ? acc[i][j] : make_double2(0, 0);
+    }
+}
+
+}  // namespace
+
+bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
+                           double w_hi, double eta, double pref, double *I_out, double2 *Gamma) {
+  LanczosScratch s;
+  bse_status r = lanczos_alloc(c, s, n_pol, n_steps);
+  const int mmax = n_steps;
+  const long long dim = c->dim;
+  double *dd = nullptr, *ee = nullptr, *Zt = nullptr, *M = nullptr, *Ip = nullptr;
+  double2 *rot = nullptr, *Y = nullptr, *Z = nullptr;
+  const size_t nm = (size_t)n_pol * mmax * mmax;
+  const size_t ny = (size_t)n_pol * mmax * dim;
+  if (r == BSE_OK && (cudaMallocAsync((void **)&dd, sizeof(double) * n_pol * mmax, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&ee, sizeof(double) * n_pol * mmax, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&rot, sizeof(double2) * n_pol * mmax, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&Zt, sizeof(double) * nm, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&M, sizeof(double) * nm, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&Ip, sizeof(double) * n_pol, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&Y, sizeof(double2) * ny, c->stream) != cudaSuccess ||
+                      cudaMallocAsync((void **)&Z, sizeof(double2) * ny, c->stream) != cudaSuccess)) {
+    cudaGetLastError();
+    r = bse_fail(c, BSE_ENOMEM, "window_seed: scratch allocation failed");
+  }
+  if (r == BSE_OK) r = lanczos_run(c, s, H, u, n_pol, n_steps);
+  if (r == BSE_OK) {
+    k_tridiag_ql<<<n_pol, 256, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.meff, mmax, dd, ee, Zt, rot, c->d_err);
+    k_window_M<<<dim3(64, n_pol), 256, 0, c->stream>>>(dd, Zt, s.meff, mmax, s.beta0, w_lo, w_hi, eta, pref, M, Ip);
+    // Ritz vectors Y_p = Zt_p Q_p, then Z_p = M_p conj(Y_p)
+    dim3 g((unsigned)((dim + 63) / 64), (unsigned)((mmax + 63) / 64), n_pol);
+    const long long qs = (long long)(n_steps + 1) * dim;
+    k_real_cgemm<<<g, 256, 0, c->stream>>>(Zt, s.Q, qs, 0, s.meff, mmax, dim, Y);
+    k_real_cgemm<<<g, 256, 0, c->stream>>>(M, Y, (long long)mmax * dim, 1, s.meff, mmax, dim, Z);
+    bse_count_launch(4);
+    if (I_out) {
+      k_sum_small<<<1, 32, 0, c->stream>>>(Ip, n_pol, I_out);
+      bse_count_launch();
+    }
+    r = bse_check_launch(c, "window seed");
+  }
+  // Gamma = sum_p Y_p^T Z_p: one transposed GEMM over the stacked (p, i) rows
+  if (r == BSE_OK) r = launch_zgemm_tn(c, (int)dim, (int)dim, n_pol * mmax, Y, Z, Gamma, 1.0);
+  void *ptrs[] = {dd, ee, rot, Zt, M, Ip, Y, Z};
+  for (void *ptr : ptrs)
+    if (ptr) cudaFreeAsync(ptr, c->stream);
+  lanczos_release(c, s);
+  return r;
+}
+
 // ---- allocation-free variant of the spectrum (bse_spectrum_static) -------------------------
 // Its Lanczos scratch lives in one file-scope device array instead of per-call allocations.
 // Every GPU that loads the library holds this array until the process exits.

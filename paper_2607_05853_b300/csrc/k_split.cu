@@ -31,7 +31,7 @@ struct SplitWS {
   __nv_bfloat16 *Wp = nullptr;   // [nk][PP][naux][kmem]   B[nu][mu] = W(q)[mu][nu]
   __nv_bfloat16 *Ap = nullptr;   // [nq][PP][rows][kmem]   M_vv pieces
   float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux]
-  float2 *T32 = nullptr;         // [nq][rows][naux]
+  float2 *T32 = nullptr;         // [nq][naux][rows]  (column nu of T = M_vv W(q) is contiguous)
   float2 *Y32 = nullptr;         // [nk][nao_max][nb][naux]
   __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V0
   __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
   const bool mirror = !q_self_conjugate(q, n1, n2, n3);
   const int nvc = nv * nc, nvv = nv * nv, ncc = nc * nc, nb = nv + nc;
   float2 *sT = sg, *sM = sT + nvv * G2CH;
-  const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * nvv) * naux;
+  const float2 *Tq = T + (long long)qq * rows * naux + (long long)k1 * nvv;  // T[q][nu][row]
   const float2 *Mk = Mc + ((long long)qq * nk + k1) * ncc * naux;
   const int nout = nvc * nvc;
   constexpr int MAXO = 16;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
     for (int e = threadIdx.x; e < (nvv + ncc) * G2CH; e += blockDim.x) {
       const int r = e / G2CH, u = e % G2CH;
       float2 v = make_float2(0.f, 0.f);
-      if (u < nn) v = r < nvv ? Tk[(long long)r * naux + n0 + u] : Mk[(long long)(r - nvv) * naux + n0 + u];
+      if (u < nn) v = r < nvv ? Tq[(long long)(n0 + u) * rows + r] : Mk[(long long)(r - nvv) * naux + n0 + u];
       sg[e] = v;
     }
     __syncthreads();
@@ -615,8 +615,9 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   }
 }
 
-// Second contraction per pair: the pair's T rows (R x N_aux) and M_cc rows (C x N_aux) are
-// contiguous in memory and are copied to shared memory in one vectorised sweep; thread
+// Second contraction per pair: the pair's T rows (R consecutive elements per column nu of the
+// column-major T) and M_cc rows (C x N_aux, contiguous) are copied to shared memory in one
+// vectorised asynchronous sweep; thread
 // (r, c) then owns the 2x2 outputs rows (i,j) in {2r, 2r+1}, columns (a,b) in {2c, 2c+1}
 // of D = T M_cc^T.  H gets D's contribution at (k1, k2) and its conjugate at (k2, k1).
 template <int NV, int NC>
@@ -631,35 +632,43 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
   const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
   const bool mirror = !q_self_conjugate(q, n1, n2, n3);
-  const float2 *Tk = T + ((long long)qq * rows + (long long)k1 * R) * naux;
+  static_assert(R % 2 == 0, "the pair's T rows are copied in 16-byte pieces");
+  const float2 *Tq = T + (long long)qq * rows * naux + (long long)k1 * R;  // T[q][nu][row]
   const float2 *Mk = Mc + ((long long)qq * nk + k1) * C * naux;
+  // asynchronous 16-byte global->shared copies: every load of the sweep is in flight at once.
+  // sT[nu][r] holds the pair's R rows of T per column nu (R consecutive elements in memory).
+  {
+    float4 *st4 = reinterpret_cast<float4 *>(sT);
+    for (int e = threadIdx.x; e < naux * (R / 2); e += blockDim.x) {
+      const int nu = e / (R / 2), h = e % (R / 2);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st4 + e)),
+                   "l"(reinterpret_cast<const float4 *>(Tq + (long long)nu * rows) + h)
+                   : "memory");
+    }
+  }
   if ((naux & 1) == 0) {
-    // asynchronous 16-byte global->shared copies: every load of the sweep is in flight at once
-    const float4 *t4 = reinterpret_cast<const float4 *>(Tk), *m4 = reinterpret_cast<const float4 *>(Mk);
-    float4 *st4 = reinterpret_cast<float4 *>(sT), *sm4 = reinterpret_cast<float4 *>(sM);
-    for (int e = threadIdx.x; e < R * naux / 2; e += blockDim.x)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st4 + e)), "l"(t4 + e) : "memory");
+    const float4 *m4 = reinterpret_cast<const float4 *>(Mk);
+    float4 *sm4 = reinterpret_cast<float4 *>(sM);
     for (int e = threadIdx.x; e < C * naux / 2; e += blockDim.x)
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sm4 + e)), "l"(m4 + e) : "memory");
-    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   } else {
-    for (int e = threadIdx.x; e < R * naux; e += blockDim.x) sT[e] = Tk[e];
     for (int e = threadIdx.x; e < C * naux; e += blockDim.x) sM[e] = Mk[e];
   }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
   __syncthreads();
   const double inv = 1.0 / nk;
   const float invf = (float)inv;
   for (int w = threadIdx.x; w < TR * TCC; w += blockDim.x) {
     const int tr = w / TCC, tc = w % TCC;
     const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
-    const float2 *pt0 = sT + r0 * naux, *pt1 = sT + r1 * naux, *pm0 = sM + m0 * naux, *pm1 = sM + m1 * naux;
+    const float2 *pt0 = sT + r0, *pt1 = sT + r1, *pm0 = sM + m0 * naux, *pm1 = sM + m1 * naux;
     float2 acc[2][2];
 #pragma unroll
     for (int x = 0; x < 2; x++)
 #pragma unroll
       for (int y = 0; y < 2; y++) acc[x][y] = make_float2(0.f, 0.f);
     for (int u = 0; u < naux; u++) {
-      const float2 tt[2] = {pt0[u], pt1[u]}, mm[2] = {pm0[u], pm1[u]};
+      const float2 tt[2] = {pt0[u * R], pt1[u * R]}, mm[2] = {pm0[u], pm1[u]};
 #pragma unroll
       for (int x = 0; x < 2; x++)
 #pragma unroll
@@ -761,8 +770,14 @@ template <int NP, int BN>
 bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
                      int prof_id) {
   using Cf = tcg::Cfg<NP, BN>;
+  tcg::Args a = args;
+  a.tiles_n = (int)grid.x;
+  a.tiles_m = (int)grid.y;
+  a.tiles_b = (int)grid.z;
+  const long long total = (long long)grid.x * grid.y * grid.z;
+  const int ctas = (int)std::min<long long>(total, c->n_sm);
   bse_prof_begin(c, prof_id);
-  tcg::k_tc_zgemm<NP, BN><<<grid, 192, Cf::SMEM, c->stream>>>(A, B, args);
+  tcg::k_tc_zgemm<NP, BN><<<ctas, 192, Cf::SMEM, c->stream>>>(A, B, a);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_zgemm");
@@ -952,8 +967,12 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
     a.n_valid = (int)c->dim;
     a.k_chunks = w->kchunks;
     a.scale = (float)(c->alpha / c->nk);
+    // the exchange block is Hermitian: element (r, c) is stored as conj at (c, r), so a lane's
+    // row index runs along memory and the stores coalesce
     a.out = H;
-    a.ldo = c->dim;
+    a.ld_row = 1;
+    a.ld_col = c->dim;
+    a.conj_out = 1;
     a.out_bstride = 0;
     a.b_batch_planes = 0;
     a.b_base = 0;
@@ -987,7 +1006,8 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       a.k_chunks = w->kchunks;
       a.scale = 1.0f;
       a.out = w->T32;
-      a.ldo = na;
+      a.ld_row = 1;
+      a.ld_col = w->rows;
       a.out_bstride = (long long)w->rows * na;
       a.b_batch_planes = 1;
       a.b_base = q0;
@@ -1057,7 +1077,8 @@ bse_status split_autotune(bse_ctx *c, int *chosen) {
     a.k_chunks = w->kchunks;
     a.scale = 1.0f;
     a.out = w->T32;
-    a.ldo = na;
+    a.ld_row = 1;
+    a.ld_col = w->rows;
     a.out_bstride = (long long)w->rows * na;
     a.b_batch_planes = 1;
     a.b_base = 0;

@@ -11,9 +11,10 @@
 //
 // Operands arrive by TMA as 3-D tensors {K, rows, plane-piece(-batch)} with 64-byte
 // swizzled rows (32 bf16 of K per stage); rows and K beyond the tensor are zero-filled.
-// One CTA computes a 128 x BN output tile: warp 0 issues TMA, warp 1 allocates tensor
-// memory and issues the MMAs from one thread, warps 2-5 drain the accumulators.  Every
-// barrier wait is bounded; a timeout sets the device error word and the CTA winds down.
+// Persistent CTAs (one per SM) walk the 128 x BN output tiles: warp 0 issues TMA, warp 1
+// allocates tensor memory and issues the MMAs from one thread, warps 2-5 drain the
+// accumulators of one tile while the next tile's operands stream in.  Every barrier wait
+// is bounded; a timeout sets the device error word and the CTA winds down.
 #pragma once
 
 #include "tc_ptx.cuh"
@@ -44,13 +45,16 @@ struct Args {
   int n_valid;           // valid columns of the output (rows of B per batch)
   int k_chunks;          // ceil(K / BK)
   float scale;
-  float2 *out;           // interleaved complex
-  long long ldo;         // row pitch of out (elements)
-  long long out_bstride; // batch stride of out (elements)
+  float2 *out;           // interleaved complex; element (row, col) of batch b at
+  long long ld_row;      //   out[b * out_bstride + row * ld_row + col * ld_col]
+  long long ld_col;      //   (ld_row = 1 makes the epilogue's stores coalesced: a lane owns a row)
+  long long out_bstride;
+  int conj_out;          // store the conjugate of each element
   int b_batch_planes;    // 0: B has no batch dimension (z = pp), else z = qlist[b_base + b]*PP + pp
   int b_base;
   const int *qlist;
   int *err;
+  int tiles_n, tiles_m, tiles_b;  // output tiles along N, M and the batch (set by the launcher)
 };
 
 template <int NP, int BN>
@@ -61,19 +65,21 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + C::S * C::STAGE);
   uint64_t *empty = full + C::S;
-  uint64_t *done = empty + C::S;
-  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  uint64_t *tfull = empty + C::S;   // accumulators of a tile are complete (MMA -> epilogue)
+  uint64_t *tempty = tfull + 1;     // accumulators drained (epilogue -> MMA)
+  uint32_t *tmem_slot = (uint32_t *)(tempty + 1);
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM, b = blockIdx.z;
+  const int total = args.tiles_n * args.tiles_m * args.tiles_b;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::S; s++) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], 1);
     }
-    tc::mbar_init(done, 1);
+    tc::mbar_init(tfull, 1);
+    tc::mbar_init(tempty, 128);
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
@@ -91,81 +97,114 @@ __global__ void __launch_bounds__(192, 1)
   const uint32_t tmem = *tmem_slot;
   const uint32_t tm_re = tmem, tm_im = tmem + BN;
 
+  // Persistent: this CTA takes tiles blockIdx.x, blockIdx.x + gridDim.x, ...; tile t is
+  // (n, m, b) with n fastest, so CTAs running together share the B operand of one batch.
+  // The producer runs ahead through the stage ring across tile boundaries, and the epilogue
+  // of tile t drains the accumulators while the producer already loads tile t + gridDim.x.
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int kc = 0; kc < args.k_chunks; kc++) {
-      const int s = kc % C::S;
-      if (kc >= C::S) {
-        if (!tc::mbar_wait_bounded(&empty[s], ((kc / C::S) & 1) ^ 1, WAIT_LIMIT)) {
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int n0 = (t % args.tiles_n) * BN, m0 = ((t / args.tiles_n) % args.tiles_m) * BM;
+      const int b = t / (args.tiles_n * args.tiles_m);
+      const int zb = args.b_batch_planes ? args.qlist[args.b_base + b] * C::PP : 0;
+      for (int kc = 0; kc < args.k_chunks; kc++, it++) {
+        const int s = it % C::S;
+        if (it >= C::S && !tc::mbar_wait_bounded(&empty[s], ((it / C::S) & 1) ^ 1, WAIT_LIMIT)) {
           atomicOr(args.err, 2);
           *abort_flag = 1;
+          ok = false;
           break;
         }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        uint8_t *st = smem + s * C::STAGE;
+        tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
+        for (int pp = 0; pp < C::PP; pp++) {
+          tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
+          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, n0, zb + pp);
+        }
       }
-      if (*abort_flag) break;
-      uint8_t *st = smem + s * C::STAGE;
-      tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
-      for (int pp = 0; pp < C::PP; pp++) {
-        tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
-        tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, n0,
-                        args.b_batch_planes ? args.qlist[args.b_base + b] * C::PP + pp : pp);
-      }
-      issued = kc + 1;
     }
-    // make sure every copy this CTA started has landed before the CTA can exit
-    for (int kc = issued - C::S < 0 ? 0 : issued - C::S; kc < issued; kc++)
-      if (!tc::mbar_wait_bounded(&full[kc % C::S], (kc / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
+    // every copy this CTA started lands before the CTA can exit
+    for (int k = it - C::S < 0 ? 0 : it - C::S; k < it; k++)
+      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t IPOS = tc::idesc_bf16(BM, BN, false);
     constexpr uint32_t INEG = tc::idesc_bf16(BM, BN, true);
-    uint32_t acc_r = 0, acc_i = 0;
-    for (int kc = 0; kc < args.k_chunks; kc++) {
-      const int s = kc % C::S;
-      if (!tc::mbar_wait_bounded(&full[s], (kc / C::S) & 1, WAIT_LIMIT)) {
+    int it = 0, tcount = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
+      if (*abort_flag) break;
+      if (tcount > 0 && !tc::mbar_wait_bounded(tempty, (tcount - 1) & 1, 4 * WAIT_LIMIT)) {
         atomicOr(args.err, 2);
         *abort_flag = 1;
         break;
       }
-      if (*abort_flag) break;
       tc::tc_fence_after();
-      const uint32_t sa = tc::smem_u32(smem + s * C::STAGE);
-      const uint32_t sb = sa + C::PP * A_TILE;
+      uint32_t acc_r = 0, acc_i = 0;
+      for (int kc = 0; kc < args.k_chunks; kc++, it++) {
+        const int s = it % C::S;
+        if (!tc::mbar_wait_bounded(&full[s], (it / C::S) & 1, WAIT_LIMIT)) {
+          atomicOr(args.err, 2);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        if (*abort_flag) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t sa = tc::smem_u32(smem + s * C::STAGE);
+        const uint32_t sb = sa + C::PP * A_TILE;
 #pragma unroll
-      for (int k16 = 0; k16 < BK / 16; k16++) {
+        for (int k16 = 0; k16 < BK / 16; k16++) {
 #pragma unroll
-        for (int pa = 0; pa < NP; pa++) {
+          for (int pa = 0; pa < NP; pa++) {
 #pragma unroll
-          for (int pb = 0; pb < NP; pb++) {
-            if (pa + pb > NP - 1) continue;
-            const uint64_t ar = tc::smem_desc(sa + (2 * pa) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-            const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-            tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
-            acc_r = 1;
-            tc::mma_bf16(tm_re, ai, bi, INEG, 1);
-            tc::mma_bf16(tm_im, ar, bi, IPOS, acc_i);
-            acc_i = 1;
-            tc::mma_bf16(tm_im, ai, br, IPOS, 1);
+            for (int pb = 0; pb < NP; pb++) {
+              if (pa + pb > NP - 1) continue;
+              const uint64_t ar = tc::smem_desc(sa + (2 * pa) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+              const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+              const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+              const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
+              tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
+              acc_r = 1;
+              tc::mma_bf16(tm_re, ai, bi, INEG, 1);
+              tc::mma_bf16(tm_im, ar, bi, IPOS, acc_i);
+              acc_i = 1;
+              tc::mma_bf16(tm_im, ai, br, IPOS, 1);
+            }
           }
         }
+        tc::mma_commit(&empty[s]);
       }
-      tc::mma_commit(&empty[s]);
+      tc::mma_commit(tfull);  // also after an abort, so the epilogue is released
     }
-    tc::mma_commit(done);
   } else if (warp >= 2) {
     // ---------------- epilogue: TMEM -> registers -> global ----------------
     const int quarter = warp % 4;
-    const bool ok = tc::mbar_wait_bounded(done, 0, 4 * WAIT_LIMIT);
-    if (!ok) atomicOr(args.err, 2);
-    tc::tc_fence_after();
-    if (ok && !*abort_flag) {
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    int tcount = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
+      const bool ok = !*abort_flag && tc::mbar_wait_bounded(tfull, tcount & 1, 4 * WAIT_LIMIT);
+      if (!ok) {
+        atomicOr(args.err, 2);
+        *abort_flag = 1;
+        break;
+      }
+      tc::tc_fence_after();
+      const int n0 = (t % args.tiles_n) * BN, m0 = ((t / args.tiles_n) % args.tiles_m) * BM;
+      const int b = t / (args.tiles_n * args.tiles_m);
       const int row = m0 + quarter * 32 + lane;
-      const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-      float2 *orow = args.out + (long long)b * args.out_bstride + (long long)row * args.ldo;
+      float2 *orow = args.out + (long long)b * args.out_bstride + (long long)row * args.ld_row;
       const bool row_ok = row < args.rows;
+      const float sim = args.conj_out ? -args.scale : args.scale;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t rr[16], ri[16];
@@ -177,13 +216,15 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 16; j++) {
             const int col = n0 + c0 + j;
             if (col < args.n_valid)
-              orow[col] = make_float2(args.scale * __uint_as_float(rr[j]), args.scale * __uint_as_float(ri[j]));
+              orow[col * args.ld_col] = make_float2(args.scale * __uint_as_float(rr[j]), sim * __uint_as_float(ri[j]));
           }
         }
       }
+      tc::tc_fence_before();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tempty)) : "memory");
     }
-    tc::tc_fence_before();
   }
+  tc::tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc::tc_fence_after();

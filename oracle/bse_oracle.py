@@ -38,7 +38,7 @@ import numpy as np
 __all__ = [
     "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
     "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
-    "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact",
+    "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact", "offset_average_eps2",
 ]
 
 TWO_PI = 2.0 * np.pi
@@ -321,4 +321,15 @@ def window_seed_exact(H, d, lo, hi, eta, pref):
         c = X.conj().T @ np.conj(dp)
         G += X @ (F * np.outer(c, c.conj())) @ X.conj().T
     return pref * G
+
+
+def offset_average_eps2(inputs_list, weights, omega, eta):
+    """k-offset averaged spectrum (§IV, k-point convergence): sum_o w_o eps2_o(omega), each
+    eps2_o from an independent calculation on the dense mesh shifted by offset o (its own
+    bands at the shifted k-points; Eq. abs_vel with its own prefactor)."""
+    tot = np.zeros(len(omega))
+    for inp, w in zip(inputs_list, weights):
+        orc = BSEOracle(inp)
+        tot += w * eps2_exact(orc.hamiltonian(), orc.dipoles(), omega, eta, orc.prefactor())
+    return tot
 

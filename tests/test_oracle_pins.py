@@ -7,6 +7,9 @@ k-space formulas, invariants the paper states (A Hermitian, §II.C), the indepen
 particle limit, LAPACK, and closed forms of the spectrum (Eq. abs_vel).
 """
 import dataclasses
+import itertools
+import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -423,3 +426,65 @@ def test_window_gradient_shift_sum_rule():
     e_lo, e_hi = O.eps2_exact(H, d, np.array(WIN), eta, pref)
     assert np.isclose(de[:, 2:].sum(), e_lo - e_hi, rtol=1e-10, atol=1e-14)
     assert np.isclose(de[:, :2].sum(), e_hi - e_lo, rtol=1e-10, atol=1e-14)
+
+
+# ---- k-offset averaging (§IV, convergence with k-point sampling) ----------------------------
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _read_offsets():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "k_offsets.txt")):
+        line = line.split("#")[0].split()
+        if not line:
+            continue
+        o = tuple(float(Fraction(x)) for x in line[:3])
+        rows.append((o, int(line[3])))
+    return rows
+
+
+def _cubic_ops():
+    ops = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            M = np.zeros((3, 3))
+            for i, (pi, si) in enumerate(zip(perm, signs)):
+                M[i, pi] = si
+            ops.append(M)
+    return ops
+
+
+def test_offset_weights_are_the_symmetry_classes_of_a_3x3x3_grid():
+    """The paper's four offsets and weights equal the orbits of the 27 offsets {0,1/3,2/3}^3
+    under the 48 cubic point operations acting on fractional coordinates of the fcc
+    reciprocal basis (mod 1): class sizes 1, 8, 6, 12 with the listed representatives."""
+    rows = _read_offsets()
+    assert sum(n for _, n in rows) == 27
+    a = _fcc(1.0)
+    b = np.linalg.inv(a).T                      # reciprocal basis (rows), 2 pi dropped
+    Tops = [b @ S.T @ np.linalg.inv(b) for S in _cubic_ops()]
+
+    def key(f):
+        return tuple(int(x) % 3 for x in np.round(np.asarray(f) * 3))
+
+    orbit = {}
+    for o in itertools.product(range(3), repeat=3):
+        f = np.array(o) / 3.0
+        orb = set()
+        for T in Tops:
+            g = f @ T
+            assert np.allclose(g * 3, np.round(g * 3), atol=1e-9)   # the group maps the grid to itself
+            orb.add(key(g))
+        orbit[key(f)] = orb
+    classes = {frozenset(v) for v in orbit.values()}
+    assert sorted(len(c) for c in classes) == sorted(n for _, n in rows)
+    for o, n in rows:
+        assert len(orbit[key(o)]) == n
+
+
+def test_package_offsets_match_the_fixture():
+    from paper_2607_05853_b300 import offsets
+    rows = _read_offsets()
+    assert len(offsets.OFFSETS) == len(rows)
+    for (o, n), po, pw in zip(rows, offsets.OFFSETS, offsets.WEIGHTS):
+        assert np.allclose(po, o) and np.isclose(pw, n / 27.0)

@@ -129,6 +129,16 @@ bse_status bse_spectrum(bse_ctx *ctx, const void *H, const double *u, int n_pol,
                         int n_steps, const double *omega, int n_w, double eta,
                         double prefactor, double *eps2, double *ab);
 
+/* Weighted accumulation of spectra: eps2_acc[w] += weight * (the eps2 bse_spectrum would
+ * write), with the same Lanczos recursion and arguments.  With one context per shifted
+ * dense mesh this gives the k-offset average of §IV (k-point convergence): four offsets
+ * (0,0,0), (1/3,0,0), (1/3,1/3,0), (2/3,1/3,0) of the mesh spacing, the symmetry-reduced
+ * classes of a 3x3x3 offset grid, with weights 1/27, 8/27, 6/27, 12/27.
+ *  eps2_acc : [n_w] float64, read and written (zero it before the first call). */
+bse_status bse_spectrum_add(bse_ctx *ctx, const void *H, const double *u, int n_pol, int n_steps,
+                            const double *omega, int n_w, double eta, double prefactor, double weight,
+                            double *eps2_acc);
+
 /* Allocation-free variant of bse_spectrum, for callers that cannot allocate device memory:
  * for example a host application that hands the library a slice of a device pool it owns
  * and forbids driver allocations inside its callbacks, or code already holding the GPU at

@@ -146,6 +146,18 @@ class BSE:
                                            float(prefactor), e, abp), "bse_spectrum")
         return eps2
 
+    def spectrum_add(self, H: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor, eta: float,
+                     prefactor: float, weight: float, eps2_acc: torch.Tensor):
+        """bse_spectrum_add: eps2_acc += weight * spectrum (eps2_acc is read and written)."""
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        h = _dev(H, self.h_dtype, "H", self.dim * self.dim)
+        a = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        o = _dev(omega, torch.float64, "omega")
+        e = _dev(eps2_acc, torch.float64, "eps2_acc", omega.numel())
+        self._check(self._lib.bse_spectrum_add(self._ctx, h, a, n_pol, int(n_steps), o, omega.numel(), float(eta),
+                                               float(prefactor), float(weight), e), "bse_spectrum_add")
+        return eps2_acc
+
     def spectrum_static(self, H: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor, eta: float,
                         prefactor: float, eps2: torch.Tensor, ab: torch.Tensor | None = None):
         """bse_spectrum_static: the spectrum without any device allocation (outputs supplied)."""

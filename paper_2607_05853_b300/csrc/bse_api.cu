@@ -343,6 +343,18 @@ bse_status bse_spectrum(bse_ctx *c, const void *H, const double *u, int n_pol, i
   return run_spectrum(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
 }
 
+bse_status bse_spectrum_add(bse_ctx *c, const void *H, const double *u, int n_pol, int n_steps,
+                            const double *omega, int n_w, double eta, double prefactor, double weight,
+                            double *eps2_acc) {
+  if (!c) return BSE_EINVAL;
+  if (!H || !u || !omega || !eps2_acc) return bse_fail(c, BSE_EINVAL, "spectrum_add: null argument");
+  if (n_pol < 1 || n_pol > 3 || n_steps < 1 || n_steps > c->dim || n_w < 1 || !(eta > 0.0) ||
+      !std::isfinite(prefactor) || !std::isfinite(weight))
+    return bse_fail(c, BSE_EINVAL, "spectrum_add: bad size or parameter");
+  return run_spectrum(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor * weight, eps2_acc,
+                      nullptr, true);
+}
+
 bse_status bse_spectrum_static(bse_ctx *c, const void *H, const double *u, int n_pol, int n_steps,
                                const double *omega, int n_w, double eta, double prefactor, double *eps2,
                                double *ab) {

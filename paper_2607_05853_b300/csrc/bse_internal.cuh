@@ -100,8 +100,8 @@ bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H);
 // spectrum (k_haydock.cu)
 bse_status run_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double2 *u);
 bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
-                        const double *omega, int n_w, double eta, double pref, double *eps2,
-                        double *ab);
+                        const double *omega, int n_w, double eta, double pref, double *eps2, double *ab,
+                        bool accumulate = false);
 bse_status run_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
                       double *omega_out, double *resid_out, double2 *vecs_out);
 // adjoint (k_adjoint.cu)

@@ -991,7 +991,8 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
 
 // eps2[w] = pref * sum_p -(1/pi) Im( beta0^2 / (z - a1 - b1^2/(z - a2 - ...)) )
 __global__ void k_contfrac(const double *a, const double *b, int ldab, const double *beta0, const int *meff,
-                           int n_pol, const double *omega, int n_w, double eta, double pref, double *eps2) {
+                           int n_pol, const double *omega, int n_w, double eta, double pref, double *eps2,
+                           int accumulate) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= n_w) return;
   const double zr = omega[w], zi = eta;
@@ -1011,7 +1012,7 @@ __global__ void k_contfrac(const double *a, const double *b, int ldab, const dou
     const double gi = -b0 * fi / d;  // Im(b0 / f)
     tot += -gi / M_PI;
   }
-  eps2[w] = pref * tot;
+  eps2[w] = accumulate ? eps2[w] + pref * tot : pref * tot;
 }
 
 __global__ void k_pack_ab(const double *a, const double *b, const double *beta0, int ldab, int n_pol,
@@ -1316,13 +1317,14 @@ bse_status run_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, 
 }
 
 bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
-                        const double *omega, int n_w, double eta, double pref, double *eps2, double *ab) {
+                        const double *omega, int n_w, double eta, double pref, double *eps2, double *ab,
+                        bool accumulate) {
   LanczosScratch s;
   bse_status r = lanczos_alloc(c, s, n_pol, n_steps);
   if (r == BSE_OK) r = lanczos_run(c, s, H, u, n_pol, n_steps);
   if (r == BSE_OK) {
     k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega,
-                                                         n_w, eta, pref, eps2);
+                                                         n_w, eta, pref, eps2, accumulate ? 1 : 0);
     bse_count_launch();
     if (ab) {
       k_pack_ab<<<dim3((n_steps + 127) / 128, n_pol), 128, 0, c->stream>>>(s.a, s.b, s.beta0, n_steps + 1,
@@ -1755,7 +1757,7 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
   r = lanczos_run(c, s, H, u, n_pol, n_steps);
   if (r != BSE_OK) return r;
   k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega, n_w, eta,
-                                                       pref, eps2);
+                                                       pref, eps2, 0);
   bse_count_launch();
   if (ab) {
     k_pack_ab<<<dim3((n_steps + 127) / 128, n_pol), 128, 0, c->stream>>>(s.a, s.b, s.beta0, n_steps + 1, n_pol,

@@ -333,6 +333,27 @@ def main():
         roof["frac"] = None
     roof.setdefault("traffic", None)
     roof["kernel"] = top
+    # tensor-pipe fraction of the split-precision assembly GEMMs (executed bf16 products:
+    # 8 real flops per complex MAC x the kept piece products; M_vv W(q) over the unique q of
+    # each q/-q pair, the exchange over the full square)
+    tensor = None
+    if args.precision != "fp64":
+        pieces = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1}[args.precision]
+        nq_half = (nk + sum(1 for q in range(nk) if _self_conj(q, spec.dense))) // 2
+        g1_flops = 8.0 * nq_half * nk * nv * nv * naux * naux * pieces
+        ex_flops = 8.0 * float(ctx.dim) ** 2 * naux * pieces
+        g1_ms, g1_n = prof["g1"]
+        ex_ms, ex_n = prof["exch"]
+        if g1_n and ex_n:
+            per = max(1, args.steps)
+            a_g1 = g1_flops / ((g1_ms / per) * 1e-3) / 1e12
+            a_ex = ex_flops / ((ex_ms / per) * 1e-3) / 1e12
+            sus = pk["bf16_tflops_sustained"]
+            tensor = {"bound": "tensor", "unit": "TFLOP/s", "peak": sus,
+                      "peak_source": pk["source"] + " (sustained bf16)",
+                      "g1_achieved": a_g1, "g1_frac": a_g1 / sus,
+                      "exchange_achieved": a_ex, "exchange_frac": a_ex / sus,
+                      "note": "executed bf16 flops per step = 8 x complex MACs x piece products"}
     roof["peak_source"] = pk["source"]
     roof["note"] = roof_note
 
@@ -383,7 +404,7 @@ def main():
                       "dipole+spectrum": statistics.mean(spec_ms)},
         "assembly_elements_per_s": asm_rate,
         "kernels_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
-        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        "roofline": roof, "tensor_roofline": tensor, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
     }
     result.update(extra)
     if args.batch16:
@@ -400,6 +421,13 @@ def main():
 
 def ctx_slab_q(ctx, spec):
     return 1
+
+
+def _self_conj(q, dense):
+    """q == -q on the mesh (every coordinate 0 or N/2)."""
+    n1, n2, n3 = dense
+    m = (q // (n2 * n3), (q // n3) % n2, q % n3)
+    return all((2 * mi) % ni == 0 for mi, ni in zip(m, (n1, n2, n3)))
 
 
 def batch16_report(precision="bf16x3"):

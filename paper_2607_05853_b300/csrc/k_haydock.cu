@@ -386,6 +386,8 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
   extern __shared__ __align__(128) uint8_t smv[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smv);
   uint64_t *empty = full + MV_STAGES;
+  int *taken = reinterpret_cast<int *>(empty + MV_STAGES);  // [MV_STAGES] warps done with a stage
+  int *issued = taken + MV_STAGES;                           // chunks copied so far
   uint8_t *ring = smv + 128;
   float4 *yb = reinterpret_cast<float4 *>(ring + MV_STAGES * MV_STAGE_BYTES);  // [NP][HT] (yr,-yr,yi,yi)
   float2 *xc = reinterpret_cast<float2 *>(yb + NP * HT);                       // [NP][HT] (xr,xi)
@@ -398,35 +400,31 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
     for (int st = 0; st < MV_STAGES; st++) {
       tc::mbar_init(&full[st], 1);
       tc::mbar_init(&empty[st], 4);
+      taken[st] = 0;
     }
+    *issued = 0;
     tc::fence_barrier_init();
   }
   __syncthreads();
-  // ---- producer state (lane 0 of warp 0): the next chunk to copy ----
+  // ---- copies: chunk n of this CTA's sequence goes to stage n % MV_STAGES.  The first
+  // MV_STAGES are issued here; afterwards the last warp to take a stage refills it ----
   constexpr int CPT = HT / MV_CHUNK;
-  int p_it = 0, p_t = blockIdx.x, p_c = 0;
-  int2 p_tl = make_int2(0, 0);
-  bool p_ok = true;
-  auto issue = [&]() {  // copy chunk p_it into stage p_it % MV_STAGES (the caller knows it is free)
-    if (p_t >= ntiles) return;
-    if (p_c == 0) p_tl = tiles[p_t];
-    const int st = p_it % MV_STAGES;
+  const int n_chunks = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * CPT;
+  auto issue = [&](int n, int2 tl) {
+    const int st = n % MV_STAGES;
     tc::mbar_arrive_expect_tx(&full[st], MV_STAGE_BYTES);
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
             tc::smem_u32(ring + st * MV_STAGE_BYTES)),
-        "l"(reinterpret_cast<uint64_t>(&tmH)), "r"(2 * p_tl.y * HT), "r"(p_tl.x * HT + p_c * MV_CHUNK),
+        "l"(reinterpret_cast<uint64_t>(&tmH)), "r"(2 * tl.y * HT), "r"(tl.x * HT + (n % CPT) * MV_CHUNK),
         "r"(tc::smem_u32(&full[st]))
         : "memory");
-    p_it++;
-    if (++p_c == CPT) {
-      p_c = 0;
-      p_t += gridDim.x;
-    }
+    atomicAdd(issued, 1);
   };
   if (threadIdx.x == 0) {
     tc::prefetch_tmap(&tmH);
-    for (int k = 0; k < MV_STAGES; k++) issue();
+    const int2 tl0 = tiles[blockIdx.x];
+    for (int k = 0; k < MV_STAGES && k < n_chunks; k++) issue(k, tl0);
   }
   int it = 0;
   bool aborted = false;  // warp-uniform; after a timeout the warp runs on without waiting so that
@@ -493,15 +491,19 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
 #pragma unroll
         for (int tt = 0; tt < 2; tt++) h[rr][tt] = rows[(warp * 4 + rr) * (HT / 2) + lane + 32 * tt];
       __syncwarp();
-      if (lane == 0 && !aborted)
+      if (lane == 0 && !aborted) {
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[st])) : "memory");
-      if (threadIdx.x == 0 && p_ok && !aborted && p_t < ntiles) {
-        // all four warps have taken chunk it out of stage st: refill it with chunk it + MV_STAGES
-        if (tc::mbar_wait_bounded(&empty[st], (it / MV_STAGES) & 1, MV_WAIT)) {
-          issue();
-        } else {
-          atomicOr(err, 2);
-          p_ok = false;
+        if (atomicAdd(&taken[st], 1) == 3) {
+          // the last of the four warps to take chunk it out of stage st refills it with chunk
+          // it + MV_STAGES (this tile's or the next one's), so no warp waits for the others
+          atomicExch(&taken[st], 0);
+          const int n = it + MV_STAGES;
+          if (n < n_chunks) {
+            if (tc::mbar_wait_bounded(&empty[st], (it / MV_STAGES) & 1, MV_WAIT))
+              issue(n, n / CPT == it / CPT ? make_int2(bi, bj) : tl_next);
+            else
+              atomicOr(err, 2);
+          }
         }
       }
       __syncwarp();
@@ -608,9 +610,12 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
     if (has_next) HMV_PARK();  // visible after the next tile's opening barrier
   }
   // chunks copied but never consumed (only after a timeout) must land before the CTA exits
-  if (threadIdx.x == 0)
-    for (int k = it; k < p_it; k++)
+  asm volatile("bar.sync 1, 128;" ::: "memory");
+  if (threadIdx.x == 0) {
+    const int n_issued = *issued;
+    for (int k = it; k < n_issued; k++)
       if (!tc::mbar_wait_bounded(&full[k % MV_STAGES], (k / MV_STAGES) & 1, MV_WAIT)) atomicOr(err, 2);
+  }
 }
 #undef HMV_FETCH
 #undef HMV_PARK

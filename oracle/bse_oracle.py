@@ -38,7 +38,7 @@ import numpy as np
 __all__ = [
     "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
     "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
-    "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact", "offset_average_eps2",
+    "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact", "offset_average_eps2", "interp_V",
 ]
 
 TWO_PI = 2.0 * np.pi
@@ -332,4 +332,11 @@ def offset_average_eps2(inputs_list, weights, omega, eta):
         orc = BSEOracle(inp)
         tot += w * eps2_exact(orc.hamiltonian(), orc.dipoles(), omega, eta, orc.prefactor())
     return tot
+
+
+def interp_V(V_R, R_W, w_RW, q):
+    """V_mu,nu(q) = sum_R w_R Vbar_mu,nu(R) e^{-i q.R}: the bare interaction's companion of the
+    W interpolation (the V kernel of §III.A with the dual-mesh R-sum of §III.B); at q = 0 it
+    is the V(0) = sum_R Vbar(R) the exchange uses."""
+    return interp_W(V_R, R_W, w_RW, q)
 

@@ -17,7 +17,9 @@ Recipe (seed = 20260000 + config unless given):
   e^{-|R'|}, G_R' real Gaussian, so that W(-q) = conj W(q) and W(R) is real; W(R) is
   the inverse transform on the coarse cell, each class copied to all of its
   minimal-length images with weight 1/(number of images);
-* V0 = s_V L_V L_V^T / N_aux with L_V real Gaussian (symmetric positive semidefinite);
+* V0 = s_V L_V L_V^T / N_aux with L_V real Gaussian (symmetric positive semidefinite), and
+  a bare V(R) on the R-set of W whose weighted sum is V0 (V(q) = V0 + a smooth PSD term
+  that vanishes at q = 0);
 * velocities from the tight-binding derivative sum_R i R_cart h(R) e^{2 pi i k.R}.
 
 None of the method's own arithmetic (dense-mesh interpolation, pair projection, kernel
@@ -269,11 +271,24 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
     W_R = np.ascontiguousarray(Wcls.real[owner])
     LV = rng.standard_normal((n_aux, n_aux))
     V0 = spec.s_V * (LV @ LV.T) / n_aux
+    # bare interaction on the coarse mesh: V(q) = V0 + s_V D(q) D(q)^dagger / N_aux with
+    # D(q) = sum_{R' != 0} G'_R' (e^{-iq.R'} - 1) e^{-|R'|} (real G', so D(-q) = conj D(q) and
+    # V(R) is real; D(0) = 0 keeps V(q = 0) = V0), folded to V(R) on the R-set of W.  Drawn
+    # from a stream of its own, so the other inputs do not depend on it.
+    rng_v = np.random.Generator(np.random.PCG64(spec.seed + 7919))
+    Gv = rng_v.standard_normal((len(Rl), n_aux, n_aux))
+    ph = np.exp(-1j * TWO_PI * (qc @ Rl.T.astype(np.float64))) - 1.0
+    Dq = np.einsum("qr,r,rmn->qmn", ph, damp, Gv, optimize=True)
+    Vq = V0[None] + spec.s_V * np.matmul(Dq, np.conj(np.transpose(Dq, (0, 2, 1)))) / n_aux
+    Vcls = np.einsum("qc,qmn->cmn", np.exp(1j * TWO_PI * (qc @ cls.T)), Vq, optimize=True) / qc.shape[0]
+    V_R = np.ascontiguousarray(Vcls.real[owner])
     if W_zero:
         W_R[:] = 0.0
         Wq[:] = 0.0
     if V_zero:
         V0[:] = 0.0
+        V_R[:] = 0.0
+        Vq[:] = 0.0
 
     return dict(
         name=spec.name, lattice=lat, tau=tau, volume=abs(np.linalg.det(lat)),
@@ -284,5 +299,5 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
         nv=spec.nv, nc=spec.nc,
         R_C=R_C.astype(np.int32), C_R=C_R,
         R_W=R_W.astype(np.int32), w_RW=w_RW, W_R=W_R, W_q_coarse=Wq, q_coarse=qc,
-        V0=V0, c_k=c_k, e_ks=e_ks, e_qp=e_qp, vel=vel,
+        V0=V0, V_R=V_R, V_q_coarse=Vq, c_k=c_k, e_ks=e_ks, e_qp=e_qp, vel=vel,
     )

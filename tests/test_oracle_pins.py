@@ -488,3 +488,19 @@ def test_package_offsets_match_the_fixture():
     assert len(offsets.OFFSETS) == len(rows)
     for (o, n), po, pw in zip(rows, offsets.OFFSETS, offsets.WEIGHTS):
         assert np.allclose(po, o) and np.isclose(pw, n / 27.0)
+
+
+# ---- bare interaction V(q) (optional output of the interpolation step) -----------------------
+def test_interp_V_reproduces_V0_and_coarse_mesh():
+    """V(q = 0) equals the V(0) the exchange uses, the dense interpolation reproduces the
+    generator's coarse-mesh V(q) when dense = coarse, and V(q) is Hermitian off the mesh."""
+    spec = dataclasses.replace(config_spec(0), dense=(3, 1, 1))
+    inp = make_inputs(spec)
+    assert np.abs(O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], np.zeros(3)) - inp["V0"]).max() \
+        <= 1e-12 * np.abs(inp["V0"]).max()
+    for iq, q in enumerate(inp["q_coarse"]):
+        Vq = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], q)
+        assert np.abs(Vq - inp["V_q_coarse"][iq]).max() <= 1e-12 * np.abs(inp["V_q_coarse"]).max()
+    q = np.array([0.137, 0.291, 0.05])
+    Vq = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], q)
+    assert np.abs(Vq - Vq.conj().T).max() <= 1e-14 * np.abs(Vq).max()

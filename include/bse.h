@@ -99,6 +99,14 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out);
  * Both inputs are read during this call's work only (the context keeps its own copy). */
 bse_status bse_interp_W(bse_ctx *ctx, const double *W_R, const double *V0, void *Wq_out);
 
+/* Optional output of step (a): the bare interaction at every dense transfer q,
+ * V(q) = sum_R w_R Vbar(R) exp(-i q.R), with the R-set and weights of W (bse_params R_W,
+ * w_RW); FP64 for every precision.  V(0) is what the exchange term uses (bse_interp_W's V0);
+ * V(q != 0) is not needed by the Q = 0 Hamiltonian (§III.A).
+ *  V_R    : [n_RW][N_aux][N_aux] float64, real.
+ *  Vq_out : [N_k][N_aux][N_aux] complex128 (row mu, column nu). */
+bse_status bse_interp_V(bse_ctx *ctx, const double *V_R, void *Vq_out);
+
 /* Step (b), per-k part: C(k) and the half-transforms Y^mu_sn(k) = sum_t C^mu_st(k) c^k_tn
  * for s on the atom of mu (C real => the second LRI term is conj(Y), §III.A), the
  * exchange factors C~^mu_{a k, i k}, and a copy of the band energies.

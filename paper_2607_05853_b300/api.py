@@ -110,6 +110,15 @@ class BSE:
         self._check(self._lib.bse_interp_W(self._ctx, a, b, c), "bse_interp_W")
         return Wq_out
 
+    def interp_V(self, V_R: torch.Tensor, Vq_out: torch.Tensor | None = None) -> torch.Tensor:
+        """bse_interp_V: the bare interaction V(q) at every dense transfer q (complex128)."""
+        if Vq_out is None:
+            Vq_out = torch.empty((self.nk, self.naux, self.naux), dtype=torch.complex128, device="cuda")
+        a = _dev(V_R, torch.float64, "V_R", self.n_RW * self.naux * self.naux)
+        b = _dev(Vq_out, torch.complex128, "Vq_out", self.nk * self.naux * self.naux)
+        self._check(self._lib.bse_interp_V(self._ctx, a, b), "bse_interp_V")
+        return Vq_out
+
     def project_pairs(self, C_R: torch.Tensor, c_k: torch.Tensor, e_qp: torch.Tensor):
         a = _dev(C_R, torch.float64, "C_R", self.n_RC * self.nao * self.nao * self.naux)
         b = _dev(c_k, torch.complex128, "c_k", self.nk * self.nao * self.nb)

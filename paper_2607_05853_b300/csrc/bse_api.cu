@@ -278,6 +278,12 @@ bse_status bse_interp_W(bse_ctx *c, const double *W_R, const double *V0, void *W
   return BSE_OK;
 }
 
+bse_status bse_interp_V(bse_ctx *c, const double *V_R, void *Vq_out) {
+  if (!c) return BSE_EINVAL;
+  if (!V_R || !Vq_out) return bse_fail(c, BSE_EINVAL, "interp_V: null V_R or Vq_out");
+  return launch_interp_W_fp64(c, V_R, (double2 *)Vq_out);
+}
+
 bse_status bse_project_pairs(bse_ctx *c, const double *C_R, const double *c_k, const double *e_qp) {
   if (!c) return BSE_EINVAL;
   if (c->stage < 1) return bse_fail(c, BSE_ESTATE, "project_pairs before interp_W");

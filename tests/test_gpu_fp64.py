@@ -160,3 +160,24 @@ def test_full_size_fp64_sampled_blocks():
         row = H[int(r), :].cpu().numpy()
         col = H[:, int(r)].cpu().numpy()
         assert np.abs(row - np.conj(col)).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("name", ["tiny", "two_d"])
+def test_interp_V_matches_oracle(name):
+    """bse_interp_V: the bare V(q) at every dense q against the oracle's R-sum (FP64), for an
+    FP64 and a split-precision context; V(q = 0) is the V(0) of the exchange."""
+    import torch
+    from paper_2607_05853_b300.api import BSE
+    inp = make_inputs(config_spec(0) if name == "tiny" else RAGGED[name])
+    n1, n2, n3 = (int(x) for x in inp["dense"])
+    nk = n1 * n2 * n3
+    for prec in ("fp64", "bf16x3"):
+        b = BSE.from_inputs(inp, precision=prec)
+        Vq = b.interp_V(torch.from_numpy(np.ascontiguousarray(inp["V_R"])).cuda()).cpu().numpy()
+        b.sync()
+        scale = np.abs(inp["V0"]).max()
+        for q in range(nk):
+            qf = np.array([q // (n2 * n3), (q // n3) % n2, q % n3], np.float64) / np.array([n1, n2, n3])
+            ref = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], qf)
+            assert np.abs(Vq[q] - ref).max() <= 1e-12 * scale, (prec, q)
+        assert np.abs(Vq[0] - inp["V0"]).max() <= 1e-12 * scale

@@ -22,6 +22,16 @@ What it computes, and where each step comes from in the paper (arXiv 2607.05853)
 * the windowed absorption integral I = int_lo^hi eps2(omega) domega (eps2 as above) and
   its seed Gamma with dI = tr(Gamma dH), by the Daleckii-Krein formula for the derivative
   of a matrix function on the full eigendecomposition.
+* finite exciton momentum Q (the q != 0 extension the paper names as future work, §V):
+  the pair (k, i, a) holds the valence band i at k and the conduction band a at k + Q, so
+  every conduction coefficient, LRI coefficient and energy of the pair is taken at k + Q.
+  The same C~ definition (§III.A) and kernel forms (Eq. W_LRI) apply: the direct kernel
+  keeps W at q = k1 - k2 (both conduction points shift by Q), the diagonal is
+  E_a(k+Q) - E_i(k), and the exchange densities psi*_{a k+Q} psi_{i k} and
+  psi*_{j k2} psi_{b k2+Q} expand in ABF Bloch sums of momentum -Q and +Q, whose Coulomb
+  integral over the crystal is N_k sum_R w_R Vbar(R) e^{+i Q.R} = N_k V(-Q) in the
+  convention V(q) = sum_R w_R Vbar(R) e^{-i q.R}.  At Q = 0 this is V(0) and the TDA
+  Hamiltonian above.
 
 Index conventions: the H row of (k, v, c) is (k*Nv + v)*Nc + c; valence window column
 v=0 is the valence band maximum (counting down), conduction column c=0 the conduction
@@ -73,7 +83,9 @@ def ks_lri(c_bra, c_ket, C_of_kket, C_of_minus_kbra):
 class BSEOracle:
     """Element-block evaluation of the TDA Hamiltonian A from the definitions above."""
 
-    def __init__(self, inp: dict, alpha: float = 2.0):
+    def __init__(self, inp: dict, alpha: float = 2.0, Q=(0, 0, 0)):
+        """Q: exciton momentum in dense-mesh steps (Q_frac = Q / N per axis).  Q != 0 with
+        alpha != 0 needs inp["V_R"] (the exchange takes V(-Q) from the R-sum)."""
         self.inp = inp
         self.alpha = float(alpha)
         self.mesh = np.asarray(inp["dense"], np.int64)
@@ -85,6 +97,14 @@ class BSEOracle:
         g = np.stack(np.meshgrid(np.arange(n1), np.arange(n2), np.arange(n3), indexing="ij"), -1)
         self.kint = g.reshape(-1, 3)
         self.kfrac = (self.kint + np.asarray(inp["k_offset"], np.float64)) / self.mesh
+        self.Q = np.mod(np.asarray(Q, np.int64), self.mesh)
+        self.finite_Q = bool(np.any(self.Q != 0))
+        if not self.finite_Q:
+            self.V_exch = inp["V0"]
+        elif self.alpha != 0.0:
+            self.V_exch = interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], -self.Q / self.mesh)
+        else:
+            self.V_exch = None
         self._Ck, self._Cmk, self._Wq, self._X1, self._X2 = {}, {}, {}, {}, {}
 
     # -- memoised pieces ---------------------------------------------------------
@@ -99,6 +119,11 @@ class BSEOracle:
             i = self.inp
             self._Cmk[ik] = lri_C_k(i["C_R"], i["R_C"], -self.kfrac[ik], i["ao_atom"], i["aux_atom"])
         return self._Cmk[ik]
+
+    def kQ(self, ik):
+        """Mesh index of k + Q (the conduction point of the pairs at k)."""
+        d = np.mod(self.kint[ik] + self.Q, self.mesh)
+        return int((d[0] * self.mesh[1] + d[1]) * self.mesh[2] + d[2])
 
     def q_index(self, ik1, ik2):
         d = np.mod(self.kint[ik1] - self.kint[ik2], self.mesh)
@@ -118,21 +143,24 @@ class BSEOracle:
     def _cc(self, ik):
         return self.inp["c_k"][ik][:, self.nv:]
 
-    def X_exch_left(self, ik):       # C~^mu_{a k, i k}  -> [mu, a, i]
+    def X_exch_left(self, ik):       # C~^mu_{a k+Q, i k}  -> [mu, a, i]
         if ik not in self._X1:
-            self._X1[ik] = ks_lri(self._cc(ik), self._cv(ik), self.C_k(ik), self.C_mk(ik))
+            kq = self.kQ(ik)
+            self._X1[ik] = ks_lri(self._cc(kq), self._cv(ik), self.C_k(ik), self.C_mk(kq))
         return self._X1[ik]
 
-    def X_exch_right(self, ik):      # C~^nu_{j k, b k}  -> [nu, j, b]
+    def X_exch_right(self, ik):      # C~^nu_{j k, b k+Q}  -> [nu, j, b]
         if ik not in self._X2:
-            self._X2[ik] = ks_lri(self._cv(ik), self._cc(ik), self.C_k(ik), self.C_mk(ik))
+            kq = self.kQ(ik)
+            self._X2[ik] = ks_lri(self._cv(ik), self._cc(kq), self.C_k(kq), self.C_mk(ik))
         return self._X2[ik]
 
     def M_vv(self, ik1, ik2):        # C~^mu_{j k2, i k1} -> [mu, j, i]
         return ks_lri(self._cv(ik2), self._cv(ik1), self.C_k(ik1), self.C_mk(ik2))
 
-    def M_cc(self, ik1, ik2):        # C~^nu_{a k1, b k2} -> [nu, a, b]
-        return ks_lri(self._cc(ik1), self._cc(ik2), self.C_k(ik2), self.C_mk(ik1))
+    def M_cc(self, ik1, ik2):        # C~^nu_{a k1+Q, b k2+Q} -> [nu, a, b]
+        p1, p2 = self.kQ(ik1), self.kQ(ik2)
+        return ks_lri(self._cc(p1), self._cc(p2), self.C_k(p2), self.C_mk(p1))
 
     # -- kernels and blocks ------------------------------------------------------------
     def direct(self, ik1, ik2):
@@ -143,9 +171,10 @@ class BSEOracle:
         return np.einsum("jiv,vab->iajb", T, Mc) / self.nk
 
     def exchange(self, ik1, ik2):
-        """(a k1*, i k1|V|j k2*, b k2) as [i, a, j, b] (the V-kernel beside Eq. W_LRI)."""
+        """(a k1+Q*, i k1|V|j k2*, b k2+Q) as [i, a, j, b] (the V-kernel beside Eq. W_LRI;
+        V(0) at Q = 0, V(-Q) otherwise)."""
         X1, X2 = self.X_exch_left(ik1), self.X_exch_right(ik2)
-        T = np.einsum("uai,uv->aiv", X1, self.inp["V0"])
+        T = np.einsum("uai,uv->aiv", X1, self.V_exch)
         return np.einsum("aiv,vjb->iajb", T, X2) / self.nk
 
     def block(self, ik1, ik2):
@@ -155,8 +184,8 @@ class BSEOracle:
             blk = blk + self.alpha * self.exchange(ik1, ik2)
         blk = blk.reshape(self.nvc, self.nvc)
         if ik1 == ik2:
-            e = self.inp["e_qp"][ik1]
-            de = (e[self.nv:][None, :] - e[: self.nv][:, None]).reshape(-1)   # (i, a)
+            ev, ec = self.inp["e_qp"][ik1][: self.nv], self.inp["e_qp"][self.kQ(ik1)][self.nv:]
+            de = (ec[None, :] - ev[:, None]).reshape(-1)                     # (i, a)
             blk = blk + np.diag(de)
         return blk
 
@@ -170,7 +199,10 @@ class BSEOracle:
 
     # -- optics ------------------------------------------------------------------------
     def dipoles(self):
-        """d_alpha,(k,i,a) = <ik|v_alpha|ak>/(E^KS_ak - E^KS_ik) (Eq. abs_vel), shape [3, dim]."""
+        """d_alpha,(k,i,a) = <ik|v_alpha|ak>/(E^KS_ak - E^KS_ik) (Eq. abs_vel), shape [3, dim].
+        Optical (vertical) transitions only: defined at Q = 0."""
+        if self.finite_Q:
+            raise ValueError("dipoles: the optical matrix elements are vertical (Q = 0)")
         e = self.inp["e_ks"]
         de = e[:, self.nv:][:, None, :] - e[:, : self.nv][:, :, None]        # [k, i, a]
         return (self.inp["vel"] / de[None]).reshape(3, -1)
@@ -262,7 +294,7 @@ def grad_from_seed(orc, Gamma):
     W(q) = sum_R w_R W(R) e^{-i q.R}; the gradient with respect to one real entry W_mu,nu(R)
     is Re tr(Gamma dH/dW_mu,nu(R)) (the symmetric pair W_mu,nu(R), W_nu,mu(-R) together moves
     the energy by twice this).  E^QP enters only the diagonal (Eq. Hamiltonian):
-    dL/dE^QP_ak = sum_i Gamma_(k,i,a),(k,i,a), dL/dE^QP_ik = -sum_a Gamma_(k,i,a),(k,i,a).
+    dL/dE^QP_a,k+Q = sum_i Gamma_(k,i,a),(k,i,a), dL/dE^QP_ik = -sum_a Gamma_(k,i,a),(k,i,a).
     Returns (dW_R [n_RW][N_aux][N_aux], de_qp [N_k][Nv+Nc])."""
     inp = orc.inp
     nk, nv, nc, nvc = orc.nk, orc.nv, orc.nc, orc.nvc
@@ -283,7 +315,8 @@ def grad_from_seed(orc, Gamma):
     dW = np.real(np.einsum("qr,quv->ruv", ph, Aq)) * inp["w_RW"][:, None, None]
     d = np.real(np.diag(Gamma)).reshape(nk, nv, nc)
     de = np.zeros((nk, nv + nc))
-    de[:, nv:] = d.sum(axis=1)
+    for k in range(nk):                  # the conduction energy of the pairs at k sits at k + Q
+        de[orc.kQ(k), nv:] += d[k].sum(axis=0)
     de[:, :nv] = -d.sum(axis=2)
     return dW, de
 

@@ -504,3 +504,104 @@ def test_interp_V_reproduces_V0_and_coarse_mesh():
     q = np.array([0.137, 0.291, 0.05])
     Vq = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], q)
     assert np.abs(Vq - Vq.conj().T).max() <= 1e-14 * np.abs(Vq).max()
+
+
+# ---------------------------------------------------------------- f3: finite exciton momentum
+def _finite_Q_brute_error(inp, orc, pairs=((0, 0), (1, 4), (5, 2)),
+                          bands=((0, 0, 0, 0), (1, 0, 0, 1), (0, 1, 1, 1))):
+    """Largest relative gap between the oracle's finite-Q direct and exchange kernels and the
+    real-space lattice sums (Bloch sums of the two-centre expansion, W(R) and Vbar(R) as
+    six-dimensional integrals, §III.A); the pair (k, i, a) holds band i at k, band a at k+Q."""
+    kf, nk, mesh, nv, c = orc.kfrac, orc.nk, tuple(inp["dense"]), orc.nv, inp["c_k"]
+    err = 0.0
+    for k1, k2 in pairs:
+        p1q, p2q = orc.kQ(k1), orc.kQ(k2)
+        D = orc.direct(k1, k2)
+        X = orc.exchange(k1, k2)
+        for (i, a, j, b) in bands:
+            p1 = (c[k2][:, j], kf[k2], c[k1][:, i], kf[k1])
+            p2 = (c[p1q][:, nv + a], kf[p1q], c[p2q][:, nv + b], kf[p2q])
+            bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
+            q1 = (c[p1q][:, nv + a], kf[p1q], c[k1][:, i], kf[k1])
+            q2 = (c[k2][:, j], kf[k2], c[p2q][:, nv + b], kf[p2q])
+            bx = _brute_kernel(inp, kf, nk, mesh, q1, q2, inp["R_W"], inp["w_RW"], inp["V_R"])
+            err = max(err, abs(bd - D[i, a, j, b]) / max(abs(bd), 1e-30),
+                      abs(bx - X[i, a, j, b]) / max(abs(bx), 1e-30))
+    return err
+
+
+@pytest.mark.parametrize("Q", [(1, 0, 0), (2, 1, 0), (1, 1, 0)])
+def test_finite_Q_kernels_match_realspace_brute_force(Q):
+    """Both kernels at Q != 0 against the lattice sums: fixes that the exchange takes
+    V(-Q) = sum_R w_R Vbar(R) e^{+iQ.R} and that the conduction points are k + Q."""
+    inp = make_inputs(tiny_spec())
+    orc = O.BSEOracle(inp, Q=Q)
+    assert _finite_Q_brute_error(inp, orc) < 1e-11
+
+
+@pytest.mark.parametrize("mistake", ["V_plus_Q", "cond_at_k", "diag_cond_at_k"])
+def test_finite_Q_planted_mistake_is_caught(mistake, monkeypatch):
+    inp = make_inputs(tiny_spec())
+    Q = (1, 1, 0)
+    mod = O.bse_oracle
+    if mistake == "V_plus_Q":
+        bad = O.BSEOracle(inp, Q=Q)
+        bad.V_exch = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], bad.Q / bad.mesh)
+        assert _finite_Q_brute_error(inp, bad) > 1e-6
+    elif mistake == "cond_at_k":
+        monkeypatch.setattr(mod.BSEOracle, "M_cc", lambda self, k1, k2: mod.ks_lri(
+            self._cc(k1), self._cc(k2), self.C_k(k2), self.C_mk(k1)))
+        assert _finite_Q_brute_error(inp, O.BSEOracle(inp, Q=Q)) > 1e-6
+    else:
+        # the diagonal is not in the kernels: the independent-particle limit catches it
+        d = make_inputs(tiny_spec(), W_zero=True, V_zero=True)
+        good = O.BSEOracle(d, alpha=0.0, Q=Q)
+        e = d["e_qp"]
+        ref = np.sort([e[good.kQ(k)][good.nv + a] - e[k][i] for k in range(good.nk)
+                       for i in range(good.nv) for a in range(good.nc)])
+        assert np.allclose(np.linalg.eigvalsh(good.hamiltonian()), ref, atol=1e-12)
+        orig = mod.BSEOracle.kQ
+        monkeypatch.setattr(mod.BSEOracle, "kQ", lambda self, k: k)
+        bad = O.BSEOracle(d, alpha=0.0, Q=Q)
+        assert not np.allclose(np.linalg.eigvalsh(bad.hamiltonian()), ref, atol=1e-6)
+        monkeypatch.setattr(mod.BSEOracle, "kQ", orig)
+
+
+def test_finite_Q_hamiltonian_hermitian_and_Q0_reduction():
+    """H(Q) is Hermitian (§II.C) at every Q; a Q equal to a whole mesh period is Q = 0."""
+    inp = make_inputs(tiny_spec())
+    for Q in [(1, 0, 0), (2, 1, 0)]:
+        H = O.BSEOracle(inp, Q=Q).hamiltonian()
+        assert np.abs(H - H.conj().T).max() <= 1e-13 * np.abs(H).max()
+    H0 = O.BSEOracle(inp).hamiltonian()
+    Hp = O.BSEOracle(inp, Q=tuple(inp["dense"])).hamiltonian()
+    assert np.array_equal(H0, Hp)
+
+
+def test_finite_Q_exchange_V_R_at_zero_is_V0():
+    """At Q = 0 the R-sum of Vbar(R) gives the V(0) the Q = 0 exchange uses, so the V_R route
+    and the V0 route build the same Hamiltonian."""
+    inp = make_inputs(tiny_spec())
+    orc = O.BSEOracle(inp)
+    Vsum = O.interp_V(inp["V_R"], inp["R_W"], inp["w_RW"], np.zeros(3))
+    assert np.abs(Vsum - inp["V0"]).max() <= 1e-12 * np.abs(inp["V0"]).max()
+
+
+def test_finite_Q_gradient_matches_central_differences():
+    """dOmega_0/dE^QP at Q != 0 (the conduction derivative lands on k + Q) against central
+    differences of LAPACK eigenvalues."""
+    inp = make_inputs(tiny_spec())
+    Q = (1, 1, 0)
+    orc = O.BSEOracle(inp, Q=Q)
+    w, X = O.adjoint_seed_lowest(orc.hamiltonian(), 1)
+    G = np.outer(X[:, 0], X[:, 0].conj())
+    _, de = O.grad_from_seed(orc, G)
+    h = 1e-6
+    for k, n in [(0, orc.nv), (orc.kQ(0), orc.nv), (3, 0), (4, orc.nv + 1)]:
+        vals = []
+        for sgn in (1, -1):
+            d = dict(inp)
+            d["e_qp"] = inp["e_qp"].copy()
+            d["e_qp"][k, n] += sgn * h
+            vals.append(np.linalg.eigvalsh(O.BSEOracle(d, Q=Q).hamiltonian())[0])
+        assert abs((vals[0] - vals[1]) / (2 * h) - de[k, n]) <= 1e-6, (k, n)

@@ -107,6 +107,23 @@ bse_status bse_interp_W(bse_ctx *ctx, const double *W_R, const double *V0, void 
  *  Vq_out : [N_k][N_aux][N_aux] complex128 (row mu, column nu). */
 bse_status bse_interp_V(bse_ctx *ctx, const double *V_R, void *Vq_out);
 
+/* Exciton momentum Q (the finite-momentum extension, §V: q != 0 blocks of the same
+ * Hamiltonian).  The pair (k, v, c) then holds the valence band v at k and the conduction
+ * band c at k + Q; the C~ coefficients (§III.A) are taken at those points, the direct kernel
+ * keeps W at q = k1 - k2, the diagonal is E_c(k+Q) - E_v(k), and the exchange kernel of
+ * Eq. W_LRI uses sum_R w_R Vbar(R) exp(+i Q.R) (= V(-Q) in bse_interp_V's convention; its
+ * value at Q = 0 is V(0)) in place of V(0).
+ *  Q   : host [3] int32, Q = Q_i / N_i per axis in dense-mesh steps (reduced mod N_i).
+ *  V_R : [n_RW][N_aux][N_aux] float64 real Vbar(R) on the images of bse_params.R_W, or NULL.
+ *        Required when Q != 0 and alpha != 0.  When given it replaces bse_interp_W's V0
+ *        (which may then be NULL) until a later call with V_R = NULL.
+ * Call after bse_setup and before bse_project_pairs; a call after bse_project_pairs
+ * requires bse_project_pairs again (BSE_ESTATE from bse_assemble otherwise), and one with
+ * V_R = NULL after one with V_R requires bse_interp_W again.  BSE_FP64 contexts only
+ * (BSE_EINVAL otherwise).  At Q != 0 bse_dipole_vector returns BSE_EINVAL: the optical
+ * dipoles are vertical transitions; bse_spectrum and bse_lowest take H(Q) as any H. */
+bse_status bse_set_momentum(bse_ctx *ctx, const int32_t *Q, const double *V_R);
+
 /* Step (b), per-k part: C(k) and the half-transforms Y^mu_sn(k) = sum_t C^mu_st(k) c^k_tn
  * for s on the atom of mu (C real => the second LRI term is conj(Y), §III.A), the
  * exchange factors C~^mu_{a k, i k}, and a copy of the band energies.

@@ -102,10 +102,11 @@ class BSE:
             pass
 
     # -- the ABI -------------------------------------------------------------------------
-    def interp_W(self, W_R: torch.Tensor, V0: torch.Tensor, Wq_out: torch.Tensor | None = None):
+    def interp_W(self, W_R: torch.Tensor, V0: torch.Tensor | None, Wq_out: torch.Tensor | None = None):
+        """bse_interp_W.  V0 may be None once set_momentum has been given V_R."""
         na = self.naux
         a = _dev(W_R, torch.float64, "W_R", self.n_RW * na * na)
-        b = _dev(V0, torch.float64, "V0", na * na)
+        b = _dev(V0, torch.float64, "V0", na * na) if V0 is not None else None
         c = _dev(Wq_out, torch.complex128, "Wq_out", self.nk * na * na) if Wq_out is not None else None
         self._check(self._lib.bse_interp_W(self._ctx, a, b, c), "bse_interp_W")
         return Wq_out
@@ -118,6 +119,14 @@ class BSE:
         b = _dev(Vq_out, torch.complex128, "Vq_out", self.nk * self.naux * self.naux)
         self._check(self._lib.bse_interp_V(self._ctx, a, b), "bse_interp_V")
         return Vq_out
+
+    def set_momentum(self, Q, V_R: torch.Tensor | None = None):
+        """bse_set_momentum: exciton momentum Q (dense-mesh steps) and, for the exchange at
+        Q != 0, the real-space bare interaction V_R."""
+        q = (ctypes.c_int32 * 3)(*[int(x) for x in Q])
+        v = None if V_R is None else _dev(V_R, torch.float64, "V_R", self.n_RW * self.naux * self.naux)
+        self._check(self._lib.bse_set_momentum(self._ctx, ctypes.cast(q, ctypes.c_void_p), v),
+                    "bse_set_momentum")
 
     def project_pairs(self, C_R: torch.Tensor, c_k: torch.Tensor, e_qp: torch.Tensor):
         a = _dev(C_R, torch.float64, "C_R", self.n_RC * self.nao * self.nao * self.naux)

@@ -257,12 +257,15 @@ __global__ void k_real_to_complex(const double *src, double2 *dst, long long n) 
 
 bse_status bse_interp_W(bse_ctx *c, const double *W_R, const double *V0, void *Wq_out) {
   if (!c) return BSE_EINVAL;
-  if (!W_R || !V0) return bse_fail(c, BSE_EINVAL, "interp_W: null W_R or V0");
+  if (!W_R || (!V0 && !c->vx_from_R)) return bse_fail(c, BSE_EINVAL, "interp_W: null W_R or V0");
   const long long nn = (long long)c->naux_tot * c->naux_tot;
-  k_real_to_complex<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(V0, c->V0c, nn);
-  bse_count_launch();
-  bse_status s = bse_check_launch(c, "V0 copy");
-  if (s != BSE_OK) return s;
+  bse_status s = BSE_OK;
+  if (!c->vx_from_R) {  // bse_set_momentum's V_R, when given, fixes the exchange interaction
+    k_real_to_complex<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(V0, c->V0c, nn);
+    bse_count_launch();
+    s = bse_check_launch(c, "V0 copy");
+    if (s != BSE_OK) return s;
+  }
   if (c->precision == BSE_FP64) {
     s = launch_interp_W_fp64(c, W_R, c->Wq);
     if (s != BSE_OK) return s;
@@ -282,6 +285,35 @@ bse_status bse_interp_V(bse_ctx *c, const double *V_R, void *Vq_out) {
   if (!c) return BSE_EINVAL;
   if (!V_R || !Vq_out) return bse_fail(c, BSE_EINVAL, "interp_V: null V_R or Vq_out");
   return launch_interp_W_fp64(c, V_R, (double2 *)Vq_out);
+}
+
+bse_status bse_set_momentum(bse_ctx *c, const int32_t *Q, const double *V_R) {
+  if (!c) return BSE_EINVAL;
+  if (!Q) return bse_fail(c, BSE_EINVAL, "set_momentum: null Q");
+  if (c->precision != BSE_FP64) return bse_fail(c, BSE_EINVAL, "set_momentum: finite momentum runs in BSE_FP64");
+  int m[3];
+  bool finite = false;
+  for (int i = 0; i < 3; i++) {
+    m[i] = (int)(((long long)Q[i] % c->mesh[i] + c->mesh[i]) % c->mesh[i]);
+    finite = finite || m[i] != 0;
+  }
+  if (finite && c->alpha != 0.0 && !V_R)
+    return bse_fail(c, BSE_EINVAL, "set_momentum: the exchange at Q != 0 needs V_R");
+  const int n1 = c->mesh[0], n2 = c->mesh[1], n3 = c->mesh[2];
+  const bool had_vx = c->vx_from_R;
+  for (int i = 0; i < 3; i++) c->Qm[i] = m[i];
+  c->qQ = (m[0] * n2 + m[1]) * n3 + m[2];
+  c->qmQ = (((n1 - m[0]) % n1) * n2 + (n2 - m[1]) % n2) * n3 + (n3 - m[2]) % n3;
+  c->vx_from_R = V_R != nullptr;
+  if (V_R) {
+    // V at the transfer -Q: sum_R w_R Vbar(R) e^{+iQ.R}
+    bse_status s = launch_interp_W_fp64(c, V_R, c->V0c, c->qmQ, 1);
+    if (s != BSE_OK) return s;
+  }
+  // the exchange factors and P = X V depend on Q; a V(0) replaced by V_R must come back
+  // through bse_interp_W before a Q = 0 assembly without V_R
+  c->stage = std::min(c->stage, (had_vx && !V_R) ? 0 : 1);
+  return BSE_OK;
 }
 
 bse_status bse_project_pairs(bse_ctx *c, const double *C_R, const double *c_k, const double *e_qp) {
@@ -335,6 +367,7 @@ bse_status bse_assemble(bse_ctx *c, void *H) {
 bse_status bse_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double *u) {
   if (!c) return BSE_EINVAL;
   if (!vel || !e_ks || !u) return bse_fail(c, BSE_EINVAL, "dipole_vector: null argument");
+  if (c->qQ != 0) return bse_fail(c, BSE_EINVAL, "dipole_vector: optical transitions are vertical (Q = 0)");
   return run_dipole_vector(c, vel, e_ks, (double2 *)u);
 }
 

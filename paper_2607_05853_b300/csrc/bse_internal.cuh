@@ -30,6 +30,11 @@ struct bse_ctx {
   int nv = 0, nc = 0, nb = 0, nvc = 0;
   double alpha = 2.0;
   int precision = BSE_FP64;
+  // exciton momentum Q (mesh steps): qQ is the flattened index of Q, qmQ of -Q, so the
+  // conduction point of the pairs at k is kdiff(k, qmQ) and k - Q is kdiff(k, qQ)
+  int Qm[3] = {0, 0, 0};
+  int qQ = 0, qmQ = 0;
+  bool vx_from_R = false;  // V0c holds sum_R w_R Vbar(R) e^{+iQ.R} (bse_set_momentum)
   int64_t dim = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -87,7 +92,7 @@ bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg);
 bse_status bse_check_launch(bse_ctx *c, const char *what);
 
 // fp64 path launchers (k_fp64.cu)
-bse_status launch_interp_W_fp64(bse_ctx *c, const double *W_R, double2 *out);
+bse_status launch_interp_W_fp64(bse_ctx *c, const double *W_R, double2 *out, int q_first = 0, int n_q = -1);
 bse_status launch_half_transform_fp64(bse_ctx *c, const double *C_R);
 bse_status launch_exchange_factors_fp64(bse_ctx *c);
 bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, int lda,

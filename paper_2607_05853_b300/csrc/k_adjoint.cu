@@ -152,13 +152,15 @@ __global__ void k_adj_ft(const double2 *__restrict__ Aq, const int *__restrict__
       if (r0 + rr < nRW) dW[(long long)(r0 + rr) * nn + e] = wRW[r0 + rr] * acc[rr];
 }
 
-// de[k][n] from the diagonal of Gamma
-__global__ void k_adj_diag(const double2 *__restrict__ Gamma, long long dim, int nk, int nv, int nc,
-                           double *__restrict__ de) {
+// de[k][n] from the diagonal of Gamma.  Valence n at k enters the pairs at k; conduction n
+// at k enters the pairs at k - Q (= kdiff(k, qQ)), whose conduction point is k.
+__global__ void k_adj_diag(const double2 *__restrict__ Gamma, long long dim, int n1, int n2, int n3, int qQ,
+                           int nv, int nc, double *__restrict__ de) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nb = nv + nc;
+  const int nb = nv + nc, nk = n1 * n2 * n3;
   if (t >= nk * nb) return;
   const int k = t / nb, n = t % nb;
+  const int kp = n < nv ? k : kdiff(k, qQ, n1, n2, n3);
   double s = 0.0;
   if (n < nv) {
     for (int a = 0; a < nc; a++) {
@@ -167,7 +169,7 @@ __global__ void k_adj_diag(const double2 *__restrict__ Gamma, long long dim, int
     }
   } else {
     for (int i = 0; i < nv; i++) {
-      const long long r = ((long long)k * nv + i) * nc + (n - nv);
+      const long long r = ((long long)kp * nv + i) * nc + (n - nv);
       s += Gamma[r * dim + r].x;
     }
   }
@@ -243,7 +245,8 @@ bse_status run_adjoint(bse_ctx *c, const double2 *Gamma, double *dW_R, double *d
   const long long nn = (long long)na * na;
   k_adj_ft<<<dim3((unsigned)((nn + 255) / 256), (c->n_RW + FTR - 1) / FTR), 256, 0, c->stream>>>(
       c->Aq, c->d_R_W, c->d_w_RW, c->n_RW, nn, c->mesh[0], c->mesh[1], c->mesh[2], dW_R);
-  k_adj_diag<<<(c->nk * c->nb + 255) / 256, 256, 0, c->stream>>>(Gamma, c->dim, c->nk, c->nv, c->nc, de_qp);
+  k_adj_diag<<<(c->nk * c->nb + 255) / 256, 256, 0, c->stream>>>(Gamma, c->dim, c->mesh[0], c->mesh[1],
+                                                                  c->mesh[2], c->qQ, c->nv, c->nc, de_qp);
   bse_count_launch(2);
   return bse_check_launch(c, "adjoint transform");
 }

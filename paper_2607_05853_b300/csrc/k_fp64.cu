@@ -3,12 +3,15 @@
 //
 //  k_interp_W        W(q) = sum_R w_R W(R) exp(-i q.R)      (R-sum of Eq. W_LRI, §III.B)
 //  k_half_transform  Y^mu_sn(k) = sum_t [sum_R C^mu_st(R) exp(i k.R)] c^k_tn, s on atom(mu)
-//  k_exchange_X      X[(k,i,a)]^mu = C~^mu_{a k, i k}                       (§III.A)
+//  k_exchange_X      X[(k,i,a)]^mu = C~^mu_{a k+Q, i k}                     (§III.A)
 //  k_project_slab    M_vv(k1,q)^mu_ij = C~^mu_{j k2, i k1},
-//                    M_cc(k1,q)^mu_ab = C~^mu_{a k1, b k2}, k2 = k1 - q      (§III.A)
+//                    M_cc(k1,q)^mu_ab = C~^mu_{a k1+Q, b k2+Q}, k2 = k1 - q (§III.A)
+//  (Q is the exciton momentum, 0 for the optical Hamiltonian; the pair (k, i, a) holds
+//   valence i at k and conduction a at k + Q)
 //  k_zgemm_nn        batched complex GEMM  C = A B (row-major), used for T = M_vv W(q)
 //                    and P = X V(0)
-//  k_g2_write        H block = (alpha X V0 X^dagger - T M_cc^T)/N_k + diagonal
+//  k_g2_write        H block = (alpha X V X^dagger - T M_cc^T)/N_k + diagonal, V = V(0) at
+//                    Q = 0 and sum_R w_R Vbar(R) e^{+iQ.R} otherwise
 //                    (Eq. Hamiltonian with the kernels of Eq. W_LRI)
 //
 // With C^mu_st(R) real the second term of the KS-basis coefficient is a conjugate of the
@@ -32,12 +35,13 @@ __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -
 
 constexpr int QB = 4;  // q values per interp block
 
+// out[q - q_first] for the transfers q = q_first .. q_first + n_q - 1.
 __global__ void k_interp_W(const double *__restrict__ WR, const int *__restrict__ RW,
                            const double *__restrict__ wRW, int nRW, int naux, int n1, int n2,
-                           int n3, double2 *__restrict__ out) {
+                           int n3, int q_first, int n_q, double2 *__restrict__ out) {
   extern __shared__ double2 ph[];  // [QB][nRW]
-  const int nk = n1 * n2 * n3;
-  const int q0 = blockIdx.y * QB;
+  const int nk = q_first + n_q;
+  const int q0 = q_first + blockIdx.y * QB;
   for (int t = threadIdx.x; t < QB * nRW; t += blockDim.x) {
     int qq = t / nRW, r = t % nRW, q = q0 + qq;
     double2 v = make_double2(0.0, 0.0);
@@ -64,7 +68,7 @@ __global__ void k_interp_W(const double *__restrict__ WR, const int *__restrict_
     }
 #pragma unroll
     for (int j = 0; j < QB; j++)
-      if (q0 + j < nk) out[(long long)(q0 + j) * nn + e] = acc[j];
+      if (q0 + j < nk) out[(long long)(q0 + j - q_first) * nn + e] = acc[j];
   }
 }
 
@@ -123,23 +127,27 @@ __global__ void k_half_transform(const double *__restrict__ CR, const int *__res
   }
 }
 
-// X[k][i][a][mu] = C~^mu_{a k, i k} = F(k,k)_{(nv+a) i} + conj(F(k,k)_{i (nv+a)}).
+// X[k][i][a][mu] = C~^mu_{a k+Q, i k} = F(k+Q,k)_{(nv+a) i} + conj(F(k,k+Q)_{i (nv+a)})
+// (k + Q = kdiff(k, qmQ); Q = 0 gives the optical pairs).
 __global__ void k_exchange_X(const double2 *__restrict__ Y, const double2 *__restrict__ ck,
                              int nao_tot, int nb, int nv, int nc, int naux, int nao_max,
                              const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
-                             const int *__restrict__ naoA, double2 *__restrict__ X) {
-  const int k = blockIdx.y;
+                             const int *__restrict__ naoA, int n1, int n2, int n3, int qmQ,
+                             double2 *__restrict__ X) {
+  const int k = blockIdx.y, kq = kdiff(k, qmQ, n1, n2, n3);
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
   if (mu >= naux) return;
   const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
   const double2 *c = ck + (long long)k * nao_tot * nb;
+  const double2 *cq = ck + (long long)kq * nao_tot * nb;
   const double2 *Yk = Y + (long long)k * nao_max * nb * naux;
+  const double2 *Yq = Y + (long long)kq * nao_max * nb * naux;
   for (int i = 0; i < nv; i++)
     for (int a = 0; a < nc; a++) {
       double2 f1 = make_double2(0, 0), f2 = make_double2(0, 0);
       for (int s = 0; s < na; s++) {
-        f1 = cadd(f1, cmulc(c[(ao0 + s) * nb + nv + a], Yk[((long long)s * nb + i) * naux + mu]));
-        f2 = cadd(f2, cmulc(c[(ao0 + s) * nb + i], Yk[((long long)s * nb + nv + a) * naux + mu]));
+        f1 = cadd(f1, cmulc(cq[(ao0 + s) * nb + nv + a], Yk[((long long)s * nb + i) * naux + mu]));
+        f2 = cadd(f2, cmulc(c[(ao0 + s) * nb + i], Yq[((long long)s * nb + nv + a) * naux + mu]));
       }
       X[(((long long)k * nv + i) * nc + a) * naux + mu] = cadd(f1, conjd(f2));
     }
@@ -147,12 +155,12 @@ __global__ void k_exchange_X(const double2 *__restrict__ Y, const double2 *__res
 
 constexpr int MAXB = 8;
 
-// grid: x = nmu_chunks * (nv + nc), y = k1, z = q - q0.  Row r < nv -> M_vv row i,
-// else M_cc row a = r - nv.
+// grid: x = nmu_chunks * (nv + nc), y = k1, z = q - q0.  Row r < nv -> M_vv row i (bands at
+// k1, k2), else M_cc row a = r - nv (bands at k1 + Q, k2 + Q; k + Q = kdiff(k, qmQ)).
 __global__ void k_project_slab(const double2 *__restrict__ Y, const double2 *__restrict__ ck,
                                int nao_tot, int nb, int nv, int nc, int naux, int nao_max,
                                const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
-                               const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
+                               const int *__restrict__ naoA, int n1, int n2, int n3, int qmQ, int q0,
                                const int *__restrict__ qlist, double2 *__restrict__ Mv,
                                double2 *__restrict__ Mc) {
   extern __shared__ double2 sc[];  // c1 [nao][nb], c2 [nao][nb]
@@ -162,16 +170,18 @@ __global__ void k_project_slab(const double2 *__restrict__ Y, const double2 *__r
   const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
   const int k1 = blockIdx.y, qq = blockIdx.z, q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
+  const int p1 = row < nv ? k1 : kdiff(k1, qmQ, n1, n2, n3);
+  const int p2 = row < nv ? k2 : kdiff(k2, qmQ, n1, n2, n3);
   double2 *c1 = sc, *c2 = sc + nao_tot * nb;
   for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
-    c1[e] = ck[(long long)k1 * nao_tot * nb + e];
-    c2[e] = ck[(long long)k2 * nao_tot * nb + e];
+    c1[e] = ck[(long long)p1 * nao_tot * nb + e];
+    c2[e] = ck[(long long)p2 * nao_tot * nb + e];
   }
   __syncthreads();
   if (mu >= naux) return;
   const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
-  const double2 *Y1 = Y + (long long)k1 * nao_max * nb * naux + mu;
-  const double2 *Y2 = Y + (long long)k2 * nao_max * nb * naux + mu;
+  const double2 *Y1 = Y + (long long)p1 * nao_max * nb * naux + mu;
+  const double2 *Y2 = Y + (long long)p2 * nao_max * nb * naux + mu;
   double2 acc1[MAXB], acc2[MAXB];
 #pragma unroll
   for (int j = 0; j < MAXB; j++) acc1[j] = acc2[j] = make_double2(0, 0);
@@ -268,8 +278,9 @@ constexpr int G2CH = 16;  // nu chunk staged in shared memory
 __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T, const double2 *__restrict__ Mc,
                                                   const double2 *__restrict__ P, const double2 *__restrict__ X,
                                                   const double *__restrict__ eqp, int nv, int nc, int naux,
-                                                  int n1, int n2, int n3, int q0, const int *__restrict__ qlist,
-                                                  double alpha, long long dim, double2 *__restrict__ H) {
+                                                  int n1, int n2, int n3, int qmQ, int q0,
+                                                  const int *__restrict__ qlist, double alpha, long long dim,
+                                                  double2 *__restrict__ H) {
   extern __shared__ double2 sm[];
   const int nk = n1 * n2 * n3;
   const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
@@ -324,7 +335,8 @@ __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T,
       int ia = o / nvc, jb = o % nvc;
       int i = ia / nc, a = ia % nc;
       double2 h = make_double2((alpha * ax[t].x - ad[t].x) * inv, (alpha * ax[t].y - ad[t].y) * inv);
-      if (q == 0 && ia == jb) h.x += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
+      if (q == 0 && ia == jb)
+        h.x += eqp[(long long)kdiff(k1, qmQ, n1, n2, n3) * nb + nv + a] - eqp[(long long)k1 * nb + i];
       H[((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb] = h;
       if (mirror) H[((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia] = conjd(h);
     }
@@ -334,13 +346,15 @@ __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T,
 }  // namespace
 
 // ------------------------------------------------------------------------------ launchers
-bse_status launch_interp_W_fp64(bse_ctx *c, const double *W_R, double2 *out) {
+bse_status launch_interp_W_fp64(bse_ctx *c, const double *W_R, double2 *out, int q_first, int n_q) {
+  if (n_q < 0) n_q = c->nk - q_first;
+  if (q_first < 0 || n_q < 1 || q_first + n_q > c->nk) return bse_fail(c, BSE_EINVAL, "interp: bad q range");
   const long long nn = (long long)c->naux_tot * c->naux_tot;
-  dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (c->nk + QB - 1) / QB);
+  dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (n_q + QB - 1) / QB);
   size_t sm = sizeof(double2) * QB * c->n_RW;
   bse_prof_begin(c, BSE_KP_INTERP);
   k_interp_W<<<grid, 256, sm, c->stream>>>(W_R, c->d_R_W, c->d_w_RW, c->n_RW, c->naux_tot,
-                                           c->mesh[0], c->mesh[1], c->mesh[2], out);
+                                           c->mesh[0], c->mesh[1], c->mesh[2], q_first, n_q, out);
   bse_prof_end(c, BSE_KP_INTERP);
   bse_count_launch();
   return bse_check_launch(c, "interp_W");
@@ -369,7 +383,7 @@ bse_status launch_exchange_factors_fp64(bse_ctx *c) {
   dim3 grid((c->naux_tot + 127) / 128, c->nk);
   k_exchange_X<<<grid, 128, 0, c->stream>>>(c->Y, c->ck, c->nao_tot, c->nb, c->nv, c->nc,
                                             c->naux_tot, c->nao_max, c->d_aux_atom, c->d_ao_start,
-                                            c->d_nao, c->X);
+                                            c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], c->qmQ, c->X);
   bse_count_launch();
   return bse_check_launch(c, "exchange_X");
 }
@@ -394,8 +408,8 @@ bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist
   bse_prof_begin(c, BSE_KP_PROJECT);
   k_project_slab<<<grid, 128, sm, c->stream>>>(c->Y, c->ck, c->nao_tot, c->nb, c->nv, c->nc,
                                                c->naux_tot, c->nao_max, c->d_aux_atom, c->d_ao_start,
-                                               c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], q0,
-                                               qlist, c->Mv, c->Mc);
+                                               c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], c->qmQ,
+                                               q0, qlist, c->Mv, c->Mc);
   bse_prof_end(c, BSE_KP_PROJECT);
   bse_count_launch();
   return bse_check_launch(c, "project_slab");
@@ -407,7 +421,7 @@ bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H) {
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_g2_write, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   bse_prof_begin(c, BSE_KP_G2);
   k_g2_write<<<grid, 256, sm, c->stream>>>(c->T, c->Mc, c->P, c->X, c->eqp, c->nv, c->nc,
-                                           c->naux_tot, c->mesh[0], c->mesh[1], c->mesh[2], q0,
+                                           c->naux_tot, c->mesh[0], c->mesh[1], c->mesh[2], c->qmQ, q0,
                                            c->d_qplus, c->alpha, c->dim, H);
   bse_prof_end(c, BSE_KP_G2);
   bse_count_launch();

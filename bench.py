@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
     ap.add_argument("--mesh", type=int, default=0, help="override the dense mesh N x N x N (profiling captures)")
+    ap.add_argument("--no-finite-q", action="store_true",
+                    help="skip the finite exciton momentum H(Q) assembly report")
     ap.add_argument("--batch16", action="store_true",
                     help="add the 16-uneven-crystal batch (one CUDA graph) report under 'batched_uneven'")
     return ap.parse_args()
@@ -388,6 +390,34 @@ def main():
                                      "spectrum_rel_L2": l2}
         del H64
         ref.close()
+
+    # ---- finite exciton momentum (outside the timed region): H(Q) on the same workload -------
+    if not args.no_finite_q:
+        VR = torch.from_numpy(np.ascontiguousarray(inp["V_R"], np.float64)).to(dev)
+        per_q = []
+        n1 = int(spec.dense[0])
+        for i, Q in enumerate(((1, 0, 0), (1, 0, 0), (n1 // 2, 0, 0), (1, 1, 0))):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            ctx.set_momentum(Q, VR)
+            ctx.interp_W(d["W_R"], None)
+            ctx.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+            ctx.assemble(H)
+            b.record(st)
+            ctx.sync()
+            if i == 0:
+                continue                    # first use of the shifted kernels: warm-up
+            w_q, r_q = ctx.lowest(H, 1, 300)
+            ctx.sync()
+            ms = a.elapsed_time(b)
+            per_q.append({"Q": list(Q), "assembly_ms": ms, "elements_per_s": dim2 / (ms / 1000.0),
+                          "lowest_exciton_eV": w_q.item()})
+        ctx.set_momentum((0, 0, 0), None)
+        extra["finite_momentum"] = {
+            "precision": args.precision, "per_Q": per_q,
+            "q0_assembly_ms": statistics.mean([p + a for p, a in zip(pre_ms, asm_ms)]),
+            "note": "H(Q) = bse_set_momentum + interp_W + project_pairs + assemble (conduction bands at k+Q, "
+                    "exchange with sum_R w_R Vbar(R) e^{+iQ.R}), Q in dense-mesh steps; outside the timed region"}
 
     clocks = clk.summary()
     result = {

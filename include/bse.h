@@ -119,8 +119,9 @@ bse_status bse_interp_V(bse_ctx *ctx, const double *V_R, void *Vq_out);
  *        (which may then be NULL) until a later call with V_R = NULL.
  * Call after bse_setup and before bse_project_pairs; a call after bse_project_pairs
  * requires bse_project_pairs again (BSE_ESTATE from bse_assemble otherwise), and one with
- * V_R = NULL after one with V_R requires bse_interp_W again.  BSE_FP64 contexts only
- * (BSE_EINVAL otherwise).  At Q != 0 bse_dipole_vector returns BSE_EINVAL: the optical
+ * V_R = NULL after one with V_R requires bse_interp_W again.  Every precision: the split
+ * precisions take the complex V in FP32 into their X V pieces.  At Q != 0
+ * bse_dipole_vector returns BSE_EINVAL: the optical
  * dipoles are vertical transitions; bse_spectrum and bse_lowest take H(Q) as any H. */
 bse_status bse_set_momentum(bse_ctx *ctx, const int32_t *Q, const double *V_R);
 

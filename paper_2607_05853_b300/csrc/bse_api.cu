@@ -274,7 +274,7 @@ bse_status bse_interp_W(bse_ctx *c, const double *W_R, const double *V0, void *W
                         c->stream) != cudaSuccess)
       return bse_fail(c, BSE_ECUDA, "interp_W: copy to Wq_out failed");
   } else {
-    s = split_interp_W(c, W_R, V0, (double2 *)Wq_out);
+    s = split_interp_W(c, W_R, (double2 *)Wq_out);
     if (s != BSE_OK) return s;
   }
   c->stage = std::max(c->stage, 1);
@@ -290,7 +290,6 @@ bse_status bse_interp_V(bse_ctx *c, const double *V_R, void *Vq_out) {
 bse_status bse_set_momentum(bse_ctx *c, const int32_t *Q, const double *V_R) {
   if (!c) return BSE_EINVAL;
   if (!Q) return bse_fail(c, BSE_EINVAL, "set_momentum: null Q");
-  if (c->precision != BSE_FP64) return bse_fail(c, BSE_EINVAL, "set_momentum: finite momentum runs in BSE_FP64");
   int m[3];
   bool finite = false;
   for (int i = 0; i < 3; i++) {

@@ -122,7 +122,7 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
 
 // split-precision path (k_split.cu)
 bse_status split_setup(bse_ctx *c);
-bse_status split_interp_W(bse_ctx *c, const double *W_R, const double *V0, double2 *Wq_out);
+bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
 bse_status split_project(bse_ctx *c, const double *C_R);
 bse_status split_y_to_fp64(bse_ctx *c);

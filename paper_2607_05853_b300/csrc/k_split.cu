@@ -7,8 +7,10 @@
 //                 M_vv written as bf16 pieces (the GEMM A operand), M_cc as FP32;
 //   k_tc_zgemm    T = M_vv W(q) on tensor cores (B operand: bf16 pieces of W(q)^T);
 //   k_g2_32       H block += -(1/N_k) T M_cc^T (+ diagonal, FP64), FP32 per pair.
-// Before the slabs, the exchange term alpha/N_k (X V0) conj(X)^T is one tensor-core GEMM
-// that writes every element of H.
+// Before the slabs, the exchange term alpha/N_k (X V) conj(X)^T is one tensor-core GEMM
+// that writes every element of H (V = V(0) at exciton momentum Q = 0, else the complex
+// sum_R w_R Vbar(R) e^{+iQ.R}).  At Q != 0 the per-k tables are relabelled once (valence
+// columns of k, conduction columns of k + Q; k_shift_tables) and the kernels run unchanged.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -33,7 +35,7 @@ struct SplitWS {
   float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux]
   float2 *T32 = nullptr;         // [nq][naux][rows]  (column nu of T = M_vv W(q) is contiguous)
   float2 *Y32 = nullptr;         // [nk][nao_max][nb][naux]
-  __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V0
+  __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V
   __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
   CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
   int bn_g1 = TC_BN;             // N tile of the M_vv W(q) GEMM (autotuned)
@@ -42,7 +44,13 @@ struct SplitWS {
   float2 *PHK = nullptr;         // [nk][n_RC]  e^{+i k.R}
   float *WR32T = nullptr;        // [n_RW][nu][mu]
   float *CR32 = nullptr;         // [n_RC][nao][nao][naux]
-  float *V032 = nullptr;         // [naux][naux]
+  float2 *V032 = nullptr;        // [naux][naux] exchange interaction V (V(0) real at Q = 0)
+  // exciton momentum Q != 0: the per-k tables relabelled so that the pairs at k read their
+  // valence columns at k and their conduction columns at k + Q (allocated on first use)
+  bool shifted = false;
+  float2 *Y32q = nullptr, *ck32q = nullptr;
+  double2 *ckq = nullptr;
+  double *eqpq = nullptr;
   float2 *ck32 = nullptr;        // [nk][nao][nb]
   float2 *X32 = nullptr;         // [dim][naux]  exchange factors
 };
@@ -293,13 +301,15 @@ __global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__res
     }
 }
 
-// P = X V(0) (V(0) real) in FP32, 64 x 64 tiles, written as bf16 pieces (operand A of the
-// exchange GEMM).
+// P = X V in FP32, 64 x 64 tiles, written as bf16 pieces (operand A of the exchange GEMM).
+// V is V(0), real, at Q = 0 (CPLX = false reads only its real parts) and the complex
+// Hermitian sum_R w_R Vbar(R) e^{+iQ.R} otherwise.
+template <bool CPLX>
 __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *__restrict__ X,
-                                                    const float *__restrict__ V0, int kmem, int np,
+                                                    const float2 *__restrict__ V0, int kmem, int np,
                                                     __nv_bfloat16 *__restrict__ Pp) {
   __shared__ float2 As[16][64];
-  __shared__ float Bs[16][64];
+  __shared__ float2 Bs[16][64];
   const int K = N;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
@@ -313,13 +323,12 @@ __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *
       const int r = e / 16, kk = e % 16, gr = row0 + r, gk = k0 + kk;
       As[kk][r] = (gr < M && gk < K) ? X[(long long)gr * K + gk] : make_float2(0.f, 0.f);
       const int kb = e / 64, cc = e % 64, gkb = k0 + kb, gc = col0 + cc;
-      Bs[kb][cc] = (gkb < K && gc < N) ? V0[(long long)gkb * N + gc] : 0.f;
+      Bs[kb][cc] = (gkb < K && gc < N) ? V0[(long long)gkb * N + gc] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; kk++) {
-      float2 a[4];
-      float b[4];
+      float2 a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
@@ -328,8 +337,12 @@ __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *
       for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 4; j++) {
-          acc[i][j].x = fmaf(a[i].x, b[j], acc[i][j].x);
-          acc[i][j].y = fmaf(a[i].y, b[j], acc[i][j].y);
+          acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+          acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+          if (CPLX) {
+            acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+            acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+          }
         }
     }
     __syncthreads();
@@ -351,6 +364,37 @@ __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *
         Pp[(2 * p + 1) * plane + (long long)r * kmem + cc] = pi[p];
       }
     }
+}
+
+// Exciton momentum Q (pairs: valence at k, conduction at k + Q): relabel the per-k tables so
+// that entry k holds the valence columns of k and the conduction columns of k + Q
+// (= kdiff(k, qmQ)).  Every Q = 0 formula of the exchange factors, pair projections and
+// diagonal then gives the Q blocks (the C~ of §III.A taken at the pair's own points).
+__global__ void k_shift_tables(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
+                               const double *__restrict__ eqp, int nao_max, int nao_tot, int nb, int nv, int naux,
+                               int n1, int n2, int n3, int qmQ, float2 *__restrict__ Yq, double2 *__restrict__ ckq,
+                               float2 *__restrict__ ck32q, double *__restrict__ eqpq) {
+  const int nk = n1 * n2 * n3;
+  const long long ny = (long long)nk * nao_max * nb * naux, nc_ = (long long)nk * nao_tot * nb;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < ny; e += stride) {
+    const long long r = e / naux;                       // row (k, s, n)
+    const int n = (int)(r % nb), k = (int)(r / ((long long)nao_max * nb));
+    const int src = n < nv ? k : kdiff(k, qmQ, n1, n2, n3);
+    Yq[e] = Y[e + (long long)(src - k) * nao_max * nb * naux];
+  }
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nc_; e += stride) {
+    const int n = (int)(e % nb), k = (int)(e / ((long long)nao_tot * nb));
+    const int src = n < nv ? k : kdiff(k, qmQ, n1, n2, n3);
+    const double2 v = ck[e + (long long)(src - k) * nao_tot * nb];
+    ckq[e] = v;
+    ck32q[e] = make_float2((float)v.x, (float)v.y);
+  }
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)nk * nb; e += stride) {
+    const int n = (int)(e % nb), k = (int)(e / nb);
+    const int src = n < nv ? k : kdiff(k, qmQ, n1, n2, n3);
+    eqpq[e] = eqp[(long long)src * nb + n];
+  }
 }
 
 __global__ void k_to_f32(const double2 *__restrict__ src, long long n, float2 *__restrict__ dst) {
@@ -701,12 +745,26 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
   }
 }
 
+bool alloc(void **p, size_t bytes) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+// The per-k tables the slabs read: relabelled at exciton momentum Q != 0, the originals at Q = 0.
+const float2 *y_tab(const SplitWS *w) { return w->shifted ? w->Y32q : w->Y32; }
+const double2 *ck_tab(const bse_ctx *c, const SplitWS *w) { return w->shifted ? w->ckq : c->ck; }
+const double *e_tab(const bse_ctx *c, const SplitWS *w) { return w->shifted ? w->eqpq : c->eqp; }
+
 template <int NV, int NC>
 void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq) {
   const int na = c->naux_tot;
   const int bs = std::min(160, (na + 31) / 32 * 32);
   const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
-  k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, na, c->nao_max, c->d_aux_atom,
+  k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom,
                                                              c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
                                                              c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap,
                                                              w->Mc32);
@@ -718,7 +776,7 @@ bool launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
   const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
   const size_t sm = sizeof(float2) * (size_t)(NV * NV + NC * NC) * c->naux_tot;
   if (sm > 200 * 1024) return false;  // the pair's rows do not fit: generic chunked kernel
-  k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->naux_tot, c->mesh[0],
+  k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->naux_tot, c->mesh[0],
                                                            c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
   return true;
 }
@@ -839,21 +897,13 @@ bse_status split_setup(bse_ctx *c) {
   w->nq = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
   w->nq = std::min(w->nq, 65535);
   if (c->mesh[2] > 1 && w->nq >= c->mesh[2]) w->nq = w->nq / c->mesh[2] * c->mesh[2];  // whole q-lines
-  auto alloc = [&](void **p, size_t bytes) -> bool {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      *p = nullptr;
-      return false;
-    }
-    return true;
-  };
   const size_t nn = (size_t)na * na;
   const size_t dimz = (size_t)c->dim;
   if (!alloc((void **)&w->PHQ, (size_t)c->nk * c->n_RW * sizeof(float2)) ||
       !alloc((void **)&w->PHK, (size_t)c->nk * c->n_RC * sizeof(float2)) ||
       !alloc((void **)&w->WR32T, (size_t)c->n_RW * nn * sizeof(float)) ||
       !alloc((void **)&w->CR32, (size_t)c->n_RC * c->nao_tot * c->nao_tot * na * sizeof(float)) ||
-      !alloc((void **)&w->V032, nn * sizeof(float)) ||
+      !alloc((void **)&w->V032, nn * sizeof(float2)) ||
       !alloc((void **)&w->ck32, (size_t)c->nk * c->nao_tot * c->nb * sizeof(float2)) ||
       !alloc((void **)&w->X32, dimz * na * sizeof(float2)) ||
       !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * 2) ||
@@ -889,19 +939,18 @@ void split_free(bse_ctx *c) {
   SplitWS *w = ws(c);
   if (!w) return;
   void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp, w->PHQ, w->PHK, w->WR32T, w->CR32, w->V032,
-                  w->ck32, w->X32};
+                  w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
   c->tc = nullptr;
 }
 
-bse_status split_interp_W(bse_ctx *c, const double *W_R, const double *V0, double2 *Wq_out) {
+bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out) {
   SplitWS *w = ws(c);
   const int na = c->naux_tot;
   const long long nn = (long long)na * na;
   k_wr_f32t<<<(unsigned)((nn * c->n_RW + 255) / 256), 256, 0, c->stream>>>(W_R, c->n_RW, na, w->WR32T);
-  k_d2f<<<(unsigned)std::min<long long>((nn + 255) / 256, 4096), 256, 0, c->stream>>>(V0, nn, w->V032);
   const size_t sm = sizeof(float2) * IQB * c->n_RW;
   if (sm > 48 * 1024 &&
       cudaFuncSetAttribute(k_interp_W32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
@@ -910,11 +959,11 @@ bse_status split_interp_W(bse_ctx *c, const double *W_R, const double *V0, doubl
   bse_prof_begin(c, BSE_KP_INTERP);
   k_interp_W32<<<grid, 256, sm, c->stream>>>(w->WR32T, w->PHQ, c->n_RW, na, c->nk, w->kmem, w->np, w->Wp, Wq_out);
   bse_prof_end(c, BSE_KP_INTERP);
-  bse_count_launch(3);
+  bse_count_launch(2);
   return bse_check_launch(c, "split interp_W");
 }
 
-// Per-k stage in FP32: Y, the exchange factors X (+ pieces of conj X) and P = X V(0) (pieces).
+// Per-k stage in FP32: Y, the exchange factors X (+ pieces of conj X) and P = X V (pieces).
 bse_status split_project(bse_ctx *c, const double *C_R) {
   SplitWS *w = ws(c);
   const int na = c->naux_tot;
@@ -934,13 +983,31 @@ bse_status split_project(bse_ctx *c, const double *C_R) {
       w->CR32, w->PHK, c->n_RC, w->ck32, c->nao_tot, c->nb, na, c->nao_max, c->d_ao_start, c->d_aux_start,
       c->d_naux, c->n_atoms, w->Y32);
   bse_prof_end(c, BSE_KP_HALF);
+  w->shifted = c->qmQ != 0;
+  if (w->shifted) {
+    const size_t ny = (size_t)c->nk * c->nao_max * c->nb * na, nckq = (size_t)c->nk * c->nao_tot * c->nb;
+    if (!w->Y32q && (!alloc((void **)&w->Y32q, ny * sizeof(float2)) ||
+                     !alloc((void **)&w->ckq, nckq * sizeof(double2)) ||
+                     !alloc((void **)&w->ck32q, nckq * sizeof(float2)) ||
+                     !alloc((void **)&w->eqpq, (size_t)c->nk * c->nb * sizeof(double))))
+      return bse_fail(c, BSE_ENOMEM, "finite momentum: relabelled per-k tables do not fit");
+    k_shift_tables<<<c->n_sm * 8, 256, 0, c->stream>>>(w->Y32, c->ck, c->eqp, c->nao_max, c->nao_tot, c->nb, c->nv,
+                                                        na, c->mesh[0], c->mesh[1], c->mesh[2], c->qmQ, w->Y32q,
+                                                        w->ckq, w->ck32q, w->eqpq);
+    bse_count_launch();
+  }
   k_exchange_X32<<<dim3((na + 127) / 128, c->nk), 128, 0, c->stream>>>(
-      w->Y32, w->ck32, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao,
-      c->dim, w->kmem, w->np, w->X32, w->Xp);
+      w->shifted ? w->Y32q : w->Y32, w->shifted ? w->ck32q : w->ck32, c->nao_tot, c->nb, c->nv, c->nc, na,
+      c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->dim, w->kmem, w->np, w->X32, w->Xp);
+  const long long nn = (long long)na * na;
+  k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->V0c, nn, w->V032);
   dim3 g((na + 63) / 64, (unsigned)((c->dim + 63) / 64));
   if (g.y > 65535) return bse_fail(c, BSE_EINVAL, "exchange factors: dim too large for the P grid");
-  k_xv0_pieces<<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
-  bse_count_launch(5);
+  if (c->vx_from_R)
+    k_xv0_pieces<true><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
+  else
+    k_xv0_pieces<false><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
+  bse_count_launch(6);
   c->y64_valid = false;
   return bse_check_launch(c, "split project");
 }
@@ -960,7 +1027,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
   SplitWS *w = ws(c);
   float2 *H = (float2 *)Hv;
   const int na = c->naux_tot;
-  // exchange: H = alpha/N_k (X V0) conj(X)^T  -- writes every element
+  // exchange: H = alpha/N_k (X V) conj(X)^T  -- writes every element
   {
     tcg::Args a{};
     a.rows = (int)c->dim;
@@ -991,7 +1058,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
       bse_prof_begin(c, BSE_KP_PROJECT);
       if (!fast_pair_kernels(c, w, q0, nq, H, true))
-        k_proj32<<<grid, 128, sm, c->stream>>>(w->Y32, c->ck, c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+        k_proj32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
                                                c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
                                                c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
       bse_prof_end(c, BSE_KP_PROJECT);
@@ -1022,7 +1089,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       size_t sm = sizeof(float2) * (c->nv * c->nv + c->nc * c->nc) * G2CH;
       bse_prof_begin(c, BSE_KP_G2);
       if (!fast_pair_kernels(c, w, q0, nq, H, false))
-        k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, c->eqp, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+        k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->nv, c->nc, na, c->mesh[0], c->mesh[1],
                                               c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
       bse_prof_end(c, BSE_KP_G2);
       bse_count_launch();

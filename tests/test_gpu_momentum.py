@@ -15,10 +15,10 @@ from test_gpu_fp64 import RAGGED, REL
 pytestmark = pytest.mark.gpu
 
 
-def _gpu_HQ(inp, Q, alpha=2.0, with_V=True):
+def _gpu_HQ(inp, Q, alpha=2.0, with_V=True, precision="fp64"):
     import torch
     from paper_2607_05853_b300.api import BSE
-    b = BSE.from_inputs(inp, precision="fp64", alpha=alpha)
+    b = BSE.from_inputs(inp, precision=precision, alpha=alpha)
     d = to_dev(inp)
     VR = torch.from_numpy(np.ascontiguousarray(inp["V_R"], np.float64)).cuda() if with_V else None
     b.set_momentum(Q, VR)
@@ -46,6 +46,23 @@ def test_finite_Q_hamiltonian_matches_oracle(name, Q):
     scale = np.abs(ref).max()
     assert np.abs(H - ref).max() <= REL * scale
     assert np.abs(H - H.conj().T).max() <= 1e-13 * scale
+
+
+# split precisions: the bound of the Q = 0 split tests (4e-6 x max|H| for bf16x3 and
+# bf16x2, 1e-4 for bf16x1); Q enters only through indices and the FP32 complex V
+SPLIT_TOL = {"bf16x3": 4e-6, "bf16x2": 4e-6, "bf16x1": 1e-4}
+
+
+@pytest.mark.parametrize("prec,name,Q", [("bf16x3", "cfg0", (1, 1, 0)), ("bf16x3", "cfg0", (2, 2, 2)),
+                                         ("bf16x2", "ragged", (1, 1, 3)), ("bf16x3", "two_d", (1, 2, 0)),
+                                         ("bf16x1", "cfg0", (3, 0, 1))])
+def test_finite_Q_split_matches_oracle(prec, name, Q):
+    inp = _inputs(name)
+    ref = O.BSEOracle(inp, Q=Q).hamiltonian()
+    b, d, H = _gpu_HQ(inp, Q, precision=prec)
+    H = H.cpu().numpy().astype(np.complex128)
+    scale = np.abs(ref).max()
+    assert np.abs(H - ref).max() <= SPLIT_TOL[prec] * scale
 
 
 def test_finite_Q_triplet_without_V_R():
@@ -118,9 +135,6 @@ def test_finite_Q_error_paths():
     with pytest.raises(BseError):
         b.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
     b.sync()
-    s = BSE.from_inputs(inp, precision="bf16x3")
-    with pytest.raises(BseError):            # split precisions: Q = 0 only
-        s.set_momentum((1, 0, 0), VR)
 
 
 def test_exciton_dispersion_monolayer_timing():

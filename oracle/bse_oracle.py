@@ -22,6 +22,15 @@ What it computes, and where each step comes from in the paper (arXiv 2607.05853)
 * the windowed absorption integral I = int_lo^hi eps2(omega) domega (eps2 as above) and
   its seed Gamma with dI = tr(Gamma dH), by the Daleckii-Krein formula for the derivative
   of a matrix function on the full eigendecomposition.
+* full BSE (§II.C): the coupling block B_{ai k1, bj k2} = alpha (a k1*, i k1|V|b k2*, j k2)
+  - (b k2*, i k1|W|a k1*, j k2) with both kernels in the LRI form of Eq. W_LRI
+  ((1/N_k) C~ V(0) C~ and (1/N_k) C~^mu_{b k2, i k1} W(k1-k2) C~^nu_{a k1, j k2}); the
+  Hamiltonian [[A, B], [-B*, -A*]]; its paired solutions +-Omega with right eigenvectors
+  (X, Y), normalised X^dagger X - Y^dagger Y = 1, found by the structure-preserving route
+  (the Hermitian positive definite M = [[A, B], [B*, A*]] made real by a unitary change of
+  basis, its Cholesky factor L, and the Hermitian eigenproblem of L^T K L, K the image of
+  diag(1, -1)); and eps2 with the Y term (Eq. full_BSE_epsilon2): the amplitude
+  sum d X - conj(d) Y, since <ak|v|ik> = conj(<ik|v|ak>) and E_i - E_a = -(E_a - E_i).
 * finite exciton momentum Q (the q != 0 extension the paper names as future work, §V):
   the pair (k, i, a) holds the valence band i at k and the conduction band a at k + Q, so
   every conduction coefficient, LRI coefficient and energy of the pair is taken at k + Q.
@@ -49,6 +58,7 @@ __all__ = [
     "interp_W", "lri_C_k", "ks_lri", "BSEOracle", "eps2_exact", "haydock_coeffs",
     "haydock_eps2", "lowest_excitons", "spectrum_prefactor", "binding_energy",
     "adjoint_seed_lowest", "grad_from_seed", "window_weight", "window_integral", "window_seed_exact", "offset_average_eps2", "interp_V",
+    "full_hamiltonian", "full_bse_pairs", "eps2_full_exact",
 ]
 
 TWO_PI = 2.0 * np.pi
@@ -189,6 +199,36 @@ class BSEOracle:
             blk = blk + np.diag(de)
         return blk
 
+    # -- coupling block of the full BSE (§II.C) -------------------------------------------
+    def coupling_exchange(self, ik1, ik2):
+        """(a k1*, i k1|V|b k2*, j k2) as [i, a, j, b]: C~_{a k1, i k1} V(0) C~_{b k2, j k2} / N_k."""
+        X1, X2 = self.X_exch_left(ik1), self.X_exch_left(ik2)          # [mu, a, i], [nu, b, j]
+        return np.einsum("uai,uv,vbj->iajb", X1, self.V_exch, X2, optimize=True) / self.nk
+
+    def coupling_direct(self, ik1, ik2):
+        """(b k2*, i k1|W|a k1*, j k2) as [i, a, j, b]: C~_{b k2, i k1} W(k1-k2) C~_{a k1, j k2} / N_k."""
+        Wq = self.W_q(self.q_index(ik1, ik2))
+        M1 = ks_lri(self._cc(ik2), self._cv(ik1), self.C_k(ik1), self.C_mk(ik2))   # [mu, b, i]
+        M2 = ks_lri(self._cc(ik1), self._cv(ik2), self.C_k(ik2), self.C_mk(ik1))   # [nu, a, j]
+        return np.einsum("ubi,uv,vaj->iajb", M1, Wq, M2, optimize=True) / self.nk
+
+    def coupling_block(self, ik1, ik2):
+        blk = -self.coupling_direct(ik1, ik2)
+        if self.alpha != 0.0:
+            blk = blk + self.alpha * self.coupling_exchange(ik1, ik2)
+        return blk.reshape(self.nvc, self.nvc)
+
+    def coupling(self):
+        """B of Eq. Hamiltonian, [dim, dim] (rows (k1, i, a), columns (k2, j, b)); Q = 0 only."""
+        if self.finite_Q:
+            raise ValueError("coupling: the full BSE is built at Q = 0")
+        B = np.empty((self.dim, self.dim), np.complex128)
+        n = self.nvc
+        for k1 in range(self.nk):
+            for k2 in range(self.nk):
+                B[k1 * n:(k1 + 1) * n, k2 * n:(k2 + 1) * n] = self.coupling_block(k1, k2)
+        return B
+
     def hamiltonian(self):
         H = np.empty((self.dim, self.dim), np.complex128)
         n = self.nvc
@@ -209,6 +249,50 @@ class BSEOracle:
 
     def prefactor(self):
         return spectrum_prefactor(self.nk, float(self.inp["volume"]))
+
+
+def full_hamiltonian(A, B):
+    """The full BSE matrix [[A, B], [-B*, -A*]] (§II.C)."""
+    return np.block([[A, B], [-np.conj(B), -np.conj(A)]])
+
+
+def full_bse_pairs(A, B):
+    """Positive solutions Omega_S of the full BSE with right eigenvectors (X_S, Y_S) normalised
+    X^dagger X - Y^dagger Y = 1 (the paired formulation of §II.C).
+
+    M = [[A, B], [B*, A*]] is Hermitian positive definite for a stable excited state.  With
+    U = (1/sqrt 2) [[1, -i], [1, i]] (blocks of identities) U^dagger M U = M_r is real
+    symmetric and U^dagger diag(1, -1) U = K = [[0, -i], [i, 0]], so H = diag(1,-1) M becomes
+    K M_r.  With M_r = L L^T, the Hermitian matrix S = L^T K L has the eigenvalues of H; an
+    orthonormal eigenvector w of S gives z = L^-T w with z^T M_r z = 1 and the eigenvector
+    Z = U z of H with Z^dagger M Z = 1; for Omega > 0, sqrt(Omega) Z = (X, Y) has
+    X^dagger X - Y^dagger Y = Z^dagger diag(1,-1) Z Omega = 1.
+    Returns (Omega [n] ascending, X [dim, n], Y [dim, n])."""
+    n = A.shape[0]
+    I = np.eye(n)
+    M = np.block([[A, B], [np.conj(B), np.conj(A)]])
+    U = np.block([[I, -1j * I], [I, 1j * I]]) / np.sqrt(2.0)
+    Mr = U.conj().T @ M @ U
+    if np.abs(Mr.imag).max() > 1e-10 * max(np.abs(Mr).max(), 1e-300):
+        raise ValueError("full_bse_pairs: [[A, B], [B*, A*]] lacks the expected structure")
+    L = np.linalg.cholesky(0.5 * (Mr.real + Mr.real.T))
+    K = np.block([[np.zeros((n, n)), -1j * I], [1j * I, np.zeros((n, n))]])
+    S = L.T @ K @ L
+    lam, Wv = np.linalg.eigh(0.5 * (S + S.conj().T))
+    pos = lam > 0
+    z = np.linalg.solve(L.T, Wv[:, pos])
+    Z = (U @ z) * np.sqrt(lam[pos])[None, :]
+    return lam[pos], Z[:n], Z[n:]
+
+
+def eps2_full_exact(A, B, d, omega, eta, pref):
+    """Full-BSE eps2 (Eq. full_BSE_epsilon2) with a Lorentzian of half width eta:
+    pref sum_S |sum_r d_r X_rS - conj(d_r) Y_rS|^2 L(omega - Omega_S), per polarisation summed."""
+    w, X, Y = full_bse_pairs(A, B)
+    d = np.atleast_2d(np.asarray(d))
+    osc = np.abs(d @ X - np.conj(d) @ Y) ** 2                              # [pol, S]
+    L = (eta / np.pi) / ((np.asarray(omega)[:, None] - w[None, :]) ** 2 + eta ** 2)
+    return pref * (L @ osc.sum(axis=0))
 
 
 def spectrum_prefactor(nk, volume):

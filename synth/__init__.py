@@ -6,6 +6,7 @@ Coulomb matrix at q=0 and velocity matrix elements). It holds none of the method
 arithmetic (no W interpolation to the dense mesh, no band-pair projection, no kernel
 contraction, no spectrum). Both the FP64 oracle and the CUDA path consume its output.
 """
-from .crystal import CrystalSpec, config_spec, make_inputs, batched_specs, kmesh_frac, kmesh_index
+from .crystal import CrystalSpec, config_spec, make_inputs, batched_specs, full_bse_spec, kmesh_frac, kmesh_index
 
-__all__ = ["CrystalSpec", "config_spec", "make_inputs", "batched_specs", "kmesh_frac", "kmesh_index"]
+__all__ = ["CrystalSpec", "config_spec", "make_inputs", "batched_specs", "full_bse_spec", "kmesh_frac",
+           "kmesh_index"]

@@ -112,6 +112,17 @@ def scaled_spec(base: CrystalSpec, **kw) -> CrystalSpec:
     return dataclasses.replace(base, **kw)
 
 
+def full_bse_spec(base: CrystalSpec) -> CrystalSpec:
+    """The same crystal with the screened-interaction scale halved, for full-BSE workloads.
+
+    The random band coefficients give conduction-valence products LRI coefficients as large
+    as valence-valence ones, so the direct part of the coupling block is as large as that
+    of the resonant block; at the calibrated s_W the matrix [[A, B], [B*, A*]] of config 0 is
+    then indefinite (an unstable full BSE with complex excitation energies), at s_W / 2 it is
+    positive definite with its lowest eigenvalue above 3 eV."""
+    return dataclasses.replace(base, name=base.name + "-fullbse", s_W=base.s_W * 0.5)
+
+
 def batched_specs(n: int = 16, seed: int = 20260003) -> list:
     """Config 3: n seeded crystals of uneven size (1-8 atoms, 9-13 NAOs/atom, 50-100
     ABFs/atom, dense meshes 6^3..10^3, Nv,Nc in {2,4,6}); coarse mesh ceil(dense/2)."""

@@ -605,3 +605,117 @@ def test_finite_Q_gradient_matches_central_differences():
             d["e_qp"][k, n] += sgn * h
             vals.append(np.linalg.eigvalsh(O.BSEOracle(d, Q=Q).hamiltonian())[0])
         assert abs((vals[0] - vals[1]) / (2 * h) - de[k, n]) <= 1e-6, (k, n)
+
+
+# ---------------------------------------------------------------- f1: full BSE (coupling block B)
+def test_coupling_kernels_match_realspace_brute_force():
+    """Both kernels of B (Eq. Hamiltonian) against the real-space lattice sums:
+    (a k1*, i k1|V|b k2*, j k2) and (b k2*, i k1|W|a k1*, j k2)."""
+    spec = tiny_spec()
+    inp = make_inputs(spec)
+    rng = np.random.default_rng(6)
+    RV = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, -1]])
+    Vbar = rng.standard_normal((len(RV), spec.n_aux, spec.n_aux))
+    inp["V0"] = Vbar.sum(axis=0)
+    orc = O.BSEOracle(inp)
+    kf, nk, mesh, nv, c = orc.kfrac, orc.nk, spec.dense, spec.nv, inp["c_k"]
+    for (k1, k2) in [(0, 0), (1, 4), (5, 2)]:
+        D = orc.coupling_direct(k1, k2)
+        X = orc.coupling_exchange(k1, k2)
+        for (i, a, j, b) in [(0, 0, 0, 0), (1, 0, 0, 1), (0, 1, 1, 0)]:
+            p1 = (c[k2][:, nv + b], kf[k2], c[k1][:, i], kf[k1])
+            p2 = (c[k1][:, nv + a], kf[k1], c[k2][:, j], kf[k2])
+            bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
+            assert abs(bd - D[i, a, j, b]) <= 1e-12 * max(1.0, abs(bd)), (k1, k2, i, a, j, b)
+            q1 = (c[k1][:, nv + a], kf[k1], c[k1][:, i], kf[k1])
+            q2 = (c[k2][:, nv + b], kf[k2], c[k2][:, j], kf[k2])
+            bx = _brute_kernel(inp, kf, nk, mesh, q1, q2, RV, np.ones(len(RV)), Vbar)
+            assert abs(bx - X[i, a, j, b]) <= 1e-12 * max(1.0, abs(bx)), (k1, k2, i, a, j, b)
+
+
+@pytest.fixture(scope="module")
+def full0():
+    from synth import full_bse_spec
+    inp = make_inputs(full_bse_spec(config_spec(0)))
+    orc = O.BSEOracle(inp)
+    return inp, orc, orc.hamiltonian(), orc.coupling(), orc.dipoles()
+
+
+def test_coupling_block_is_symmetric(full0):
+    """The paper states B = B^T (§II.C)."""
+    _, _, A, B, _ = full0
+    assert np.abs(B - B.T).max() <= 1e-13 * np.abs(B).max()
+
+
+def test_full_bse_paired_solutions(full0):
+    """+-Omega pairs (§II.C): the eigenvalues of [[A, B], [-B*, -A*]] (LAPACK geev) are the
+    returned Omega and their negatives; (X, Y) are right eigenvectors with
+    X^dagger X - Y^dagger Y = 1 and [X^dagger, -Y^dagger] left eigenvectors."""
+    _, _, A, B, _ = full0
+    n = A.shape[0]
+    w, X, Y = O.full_bse_pairs(A, B)
+    H = O.full_hamiltonian(A, B)
+    ev = np.sort(np.linalg.eigvals(H).real)
+    assert np.abs(ev[n:] - w).max() <= 1e-10 and np.abs(ev[:n][::-1] + w).max() <= 1e-10
+    Z = np.vstack([X, Y])
+    assert np.abs(H @ Z - Z * w).max() <= 1e-11
+    assert np.abs(X.conj().T @ X - Y.conj().T @ Y - np.eye(n)).max() <= 1e-12
+    ZL = np.hstack([X.conj().T, -Y.conj().T])
+    assert np.abs(ZL @ H - w[:, None] * ZL).max() <= 1e-11
+
+
+def test_full_bse_sum_rule(full0):
+    """sum_S Omega_S |d X_S - conj(d) Y_S|^2 = Re(d^T A conj(d) + d^T B d): the squared norm of
+    (conj d, d) in the metric [[A, B], [B*, A*]], spread over the +-Omega pairs.  Fixes the
+    sign of the Y term and the X/Y normalisation without an eigensolver."""
+    _, _, A, B, d = full0
+    w, X, Y = O.full_bse_pairs(A, B)
+    osc = np.abs(d @ X - np.conj(d) @ Y) ** 2
+    lhs = (w[None, :] * osc).sum(axis=1)
+    rhs = np.real(np.einsum("pr,rs,ps->p", d, A, np.conj(d)) + np.einsum("pr,rs,ps->p", d, B, d))
+    assert np.allclose(lhs, rhs, rtol=1e-11)
+    bad = np.abs(d @ X + np.conj(d) @ Y) ** 2                                # Y sign slipped
+    assert not np.allclose((w[None, :] * bad).sum(axis=1), rhs, rtol=1e-6)
+
+
+def test_full_bse_two_level_closed_form():
+    """One pair: H = [[a, b], [-b*, -a]] has Omega = sqrt(a^2 - |b|^2), Y/X = (Omega - a)/b,
+    |X|^2 - |Y|^2 = 1; eps2 is one Lorentzian of weight |d X - d* Y|^2."""
+    a, b, d = 3.0, 0.7 - 0.4j, np.array([[0.3 + 0.8j]])
+    w, X, Y = O.full_bse_pairs(np.array([[a]], complex), np.array([[b]]))
+    Om = np.sqrt(a * a - abs(b) ** 2)
+    assert np.isclose(w[0], Om, rtol=1e-14)
+    assert np.isclose(Y[0, 0] / X[0, 0], (Om - a) / b, rtol=1e-12)
+    assert np.isclose(abs(X[0, 0]) ** 2 - abs(Y[0, 0]) ** 2, 1.0, rtol=1e-13)
+    x2 = 1.0 / (1.0 - abs((Om - a) / b) ** 2)
+    weight = x2 * abs(d[0, 0] - np.conj(d[0, 0]) * (Om - a) / b) ** 2
+    om = np.array([2.0, Om, 3.5])
+    ref = weight * (0.1 / np.pi) / ((om - Om) ** 2 + 0.01)
+    assert np.allclose(O.eps2_full_exact(np.array([[a]], complex), np.array([[b]]), d, om, 0.1, 1.0), ref,
+                       rtol=1e-12)
+
+
+def test_full_bse_without_coupling_is_tda(full0):
+    """B = 0: the full BSE reduces to the TDA (X = TDA eigenvectors, Y = 0)."""
+    _, orc, A, B, d = full0
+    om = np.linspace(0.0, 10.0, 201)
+    e_full = O.eps2_full_exact(A, np.zeros_like(B), d, om, 0.1, orc.prefactor())
+    e_tda = O.eps2_exact(A, d, om, 0.1, orc.prefactor())
+    assert np.abs(e_full - e_tda).max() <= 1e-12 * np.abs(e_tda).max()
+
+
+def test_full_bse_planted_coupling_mistake_is_caught(monkeypatch):
+    """A transposed conduction-valence pair in the direct part of B fails the brute force."""
+    inp = make_inputs(tiny_spec())
+    mod = O.bse_oracle
+    monkeypatch.setattr(mod.BSEOracle, "coupling_direct", lambda self, k1, k2: np.einsum(
+        "ubi,uv,vaj->iajb", mod.ks_lri(self._cc(k1), self._cv(k2), self.C_k(k2), self.C_mk(k1)),
+        self.W_q(self.q_index(k1, k2)),
+        mod.ks_lri(self._cc(k2), self._cv(k1), self.C_k(k1), self.C_mk(k2)), optimize=True) / self.nk)
+    orc = O.BSEOracle(inp)
+    kf, nk, mesh, nv, c = orc.kfrac, orc.nk, tuple(inp["dense"]), orc.nv, inp["c_k"]
+    k1, k2, (i, a, j, b) = 1, 4, (1, 0, 0, 1)
+    p1 = (c[k2][:, nv + b], kf[k2], c[k1][:, i], kf[k1])
+    p2 = (c[k1][:, nv + a], kf[k1], c[k2][:, j], kf[k2])
+    bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
+    assert abs(bd - orc.coupling_direct(k1, k2)[i, a, j, b]) > 1e-6 * abs(bd)

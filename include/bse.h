@@ -139,6 +139,41 @@ bse_status bse_project_pairs(bse_ctx *ctx, const double *C_R, const double *c_k,
  * split precisions.  Every element is written. */
 bse_status bse_assemble(bse_ctx *ctx, void *H);
 
+/* Full BSE (§II.C): the coupling block
+ *   B_{ai k1, bj k2} = alpha (a k1*, i k1|V|b k2*, j k2) - (b k2*, i k1|W|a k1*, j k2),
+ * both kernels in the LRI form of Eq. W_LRI: (1/N_k) C~_{a k1, i k1} V(0) C~_{b k2, j k2} and
+ * (1/N_k) C~_{b k2, i k1} W(k1 - k2) C~_{a k1, j k2}.  B is complex symmetric (B = B^T).
+ *  B : [dim][dim], rows and columns ordered as H's; complex128 for BSE_FP64.  Every element
+ *      is written.  Call after bse_project_pairs.  BSE_EINVAL at Q != 0 and, for now, for
+ *      the split precisions.  Workspace for the conduction-valence projections is allocated
+ *      on the first call. */
+bse_status bse_assemble_coupling(bse_ctx *ctx, void *B);
+
+/* Full-BSE spectrum (Eq. full_BSE_epsilon2, §II.C): for H = [[A, B], [-B*, -A*]] with
+ * positive solutions Omega_S, amplitudes (X_S, Y_S) normalised X^dagger X - Y^dagger Y = 1,
+ *   eps2(w) = prefactor sum_p sum_S |sum_r d_p,r X_rS - conj(d_p,r) Y_rS|^2 L_eta(w - Omega_S),
+ * d_p = conj(u[p]) (u from bse_dipole_vector), L_eta the Lorentzian of half width eta.
+ * Computed by a Lanczos recursion in the inner product of M = [[A, B], [B*, A*]] from the
+ * start vector (u, conj u) and a Gauss quadrature of its tridiagonal (exact when n_steps
+ * reaches an invariant subspace, e.g. n_steps = 2 dim); an odd recursion length is cut to
+ * the even one below it.
+ *  A, B : [dim][dim] from bse_assemble and bse_assemble_coupling (complex128 for BSE_FP64,
+ *         complex64 otherwise), read only.
+ *  u    : [n_pol][dim] complex128; n_pol 1..3; 2 <= n_steps <= 2 dim; omega [n_w]; eps2 [n_w].
+ * M must be positive definite (a stable excited state): otherwise the recursion stops and
+ * bse_sync returns BSE_EDEVICE.  Krylov workspace (2 x n_pol x (n_steps+1) x 2 dim complex128)
+ * is allocated and freed on the stream per call. */
+bse_status bse_spectrum_full(bse_ctx *ctx, const void *A, const void *B, const double *u, int n_pol,
+                             int n_steps, const double *omega, int n_w, double eta, double prefactor,
+                             double *eps2);
+
+/* The n_eig lowest positive full-BSE excitation energies Omega_S (the paired eigenproblem of
+ * §II.C) by the same recursion from a seeded random start, with Lanczos residual bounds.
+ *  omega_out, resid_out : [n_eig] float64 (resid_out may be NULL); 2 n_eig <= n_steps <= 2 dim.
+ * Unconverged or missing values are NaN. */
+bse_status bse_lowest_full(bse_ctx *ctx, const void *A, const void *B, int n_eig, int n_steps,
+                           uint64_t seed, double *omega_out, double *resid_out);
+
 /* u_alpha,(k,i,a) = conj(vel[alpha][k][i][a] / (e_ks[k][nv+a] - e_ks[k][i])).
  *  vel : [3][N_k][nv][nc] complex128 <ik|v_alpha|ak>;  e_ks : [N_k][nv+nc] float64;
  *  u   : [3][dim] complex128 output.  A zero denominator gives BSE_EDEVICE at bse_sync. */

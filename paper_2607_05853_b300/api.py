@@ -141,6 +141,14 @@ class BSE:
         self._check(self._lib.bse_assemble(self._ctx, h), "bse_assemble")
         return H
 
+    def assemble_coupling(self, B: torch.Tensor | None = None) -> torch.Tensor:
+        """bse_assemble_coupling: the full-BSE coupling block B (same layout and dtype as H)."""
+        if B is None:
+            B = torch.empty((self.dim, self.dim), dtype=self.h_dtype, device="cuda")
+        b = _dev(B, self.h_dtype, "B", self.dim * self.dim)
+        self._check(self._lib.bse_assemble_coupling(self._ctx, b), "bse_assemble_coupling")
+        return B
+
     def dipole_vector(self, vel: torch.Tensor, e_ks: torch.Tensor, u: torch.Tensor | None = None) -> torch.Tensor:
         if u is None:
             u = torch.empty((3, self.dim), dtype=torch.complex128, device="cuda")
@@ -198,6 +206,31 @@ class BSE:
                                          om.data_ptr(), rs.data_ptr(), vec.data_ptr() if vectors else None),
                     "bse_lowest")
         return (om, rs, vec) if vectors else (om, rs)
+
+    def spectrum_full(self, A: torch.Tensor, B: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor,
+                      eta: float, prefactor: float, eps2: torch.Tensor | None = None) -> torch.Tensor:
+        """bse_spectrum_full: eps2 of the full BSE (X and Y amplitudes)."""
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        if eps2 is None:
+            eps2 = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+        a = _dev(A, self.h_dtype, "A", self.dim * self.dim)
+        b = _dev(B, self.h_dtype, "B", self.dim * self.dim)
+        uu = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        om = _dev(omega, torch.float64, "omega")
+        e = _dev(eps2, torch.float64, "eps2", omega.numel())
+        self._check(self._lib.bse_spectrum_full(self._ctx, a, b, uu, int(n_pol), int(n_steps), om, int(omega.numel()),
+                                                float(eta), float(prefactor), e), "bse_spectrum_full")
+        return eps2
+
+    def lowest_full(self, A: torch.Tensor, B: torch.Tensor, n_eig: int, n_steps: int, seed: int = 12345):
+        """bse_lowest_full: the lowest positive full-BSE excitation energies and residual bounds."""
+        om = torch.empty(n_eig, dtype=torch.float64, device="cuda")
+        rs = torch.empty(n_eig, dtype=torch.float64, device="cuda")
+        a = _dev(A, self.h_dtype, "A", self.dim * self.dim)
+        b = _dev(B, self.h_dtype, "B", self.dim * self.dim)
+        self._check(self._lib.bse_lowest_full(self._ctx, a, b, int(n_eig), int(n_steps), ctypes.c_uint64(seed),
+                                              om.data_ptr(), rs.data_ptr()), "bse_lowest_full")
+        return om, rs
 
     def adjoint_seed(self, vecs: torch.Tensor, g: torch.Tensor, Gamma: torch.Tensor | None = None):
         r = vecs.shape[0]

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libbse.so")
-SOURCES = ["bse_api.cu", "k_fp64.cu", "k_haydock.cu", "k_split.cu", "k_adjoint.cu", "bse_batch.cu"]
+SOURCES = ["bse_api.cu", "k_fp64.cu", "k_haydock.cu", "k_split.cu", "k_adjoint.cu", "bse_batch.cu", "k_fullbse.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-shared", "-Xcompiler", "-fPIC", "-diag-suppress", "177"]
 

@@ -96,7 +96,7 @@ static void release(bse_ctx *c) {
   c->pool.clear();
   void *ptrs[] = {c->d_qplus, c->d_qall, c->Aq, c->d_R_C, c->d_R_W, c->d_w_RW, c->d_aux_atom, c->d_ao_start, c->d_nao,
                   c->d_aux_start, c->d_naux, c->d_err, c->Wq, c->V0c, c->Y, c->ck,
-                  c->eqp, c->X, c->P, c->Mv, c->Mc, c->T};
+                  c->eqp, c->X, c->P, c->Mv, c->Mc, c->T, c->Bm1, c->Bt1, c->Bm2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   split_free(c);
@@ -363,6 +363,39 @@ bse_status bse_assemble(bse_ctx *c, void *H) {
   return BSE_OK;
 }
 
+bse_status bse_assemble_coupling(bse_ctx *c, void *B) {
+  if (!c) return BSE_EINVAL;
+  if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "assemble_coupling before project_pairs");
+  if (!B) return bse_fail(c, BSE_EINVAL, "assemble_coupling: null B");
+  if (c->qQ != 0) return bse_fail(c, BSE_EINVAL, "assemble_coupling: the full BSE is built at Q = 0");
+  if (c->precision != BSE_FP64) return split_assemble_coupling(c, B);
+  const int na = c->naux_tot;
+  const long long rows = (long long)c->nk * c->nvc;
+  if (!c->Bm1) {
+    const size_t per_q = (size_t)3 * rows * na * sizeof(double2);
+    const size_t budget = (size_t)768 << 20;
+    c->slab_cv = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
+    c->slab_cv = std::min(c->slab_cv, 65535);
+    const size_t n = (size_t)c->slab_cv * rows * na;
+    bse_status s = dalloc(c, &c->Bm1, n);
+    if (s == BSE_OK) s = dalloc(c, &c->Bt1, n);
+    if (s == BSE_OK) s = dalloc(c, &c->Bm2, n);
+    if (s != BSE_OK) return s;
+  }
+  const int nqp = (int)c->qplus.size();
+  for (int q0 = 0; q0 < nqp; q0 += c->slab_cv) {
+    const int nq = std::min(c->slab_cv, nqp - q0);
+    bse_status s = launch_project_cv_slab_fp64(c, q0, nq, c->d_qplus, c->Bm1, c->Bm2);
+    if (s != BSE_OK) return s;
+    s = launch_zgemm_fp64(c, (int)rows, na, na, c->Bm1, na, rows * na, c->Wq, na, (long long)na * na, c->Bt1, na,
+                          rows * na, nq, BSE_KP_G1, c->d_qplus + q0);
+    if (s != BSE_OK) return s;
+    s = launch_g2_coupling_fp64(c, q0, nq, c->Bt1, c->Bm2, (double2 *)B);
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
 bse_status bse_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double *u) {
   if (!c) return BSE_EINVAL;
   if (!vel || !e_ks || !u) return bse_fail(c, BSE_EINVAL, "dipole_vector: null argument");
@@ -402,6 +435,25 @@ bse_status bse_spectrum_static(bse_ctx *c, const void *H, const double *u, int n
       !std::isfinite(prefactor))
     return bse_fail(c, BSE_EINVAL, "spectrum_static: bad size or parameter");
   return run_spectrum_static(c, H, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
+}
+
+bse_status bse_spectrum_full(bse_ctx *c, const void *A, const void *B, const double *u, int n_pol, int n_steps,
+                             const double *omega, int n_w, double eta, double prefactor, double *eps2) {
+  if (!c) return BSE_EINVAL;
+  if (!A || !B || !u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum_full: null argument");
+  if (n_pol < 1 || n_pol > 3 || n_steps < 2 || n_steps > 2 * c->dim || n_w < 1 || !(eta > 0.0) ||
+      !std::isfinite(prefactor))
+    return bse_fail(c, BSE_EINVAL, "spectrum_full: bad size or parameter");
+  return run_spectrum_full(c, A, B, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2);
+}
+
+bse_status bse_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, int n_steps, uint64_t seed,
+                           double *omega_out, double *resid_out) {
+  if (!c) return BSE_EINVAL;
+  if (!A || !B || !omega_out) return bse_fail(c, BSE_EINVAL, "lowest_full: null argument");
+  if (n_steps < 2 || n_steps > 2 * c->dim || n_eig < 1 || 2 * n_eig > n_steps)
+    return bse_fail(c, BSE_EINVAL, "lowest_full: bad size");
+  return run_lowest_full(c, A, B, n_eig, n_steps, seed, omega_out, resid_out);
 }
 
 bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
@@ -446,6 +498,8 @@ bse_status bse_sync(bse_ctx *c) {
       cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
     return bse_fail(c, BSE_ECUDA, "sync: error word unreadable");
   if (w & BSE_DERR_TIMEOUT) return bse_fail(c, BSE_ETIMEOUT, "a bounded device wait gave up");
+  if (w & BSE_DERR_INDEFINITE)
+    return bse_fail(c, BSE_EDEVICE, "full BSE: [[A, B], [B*, A*]] is not positive definite (unstable excitations)");
   if (w) return bse_fail(c, BSE_EDEVICE, "device check failed, code " + std::to_string(w));
   return BSE_OK;
 }

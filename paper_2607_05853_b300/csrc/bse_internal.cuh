@@ -13,7 +13,8 @@ enum : int {
   BSE_DERR_BOUNDS = 1,      // an index check failed
   BSE_DERR_TIMEOUT = 2,     // a bounded mbarrier / flag wait gave up
   BSE_DERR_ZERO_DENOM = 4,  // E_c - E_v == 0 in a dipole denominator
-  BSE_DERR_TMEM = 8         // tensor-memory allocation returned an unusable address
+  BSE_DERR_TMEM = 8,        // tensor-memory allocation returned an unusable address
+  BSE_DERR_INDEFINITE = 16  // full BSE: [[A, B], [B*, A*]] is not positive definite
 };
 
 struct bse_ctx {
@@ -69,6 +70,9 @@ struct bse_ctx {
   int *d_qall = nullptr;   // 0 .. N_k-1 (every transfer, for the adjoint)
   double2 *Aq = nullptr;   // [nk][naux][naux] dL/dW(q) (adjoint workspace, allocated on first use)
   double2 *Mv = nullptr, *Mc = nullptr, *T = nullptr;  // [slab][nk][nv*nv | nc*nc][naux]
+  // coupling block (full BSE, FP64 path; allocated on first use): [slab_cv][nk][nc*nv][naux]
+  double2 *Bm1 = nullptr, *Bt1 = nullptr, *Bm2 = nullptr;
+  int slab_cv = 0;
 
   // split-precision workspace (tensor-core path)
   void *tc = nullptr;
@@ -101,6 +105,8 @@ bse_status launch_zgemm_fp64(bse_ctx *c, int M, int N, int K, const double2 *A, 
                              const int *bidx = nullptr);
 bse_status launch_project_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist);
 bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H);
+bse_status launch_project_cv_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist, double2 *M1, double2 *M2);
+bse_status launch_g2_coupling_fp64(bse_ctx *c, int q0, int nq, const double2 *T1, const double2 *M2, double2 *B);
 
 // spectrum (k_haydock.cu)
 bse_status run_dipole_vector(bse_ctx *c, const double *vel, const double *e_ks, double2 *u);
@@ -116,6 +122,15 @@ bse_status launch_zgemm_tn(bse_ctx *c, int M, int N, int K, const double2 *A, co
                            double alpha);
 bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
                            double w_hi, double eta, double pref, double *I_out, double2 *Gamma);
+// Eigen-decomposition of n_pol tridiagonals (a, b; order meff[p] <= mmax): eigenvalues in
+// dd[p][i], eigenvectors in Zt[p][i][k] (implicit QL, k_haydock.cu).
+bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
+                             int n_pol, double *dd, double *ee, double *Zt, double2 *rot);
+// full BSE (k_fullbse.cu)
+bse_status run_spectrum_full(bse_ctx *c, const void *A, const void *B, const double2 *u, int n_pol, int n_steps,
+                             const double *omega, int n_w, double eta, double pref, double *eps2);
+bse_status run_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, int n_steps, uint64_t seed,
+                           double *omega_out, double *resid_out);
 bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps,
                                const double *omega, int n_w, double eta, double pref, double *eps2,
                                double *ab);
@@ -124,6 +139,7 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
 bse_status split_setup(bse_ctx *c);
 bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
+bse_status split_assemble_coupling(bse_ctx *c, void *B);
 bse_status split_project(bse_ctx *c, const double *C_R);
 bse_status split_y_to_fp64(bse_ctx *c);
 bse_status split_autotune(bse_ctx *c, int *chosen);

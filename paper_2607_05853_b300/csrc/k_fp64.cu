@@ -10,6 +10,9 @@
 //   valence i at k and conduction a at k + Q)
 //  k_zgemm_nn        batched complex GEMM  C = A B (row-major), used for T = M_vv W(q)
 //                    and P = X V(0)
+//  k_project_cv_slab coupling block B (full BSE): M1(k1,q)^mu_bi = C~^mu_{b k2, i k1},
+//                    M2(k1,q)^mu_aj = C~^mu_{a k1, j k2}                    (§II.C, §III.A)
+//  k_g2_coupling     B block = (alpha X V X^T - T1 M2^T)/N_k with T1 = M1 W(q); B = B^T
 //  k_g2_write        H block = (alpha X V X^dagger - T M_cc^T)/N_k + diagonal, V = V(0) at
 //                    Q = 0 and sum_R w_R Vbar(R) e^{+iQ.R} otherwise
 //                    (Eq. Hamiltonian with the kernels of Eq. W_LRI)
@@ -220,6 +223,58 @@ __global__ void k_project_slab(const double2 *__restrict__ Y, const double2 *__r
   }
 }
 
+// Conduction-valence projections of one q-slab for the coupling block.  grid: x = nmu_chunks *
+// 2 nc, y = k1, z = q - q0.  Row r < nc -> M1 row b = r (columns i), else M2 row a = r - nc
+// (columns j).  With F as above:
+//   M1[b][i] = F(k2,k1)_{(nv+b) i} + conj(F(k1,k2)_{i (nv+b)}),
+//   M2[a][j] = F(k1,k2)_{(nv+a) j} + conj(F(k2,k1)_{j (nv+a)}).
+__global__ void k_project_cv_slab(const double2 *__restrict__ Y, const double2 *__restrict__ ck,
+                                  int nao_tot, int nb, int nv, int nc, int naux, int nao_max,
+                                  const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
+                                  const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
+                                  const int *__restrict__ qlist, double2 *__restrict__ M1,
+                                  double2 *__restrict__ M2) {
+  extern __shared__ double2 sc[];  // c1 [nao][nb], c2 [nao][nb]
+  const int nk = n1 * n2 * n3;
+  const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
+  const int row = blockIdx.x / nchunk;
+  const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
+  const int k1 = blockIdx.y, qq = blockIdx.z, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  double2 *c1 = sc, *c2 = sc + nao_tot * nb;
+  for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
+    c1[e] = ck[(long long)k1 * nao_tot * nb + e];
+    c2[e] = ck[(long long)k2 * nao_tot * nb + e];
+  }
+  __syncthreads();
+  if (mu >= naux) return;
+  const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+  const double2 *Y1 = Y + (long long)k1 * nao_max * nb * naux + mu;
+  const double2 *Y2 = Y + (long long)k2 * nao_max * nb * naux + mu;
+  const bool first = row < nc;
+  const int cb = nv + (first ? row : row - nc);            // the conduction band of this row
+  // first: bra conduction at k2, valence kets at k1; else bra conduction at k1, kets at k2
+  const double2 *cc = first ? c2 : c1, *cvv = first ? c1 : c2;
+  const double2 *Yv = first ? Y1 : Y2, *Yc = first ? Y2 : Y1;
+  double2 acc1[MAXB], acc2[MAXB];
+#pragma unroll
+  for (int j = 0; j < MAXB; j++) acc1[j] = acc2[j] = make_double2(0, 0);
+  for (int s = 0; s < na; s++) {
+    const double2 cs = cc[(ao0 + s) * nb + cb];
+    const double2 yc = Yc[((long long)s * nb + cb) * naux];
+#pragma unroll
+    for (int j = 0; j < MAXB; j++)
+      if (j < nv) {
+        acc1[j] = cadd(acc1[j], cmulc(cs, Yv[((long long)s * nb + j) * naux]));
+        acc2[j] = cadd(acc2[j], cmulc(cvv[(ao0 + s) * nb + j], yc));
+      }
+  }
+  double2 *out = (first ? M1 : M2) + ((((long long)qq * nk + k1) * nc + (cb - nv)) * nv) * naux + mu;
+#pragma unroll
+  for (int j = 0; j < MAXB; j++)
+    if (j < nv) out[(long long)j * naux] = cadd(acc1[j], conjd(acc2[j]));
+}
+
 // Batched row-major complex GEMM C = A B, 64x64 tiles, 4x4 complex outputs per thread.
 __global__ void __launch_bounds__(256) k_zgemm_nn(int M, int N, int K, const double2 *__restrict__ A,
                                                   int lda, long long sA, const double2 *__restrict__ B,
@@ -343,6 +398,71 @@ __global__ void __launch_bounds__(256) k_g2_write(const double2 *__restrict__ T,
   }
 }
 
+// One block per pair (k1, q): the nvc x nvc block of B at rows k1, columns k2 = k1 - q,
+// B[(k1,i,a),(k2,j,b)] = (alpha sum_mu P[(k1,i,a)] X[(k2,j,b)] - sum_nu T1[(b,i)] M2[(a,j)]) / N_k,
+// and its transpose at (k2, k1) (B is symmetric).
+__global__ void __launch_bounds__(256) k_g2_coupling(const double2 *__restrict__ T1, const double2 *__restrict__ M2,
+                                                     const double2 *__restrict__ P, const double2 *__restrict__ X,
+                                                     int nv, int nc, int naux, int n1, int n2, int n3, int q0,
+                                                     const int *__restrict__ qlist, double alpha, long long dim,
+                                                     double2 *__restrict__ B) {
+  extern __shared__ double2 sm[];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  const int nvc = nv * nc;
+  double2 *sT = sm, *sM = sT + nvc * G2CH, *sP = sM + nvc * G2CH, *sX = sP + nvc * G2CH;
+  const double2 *Tk = T1 + ((long long)qq * nk + k1) * nvc * naux;
+  const double2 *Mk = M2 + ((long long)qq * nk + k1) * nvc * naux;
+  const double2 *Pk = P + (long long)k1 * nvc * naux;
+  const double2 *Xk = X + (long long)k2 * nvc * naux;
+  const int nout = nvc * nvc;
+  constexpr int MAXO = 16;  // nvc <= 64 -> at most 16 outputs per thread
+  double2 ad[MAXO], ax[MAXO];
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) ad[t] = ax[t] = make_double2(0, 0);
+  for (int n0 = 0; n0 < naux; n0 += G2CH) {
+    const int nn = min(G2CH, naux - n0);
+    for (int e = threadIdx.x; e < 4 * nvc * G2CH; e += blockDim.x) {
+      const int r = e / G2CH, u = e % G2CH, part = r / nvc, rr = r % nvc;
+      double2 v = make_double2(0, 0);
+      if (u < nn) {
+        const double2 *src = part == 0 ? Tk : part == 1 ? Mk : part == 2 ? Pk : Xk;
+        v = src[(long long)rr * naux + n0 + u];
+      }
+      sm[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < MAXO; t++) {
+      const int o = threadIdx.x + t * blockDim.x;
+      if (o < nout) {
+        const int ia = o / nvc, jb = o % nvc;
+        const int i = ia / nc, a = ia % nc, j = jb / nc, b = jb % nc;
+        const double2 *pt = sT + (b * nv + i) * G2CH, *pm = sM + (a * nv + j) * G2CH;
+        const double2 *pp = sP + ia * G2CH, *px = sX + jb * G2CH;
+        for (int u = 0; u < nn; u++) {
+          ad[t] = cadd(ad[t], cmul(pt[u], pm[u]));
+          ax[t] = cadd(ax[t], cmul(pp[u], px[u]));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const double inv = 1.0 / nk;
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) {
+    const int o = threadIdx.x + t * blockDim.x;
+    if (o < nout) {
+      const int ia = o / nvc, jb = o % nvc;
+      const double2 h = make_double2((alpha * ax[t].x - ad[t].x) * inv, (alpha * ax[t].y - ad[t].y) * inv);
+      B[((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb] = h;
+      if (mirror) B[((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia] = h;
+    }
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------ launchers
@@ -426,4 +546,30 @@ bse_status launch_g2_write_fp64(bse_ctx *c, int q0, int nq, double2 *H) {
   bse_prof_end(c, BSE_KP_G2);
   bse_count_launch();
   return bse_check_launch(c, "g2_write");
+}
+
+bse_status launch_project_cv_slab_fp64(bse_ctx *c, int q0, int nq, const int *qlist, double2 *M1, double2 *M2) {
+  const int nchunk = (c->naux_tot + 127) / 128;
+  dim3 grid(nchunk * 2 * c->nc, c->nk, nq);
+  size_t sm = sizeof(double2) * 2 * c->nao_tot * c->nb;
+  if (sm > 48 * 1024) return bse_fail(c, BSE_EINVAL, "project: N_ao * (nv + nc) too large");
+  bse_prof_begin(c, BSE_KP_PROJECT);
+  k_project_cv_slab<<<grid, 128, sm, c->stream>>>(c->Y, c->ck, c->nao_tot, c->nb, c->nv, c->nc, c->naux_tot,
+                                                  c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
+                                                  c->mesh[1], c->mesh[2], q0, qlist, M1, M2);
+  bse_prof_end(c, BSE_KP_PROJECT);
+  bse_count_launch();
+  return bse_check_launch(c, "project_cv_slab");
+}
+
+bse_status launch_g2_coupling_fp64(bse_ctx *c, int q0, int nq, const double2 *T1, const double2 *M2, double2 *B) {
+  dim3 grid(c->nk, nq);
+  size_t sm = sizeof(double2) * 4 * c->nvc * G2CH;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_g2_coupling, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  bse_prof_begin(c, BSE_KP_G2);
+  k_g2_coupling<<<grid, 256, sm, c->stream>>>(T1, M2, c->P, c->X, c->nv, c->nc, c->naux_tot, c->mesh[0], c->mesh[1],
+                                              c->mesh[2], q0, c->d_qplus, c->alpha, c->dim, B);
+  bse_prof_end(c, BSE_KP_G2);
+  bse_count_launch();
+  return bse_check_launch(c, "g2_coupling");
 }

@@ -1617,6 +1617,13 @@ __global__ void __launch_bounds__(256) k_real_cgemm(const double *__restrict__ A
 
 }  // namespace
 
+bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
+                             int n_pol, double *dd, double *ee, double *Zt, double2 *rot) {
+  k_tridiag_ql<<<n_pol, 256, 0, c->stream>>>(a, b, ldab, meff, mmax, dd, ee, Zt, rot, c->d_err);
+  bse_count_launch();
+  return bse_check_launch(c, "tridiagonal QL");
+}
+
 bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
                            double w_hi, double eta, double pref, double *I_out, double2 *Gamma) {
   LanczosScratch s;

@@ -1100,6 +1100,10 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
   return BSE_OK;
 }
 
+bse_status split_assemble_coupling(bse_ctx *c, void *) {
+  return bse_fail(c, BSE_EINVAL, "assemble_coupling: the split precisions do not build B yet");
+}
+
 // ---- autotuner ----------------------------------------------------------------------------
 // Picks the N tile of the T = M_vv W(q) tensor-core GEMM by timing one q-slab launch per
 // candidate (values do not change the timing, so no inputs are needed), keeps the fastest,

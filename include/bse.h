@@ -143,10 +143,10 @@ bse_status bse_assemble(bse_ctx *ctx, void *H);
  *   B_{ai k1, bj k2} = alpha (a k1*, i k1|V|b k2*, j k2) - (b k2*, i k1|W|a k1*, j k2),
  * both kernels in the LRI form of Eq. W_LRI: (1/N_k) C~_{a k1, i k1} V(0) C~_{b k2, j k2} and
  * (1/N_k) C~_{b k2, i k1} W(k1 - k2) C~_{a k1, j k2}.  B is complex symmetric (B = B^T).
- *  B : [dim][dim], rows and columns ordered as H's; complex128 for BSE_FP64.  Every element
- *      is written.  Call after bse_project_pairs.  BSE_EINVAL at Q != 0 and, for now, for
- *      the split precisions.  Workspace for the conduction-valence projections is allocated
- *      on the first call. */
+ *  B : [dim][dim], rows and columns ordered as H's; complex128 for BSE_FP64, complex64 for
+ *      the split precisions (tensor-core contractions as in bse_assemble).  Every element is
+ *      written.  Call after bse_project_pairs.  BSE_EINVAL at Q != 0.  Workspace for the
+ *      conduction-valence projections is allocated on the first call. */
 bse_status bse_assemble_coupling(bse_ctx *ctx, void *B);
 
 /* Full-BSE spectrum (Eq. full_BSE_epsilon2, §II.C): for H = [[A, B], [-B*, -A*]] with

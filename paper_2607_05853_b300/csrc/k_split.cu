@@ -53,6 +53,13 @@ struct SplitWS {
   double *eqpq = nullptr;
   float2 *ck32 = nullptr;        // [nk][nao][nb]
   float2 *X32 = nullptr;         // [dim][naux]  exchange factors
+  // coupling block B of the full BSE (allocated on first use)
+  int nqB = 0, rowsB = 0;        // q per slab; rows (k1, b, i) of M1 per q
+  __nv_bfloat16 *ApB = nullptr;  // [nqB][PP][rowsB][kmem]  M1 pieces
+  __nv_bfloat16 *XpB = nullptr;  // [PP][dim][kmem]         pieces of X (no conjugate)
+  float2 *McB = nullptr;         // [nqB][nk][nc*nv][naux]   M2
+  float2 *TB = nullptr;          // [nqB][naux][rowsB]       T1 = M1 W(q)
+  CUtensorMap tmA_B, tmB_xB;
 };
 
 SplitWS *ws(bse_ctx *c) { return (SplitWS *)c->tc; }
@@ -486,7 +493,161 @@ __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict
   }
 }
 
+// Conduction-valence projections of one q-slab for the coupling block (FP32).  grid: x =
+// nmu_chunks * 2 nc, y = q - q0, z = k1.  Row r < nc: M1 row b = r, C~_{b k2, i k1} for the
+// valence i, written as bf16 pieces (GEMM operand A, row (k1, b, i)); else M2 row a = r - nc,
+// C~_{a k1, j k2}, FP32 (row (k1, a, j)).  F as in k_proj32.
+__global__ void k_proj_cv32(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot, int nb, int nv,
+                            int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
+                            const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1, int n2, int n3,
+                            int q0, const int *__restrict__ qlist, int np, int rowsB, int kmem,
+                            __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ M2) {
+  extern __shared__ float2 scf[];
+  const int nk = n1 * n2 * n3;
+  const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
+  const int row = blockIdx.x / nchunk;
+  const int mu = (blockIdx.x % nchunk) * blockDim.x + threadIdx.x;
+  const int qq = blockIdx.y, q = qlist[q0 + qq], k1 = blockIdx.z;
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  float2 *c1 = scf, *c2 = scf + nao_tot * nb;
+  for (int e = threadIdx.x; e < nao_tot * nb; e += blockDim.x) {
+    const double2 a = ck[(long long)k1 * nao_tot * nb + e], b = ck[(long long)k2 * nao_tot * nb + e];
+    c1[e] = make_float2((float)a.x, (float)a.y);
+    c2[e] = make_float2((float)b.x, (float)b.y);
+  }
+  __syncthreads();
+  if (mu >= naux) return;
+  const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+  const float2 *Y1 = Y + (long long)k1 * nao_max * nb * naux + mu;
+  const float2 *Y2 = Y + (long long)k2 * nao_max * nb * naux + mu;
+  const bool first = row < nc;
+  const int cb = nv + (first ? row : row - nc);
+  const float2 *cc = first ? c2 : c1, *cv = first ? c1 : c2;   // bra conduction, valence kets
+  const float2 *Yv = first ? Y1 : Y2, *Yc = first ? Y2 : Y1;
+  float2 acc1[MAXB], acc2[MAXB];
+#pragma unroll
+  for (int j = 0; j < MAXB; j++) acc1[j] = acc2[j] = make_float2(0.f, 0.f);
+  for (int s = 0; s < na; s++) {
+    const float2 cs = cc[(ao0 + s) * nb + cb];
+    const float2 yc = Yc[((long long)s * nb + cb) * naux];
+#pragma unroll
+    for (int j = 0; j < MAXB; j++)
+      if (j < nv) {
+        const float2 t1 = fcmulc(cs, Yv[((long long)s * nb + j) * naux]);
+        const float2 t2 = fcmulc(cv[(ao0 + s) * nb + j], yc);
+        acc1[j].x += t1.x; acc1[j].y += t1.y;
+        acc2[j].x += t2.x; acc2[j].y += t2.y;
+      }
+  }
+  if (first) {
+    const long long plane = (long long)rowsB * kmem;
+    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + ((long long)(k1 * nc + row) * nv) * kmem + mu;
+#pragma unroll
+    for (int j = 0; j < MAXB; j++)
+      if (j < nv) {
+        __nv_bfloat16 pr[3], pi[3];
+        split_pieces<float>(acc1[j].x + acc2[j].x, np, pr);
+        split_pieces<float>(acc1[j].y - acc2[j].y, np, pi);
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+          if (p >= np) break;
+          out[(2 * p) * plane + (long long)j * kmem] = pr[p];
+          out[(2 * p + 1) * plane + (long long)j * kmem] = pi[p];
+        }
+      }
+  } else {
+    float2 *out = M2 + ((((long long)qq * nk + k1) * nc + (row - nc)) * nv) * naux + mu;
+#pragma unroll
+    for (int j = 0; j < MAXB; j++)
+      if (j < nv) out[(long long)j * naux] = make_float2(acc1[j].x + acc2[j].x, acc1[j].y - acc2[j].y);
+  }
+}
+
+// dst[pp][r][k] pieces of src [rows][naux] (FP32 complex, no conjugate).
+__global__ void k_pieces_f32(const float2 *__restrict__ src, long long rows, int naux, int kmem, int np,
+                             __nv_bfloat16 *__restrict__ dst) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * naux) return;
+  const long long r = e / naux;
+  const int k = (int)(e % naux);
+  const float2 v = src[e];
+  __nv_bfloat16 pr[3], pi[3];
+  split_pieces<float>(v.x, np, pr);
+  split_pieces<float>(v.y, np, pi);
+  const long long plane = rows * kmem;
+#pragma unroll
+  for (int p = 0; p < 3; p++) {
+    if (p >= np) break;
+    dst[(2 * p) * plane + r * kmem + k] = pr[p];
+    dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
+  }
+}
+
 constexpr int G2CH = 32;
+
+// B block (k1, k2 = k1 - q) += -(1/N_k) sum_nu T1[(k1,b,i)][nu] M2[(k1,a,j)][nu], and the same
+// value at the transposed position (k2, k1) (B is symmetric).  T1 [q][nu][rowsB].
+__global__ void __launch_bounds__(256) k_g2c_32(const float2 *__restrict__ T, const float2 *__restrict__ M2, int nv,
+                                                int nc, int naux, int n1, int n2, int n3, int q0,
+                                                const int *__restrict__ qlist, int rowsB, long long dim,
+                                                float2 *__restrict__ B) {
+  extern __shared__ float2 sg[];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  const int nvc = nv * nc;
+  float2 *sT = sg, *sM = sT + nvc * G2CH;
+  const float2 *Tq = T + (long long)qq * rowsB * naux + (long long)k1 * nvc;
+  const float2 *Mk = M2 + ((long long)qq * nk + k1) * nvc * naux;
+  const int nout = nvc * nvc;
+  constexpr int MAXO = 16;
+  float2 ad[MAXO];
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) ad[t] = make_float2(0.f, 0.f);
+  for (int n0 = 0; n0 < naux; n0 += G2CH) {
+    const int nn = min(G2CH, naux - n0);
+    for (int e = threadIdx.x; e < 2 * nvc * G2CH; e += blockDim.x) {
+      const int r = e / G2CH, u = e % G2CH;
+      float2 v = make_float2(0.f, 0.f);
+      if (u < nn) v = r < nvc ? Tq[(long long)(n0 + u) * rowsB + r] : Mk[(long long)(r - nvc) * naux + n0 + u];
+      sg[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < MAXO; t++) {
+      const int o = threadIdx.x + t * blockDim.x;
+      if (o < nout) {
+        const int ia = o / nvc, jb = o % nvc;
+        const int i = ia / nc, a = ia % nc, j = jb / nc, b = jb % nc;
+        const float2 *pt = sT + (b * nv + i) * G2CH, *pm = sM + (a * nv + j) * G2CH;
+        float xr = ad[t].x, xi = ad[t].y;
+        for (int u = 0; u < nn; u++) {
+          xr = fmaf(pt[u].x, pm[u].x, fmaf(-pt[u].y, pm[u].y, xr));
+          xi = fmaf(pt[u].x, pm[u].y, fmaf(pt[u].y, pm[u].x, xi));
+        }
+        ad[t] = make_float2(xr, xi);
+      }
+    }
+    __syncthreads();
+  }
+  const float inv = 1.0f / nk;
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) {
+    const int o = threadIdx.x + t * blockDim.x;
+    if (o < nout) {
+      const int ia = o / nvc, jb = o % nvc;
+      float2 *hp = B + ((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb;
+      const float2 hx = *hp;
+      *hp = make_float2(fmaf(-inv, ad[t].x, hx.x), fmaf(-inv, ad[t].y, hx.y));
+      if (mirror) {
+        float2 *hm = B + ((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia;
+        const float2 mx = *hm;
+        *hm = make_float2(fmaf(-inv, ad[t].x, mx.x), fmaf(-inv, ad[t].y, mx.y));
+      }
+    }
+  }
+}
 
 // H block (k1, k2 = k1 - q) += -(1/N_k) sum_nu T[(k1,i,j)][nu] M_cc[(k1,a,b)][nu] (+ diagonal).
 __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
@@ -939,7 +1100,7 @@ void split_free(bse_ctx *c) {
   SplitWS *w = ws(c);
   if (!w) return;
   void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp, w->PHQ, w->PHK, w->WR32T, w->CR32, w->V032,
-                  w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq};
+                  w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq, w->ApB, w->XpB, w->McB, w->TB};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
@@ -1100,8 +1261,106 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
   return BSE_OK;
 }
 
-bse_status split_assemble_coupling(bse_ctx *c, void *) {
-  return bse_fail(c, BSE_EINVAL, "assemble_coupling: the split precisions do not build B yet");
+// Coupling block B (full BSE) in the split precisions: the exchange part alpha/N_k P X^T as one
+// tensor-core GEMM (operand B: pieces of X; B symmetric, so each element is stored at its
+// transposed position for coalesced stores) writing every element, then per q-slab the
+// conduction-valence projections, T1 = M1 W(q) on tensor cores and -T1 M2^T / N_k added by
+// k_g2c_32 (with the transposed copy).
+bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
+  SplitWS *w = ws(c);
+  float2 *B = (float2 *)Bv;
+  const int na = c->naux_tot;
+  if (c->nv > MAXB || c->nvc > 64) return bse_fail(c, BSE_EINVAL, "assemble_coupling: band window too wide");
+  if (!w->ApB) {
+    w->rowsB = c->nk * c->nc * c->nv;
+    const size_t per_q = (size_t)w->pp * w->rowsB * w->kmem * 2 + (size_t)c->nk * c->nvc * na * 8 +
+                         (size_t)w->rowsB * na * 8;
+    const size_t budget = (size_t)1536 << 20;
+    w->nqB = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
+    w->nqB = std::min(w->nqB, 65535);
+    if (c->mesh[2] > 1 && w->nqB >= c->mesh[2]) w->nqB = w->nqB / c->mesh[2] * c->mesh[2];
+    const size_t apb = (size_t)w->nqB * w->pp * w->rowsB * w->kmem * 2, xpb = (size_t)w->pp * c->dim * w->kmem * 2;
+    if (!alloc((void **)&w->ApB, apb) || !alloc((void **)&w->XpB, xpb) ||
+        !alloc((void **)&w->McB, (size_t)w->nqB * c->nk * c->nvc * na * 8) ||
+        !alloc((void **)&w->TB, (size_t)w->nqB * w->rowsB * na * 8))
+      return bse_fail(c, BSE_ENOMEM, "assemble_coupling: workspace allocation failed");
+    if (cudaMemsetAsync(w->ApB, 0, apb, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(w->XpB, 0, xpb, c->stream) != cudaSuccess)
+      return bse_fail(c, BSE_ECUDA, "assemble_coupling: workspace initialisation failed");
+    if (!make_map(&w->tmA_B, w->ApB, na, w->rowsB, (long long)w->pp * w->nqB, w->kmem, tcg::BM) ||
+        !make_map(&w->tmB_xB, w->XpB, na, c->dim, w->pp, w->kmem, TC_BN))
+      return bse_fail(c, BSE_ECUDA, "assemble_coupling: tensor map encoding failed");
+  }
+  {
+    const long long n = c->dim * na;
+    k_pieces_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(w->X32, c->dim, na, w->kmem, w->np, w->XpB);
+    bse_count_launch();
+    tcg::Args a{};
+    a.rows = (int)c->dim;
+    a.n_valid = (int)c->dim;
+    a.k_chunks = w->kchunks;
+    a.scale = (float)(c->alpha / c->nk);
+    a.out = B;
+    a.ld_row = 1;
+    a.ld_col = c->dim;
+    a.conj_out = 0;
+    a.out_bstride = 0;
+    a.b_batch_planes = 0;
+    a.b_base = 0;
+    a.qlist = nullptr;
+    a.err = c->d_err;
+    dim3 grid((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
+    bse_status s = launch_tc_np(c, w->np, TC_BN, w->tmA_x, w->tmB_xB, a, grid, BSE_KP_EXCH);
+    if (s != BSE_OK) return s;
+  }
+  const int nchunk = (na + 127) / 128;
+  const int nqp = (int)c->qplus.size();
+  for (int q0 = 0; q0 < nqp; q0 += w->nqB) {
+    const int nq = std::min(w->nqB, nqp - q0);
+    {
+      dim3 grid(nchunk * 2 * c->nc, nq, c->nk);
+      size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
+      bse_prof_begin(c, BSE_KP_PROJECT);
+      k_proj_cv32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na,
+                                                c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
+                                                c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem,
+                                                w->ApB, w->McB);
+      bse_prof_end(c, BSE_KP_PROJECT);
+      bse_count_launch();
+      bse_status s = bse_check_launch(c, "proj_cv32");
+      if (s != BSE_OK) return s;
+    }
+    {
+      tcg::Args a{};
+      a.rows = w->rowsB;
+      a.n_valid = na;
+      a.k_chunks = w->kchunks;
+      a.scale = 1.0f;
+      a.out = w->TB;
+      a.ld_row = 1;
+      a.ld_col = w->rowsB;
+      a.out_bstride = (long long)w->rowsB * na;
+      a.b_batch_planes = 1;
+      a.b_base = q0;
+      a.qlist = c->d_qplus;
+      a.err = c->d_err;
+      dim3 grid((unsigned)((na + w->bn_g1 - 1) / w->bn_g1), (unsigned)((w->rowsB + tcg::BM - 1) / tcg::BM), nq);
+      bse_status s = launch_tc_np(c, w->np, w->bn_g1, w->tmA_B, w->tmB_g1, a, grid, BSE_KP_G1);
+      if (s != BSE_OK) return s;
+    }
+    {
+      dim3 grid(c->nk, nq);
+      size_t sm = sizeof(float2) * 2 * c->nvc * G2CH;
+      bse_prof_begin(c, BSE_KP_G2);
+      k_g2c_32<<<grid, 256, sm, c->stream>>>(w->TB, w->McB, c->nv, c->nc, na, c->mesh[0], c->mesh[1], c->mesh[2],
+                                             q0, c->d_qplus, w->rowsB, c->dim, B);
+      bse_prof_end(c, BSE_KP_G2);
+      bse_count_launch();
+      bse_status s = bse_check_launch(c, "g2c_32");
+      if (s != BSE_OK) return s;
+    }
+  }
+  return BSE_OK;
 }
 
 // ---- autotuner ----------------------------------------------------------------------------

@@ -39,6 +39,37 @@ def test_coupling_block_matches_oracle(name):
     assert np.abs(B - B.T).max() <= 1e-13 * scale
 
 
+# split precisions: the Q = 0 split tests' bound (4e-6 of max|H| for bf16x3 and bf16x2,
+# 1e-4 for bf16x1), taken relative to max|A|: B's contractions have A's operand magnitudes
+SPLIT_TOL = {"bf16x3": 4e-6, "bf16x2": 4e-6, "bf16x1": 1e-4}
+
+
+@pytest.mark.parametrize("prec,name", [("bf16x3", "cfg0"), ("bf16x2", "ragged"), ("bf16x3", "wide"),
+                                       ("bf16x1", "cfg0"), ("bf16x3", "two_d")])
+def test_coupling_block_split_matches_oracle(prec, name):
+    inp = make_inputs(config_spec(0) if name == "cfg0" else RAGGED[name])
+    orc = O.BSEOracle(inp)
+    Aref, ref = orc.hamiltonian(), orc.coupling()
+    b, d, A, B = _gpu_AB(inp, precision=prec)
+    B = B.cpu().numpy().astype(np.complex128)
+    assert np.abs(B - ref).max() <= SPLIT_TOL[prec] * np.abs(Aref).max()
+    assert np.abs(B - B.T).max() <= SPLIT_TOL[prec] * np.abs(Aref).max()
+
+
+def test_full_spectrum_split_matches_oracle():
+    """bf16x3 A and B (complex64) with the FP64 recursion, full length."""
+    import torch
+    inp = make_inputs(full_bse_spec(config_spec(0)))
+    orc = O.BSEOracle(inp)
+    om = np.linspace(0.0, 12.0, 241)
+    ref = O.eps2_full_exact(orc.hamiltonian(), orc.coupling(), orc.dipoles(), om, ETA, orc.prefactor())
+    b, d, A, B = _gpu_AB(inp, precision="bf16x3")
+    u = b.dipole_vector(d["vel"], d["e_ks"])
+    eps = b.spectrum_full(A, B, u, 2 * b.dim, torch.from_numpy(om).cuda(), ETA, orc.prefactor())
+    b.sync()
+    assert np.linalg.norm(eps.cpu().numpy() - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("name", ["cfg0", "ragged", "two_d"])
 def test_full_spectrum_full_length_matches_oracle(name):
     """With 2 dim steps the Krylov space is the whole space: the quadrature is exact."""

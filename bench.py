@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
     ap.add_argument("--mesh", type=int, default=0, help="override the dense mesh N x N x N (profiling captures)")
+    ap.add_argument("--no-full-bse", action="store_true", help="skip the full-BSE (coupling block) report")
     ap.add_argument("--no-finite-q", action="store_true",
                     help="skip the finite exciton momentum H(Q) assembly report")
     ap.add_argument("--batch16", action="store_true",
@@ -419,6 +420,14 @@ def main():
             "note": "H(Q) = bse_set_momentum + interp_W + project_pairs + assemble (conduction bands at k+Q, "
                     "exchange with sum_R w_R Vbar(R) e^{+iQ.R}), Q in dense-mesh steps; outside the timed region"}
 
+    # ---- full BSE (outside the timed region): coupling block, paired spectrum, lowest Omega ----
+    if not args.no_full_bse:
+        from paper_2607_05853_b300.api import BseError
+        try:
+            extra["full_bse"] = full_bse_report(spec, args, dev, nsteps, omega, pk)
+        except BseError as e:          # e.g. an indefinite [[A, B], [B*, A*]]: report, keep the line
+            extra["full_bse"] = {"error": str(e)}
+
     clocks = clk.summary()
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -447,6 +456,73 @@ def main():
         print(json.dumps(result))
     if world > 1:
         dist.destroy_process_group()
+
+
+def full_bse_report(spec, args, dev, nsteps, omega, pk):
+    """Full BSE on the same geometry with the W scale halved (the synthetic inputs need it for
+    [[A, B], [B*, A*]] to be positive definite): A and B assembled, the 3-polarisation
+    full-BSE spectrum (Lanczos in the M inner product, nsteps steps) next to the TDA one, the
+    lowest paired excitations; per-kernel times from the library's event profile."""
+    import torch
+    from paper_2607_05853_b300.api import BSE
+    from synth import full_bse_spec, make_inputs
+    fspec = full_bse_spec(spec)
+    inp = make_inputs(fspec)
+    d = {k: torch.from_numpy(np.ascontiguousarray(inp[k], np.float64)).to(dev)
+         for k in ("W_R", "V0", "C_R", "e_qp", "e_ks")}
+    d.update({k: torch.from_numpy(np.ascontiguousarray(inp[k], np.complex128)).to(dev) for k in ("c_k", "vel")})
+    ctx = BSE.from_inputs(inp, precision=args.precision)
+    A = torch.empty((ctx.dim, ctx.dim), dtype=ctx.h_dtype, device=dev)
+    B = torch.empty_like(A)
+    pref = 4.0 * np.pi ** 2 / (3.0 * fspec.n_k * float(inp["volume"]))
+    st = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    eps_f = torch.empty(omega.numel(), dtype=torch.float64, device=dev)
+    eps_t = torch.empty_like(eps_f)
+    for rep in range(2):                    # the first pass warms up (allocations, tensor maps)
+        ctx.sync()
+        ev[0].record(st)
+        ctx.interp_W(d["W_R"], d["V0"])
+        ctx.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+        ctx.assemble(A)
+        u = ctx.dipole_vector(d["vel"], d["e_ks"])
+        ctx.profile(rep == 1)               # per-kernel times of B's assembly and the full spectrum only
+        ev[1].record(st)
+        ctx.assemble_coupling(B)
+        ev[2].record(st)
+        ctx.spectrum_full(A, B, u, nsteps, omega, args.eta, pref, eps_f)
+        ev[3].record(st)
+        if rep == 1:
+            prof_f = {k: ctx.profile_read(k) for k in ("matvec", "reorth", "project", "g1", "g2", "exch")}
+        ctx.profile(False)
+        ctx.spectrum(A, u, nsteps, omega, args.eta, pref, eps_t)
+        ev[4].record(st)
+        w_f, r_f = ctx.lowest_full(A, B, 10, 400)
+        ev[5].record(st)
+        ctx.sync()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(5)]
+    # the spectrum's product reads A and B once per step (both complex64 or complex128)
+    el = 16 if args.precision == "fp64" else 8
+    mv_ms, mv_n = prof_f["matvec"]
+    mv_launch = mv_ms / max(mv_n, 1)
+    alg = 2.0 * float(ctx.dim) ** 2 * el
+    achieved = alg / (mv_launch * 1e-3) / 1e9 if mv_n else None
+    out = {
+        "workload": fspec.name, "dim": ctx.dim, "w_scale": fspec.s_W, "haydock_steps": nsteps,
+        "per_k_and_A_ms": ms[0], "assemble_B_ms": ms[1], "spectrum_full_ms": ms[2], "spectrum_tda_ms": ms[3],
+        "lowest_full_ms": ms[4],
+        "lowest_full_eV": w_f.tolist(), "lowest_full_resid_eV": r_f.tolist(),
+        "eps2_full_vs_tda_rel_L2": (torch.linalg.norm(eps_f - eps_t) / torch.linalg.norm(eps_t)).item(),
+        "kernels_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof_f.items() if v[1]},
+        "product_roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": pk["hbm_gbs"],
+                             "frac": achieved / pk["hbm_gbs"] if achieved else None,
+                             "note": "k_mmv: algorithmic bytes = A and B each read once (2 dim^2 elements) "
+                                     "per launch, all polarisations at once"},
+    }
+    del A, B
+    ctx.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def ctx_slab_q(ctx, spec):

@@ -126,6 +126,13 @@ bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_po
 // dd[p][i], eigenvectors in Zt[p][i][k] (implicit QL, k_haydock.cu).
 bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
                              int n_pol, double *dd, double *ee, double *Zt, double2 *rot);
+// Half-read products W = Hm Z (np <= 3 vectors) of a complex64 Hermitian or complex symmetric
+// matrix through the TDA's tiled TMA kernel (k_haydock.cu).  halfmv_alloc leaves *out null
+// when the path does not apply (FP64 context or odd dim).
+struct HalfMV;
+bse_status halfmv_alloc(bse_ctx *c, HalfMV **out);
+void halfmv_release(bse_ctx *c, HalfMV *h);
+bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const float2 *Z, int np, double2 *W);
 // full BSE (k_fullbse.cu)
 bse_status run_spectrum_full(bse_ctx *c, const void *A, const void *B, const double2 *u, int n_pol, int n_steps,
                              const double *omega, int n_w, double eta, double pref, double *eps2);

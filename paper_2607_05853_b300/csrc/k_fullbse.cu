@@ -322,6 +322,33 @@ __global__ void __launch_bounds__(VB) k_fl_scale(const double2 *__restrict__ R, 
   }
 }
 
+// Operands of the half-read products: Z[0][p] = x, Z[1][p] = conj(y), Z[2][p] = y,
+// Z[3][p] = conj(x) for V[p] = (x, y), complex64.
+__global__ void k_fl_pack(const double2 *__restrict__ V, long long vs, long long dim, int n_pol,
+                          float2 *__restrict__ Z) {
+  const int p = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  const double2 x = V[p * vs + e], y = V[p * vs + dim + e];
+  const long long zs = (long long)n_pol * dim, o = (long long)p * dim + e;
+  Z[o] = make_float2((float)x.x, (float)x.y);
+  Z[zs + o] = make_float2((float)y.x, -(float)y.y);
+  Z[2 * zs + o] = make_float2((float)y.x, (float)y.y);
+  Z[3 * zs + o] = make_float2((float)x.x, -(float)x.y);
+}
+
+// S[p] = (A x + B y, conj(B conj(x) + A conj(y))) from W[k][p] = product k of k_fl_pack's order.
+__global__ void k_fl_combine(const double2 *__restrict__ W, long long dim, int n_pol, double2 *__restrict__ S,
+                             long long ss) {
+  const int p = blockIdx.y;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= dim) return;
+  const long long ws = (long long)n_pol * dim, o = (long long)p * dim + e;
+  const double2 ax = W[o], ay = W[ws + o], by = W[2 * ws + o], bx = W[3 * ws + o];
+  S[p * ss + e] = make_double2(ax.x + by.x, ax.y + by.y);
+  S[p * ss + dim + e] = make_double2(bx.x + ay.x, -(bx.y + ay.y));
+}
+
 __global__ void k_fl_even(const int *__restrict__ meff, int n_pol, int *__restrict__ meven) {
   const int p = threadIdx.x;
   if (p < n_pol) meven[p] = meff[p] & ~1;
@@ -380,6 +407,9 @@ __global__ void k_full_lowest(const double *__restrict__ dd, const double *__res
 }
 
 struct FullScratch {
+  HalfMV *hm = nullptr;    // half-read products (complex64 A, B of even order), else null
+  float2 *Z = nullptr;     // [4][n_pol][dim] product operands
+  double2 *W = nullptr;    // [4][n_pol][dim] products
   double2 *Q = nullptr, *P = nullptr, *R = nullptr, *S = nullptr, *coef = nullptr, *part = nullptr, *rot = nullptr;
   double *a = nullptr, *b = nullptr, *beta0 = nullptr, *dd = nullptr, *ee = nullptr, *Zt = nullptr;
   int *meff = nullptr, *meven = nullptr;
@@ -387,9 +417,12 @@ struct FullScratch {
 };
 
 void full_release(bse_ctx *c, FullScratch &s) {
-  void *ptrs[] = {s.Q, s.P, s.R, s.S, s.coef, s.part, s.rot, s.a, s.b, s.beta0, s.dd, s.ee, s.Zt, s.meff, s.meven};
+  void *ptrs[] = {s.Q, s.P, s.R, s.S, s.coef, s.part, s.rot, s.a, s.b, s.beta0, s.dd, s.ee, s.Zt, s.meff, s.meven,
+                  s.Z, s.W};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
+  halfmv_release(c, s.hm);
+  s.hm = nullptr;
 }
 
 bse_status full_alloc(bse_ctx *c, FullScratch &s, int n_pol, int n_steps) {
@@ -416,6 +449,13 @@ bse_status full_alloc(bse_ctx *c, FullScratch &s, int n_pol, int n_steps) {
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "full BSE: Krylov scratch allocation failed");
   }
+  bse_status r = halfmv_alloc(c, &s.hm);
+  if (r != BSE_OK) return r;
+  if (s.hm && (cudaMallocAsync((void **)&s.Z, sizeof(float2) * 4 * n_pol * c->dim, st) != cudaSuccess ||
+               cudaMallocAsync((void **)&s.W, sizeof(double2) * 4 * n_pol * c->dim, st) != cudaSuccess)) {
+    cudaGetLastError();
+    return bse_fail(c, BSE_ENOMEM, "full BSE: product scratch allocation failed");
+  }
   return BSE_OK;
 }
 
@@ -426,8 +466,25 @@ void launch_mmv(bse_ctx *c, const void *A, const void *B, const double2 *V, long
   k_mmv<T, NP, RPW><<<blocks, 256, 0, c->stream>>>((const T *)A, (const T *)B, c->dim, V, vs, S, 2 * c->dim);
 }
 
-// S [n_pol][2 dim] = M V, V[p] at V + p vs.
-void mmv(bse_ctx *c, int n_pol, const void *A, const void *B, const double2 *V, long long vs, double2 *S) {
+// S [n_pol][2 dim] = M V, V[p] at V + p vs.  Complex64 A, B of even order: four half-read
+// products through the TDA's tiled TMA kernel (A x, A conj(y) Hermitian; B y, B conj(x)
+// symmetric), each reading the upper-triangle tiles once for all polarisations, so A and B
+// are each read once per step; otherwise one full-read pass (k_mmv).
+bse_status mmv(bse_ctx *c, FullScratch &s, int n_pol, const void *A, const void *B, const double2 *V, long long vs,
+               double2 *S) {
+  if (s.hm) {
+    const long long dim = c->dim, zs = (long long)n_pol * dim;
+    const dim3 g((unsigned)((dim + 255) / 256), n_pol);
+    k_fl_pack<<<g, 256, 0, c->stream>>>(V, vs, dim, n_pol, s.Z);
+    bse_count_launch();
+    bse_status r = BSE_OK;
+    for (int k = 0; k < 4 && r == BSE_OK; k++)
+      r = halfmv_run(c, s.hm, k < 2 ? A : B, k >= 2, s.Z + k * zs, n_pol, s.W + k * zs);
+    if (r != BSE_OK) return r;
+    k_fl_combine<<<g, 256, 0, c->stream>>>(s.W, dim, n_pol, S, 2 * dim);
+    bse_count_launch();
+    return BSE_OK;
+  }
   const bool c64 = c->precision != BSE_FP64;
   bse_prof_begin(c, BSE_KP_MATVEC);
   if (c64) {
@@ -441,6 +498,7 @@ void mmv(bse_ctx *c, int n_pol, const void *A, const void *B, const double2 *V, 
   }
   bse_prof_end(c, BSE_KP_MATVEC);
   bse_count_launch();
+  return BSE_OK;
 }
 
 // The recursion; leaves a, b, beta0, meff in s and the even orders in s.meven.
@@ -460,12 +518,13 @@ bse_status full_lanczos(bse_ctx *c, FullScratch &s, const void *A, const void *B
     cudaStreamSynchronize(st);
   }
   k_fl_start<<<dim3((unsigned)((dim + 255) / 256), n_pol), 256, 0, st>>>(u, dim, seed, s.R, vs);
-  mmv(c, n_pol, A, B, s.R, vs, s.S);  // S = M v
+  bse_status r = mmv(c, s, n_pol, A, B, s.R, vs, s.S);  // S = M v
+  if (r != BSE_OK) return r;
   k_fl_dot_part<<<dim3(s.nblk, n_pol), VB, 0, st>>>(s.R, vs, s.S, vs, dim, 1.0, nullptr, 0, s.part, s.nblk);
   k_fl_norm0<<<dim3(gv, n_pol), VB, 0, st>>>(s.R, s.S, vs, dim, s.part, s.nblk, s.Q, s.P, qs, s.beta0, s.meff,
                                               c->d_err);
   bse_count_launch(3);
-  bse_status r = bse_check_launch(c, "full BSE start");
+  r = bse_check_launch(c, "full BSE start");
   if (r != BSE_OK) return r;
   for (int j = 0; j < n_steps; j++) {
     const double2 *pj = s.P + (long long)j * n2;
@@ -478,7 +537,8 @@ bse_status full_lanczos(bse_ctx *c, FullScratch &s, const void *A, const void *B
       k_fl_rupdate<<<dim3(ge, n_pol), VB, 0, st>>>(s.R, vs, dim, s.Q, qs, j, s.coef, ldab, s.meff);
     }
     bse_prof_end(c, BSE_KP_REORTH);
-    mmv(c, n_pol, A, B, s.R, vs, s.S);  // S = M r
+    r = mmv(c, s, n_pol, A, B, s.R, vs, s.S);  // S = M r
+    if (r != BSE_OK) return r;
     k_fl_dot_part<<<dim3(s.nblk, n_pol), VB, 0, st>>>(s.R, vs, s.S, vs, dim, 1.0, s.meff, j, s.part, s.nblk);
     k_fl_scale<<<dim3(gv, n_pol), VB, 0, st>>>(s.R, s.S, vs, dim, s.Q, s.P, qs, j, n_steps, s.b, ldab, s.meff,
                                                s.part, s.nblk, c->d_err);

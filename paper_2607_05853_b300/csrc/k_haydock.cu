@@ -377,7 +377,9 @@ struct HmvSmem {
   static constexpr int BYTES = 128 + MV_STAGES * MV_STAGE_BYTES + XB + 4 * USTR;
 };
 
-template <int NP>
+// SYM = true: H is complex symmetric (H^T = H) instead of Hermitian; the mirrored tile then
+// contributes H_t^T y, which only changes how the row vector y is parked for the column sums.
+template <int NP, bool SYM = false>
 __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
                                                          int nb, const int2 *__restrict__ tiles, int ntiles,
                                                          const float2 *__restrict__ Q32, long long qs, int j,
@@ -450,7 +452,8 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
     _Pragma("unroll") for (int k = 0; k < XPT; k++) {                                             \
       const int e = threadIdx.x + 128 * k;                                                        \
       if (e < NP * HT) {                                                                          \
-        yb[e] = make_float4(pre_r[k].x, -pre_r[k].x, pre_r[k].y, pre_r[k].y);                     \
+        yb[e] = SYM ? make_float4(pre_r[k].x, pre_r[k].x, -pre_r[k].y, pre_r[k].y)                \
+                    : make_float4(pre_r[k].x, -pre_r[k].x, pre_r[k].y, pre_r[k].y);               \
         xc[e] = pre_c[k];                                                                         \
       }                                                                                           \
     }                                                                                             \
@@ -509,7 +512,8 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
       __syncwarp();
       // with hp = (hr, hi) as loaded and hs = (hi, hr):
       //   h x       = hp (xr, xr) + hs (-xi, xi)
-      //   conj(h) y = hp (yr, -yr) + hs (yi, yi)
+      //   conj(h) y = hp (yr, -yr) + hs (yi, yi)      (Hermitian: the mirrored tile is H_t^dagger)
+      //   h y       = hp (yr, yr) + hs (-yi, yi)      (SYM: the mirrored tile is H_t^T)
       unsigned long long U[4][NP];
 #pragma unroll
       for (int rr = 0; rr < 4; rr++)
@@ -1616,6 +1620,89 @@ __global__ void __launch_bounds__(256) k_real_cgemm(const double *__restrict__ A
 }
 
 }  // namespace
+
+// ---- half-read products for other callers (full BSE) -------------------------------------
+struct HalfMV {
+  int nbt = 0, ntiles = 0;
+  int2 *tiles = nullptr;
+  float2 *part = nullptr;   // [nbt][nbt][HT][3]
+  int *ones = nullptr;      // [3] recursion lengths for the kernels' liveness test (all live)
+  double *apart = nullptr;  // [3][nbt] (unused alpha partials of the reduction)
+  double2 *Qdummy = nullptr;
+};
+
+bse_status halfmv_alloc(bse_ctx *c, HalfMV **out) {
+  *out = nullptr;
+  if (c->precision == BSE_FP64 || c->dim % 2) return BSE_OK;  // complex64 H of even order only
+  HalfMV *h = new HalfMV();
+  const long long dim = c->dim;
+  h->nbt = (int)((dim + HT - 1) / HT);
+  std::vector<int2> tl;
+  for (int bi = 0; bi < h->nbt; bi++)
+    for (int bj = bi; bj < h->nbt; bj++) tl.push_back(make_int2(bi, bj));
+  h->ntiles = (int)tl.size();
+  const int ones[3] = {1, 1, 1};
+  cudaStream_t st = c->stream;
+  if (cudaMallocAsync((void **)&h->part, sizeof(float2) * (size_t)h->nbt * h->nbt * HT * 3, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->tiles, sizeof(int2) * tl.size(), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->ones, sizeof(int) * 3, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->apart, sizeof(double) * 3 * h->nbt, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->Qdummy, sizeof(double2) * 3 * dim, st) != cudaSuccess ||
+      cudaMemcpyAsync(h->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(h->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(h->Qdummy, 0, sizeof(double2) * 3 * dim, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    halfmv_release(c, h);
+    return bse_fail(c, BSE_ENOMEM, "half-read product scratch allocation failed");
+  }
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_hmv_tma<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
+    cudaFuncSetAttribute(k_hmv_tma<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
+    cudaFuncSetAttribute(k_hmv_tma<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
+    cudaFuncSetAttribute(k_hmv_tma<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
+    cudaFuncSetAttribute(k_hmv_tma<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
+    cudaFuncSetAttribute(k_hmv_tma<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
+    attr = true;
+  }
+  *out = h;
+  return BSE_OK;
+}
+
+void halfmv_release(bse_ctx *c, HalfMV *h) {
+  if (!h) return;
+  void *ptrs[] = {h->part, h->tiles, h->ones, h->apart, h->Qdummy};
+  for (void *p : ptrs)
+    if (p) cudaFreeAsync(p, c->stream);
+  delete h;
+}
+
+// W[p] = Hm Z[p] (p < np <= 3) for a complex64 Hm, Hermitian (sym = false) or complex
+// symmetric (sym = true), reading only its upper-triangle 128 x 128 tiles.  Z [np][dim]
+// complex64, W [np][dim] complex128.
+bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const float2 *Z, int np, double2 *W) {
+  const long long dim = c->dim;
+  CUtensorMap tm;
+  if (!encode_rows_f32(&tm, Hm, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK))
+    return bse_fail(c, BSE_ECUDA, "half-read product: tensor map encoding failed");
+  cudaStream_t st = c->stream;
+  const int grid = std::min(h->ntiles, MV_CTAS * c->n_sm);
+  bse_prof_begin(c, BSE_KP_MATVEC);
+#define HALF_LAUNCH(NPV, SYMV)                                                                                 \
+  k_hmv_tma<NPV, SYMV><<<grid, 128, hmv_tma_smem<NPV>(), st>>>(tm, dim, h->nbt, h->tiles, h->ntiles, Z, dim, 0, \
+                                                             h->part, h->ones, c->d_err)
+  if (np == 1) { if (sym) HALF_LAUNCH(1, true); else HALF_LAUNCH(1, false); }
+  else if (np == 2) { if (sym) HALF_LAUNCH(2, true); else HALF_LAUNCH(2, false); }
+  else { if (sym) HALF_LAUNCH(3, true); else HALF_LAUNCH(3, false); }
+#undef HALF_LAUNCH
+  bse_prof_end(c, BSE_KP_MATVEC);
+  if (np == 1) k_hmv_reduce<1><<<h->nbt, 2 * HT * 1, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
+  else if (np == 2) k_hmv_reduce<2><<<h->nbt, 2 * HT * 2, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
+  else k_hmv_reduce<3><<<h->nbt, 2 * HT * 3, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
+  bse_count_launch(2);
+  return bse_check_launch(c, "half-read product");
+}
 
 bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
                              int n_pol, double *dd, double *ee, double *Zt, double2 *rot) {

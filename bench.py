@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--small", action="store_true", help="tiny workload (for profiling captures)")
     ap.add_argument("--mesh", type=int, default=0, help="override the dense mesh N x N x N (profiling captures)")
     ap.add_argument("--no-full-bse", action="store_true", help="skip the full-BSE (coupling block) report")
+    ap.add_argument("--full-bse-only", action="store_true",
+                    help="print only the full-BSE report (for profiling captures of its kernels)")
     ap.add_argument("--no-finite-q", action="store_true",
                     help="skip the finite exciton momentum H(Q) assembly report")
     ap.add_argument("--batch16", action="store_true",
@@ -213,8 +215,14 @@ def main():
     from synth import make_inputs
 
     spec = workload(args.small, args.mesh)
-    inp = make_inputs(spec)
     dev = torch.device("cuda", local)
+    if args.full_bse_only:
+        omega = torch.linspace(0.0, 10.0, args.n_omega, dtype=torch.float64, device=dev)
+        dim = spec.n_k * spec.nv * spec.nc
+        print(json.dumps({"full_bse": full_bse_report(spec, args, dev, min(args.haydock_steps, 2 * dim), omega,
+                                                      peaks())}))
+        return
+    inp = make_inputs(spec)
 
     def h2d(x, dt):
         return torch.from_numpy(np.ascontiguousarray(x, dt)).pin_memory()

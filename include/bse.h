@@ -159,7 +159,8 @@ bse_status bse_assemble_coupling(bse_ctx *ctx, void *B);
  * the even one below it.
  *  A, B : [dim][dim] from bse_assemble and bse_assemble_coupling (complex128 for BSE_FP64,
  *         complex64 otherwise), read only.
- *  u    : [n_pol][dim] complex128; n_pol 1..3; 2 <= n_steps <= 2 dim; omega [n_w]; eps2 [n_w].
+ *  u    : [n_pol][dim] complex128; n_pol 1..3; 2 <= n_steps <= min(2 dim, 6400); omega [n_w];
+ *         eps2 [n_w].
  * M must be positive definite (a stable excited state): otherwise the recursion stops and
  * bse_sync returns BSE_EDEVICE.  Krylov workspace (2 x n_pol x (n_steps+1) x 2 dim complex128)
  * is allocated and freed on the stream per call. */
@@ -169,7 +170,8 @@ bse_status bse_spectrum_full(bse_ctx *ctx, const void *A, const void *B, const d
 
 /* The n_eig lowest positive full-BSE excitation energies Omega_S (the paired eigenproblem of
  * §II.C) by the same recursion from a seeded random start, with Lanczos residual bounds.
- *  omega_out, resid_out : [n_eig] float64 (resid_out may be NULL); 2 n_eig <= n_steps <= 2 dim.
+ *  omega_out, resid_out : [n_eig] float64 (resid_out may be NULL);
+ *  2 n_eig <= n_steps <= min(2 dim, 6400).
  * Unconverged or missing values are NaN. */
 bse_status bse_lowest_full(bse_ctx *ctx, const void *A, const void *B, int n_eig, int n_steps,
                            uint64_t seed, double *omega_out, double *resid_out);

@@ -441,8 +441,8 @@ bse_status bse_spectrum_full(bse_ctx *c, const void *A, const void *B, const dou
                              const double *omega, int n_w, double eta, double prefactor, double *eps2) {
   if (!c) return BSE_EINVAL;
   if (!A || !B || !u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum_full: null argument");
-  if (n_pol < 1 || n_pol > 3 || n_steps < 2 || n_steps > 2 * c->dim || n_w < 1 || !(eta > 0.0) ||
-      !std::isfinite(prefactor))
+  if (n_pol < 1 || n_pol > 3 || n_steps < 2 || n_steps > 2 * c->dim || n_steps > BSE_FULL_MAX_STEPS || n_w < 1 ||
+      !(eta > 0.0) || !std::isfinite(prefactor))
     return bse_fail(c, BSE_EINVAL, "spectrum_full: bad size or parameter");
   return run_spectrum_full(c, A, B, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2);
 }
@@ -451,7 +451,7 @@ bse_status bse_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, 
                            double *omega_out, double *resid_out) {
   if (!c) return BSE_EINVAL;
   if (!A || !B || !omega_out) return bse_fail(c, BSE_EINVAL, "lowest_full: null argument");
-  if (n_steps < 2 || n_steps > 2 * c->dim || n_eig < 1 || 2 * n_eig > n_steps)
+  if (n_steps < 2 || n_steps > 2 * c->dim || n_steps > BSE_FULL_MAX_STEPS || n_eig < 1 || 2 * n_eig > n_steps)
     return bse_fail(c, BSE_EINVAL, "lowest_full: bad size");
   return run_lowest_full(c, A, B, n_eig, n_steps, seed, omega_out, resid_out);
 }

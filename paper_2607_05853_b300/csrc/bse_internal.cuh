@@ -122,10 +122,6 @@ bse_status launch_zgemm_tn(bse_ctx *c, int M, int N, int K, const double2 *A, co
                            double alpha);
 bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
                            double w_hi, double eta, double pref, double *I_out, double2 *Gamma);
-// Eigen-decomposition of n_pol tridiagonals (a, b; order meff[p] <= mmax): eigenvalues in
-// dd[p][i], eigenvectors in Zt[p][i][k] (implicit QL, k_haydock.cu).
-bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
-                             int n_pol, double *dd, double *ee, double *Zt, double2 *rot);
 // Half-read products W = Hm Z (np <= 3 vectors) of a complex64 Hermitian or complex symmetric
 // matrix through the TDA's tiled TMA kernel (k_haydock.cu).  halfmv_alloc leaves *out null
 // when the path does not apply (FP64 context or odd dim).
@@ -133,6 +129,14 @@ struct HalfMV;
 bse_status halfmv_alloc(bse_ctx *c, HalfMV **out);
 void halfmv_release(bse_ctx *c, HalfMV *h);
 bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const float2 *Z, int np, double2 *W);
+// FP32-projection reorthogonalisation pass (k_haydock.cu): coef_i = D32_i^H W,
+// W -= sum_{i<=j} coef_i U32_i; rpart holds [n_pol][ldp][reorth32_chunks(n)] partials.
+int reorth32_chunks(long long n);
+bse_status launch_reorth32_pass(bse_ctx *c, double2 *W, long long n, const float2 *D32, const float2 *U32,
+                                long long qs, int j, float2 *rpart, int ldp, double2 *coef, const int *meff,
+                                int n_pol);
+// full BSE (k_fullbse.cu); the tridiagonal solver keeps 4 x n_steps doubles in shared memory
+constexpr int BSE_FULL_MAX_STEPS = 6400;
 // full BSE (k_fullbse.cu)
 bse_status run_spectrum_full(bse_ctx *c, const void *A, const void *B, const double2 *u, int n_pol, int n_steps,
                              const double *omega, int n_w, double eta, double pref, double *eps2);

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(VB) k_fl_norm0(const double2 *__restrict__ R, 
                                                  long long vs, long long dim, const double2 *__restrict__ part,
                                                  int nblk, double2 *__restrict__ Q, double2 *__restrict__ P,
                                                  long long qs, double *__restrict__ beta0, int *__restrict__ meff,
-                                                 int *err) {
+                                                 int *err, float2 *__restrict__ Q32, float2 *__restrict__ P32) {
   __shared__ double red[VB / 32];
   const int p = blockIdx.y;
   const double b2 = sum_parts(part + (long long)p * nblk, nblk, red).x;
@@ -222,8 +222,13 @@ __global__ void __launch_bounds__(VB) k_fl_norm0(const double2 *__restrict__ R, 
   if (blockIdx.x == 0 && threadIdx.x == 0) beta0[p] = b;
   for (long long e = (long long)blockIdx.x * VB + threadIdx.x; e < 2 * dim; e += (long long)gridDim.x * VB) {
     const double2 v = R[p * vs + e], sv = S[p * vs + e];
-    Q[p * qs + e] = make_double2(v.x * inv, v.y * inv);
-    P[p * qs + e] = make_double2(sv.x * inv, sv.y * inv);
+    const double2 qv = make_double2(v.x * inv, v.y * inv), pv = make_double2(sv.x * inv, sv.y * inv);
+    Q[p * qs + e] = qv;
+    P[p * qs + e] = pv;
+    if (Q32) {
+      Q32[p * qs + e] = make_float2((float)qv.x, (float)qv.y);
+      P32[p * qs + e] = make_float2((float)pv.x, (float)pv.y);
+    }
   }
 }
 
@@ -296,7 +301,8 @@ __global__ void __launch_bounds__(VB) k_fl_scale(const double2 *__restrict__ R, 
                                                  long long vs, long long dim, double2 *__restrict__ Q,
                                                  double2 *__restrict__ P, long long qs, int j, int n_steps,
                                                  double *__restrict__ b, int ldab, int *__restrict__ meff,
-                                                 const double2 *__restrict__ part, int nblk, int *err) {
+                                                 const double2 *__restrict__ part, int nblk, int *err,
+                                                 float2 *__restrict__ Q32, float2 *__restrict__ P32) {
   __shared__ double red[VB / 32];
   const int p = blockIdx.y;
   if (j >= meff[p]) return;
@@ -317,8 +323,14 @@ __global__ void __launch_bounds__(VB) k_fl_scale(const double2 *__restrict__ R, 
   const long long n2 = 2 * dim;
   for (long long e = (long long)blockIdx.x * VB + threadIdx.x; e < n2; e += (long long)gridDim.x * VB) {
     const double2 r = R[p * vs + e], s = S[p * vs + e];
-    Q[p * qs + (long long)(j + 1) * n2 + e] = make_double2(r.x * inv, r.y * inv);
-    P[p * qs + (long long)(j + 1) * n2 + e] = make_double2(s.x * inv, s.y * inv);
+    const long long o = p * qs + (long long)(j + 1) * n2 + e;
+    const double2 qv = make_double2(r.x * inv, r.y * inv), pv = make_double2(s.x * inv, s.y * inv);
+    Q[o] = qv;
+    P[o] = pv;
+    if (Q32) {
+      Q32[o] = make_float2((float)qv.x, (float)qv.y);
+      P32[o] = make_float2((float)pv.x, (float)pv.y);
+    }
   }
 }
 
@@ -349,13 +361,91 @@ __global__ void k_fl_combine(const double2 *__restrict__ W, long long dim, int n
   S[p * ss + dim + e] = make_double2(bx.x + ay.x, -(bx.y + ay.y));
 }
 
+// Eigenvalues of each tridiagonal (a_p, b_p; order mq[p]) with the first and last components
+// of every eigenvector -- all the Gauss quadrature and the residual bounds need.  The implicit
+// QL algorithm with Wilkinson-type shifts (Bowdler, Martin, Reinsch and Wilkinson, Numer. Math.
+// 11 (1968) 293) run by one thread on shared-memory copies of the diagonal, off-diagonal and the
+// two tracked rows of the eigenvector matrix (started at the identity), each rotation applied
+// to them as it is formed.  Output: theta [p][mmax], z0 [p][mmax], zl [p][mmax].
+constexpr int QL_SWEEPS = 60;
+__global__ void k_tridiag_ql_ends(const double *__restrict__ a, const double *__restrict__ b, int ldab,
+                                  const int *__restrict__ mq, int mmax, double *__restrict__ theta,
+                                  double *__restrict__ z0o, double *__restrict__ zlo, int *err) {
+  extern __shared__ double qs_[];
+  const int p = blockIdx.x, m = mq[p];
+  double *d = qs_, *e = d + m, *z0 = e + m, *zl = z0 + m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    d[i] = a[p * ldab + i];
+    e[i] = i < m - 1 ? b[p * ldab + i] : 0.0;
+    z0[i] = i == 0 ? 1.0 : 0.0;
+    zl[i] = i == m - 1 ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < m; l++) {
+      for (int sweep = 0;; sweep++) {
+        int mm = l;
+        while (mm < m - 1) {
+          const double scale = fabs(d[mm]) + fabs(d[mm + 1]);
+          if (fabs(e[mm]) <= 1e-16 * scale || fabs(e[mm]) < 1e-300) break;
+          mm++;
+        }
+        if (mm == l) break;
+        if (sweep >= QL_SWEEPS) {
+          atomicOr(err, BSE_DERR_BOUNDS);
+          break;
+        }
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = hypot(g, 1.0);
+        g = d[mm] - d[l] + e[l] / (g + copysign(r, g));
+        double sn = 1.0, cn = 1.0, pp = 0.0;
+        bool split = false;
+        for (int i = mm - 1; i >= l; i--) {
+          const double f = sn * e[i], bb = cn * e[i];
+          r = hypot(f, g);
+          e[i + 1] = r;
+          if (r == 0.0) {
+            d[i + 1] -= pp;
+            e[mm] = 0.0;
+            split = true;
+            break;
+          }
+          sn = f / r;
+          cn = g / r;
+          g = d[i + 1] - pp;
+          r = (d[i] - g) * sn + 2.0 * cn * bb;
+          pp = sn * r;
+          d[i + 1] = g + pp;
+          g = cn * r - bb;
+          const double a0 = z0[i], a1 = z0[i + 1], c0 = zl[i], c1 = zl[i + 1];
+          z0[i + 1] = sn * a0 + cn * a1;
+          z0[i] = cn * a0 - sn * a1;
+          zl[i + 1] = sn * c0 + cn * c1;
+          zl[i] = cn * c0 - sn * c1;
+        }
+        if (!split) {
+          d[l] -= pp;
+          e[l] = g;
+          e[mm] = 0.0;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < mmax; i += blockDim.x) {
+    theta[(long long)p * mmax + i] = i < m ? d[i] : 0.0;
+    z0o[(long long)p * mmax + i] = i < m ? z0[i] : 0.0;
+    zlo[(long long)p * mmax + i] = i < m ? zl[i] : 0.0;
+  }
+}
+
 __global__ void k_fl_even(const int *__restrict__ meff, int n_pol, int *__restrict__ meven) {
   const int p = threadIdx.x;
   if (p < n_pol) meven[p] = meff[p] & ~1;
 }
 
 // eps2[w] = pref sum_p beta0_p^2 sum_i z_i0^2 L(w - |theta_i|) / (2 |theta_i|)
-__global__ void k_full_eps2(const double *__restrict__ dd, const double *__restrict__ Zt, const int *__restrict__ mq,
+__global__ void k_full_eps2(const double *__restrict__ dd, const double *__restrict__ Z0, const int *__restrict__ mq,
                             int mmax, const double *__restrict__ beta0, int n_pol, const double *__restrict__ omega,
                             int n_w, double eta, double pref, double *__restrict__ eps2) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,10 +454,10 @@ __global__ void k_full_eps2(const double *__restrict__ dd, const double *__restr
   double tot = 0.0;
   for (int p = 0; p < n_pol; p++) {
     const int m = mq[p];
-    const double *d = dd + (long long)p * mmax, *Z = Zt + (long long)p * mmax * mmax;
+    const double *d = dd + (long long)p * mmax, *Z = Z0 + (long long)p * mmax;
     double acc = 0.0;
     for (int i = 0; i < m; i++) {
-      const double th = fabs(d[i]), z = Z[(long long)i * mmax];
+      const double th = fabs(d[i]), z = Z[i];
       if (th > 0.0) {
         const double x = om - th;
         acc += z * z * (eta / M_PI) / (x * x + eta * eta) / (2.0 * th);
@@ -379,7 +469,7 @@ __global__ void k_full_eps2(const double *__restrict__ dd, const double *__restr
 }
 
 // The n_eig smallest positive Ritz values (ascending) and residuals |b_{m-1} z_i,m-1|.
-__global__ void k_full_lowest(const double *__restrict__ dd, const double *__restrict__ Zt, const int *__restrict__ mq,
+__global__ void k_full_lowest(const double *__restrict__ dd, const double *__restrict__ ZL, const int *__restrict__ mq,
                               int mmax, const double *__restrict__ b, int n_eig, double *__restrict__ omega,
                               double *__restrict__ resid) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -400,7 +490,7 @@ __global__ void k_full_lowest(const double *__restrict__ dd, const double *__res
       continue;
     }
     omega[e] = dd[best];
-    if (resid) resid[e] = fabs(b[m - 1] * Zt[(long long)best * mmax + m - 1]);
+    if (resid) resid[e] = fabs(b[m - 1] * ZL[best]);
     last = dd[best];
     last_i = best;
   }
@@ -409,16 +499,17 @@ __global__ void k_full_lowest(const double *__restrict__ dd, const double *__res
 struct FullScratch {
   HalfMV *hm = nullptr;    // half-read products (complex64 A, B of even order), else null
   float2 *Z = nullptr;     // [4][n_pol][dim] product operands
+  float2 *Q32 = nullptr, *P32 = nullptr, *rpart = nullptr;  // complex64 A, B: FP32 shadows of the bases
   double2 *W = nullptr;    // [4][n_pol][dim] products
-  double2 *Q = nullptr, *P = nullptr, *R = nullptr, *S = nullptr, *coef = nullptr, *part = nullptr, *rot = nullptr;
-  double *a = nullptr, *b = nullptr, *beta0 = nullptr, *dd = nullptr, *ee = nullptr, *Zt = nullptr;
+  double2 *Q = nullptr, *P = nullptr, *R = nullptr, *S = nullptr, *coef = nullptr, *part = nullptr;
+  double *a = nullptr, *b = nullptr, *beta0 = nullptr, *dd = nullptr, *z0 = nullptr, *zl = nullptr;
   int *meff = nullptr, *meven = nullptr;
   int nblk = 0;
 };
 
 void full_release(bse_ctx *c, FullScratch &s) {
-  void *ptrs[] = {s.Q, s.P, s.R, s.S, s.coef, s.part, s.rot, s.a, s.b, s.beta0, s.dd, s.ee, s.Zt, s.meff, s.meven,
-                  s.Z, s.W};
+  void *ptrs[] = {s.Q, s.P, s.R, s.S, s.coef, s.part, s.a, s.b, s.beta0, s.dd, s.z0, s.zl, s.meff, s.meven,
+                  s.Z, s.W, s.Q32, s.P32, s.rpart};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
   halfmv_release(c, s.hm);
@@ -428,7 +519,6 @@ void full_release(bse_ctx *c, FullScratch &s) {
 bse_status full_alloc(bse_ctx *c, FullScratch &s, int n_pol, int n_steps) {
   const long long n2 = 2 * c->dim;
   const size_t qn = (size_t)n_pol * (n_steps + 1) * n2;
-  const size_t mm = (size_t)n_pol * n_steps * n_steps;
   s.nblk = (int)((n2 + VCH - 1) / VCH);
   cudaStream_t st = c->stream;
   if (cudaMallocAsync((void **)&s.Q, sizeof(double2) * qn, st) != cudaSuccess ||
@@ -437,13 +527,12 @@ bse_status full_alloc(bse_ctx *c, FullScratch &s, int n_pol, int n_steps) {
       cudaMallocAsync((void **)&s.S, sizeof(double2) * n_pol * n2, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.coef, sizeof(double2) * n_pol * (n_steps + 1), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.part, sizeof(double2) * n_pol * s.nblk, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&s.rot, sizeof(double2) * n_pol * n_steps, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.a, sizeof(double) * n_pol * (n_steps + 1), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.b, sizeof(double) * n_pol * (n_steps + 1), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.beta0, sizeof(double) * n_pol, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.dd, sizeof(double) * n_pol * n_steps, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&s.ee, sizeof(double) * n_pol * n_steps, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&s.Zt, sizeof(double) * mm, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.z0, sizeof(double) * n_pol * n_steps, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.zl, sizeof(double) * n_pol * n_steps, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.meven, sizeof(int) * n_pol, st) != cudaSuccess) {
     cudaGetLastError();
@@ -451,6 +540,14 @@ bse_status full_alloc(bse_ctx *c, FullScratch &s, int n_pol, int n_steps) {
   }
   bse_status r = halfmv_alloc(c, &s.hm);
   if (r != BSE_OK) return r;
+  if (c->precision != BSE_FP64 &&
+      (cudaMallocAsync((void **)&s.Q32, sizeof(float2) * qn, st) != cudaSuccess ||
+       cudaMallocAsync((void **)&s.P32, sizeof(float2) * qn, st) != cudaSuccess ||
+       cudaMallocAsync((void **)&s.rpart, sizeof(float2) * (size_t)n_pol * (n_steps + 1) * reorth32_chunks(n2), st) !=
+           cudaSuccess)) {
+    cudaGetLastError();
+    return bse_fail(c, BSE_ENOMEM, "full BSE: reorthogonalisation scratch allocation failed");
+  }
   if (s.hm && (cudaMallocAsync((void **)&s.Z, sizeof(float2) * 4 * n_pol * c->dim, st) != cudaSuccess ||
                cudaMallocAsync((void **)&s.W, sizeof(double2) * 4 * n_pol * c->dim, st) != cudaSuccess)) {
     cudaGetLastError();
@@ -522,7 +619,7 @@ bse_status full_lanczos(bse_ctx *c, FullScratch &s, const void *A, const void *B
   if (r != BSE_OK) return r;
   k_fl_dot_part<<<dim3(s.nblk, n_pol), VB, 0, st>>>(s.R, vs, s.S, vs, dim, 1.0, nullptr, 0, s.part, s.nblk);
   k_fl_norm0<<<dim3(gv, n_pol), VB, 0, st>>>(s.R, s.S, vs, dim, s.part, s.nblk, s.Q, s.P, qs, s.beta0, s.meff,
-                                              c->d_err);
+                                              c->d_err, s.Q32, s.P32);
   bse_count_launch(3);
   r = bse_check_launch(c, "full BSE start");
   if (r != BSE_OK) return r;
@@ -533,16 +630,22 @@ bse_status full_lanczos(bse_ctx *c, FullScratch &s, const void *A, const void *B
                                               s.nblk);
     bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
-      k_fl_rdots<<<dim3(j + 1, n_pol), VB, 0, st>>>(s.R, vs, dim, s.P, qs, j, s.coef, ldab, s.meff);
-      k_fl_rupdate<<<dim3(ge, n_pol), VB, 0, st>>>(s.R, vs, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+      if (s.Q32) {  // FP32 projections: c_i = p_i^H r from the P shadow, r -= c_i q_i from the Q shadow
+        r = launch_reorth32_pass(c, s.R, n2, s.P32, s.Q32, qs, j, s.rpart, ldab, s.coef, s.meff, n_pol);
+        if (r != BSE_OK) return r;
+      } else {
+        k_fl_rdots<<<dim3(j + 1, n_pol), VB, 0, st>>>(s.R, vs, dim, s.P, qs, j, s.coef, ldab, s.meff);
+        k_fl_rupdate<<<dim3(ge, n_pol), VB, 0, st>>>(s.R, vs, dim, s.Q, qs, j, s.coef, ldab, s.meff);
+        bse_count_launch(2);
+      }
     }
     bse_prof_end(c, BSE_KP_REORTH);
     r = mmv(c, s, n_pol, A, B, s.R, vs, s.S);  // S = M r
     if (r != BSE_OK) return r;
     k_fl_dot_part<<<dim3(s.nblk, n_pol), VB, 0, st>>>(s.R, vs, s.S, vs, dim, 1.0, s.meff, j, s.part, s.nblk);
     k_fl_scale<<<dim3(gv, n_pol), VB, 0, st>>>(s.R, s.S, vs, dim, s.Q, s.P, qs, j, n_steps, s.b, ldab, s.meff,
-                                               s.part, s.nblk, c->d_err);
-    bse_count_launch(8);
+                                               s.part, s.nblk, c->d_err, s.Q32, s.P32);
+    bse_count_launch(4);
     r = bse_check_launch(c, "full BSE step");
     if (r != BSE_OK) return r;
   }
@@ -550,7 +653,13 @@ bse_status full_lanczos(bse_ctx *c, FullScratch &s, const void *A, const void *B
   bse_count_launch();
   r = bse_check_launch(c, "full BSE order");
   if (r != BSE_OK) return r;
-  return launch_tridiag_ql(c, s.a, s.b, ldab, s.meven, n_steps, n_pol, s.dd, s.ee, s.Zt, s.rot);
+  const size_t sm = sizeof(double) * 4 * n_steps;
+  if (sm > 200 * 1024) return bse_fail(c, BSE_EINVAL, "full BSE: recursion longer than the tridiagonal solver holds");
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(k_tridiag_ql_ends, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_tridiag_ql_ends<<<n_pol, 32, sm, st>>>(s.a, s.b, ldab, s.meven, n_steps, s.dd, s.z0, s.zl, c->d_err);
+  bse_count_launch();
+  return bse_check_launch(c, "full BSE tridiagonal");
 }
 
 }  // namespace
@@ -561,7 +670,7 @@ bse_status run_spectrum_full(bse_ctx *c, const void *A, const void *B, const dou
   bse_status r = full_alloc(c, s, n_pol, n_steps);
   if (r == BSE_OK) r = full_lanczos(c, s, A, B, u, 0, n_pol, n_steps);
   if (r == BSE_OK) {
-    k_full_eps2<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.dd, s.Zt, s.meven, n_steps, s.beta0, n_pol, omega, n_w,
+    k_full_eps2<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.dd, s.z0, s.meven, n_steps, s.beta0, n_pol, omega, n_w,
                                                           eta, pref, eps2);
     bse_count_launch();
     r = bse_check_launch(c, "full BSE spectrum");
@@ -576,7 +685,7 @@ bse_status run_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, 
   bse_status r = full_alloc(c, s, 1, n_steps);
   if (r == BSE_OK) r = full_lanczos(c, s, A, B, nullptr, seed, 1, n_steps);
   if (r == BSE_OK) {
-    k_full_lowest<<<1, 32, 0, c->stream>>>(s.dd, s.Zt, s.meven, n_steps, s.b, n_eig, omega_out, resid_out);
+    k_full_lowest<<<1, 32, 0, c->stream>>>(s.dd, s.zl, s.meven, n_steps, s.b, n_eig, omega_out, resid_out);
     bse_count_launch();
     r = bse_check_launch(c, "full BSE lowest");
   }

@@ -1436,16 +1436,22 @@ __device__ __forceinline__ double window_df(double x, double lo, double hi, doub
 // On exit d holds the eigenvalues (unsorted) and Zt the eigenvectors.  A block that fails to
 // converge sets the error word.
 constexpr int QL_MAX_SWEEPS = 60;
+// With in_smem, d, e and the sweep's rotations live in shared memory (4 mmax doubles,
+// dynamic): thread 0's sweeps are a serial chain of dependent updates, which global memory
+// stretches to its latency per step; d is copied to dd at the end.  Without, they live in
+// dd, ee and rot (orders beyond the shared-memory budget).
 __global__ void __launch_bounds__(256) k_tridiag_ql(const double *__restrict__ a, const double *__restrict__ b,
                                                     int ldab, const int *__restrict__ meff, int mmax,
                                                     double *__restrict__ dd, double *__restrict__ ee,
-                                                    double *__restrict__ Zt, double2 *__restrict__ rot, int *err) {
+                                                    double *__restrict__ Zt, double2 *__restrict__ rot, int *err,
+                                                    int in_smem) {
   __shared__ int s_mm, s_first, s_last;
+  extern __shared__ double ql_sm[];
   const int p = blockIdx.x;
   const int m = meff[p];
-  double *d = dd + (long long)p * mmax, *e = ee + (long long)p * mmax;
+  double *d = in_smem ? ql_sm : dd + (long long)p * mmax, *e = in_smem ? d + mmax : ee + (long long)p * mmax;
   double *Z = Zt + (long long)p * mmax * mmax;
-  double2 *cs = rot + (long long)p * mmax;
+  double2 *cs = in_smem ? reinterpret_cast<double2 *>(ql_sm + 2 * mmax) : rot + (long long)p * mmax;
   for (int i = threadIdx.x; i < mmax; i += blockDim.x) {
     d[i] = i < m ? a[p * ldab + i] : 0.0;
     e[i] = i < m - 1 ? b[p * ldab + i] : 0.0;
@@ -1517,6 +1523,19 @@ __global__ void __launch_bounds__(256) k_tridiag_ql(const double *__restrict__ a
       __syncthreads();
     }
   }
+  if (in_smem)
+    for (int i = threadIdx.x; i < mmax; i += blockDim.x) dd[(long long)p * mmax + i] = d[i];
+}
+
+// Launch k_tridiag_ql with its working arrays in shared memory when they fit.
+void tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax, int n_pol,
+                double *dd, double *ee, double *Zt, double2 *rot) {
+  const size_t sm = sizeof(double) * 4 * (size_t)mmax;
+  const int in_smem = sm <= 200 * 1024;
+  if (in_smem && sm > 48 * 1024)
+    cudaFuncSetAttribute(k_tridiag_ql, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_tridiag_ql<<<n_pol, 256, in_smem ? sm : 0, c->stream>>>(a, b, ldab, meff, mmax, dd, ee, Zt, rot, c->d_err,
+                                                            in_smem);
 }
 
 // M_p[i][l] = pref |u_p|^2 F_il v_i v_l with v_i = Zt[i][0]; Ipart[p] = pref |u_p|^2 sum_i v_i^2 f(theta_i).
@@ -1704,11 +1723,22 @@ bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const flo
   return bse_check_launch(c, "half-read product");
 }
 
-bse_status launch_tridiag_ql(bse_ctx *c, const double *a, const double *b, int ldab, const int *meff, int mmax,
-                             int n_pol, double *dd, double *ee, double *Zt, double2 *rot) {
-  k_tridiag_ql<<<n_pol, 256, 0, c->stream>>>(a, b, ldab, meff, mmax, dd, ee, Zt, rot, c->d_err);
-  bse_count_launch();
-  return bse_check_launch(c, "tridiagonal QL");
+int reorth32_chunks(long long n) { return (int)((n + RCH - 1) / RCH); }
+
+// One reorthogonalisation pass with FP32 projections (the complex64 path's chunked kernels):
+// coef_i = D32_i^H W, W -= sum_{i<=j} coef_i U32_i, per polarisation; vectors of even length n.
+bse_status launch_reorth32_pass(bse_ctx *c, double2 *W, long long n, const float2 *D32, const float2 *U32,
+                                long long qs, int j, float2 *rpart, int ldp, double2 *coef, const int *meff,
+                                int n_pol) {
+  if (n % 2) return bse_fail(c, BSE_EINVAL, "reorthogonalisation: odd vector length");
+  const int nrch = reorth32_chunks(n);
+  cudaStream_t st = c->stream;
+  k_reorth_dots_chunk<<<dim3(nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(W, n, D32, qs, j, rpart, nrch, ldp,
+                                                                             meff);
+  k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(rpart, nrch, ldp, j, coef, ldp, meff);
+  k_reorth_update32<<<dim3((unsigned)((n / 2 + 255) / 256), n_pol), 256, 0, st>>>(W, n, U32, qs, j, coef, ldp, meff);
+  bse_count_launch(3);
+  return BSE_OK;
 }
 
 bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_pol, int n_steps, double w_lo,
@@ -1734,7 +1764,7 @@ bse_status run_window_seed(bse_ctx *c, const void *H, const double2 *u, int n_po
   }
   if (r == BSE_OK) r = lanczos_run(c, s, H, u, n_pol, n_steps);
   if (r == BSE_OK) {
-    k_tridiag_ql<<<n_pol, 256, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.meff, mmax, dd, ee, Zt, rot, c->d_err);
+    tridiag_ql(c, s.a, s.b, n_steps + 1, s.meff, mmax, n_pol, dd, ee, Zt, rot);
     k_window_M<<<dim3(64, n_pol), 256, 0, c->stream>>>(dd, Zt, s.meff, mmax, s.beta0, w_lo, w_hi, eta, pref, M, Ip);
     // Ritz vectors Y_p = Zt_p Q_p, then Z_p = M_p conj(Y_p)
     dim3 g((unsigned)((dim + 63) / 64), (unsigned)((mmax + 63) / 64), n_pol);

@@ -149,6 +149,16 @@ bse_status bse_assemble(bse_ctx *ctx, void *H);
  *      conduction-valence projections is allocated on the first call. */
 bse_status bse_assemble_coupling(bse_ctx *ctx, void *B);
 
+/* Step (d) without H in memory: the same Haydock spectrum as bse_spectrum, with every Lanczos
+ * product H x recomputed from the context's pair tables -- the exchange and diagonal as
+ * small dense products, the direct term q-slab by q-slab (pair projections, M_vv W(q) on
+ * tensor cores, each nvc x nvc block applied as soon as it is formed).  Memory stays at the
+ * slab workspace instead of dim^2 elements; each step costs about one assembly.  For
+ * Hamiltonians beyond HBM (dense meshes of §IV).  Split precisions only (BSE_EINVAL for
+ * BSE_FP64); call after bse_project_pairs; arguments as bse_spectrum without H. */
+bse_status bse_spectrum_matfree(bse_ctx *ctx, const double *u, int n_pol, int n_steps, const double *omega,
+                                int n_w, double eta, double prefactor, double *eps2, double *ab);
+
 /* Full-BSE spectrum (Eq. full_BSE_epsilon2, §II.C): for H = [[A, B], [-B*, -A*]] with
  * positive solutions Omega_S, amplitudes (X_S, Y_S) normalised X^dagger X - Y^dagger Y = 1,
  *   eps2(w) = prefactor sum_p sum_S |sum_r d_p,r X_rS - conj(d_p,r) Y_rS|^2 L_eta(w - Omega_S),

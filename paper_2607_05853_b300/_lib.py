@@ -18,7 +18,8 @@ EXPORTS = ["bse_setup", "bse_interp_W", "bse_project_pairs", "bse_assemble", "bs
            "bse_nao", "bse_launch_count", "bse_free", "bse_profile", "bse_profile_read",
            "bse_spectrum_static", "bse_adjoint_seed", "bse_adjoint", "bse_batch_assemble",
            "bse_batch_release", "bse_autotune", "bse_window_seed", "bse_spectrum_add", "bse_interp_V",
-           "bse_set_momentum", "bse_assemble_coupling", "bse_spectrum_full", "bse_lowest_full"]
+           "bse_set_momentum", "bse_assemble_coupling", "bse_spectrum_full", "bse_lowest_full",
+           "bse_spectrum_matfree"]
 KERNEL_IDS = {"interp": 0, "half": 1, "project": 2, "g1": 3, "g2": 4, "exch": 5, "matvec": 6, "reorth": 7}
 
 
@@ -66,6 +67,7 @@ def load() -> ctypes.CDLL:
     lib.bse_assemble_coupling.argtypes = [vp, vp]
     lib.bse_spectrum_full.argtypes = [vp, vp, vp, vp, c_int, c_int, vp, c_int, c_double, c_double, vp]
     lib.bse_lowest_full.argtypes = [vp, vp, vp, c_int, c_int, c_uint64, vp, vp]
+    lib.bse_spectrum_matfree.argtypes = [vp, vp, c_int, c_int, vp, c_int, c_double, c_double, vp, vp]
     lib.bse_project_pairs.argtypes = [vp, vp, vp, vp]
     lib.bse_assemble.argtypes = [vp, vp]
     lib.bse_dipole_vector.argtypes = [vp, vp, vp, vp]

@@ -207,6 +207,20 @@ class BSE:
                     "bse_lowest")
         return (om, rs, vec) if vectors else (om, rs)
 
+    def spectrum_matfree(self, u: torch.Tensor, n_steps: int, omega: torch.Tensor, eta: float, prefactor: float,
+                         eps2: torch.Tensor | None = None, ab: torch.Tensor | None = None) -> torch.Tensor:
+        """bse_spectrum_matfree: the Haydock spectrum with H recomputed per Lanczos product."""
+        n_pol = u.shape[0] if u.dim() == 2 else 1
+        if eps2 is None:
+            eps2 = torch.empty(omega.numel(), dtype=torch.float64, device="cuda")
+        uu = _dev(u, torch.complex128, "u", n_pol * self.dim)
+        om = _dev(omega, torch.float64, "omega")
+        e = _dev(eps2, torch.float64, "eps2", omega.numel())
+        a = _dev(ab, torch.float64, "ab", n_pol * 3 * n_steps) if ab is not None else None
+        self._check(self._lib.bse_spectrum_matfree(self._ctx, uu, int(n_pol), int(n_steps), om, int(omega.numel()),
+                                                   float(eta), float(prefactor), e, a), "bse_spectrum_matfree")
+        return eps2
+
     def spectrum_full(self, A: torch.Tensor, B: torch.Tensor, u: torch.Tensor, n_steps: int, omega: torch.Tensor,
                       eta: float, prefactor: float, eps2: torch.Tensor | None = None) -> torch.Tensor:
         """bse_spectrum_full: eps2 of the full BSE (X and Y amplitudes)."""

@@ -456,6 +456,19 @@ bse_status bse_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, 
   return run_lowest_full(c, A, B, n_eig, n_steps, seed, omega_out, resid_out);
 }
 
+bse_status bse_spectrum_matfree(bse_ctx *c, const double *u, int n_pol, int n_steps, const double *omega, int n_w,
+                                double eta, double prefactor, double *eps2, double *ab) {
+  if (!c) return BSE_EINVAL;
+  if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "spectrum_matfree before project_pairs");
+  if (!u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum_matfree: null argument");
+  if (c->precision == BSE_FP64)
+    return bse_fail(c, BSE_EINVAL, "spectrum_matfree: the matrix-free product runs in the split precisions");
+  if (n_pol < 1 || n_pol > 3 || n_steps < 1 || n_steps > c->dim || n_w < 1 || !(eta > 0.0) ||
+      !std::isfinite(prefactor))
+    return bse_fail(c, BSE_EINVAL, "spectrum_matfree: bad size or parameter");
+  return run_spectrum_matfree(c, (const double2 *)u, n_pol, n_steps, omega, n_w, eta, prefactor, eps2, ab);
+}
+
 bse_status bse_lowest(bse_ctx *c, const void *H, int n_eig, int n_steps, uint64_t seed,
                       double *omega_out, double *resid_out, double *vecs_out) {
   if (!c) return BSE_EINVAL;

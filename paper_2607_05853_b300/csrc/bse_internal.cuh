@@ -151,6 +151,12 @@ bse_status split_setup(bse_ctx *c);
 bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
 bse_status split_assemble_coupling(bse_ctx *c, void *B);
+// W[p] = H x[p] (x[p] at x + p xs, W [n_pol][dim]) without H (split precisions), and the
+// early-stop scale of the matrix-free recursion
+bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_pol, double2 *W);
+bse_status split_matfree_hmax(bse_ctx *c, double *hmax);
+bse_status run_spectrum_matfree(bse_ctx *c, const double2 *u, int n_pol, int n_steps, const double *omega, int n_w,
+                                double eta, double pref, double *eps2, double *ab);
 bse_status split_project(bse_ctx *c, const double *C_R);
 bse_status split_y_to_fp64(bse_ctx *c);
 bse_status split_autotune(bse_ctx *c, int *chosen);

@@ -1157,7 +1157,7 @@ struct LanczosScratch {
   int *meff = nullptr;
 };
 
-bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) {
+bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, bool matfree = false) {
   const long long dim = c->dim;
   const size_t qbytes = sizeof(double2) * (size_t)n_pol * (n_steps + 1) * dim;
   cudaStream_t st = c->stream;
@@ -1184,7 +1184,7 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps) 
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "spectrum: reorthogonalisation scratch allocation failed");
   }
-  if (c->precision != BSE_FP64 && dim % 2 == 0) {
+  if (c->precision != BSE_FP64 && dim % 2 == 0 && !matfree) {
     if (cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
       cudaGetLastError();
       return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
@@ -1209,9 +1209,11 @@ void lanczos_release(bse_ctx *c, LanczosScratch &s) {
     if (p) cudaFreeAsync(p, c->stream);
 }
 
-// Runs the recursion; a, b, beta0, meff are left in s.
+// Runs the recursion; a, b, beta0, meff are left in s.  H == nullptr: the matrix-free product
+// (split precisions; H x recomputed from the pair tables each step).
 bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const double2 *u, int n_pol,
                        int n_steps) {
+  const bool matfree = H == nullptr;
   const long long dim = c->dim;
   const long long qs = (long long)(n_steps + 1) * dim;
   const int ldab = n_steps + 1;
@@ -1229,12 +1231,17 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       }
     }
   }
-  // max |H|
-  if (c64)
-    k_absmax_part<float2><<<1024, 256, 0, st>>>((const float2 *)H, dim * dim, s.part);
-  else
-    k_absmax_part<double2><<<1024, 256, 0, st>>>((const double2 *)H, dim * dim, s.part);
-  k_absmax_final<<<1, 32, 0, st>>>(s.part, 1024, s.hmax);
+  // max |H| (matrix-free: twice the largest band energy)
+  if (matfree) {
+    bse_status rr = split_matfree_hmax(c, s.hmax);
+    if (rr != BSE_OK) return rr;
+  } else {
+    if (c64)
+      k_absmax_part<float2><<<1024, 256, 0, st>>>((const float2 *)H, dim * dim, s.part);
+    else
+      k_absmax_part<double2><<<1024, 256, 0, st>>>((const double2 *)H, dim * dim, s.part);
+    k_absmax_final<<<1, 32, 0, st>>>(s.part, 1024, s.hmax);
+  }
   k_fill_meff<<<n_pol, 256, 0, st>>>(s.meff, n_pol, n_steps, s.a, s.b, ldab);
   k_lanczos_init<<<n_pol, 1024, 0, st>>>(u, dim, s.Q, qs, s.beta0, s.Q32);
   bse_count_launch(4);
@@ -1245,7 +1252,10 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const unsigned el2_blocks = (unsigned)((dim / 2 + 255) / 256);
   for (int j = 0; j < n_steps; j++) {
     bse_prof_begin(c, BSE_KP_MATVEC);
-    if (c64 && s.tma) {
+    if (matfree) {
+      r = split_matvec_free(c, s.Q + (long long)j * dim, qs, n_pol, s.W);
+      if (r != BSE_OK) return r;
+    } else if (c64 && s.tma) {
       const int grid = std::min(s.ntiles, MV_CTAS * c->n_sm);
       if (n_pol == 1) {
         k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
@@ -1286,7 +1296,7 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       else if (n_pol == 2) k_matvec_c128<2><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
       else k_matvec_c128<3><<<mv_blocks, 256, 0, st>>>((const double2 *)H, dim, s.Q, qs, j, s.W, s.meff);
     }
-    if (!s.hpart) bse_count_launch();
+    if (!s.hpart && !matfree) bse_count_launch();
     bse_prof_end(c, BSE_KP_MATVEC);
     if (!s.hpart) {  // the full-read matvecs write W directly: alpha_j partials in a separate pass
       k_alpha_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, s.Q, qs, j, s.meff, s.nbt, s.apart);
@@ -1341,6 +1351,26 @@ bse_status run_spectrum(bse_ctx *c, const void *H, const double2 *u, int n_pol, 
       bse_count_launch();
     }
     r = bse_check_launch(c, "continued fraction");
+  }
+  lanczos_release(c, s);
+  return r;
+}
+
+bse_status run_spectrum_matfree(bse_ctx *c, const double2 *u, int n_pol, int n_steps, const double *omega, int n_w,
+                                double eta, double pref, double *eps2, double *ab) {
+  LanczosScratch s;
+  bse_status r = lanczos_alloc(c, s, n_pol, n_steps, true);
+  if (r == BSE_OK) r = lanczos_run(c, s, nullptr, u, n_pol, n_steps);
+  if (r == BSE_OK) {
+    k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega,
+                                                         n_w, eta, pref, eps2, 0);
+    bse_count_launch();
+    if (ab) {
+      k_pack_ab<<<dim3((n_steps + 127) / 128, n_pol), 128, 0, c->stream>>>(s.a, s.b, s.beta0, n_steps + 1,
+                                                                          n_pol, n_steps, ab);
+      bse_count_launch();
+    }
+    r = bse_check_launch(c, "matrix-free continued fraction");
   }
   lanczos_release(c, s);
   return r;

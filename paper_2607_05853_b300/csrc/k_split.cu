@@ -60,6 +60,11 @@ struct SplitWS {
   float2 *McB = nullptr;         // [nqB][nk][nc*nv][naux]   M2
   float2 *TB = nullptr;          // [nqB][naux][rowsB]       T1 = M1 W(q)
   CUtensorMap tmA_B, tmB_xB;
+  // matrix-free products (allocated on first use): per-slab partial vectors and exchange sums
+  double2 *mf_fwd = nullptr, *mf_bwd = nullptr;  // [3][nq][nk][nvc]
+  double2 *mf_zp = nullptr;                      // [3][nchunk][naux] partial X^dagger x
+  double2 *mf_z2 = nullptr;                      // [3][naux]         V X^dagger x
+  int mf_nch = 0;
 };
 
 SplitWS *ws(bse_ctx *c) { return (SplitWS *)c->tc; }
@@ -583,7 +588,200 @@ __global__ void k_pieces_f32(const float2 *__restrict__ src, long long rows, int
   }
 }
 
+// ---- matrix-free products H x (no H stored) ---------------------------------------------
+// The exchange part (alpha/N_k) X V X^dagger x in three small passes, the diagonal, and per
+// q-slab the direct blocks D = -(1/N_k) T M_cc^T formed as for H and applied at once.
+constexpr int MF_RB = 128;  // rows of X per partial of X^dagger x
+
+// zp[p][chunk][mu] = sum over the chunk's rows r of conj(X[r][mu]) x[p][r]
+__global__ void k_mf_xh(const float2 *__restrict__ X, long long dim, int naux, const double2 *__restrict__ x,
+                        long long xs, int nch, double2 *__restrict__ zp) {
+  const int ch = blockIdx.x, p = blockIdx.y;
+  const long long r0 = (long long)ch * MF_RB, r1 = min(dim, r0 + MF_RB);
+  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (long long r = r0; r < r1; r++) {
+      const float2 a = X[r * naux + mu];
+      const double2 v = x[p * xs + r];
+      sr += (double)a.x * v.x + (double)a.y * v.y;
+      si += (double)a.x * v.y - (double)a.y * v.x;
+    }
+    zp[((long long)p * nch + ch) * naux + mu] = make_double2(sr, si);
+  }
+}
+
+// z2[p][mu] = sum_nu V[mu][nu] z[p][nu], z[p][nu] = sum_chunk zp[p][chunk][nu]
+__global__ void k_mf_zv(const double2 *__restrict__ zp, int nch, int naux, const float2 *__restrict__ V,
+                        double2 *__restrict__ z2) {
+  extern __shared__ double2 zs[];
+  const int p = blockIdx.x;
+  for (int nu = threadIdx.x; nu < naux; nu += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int ch = 0; ch < nch; ch++) {
+      const double2 v = zp[((long long)p * nch + ch) * naux + nu];
+      sr += v.x;
+      si += v.y;
+    }
+    zs[nu] = make_double2(sr, si);
+  }
+  __syncthreads();
+  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int nu = 0; nu < naux; nu++) {
+      const float2 v = V[(long long)mu * naux + nu];
+      const double2 z = zs[nu];
+      sr += (double)v.x * z.x - (double)v.y * z.y;
+      si += (double)v.x * z.y + (double)v.y * z.x;
+    }
+    z2[(long long)p * naux + mu] = make_double2(sr, si);
+  }
+}
+
+// W[p][r] = (E_c - E_v)[r] x[p][r] + (alpha/N_k) sum_mu X[r][mu] z2[p][mu]  (a warp per row)
+__global__ void k_mf_xv(const float2 *__restrict__ X, long long dim, int naux, const double2 *__restrict__ z2,
+                        const double *__restrict__ eqp, int nv, int nc, double scale, const double2 *__restrict__ x,
+                        long long xs, int n_pol, double2 *__restrict__ W) {
+  const long long r = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (r >= dim) return;
+  const int nvc = nv * nc, nb = nv + nc;
+  const long long k = r / nvc;
+  const int ia = (int)(r % nvc), i = ia / nc, a = ia % nc;
+  const double de = eqp[k * nb + nv + a] - eqp[k * nb + i];
+  for (int p = 0; p < n_pol; p++) {
+    double sr = 0.0, si = 0.0;
+    for (int mu = lane; mu < naux; mu += 32) {
+      const float2 xv = X[r * naux + mu];
+      const double2 z = z2[(long long)p * naux + mu];
+      sr += (double)xv.x * z.x - (double)xv.y * z.y;
+      si += (double)xv.x * z.y + (double)xv.y * z.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    if (lane == 0) {
+      const double2 v = x[p * xs + r];
+      W[(long long)p * dim + r] = make_double2(de * v.x + scale * sr, de * v.y + scale * si);
+    }
+  }
+}
+
 constexpr int G2CH = 32;
+
+// Direct blocks of one q-slab applied without storing them.  Per pair (k1, q): D[ia][jb] =
+// -(1/N_k) sum_nu T[(k1,i,j)][nu] M_cc[(k1,a,b)][nu] in shared memory (as k_g2_32 forms it),
+// then fwd[p][qq][k1] = D x[p][k2] and, for a block with a mirror (q != -q),
+// bwd[p][qq][k2] = D^dagger x[p][k1] (else 0).
+__global__ void __launch_bounds__(256) k_g2mv_32(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                                 int nv, int nc, int naux, int n1, int n2, int n3, int q0,
+                                                 const int *__restrict__ qlist, int rows, const double2 *__restrict__ x,
+                                                 long long xs, int n_pol, int nqs, double2 *__restrict__ fwd,
+                                                 double2 *__restrict__ bwd) {
+  extern __shared__ float2 sg[];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  const int nvc = nv * nc, nvv = nv * nv, ncc = nc * nc;
+  float2 *sT = sg, *sM = sT + nvv * G2CH, *sD = sM + ncc * G2CH;
+  const float2 *Tq = T + (long long)qq * rows * naux + (long long)k1 * nvv;
+  const float2 *Mk = Mc + ((long long)qq * nk + k1) * ncc * naux;
+  const int nout = nvc * nvc;
+  constexpr int MAXO = 16;
+  float2 ad[MAXO];
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) ad[t] = make_float2(0.f, 0.f);
+  for (int n0 = 0; n0 < naux; n0 += G2CH) {
+    const int nn = min(G2CH, naux - n0);
+    for (int e = threadIdx.x; e < (nvv + ncc) * G2CH; e += blockDim.x) {
+      const int r = e / G2CH, u = e % G2CH;
+      float2 v = make_float2(0.f, 0.f);
+      if (u < nn) v = r < nvv ? Tq[(long long)(n0 + u) * rows + r] : Mk[(long long)(r - nvv) * naux + n0 + u];
+      sg[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < MAXO; t++) {
+      const int o = threadIdx.x + t * blockDim.x;
+      if (o < nout) {
+        const int ia = o / nvc, jb = o % nvc;
+        const int i = ia / nc, a = ia % nc, j = jb / nc, b = jb % nc;
+        const float2 *pt = sT + (i * nv + j) * G2CH, *pm = sM + (a * nc + b) * G2CH;
+        float xr = ad[t].x, xi = ad[t].y;
+        for (int u = 0; u < nn; u++) {
+          xr = fmaf(pt[u].x, pm[u].x, fmaf(-pt[u].y, pm[u].y, xr));
+          xi = fmaf(pt[u].x, pm[u].y, fmaf(pt[u].y, pm[u].x, xi));
+        }
+        ad[t] = make_float2(xr, xi);
+      }
+    }
+    __syncthreads();
+  }
+  const float inv = 1.0f / nk;
+#pragma unroll
+  for (int t = 0; t < MAXO; t++) {
+    const int o = threadIdx.x + t * blockDim.x;
+    if (o < nout) sD[o] = make_float2(-inv * ad[t].x, -inv * ad[t].y);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * n_pol * nvc; e += blockDim.x) {
+    const int side = e / (n_pol * nvc), p = (e / nvc) % n_pol, r = e % nvc;
+    double sr = 0.0, si = 0.0;
+    if (side == 0) {  // row ia = r of D times x[k2]
+      const double2 *xv = x + p * xs + (long long)k2 * nvc;
+      for (int jb = 0; jb < nvc; jb++) {
+        const float2 d = sD[r * nvc + jb];
+        const double2 v = xv[jb];
+        sr += (double)d.x * v.x - (double)d.y * v.y;
+        si += (double)d.x * v.y + (double)d.y * v.x;
+      }
+      fwd[(((long long)p * nqs + qq) * nk + k1) * nvc + r] = make_double2(sr, si);
+    } else {          // column jb = r of D, conjugated, times x[k1]
+      if (mirror) {
+        const double2 *xv = x + p * xs + (long long)k1 * nvc;
+        for (int ia = 0; ia < nvc; ia++) {
+          const float2 d = sD[ia * nvc + r];
+          const double2 v = xv[ia];
+          sr += (double)d.x * v.x + (double)d.y * v.y;
+          si += (double)d.x * v.y - (double)d.y * v.x;
+        }
+      }
+      bwd[(((long long)p * nqs + qq) * nk + k2) * nvc + r] = make_double2(sr, si);
+    }
+  }
+}
+
+// W[p][k nvc + r] += sum over the slab's nq transfers of fwd + bwd (fixed order)
+__global__ void k_mf_reduce(const double2 *__restrict__ fwd, const double2 *__restrict__ bwd, int nq, int nqs,
+                            int nk, int nvc, int n_pol, double2 *__restrict__ W) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)nk * nvc;
+  if (e >= n_pol * per) return;
+  const int p = (int)(e / per);
+  const long long kr = e % per;
+  double2 acc = W[e];
+  for (int qq = 0; qq < nq; qq++) {
+    const double2 f = fwd[((long long)p * nqs + qq) * per + kr], b = bwd[((long long)p * nqs + qq) * per + kr];
+    acc.x += f.x + b.x;
+    acc.y += f.y + b.y;
+  }
+  W[e] = acc;
+}
+
+// hmax[0] = 2 max |E| over the band window (scale of the early-stop threshold)
+__global__ void k_mf_hmax(const double *__restrict__ eqp, long long n, double *__restrict__ hmax) {
+  __shared__ double red[256];
+  double m = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(eqp[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) hmax[0] = 2.0 * red[0];
+}
 
 // B block (k1, k2 = k1 - q) += -(1/N_k) sum_nu T1[(k1,b,i)][nu] M2[(k1,a,j)][nu], and the same
 // value at the transposed position (k2, k1) (B is symmetric).  T1 [q][nu][rowsB].
@@ -1361,6 +1559,82 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
     }
   }
   return BSE_OK;
+}
+
+// W[p] = H x[p] for the split-precision context without H: exchange and diagonal, then the
+// direct term slab by slab (projections and M_vv W(q) on tensor cores as in split_assemble).
+bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_pol, double2 *W) {
+  SplitWS *w = ws(c);
+  const int na = c->naux_tot;
+  if (c->nv * c->nc > 64) return bse_fail(c, BSE_EINVAL, "matrix-free product: band window too wide");
+  if (!w->mf_fwd) {
+    w->mf_nch = (int)((c->dim + MF_RB - 1) / MF_RB);
+    const size_t npart = (size_t)3 * w->nq * c->nk * c->nvc;
+    if (!alloc((void **)&w->mf_fwd, npart * sizeof(double2)) || !alloc((void **)&w->mf_bwd, npart * sizeof(double2)) ||
+        !alloc((void **)&w->mf_zp, (size_t)3 * w->mf_nch * na * sizeof(double2)) ||
+        !alloc((void **)&w->mf_z2, (size_t)3 * na * sizeof(double2)))
+      return bse_fail(c, BSE_ENOMEM, "matrix-free product: workspace allocation failed");
+  }
+  cudaStream_t st = c->stream;
+  k_mf_xh<<<dim3(w->mf_nch, n_pol), 256, 0, st>>>(w->X32, c->dim, na, x, xs, w->mf_nch, w->mf_zp);
+  k_mf_zv<<<n_pol, 256, sizeof(double2) * na, st>>>(w->mf_zp, w->mf_nch, na, w->V032, w->mf_z2);
+  k_mf_xv<<<(unsigned)((c->dim + 7) / 8), 256, 0, st>>>(w->X32, c->dim, na, w->mf_z2, e_tab(c, w), c->nv, c->nc,
+                                                        c->alpha / c->nk, x, xs, n_pol, W);
+  bse_count_launch(3);
+  bse_status s = bse_check_launch(c, "matrix-free exchange");
+  if (s != BSE_OK) return s;
+  const int nqp = (int)c->qplus.size();
+  const int nchunk = (na + 127) / 128;
+  for (int q0 = 0; q0 < nqp; q0 += w->nq) {
+    const int nq = std::min(w->nq, nqp - q0);
+    {
+      dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
+      size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
+      if (!fast_pair_kernels(c, w, q0, nq, nullptr, true))
+        k_proj32<<<grid, 128, sm, st>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+                                        c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], q0,
+                                        c->d_qplus, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
+      bse_count_launch();
+    }
+    {
+      tcg::Args a{};
+      a.rows = w->rows;
+      a.n_valid = na;
+      a.k_chunks = w->kchunks;
+      a.scale = 1.0f;
+      a.out = w->T32;
+      a.ld_row = 1;
+      a.ld_col = w->rows;
+      a.out_bstride = (long long)w->rows * na;
+      a.b_batch_planes = 1;
+      a.b_base = q0;
+      a.qlist = c->d_qplus;
+      a.err = c->d_err;
+      dim3 grid((unsigned)((na + w->bn_g1 - 1) / w->bn_g1), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
+      s = launch_tc_np(c, w->np, w->bn_g1, w->tmA_g1, w->tmB_g1, a, grid, -1);
+      if (s != BSE_OK) return s;
+    }
+    {
+      const size_t sm = sizeof(float2) * ((size_t)(c->nv * c->nv + c->nc * c->nc) * G2CH + (size_t)c->nvc * c->nvc);
+      k_g2mv_32<<<dim3(c->nk, nq), 256, sm, st>>>(w->T32, w->Mc32, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                                  c->mesh[2], q0, c->d_qplus, w->rows, x, xs, n_pol, w->nq, w->mf_fwd,
+                                                  w->mf_bwd);
+      const long long n = (long long)n_pol * c->nk * c->nvc;
+      k_mf_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w->mf_fwd, w->mf_bwd, nq, w->nq, c->nk, c->nvc, n_pol,
+                                                               W);
+      bse_count_launch(2);
+      s = bse_check_launch(c, "matrix-free direct slab");
+      if (s != BSE_OK) return s;
+    }
+  }
+  return BSE_OK;
+}
+
+bse_status split_matfree_hmax(bse_ctx *c, double *hmax) {
+  SplitWS *w = ws(c);
+  k_mf_hmax<<<1, 256, 0, c->stream>>>(e_tab(c, w), (long long)c->nk * c->nb, hmax);
+  bse_count_launch();
+  return bse_check_launch(c, "matrix-free scale");
 }
 
 // ---- autotuner ----------------------------------------------------------------------------

@@ -1104,6 +1104,175 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
   }
 }
 
+// Register-blocked conduction-valence projections for the coupling block (windows with Nv, Nc
+// in {2, 4, 6}): per mu the bands of k1 and k2 are loaded once and
+//   M1[b][i] = sum_s conj(c2_s,nv+b) y1_s,i + c1_s,i conj(y2_s,nv+b)   (C~_{b k2, i k1}),
+//   M2[a][j] = sum_s conj(c1_s,nv+a) y2_s,j + c2_s,j conj(y1_s,nv+a)   (C~_{a k1, j k2}),
+// M1 written as bf16 pieces (GEMM operand, row (k1, b, i)), M2 in FP32 (row (k1, a, j)).
+// grid: x = q - q0, y = k1; block: mu chunk, loop over mu.
+template <int NV, int NC>
+__global__ void __launch_bounds__(160) k_proj_cv32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
+                                                     int nao_tot, int naux, int nao_max,
+                                                     const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
+                                                     const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
+                                                     const int *__restrict__ qlist, int np, int rowsB, int kmem,
+                                                     __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ M2) {
+  constexpr int NB = NV + NC, NVC = NV * NC;
+  extern __shared__ float2 scf[];
+  const int nk = n1 * n2 * n3;
+  const int qq = blockIdx.x, q = qlist[q0 + qq], k1 = blockIdx.y;
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  float2 *c1 = scf, *c2 = scf + nao_tot * NB;
+  for (int e = threadIdx.x; e < nao_tot * NB; e += blockDim.x) {
+    const double2 a = ck[(long long)k1 * nao_tot * NB + e], b = ck[(long long)k2 * nao_tot * NB + e];
+    c1[e] = make_float2((float)a.x, (float)a.y);
+    c2[e] = make_float2((float)b.x, (float)b.y);
+  }
+  __syncthreads();
+  const long long plane = (long long)rowsB * kmem;
+  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
+    const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
+    const float2 *Y1 = Y + (long long)k1 * nao_max * NB * naux + mu;
+    const float2 *Y2 = Y + (long long)k2 * nao_max * NB * naux + mu;
+    float2 m1[NC][NV], m2[NC][NV];
+#pragma unroll
+    for (int b = 0; b < NC; b++)
+#pragma unroll
+      for (int i = 0; i < NV; i++) m1[b][i] = m2[b][i] = make_float2(0.f, 0.f);
+    for (int s = 0; s < na; s++) {
+      float2 y1[NB], y2[NB];
+#pragma unroll
+      for (int n = 0; n < NB; n++) {
+        y1[n] = Y1[((long long)s * NB + n) * naux];
+        y2[n] = Y2[((long long)s * NB + n) * naux];
+      }
+      const float2 *cs1 = c1 + (ao0 + s) * NB, *cs2 = c2 + (ao0 + s) * NB;
+#pragma unroll
+      for (int b = 0; b < NC; b++) {
+        const float2 cb2 = cs2[NV + b], cb1 = cs1[NV + b];
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+          const float2 ci1 = cs1[i], ci2 = cs2[i];
+          // m1[b][i] += conj(cb2) y1[i] + ci1 conj(y2[NV+b])
+          float xr = m1[b][i].x, xi = m1[b][i].y;
+          xr = fmaf(cb2.x, y1[i].x, fmaf(cb2.y, y1[i].y, xr));
+          xi = fmaf(cb2.x, y1[i].y, fmaf(-cb2.y, y1[i].x, xi));
+          xr = fmaf(ci1.x, y2[NV + b].x, fmaf(ci1.y, y2[NV + b].y, xr));
+          xi = fmaf(ci1.y, y2[NV + b].x, fmaf(-ci1.x, y2[NV + b].y, xi));
+          m1[b][i] = make_float2(xr, xi);
+          // m2[b][i] (= M2[a = b][j = i]) += conj(cb1) y2[i] + ci2 conj(y1[NV+b])
+          xr = m2[b][i].x;
+          xi = m2[b][i].y;
+          xr = fmaf(cb1.x, y2[i].x, fmaf(cb1.y, y2[i].y, xr));
+          xi = fmaf(cb1.x, y2[i].y, fmaf(-cb1.y, y2[i].x, xi));
+          xr = fmaf(ci2.x, y1[NV + b].x, fmaf(ci2.y, y1[NV + b].y, xr));
+          xi = fmaf(ci2.y, y1[NV + b].x, fmaf(-ci2.x, y1[NV + b].y, xi));
+          m2[b][i] = make_float2(xr, xi);
+        }
+      }
+    }
+    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)k1 * NVC * kmem + mu;
+#pragma unroll
+    for (int b = 0; b < NC; b++)
+#pragma unroll
+      for (int i = 0; i < NV; i++) {
+        __nv_bfloat16 pr[3], pi[3];
+        split_pieces<float>(m1[b][i].x, np, pr);
+        split_pieces<float>(m1[b][i].y, np, pi);
+        const long long r = (long long)(b * NV + i) * kmem;
+#pragma unroll
+        for (int p = 0; p < 3; p++) {
+          if (p >= np) break;
+          out[(2 * p) * plane + r] = pr[p];
+          out[(2 * p + 1) * plane + r] = pi[p];
+        }
+      }
+    float2 *mo = M2 + (((long long)qq * nk + k1) * NVC) * naux + mu;
+#pragma unroll
+    for (int a = 0; a < NC; a++)
+#pragma unroll
+      for (int j = 0; j < NV; j++) mo[(long long)(a * NV + j) * naux] = m2[a][j];
+  }
+}
+
+// Register-blocked coupling block writer: the pair's NVC rows of T1 ((b, i), consecutive per
+// column nu) and of M2 ((a, j)) copied to shared memory in one asynchronous sweep; a thread
+// owns 2 x 2 products T1 row x M2 row and adds -(1/N_k) of each to B at (k1, i, a; k2, j, b)
+// and, for a block with a mirror, the same value at the transposed position.
+template <int NV, int NC>
+__global__ void __launch_bounds__(256) k_g2c_32_t(const float2 *__restrict__ T, const float2 *__restrict__ M2,
+                                                  int naux, int n1, int n2, int n3, int q0,
+                                                  const int *__restrict__ qlist, int rowsB, long long dim,
+                                                  float2 *__restrict__ B) {
+  constexpr int R = NV * NC, TR = (R + 1) / 2, NVC = NV * NC;
+  extern __shared__ float2 sg2[];
+  float2 *sT = sg2, *sM = sg2 + R * naux;
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  static_assert(R % 2 == 0, "the pair's T1 rows are copied in 16-byte pieces");
+  const float2 *Tq = T + (long long)qq * rowsB * naux + (long long)k1 * R;  // T1[q][nu][row]
+  const float2 *Mk = M2 + ((long long)qq * nk + k1) * R * naux;
+  {
+    float4 *st4 = reinterpret_cast<float4 *>(sT);
+    for (int e = threadIdx.x; e < naux * (R / 2); e += blockDim.x) {
+      const int nu = e / (R / 2), h = e % (R / 2);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st4 + e)),
+                   "l"(reinterpret_cast<const float4 *>(Tq + (long long)nu * rowsB) + h)
+                   : "memory");
+    }
+  }
+  if ((naux & 1) == 0) {
+    const float4 *m4 = reinterpret_cast<const float4 *>(Mk);
+    float4 *sm4 = reinterpret_cast<float4 *>(sM);
+    for (int e = threadIdx.x; e < R * naux / 2; e += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sm4 + e)), "l"(m4 + e) : "memory");
+  } else {
+    for (int e = threadIdx.x; e < R * naux; e += blockDim.x) sM[e] = Mk[e];
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const float invf = 1.0f / nk;
+  for (int w = threadIdx.x; w < TR * TR; w += blockDim.x) {
+    const int tr = w / TR, tm = w % TR;
+    const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tm, m1 = min(2 * tm + 1, R - 1);
+    const float2 *pt0 = sT + r0, *pt1 = sT + r1, *pm0 = sM + m0 * naux, *pm1 = sM + m1 * naux;
+    float2 acc[2][2];
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) acc[x][y] = make_float2(0.f, 0.f);
+    for (int u = 0; u < naux; u++) {
+      const float2 tt[2] = {pt0[u * R], pt1[u * R]}, mm[2] = {pm0[u], pm1[u]};
+#pragma unroll
+      for (int x = 0; x < 2; x++)
+#pragma unroll
+        for (int y = 0; y < 2; y++) {
+          acc[x][y].x = fmaf(tt[x].x, mm[y].x, fmaf(-tt[x].y, mm[y].y, acc[x][y].x));
+          acc[x][y].y = fmaf(tt[x].x, mm[y].y, fmaf(tt[x].y, mm[y].x, acc[x][y].y));
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++) {
+        const int bi = 2 * tr + x, aj = 2 * tm + y;   // T1 row (b, i), M2 row (a, j)
+        if (bi >= R || aj >= R) continue;
+        const int b = bi / NV, i = bi % NV, a = aj / NV, j = aj % NV;
+        const int ia = i * NC + a, jb = j * NC + b;
+        float2 *hp = B + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
+        const float2 hx = *hp;
+        *hp = make_float2(fmaf(-invf, acc[x][y].x, hx.x), fmaf(-invf, acc[x][y].y, hx.y));
+        if (mirror) {
+          float2 *hm = B + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
+          const float2 mx = *hm;
+          *hm = make_float2(fmaf(-invf, acc[x][y].x, mx.x), fmaf(-invf, acc[x][y].y, mx.y));
+        }
+      }
+  }
+}
+
 bool alloc(void **p, size_t bytes) {
   if (cudaMalloc(p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -1154,6 +1323,37 @@ bool fast_pair_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H, bool p
   BSE_FAST(2, 2) BSE_FAST(2, 4) BSE_FAST(2, 6) BSE_FAST(4, 2) BSE_FAST(4, 4) BSE_FAST(4, 6)
   BSE_FAST(6, 2) BSE_FAST(6, 4) BSE_FAST(6, 6)
 #undef BSE_FAST
+  return false;
+}
+
+// The register-blocked coupling-block kernels for windows with Nv, Nc in {2, 4, 6}; false
+// means the caller runs the generic ones.
+template <int NV, int NC>
+bool launch_cv_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *B, bool proj) {
+  const int na = c->naux_tot;
+  if (proj) {
+    const int bs = std::min(160, (na + 31) / 32 * 32);
+    const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
+    k_proj_cv32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(
+        y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
+        c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem, w->ApB, w->McB);
+    return true;
+  }
+  constexpr int threads = ((NV * NC + 1) / 2) * ((NV * NC + 1) / 2);
+  const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
+  const size_t sm = sizeof(float2) * (size_t)(2 * NV * NC) * na;
+  if (sm > 200 * 1024) return false;
+  k_g2c_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->TB, w->McB, na, c->mesh[0], c->mesh[1], c->mesh[2],
+                                                            q0, c->d_qplus, w->rowsB, c->dim, B);
+  return true;
+}
+
+bool fast_cv_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *B, bool proj) {
+#define BSE_FAST_CV(NV, NC) \
+  if (c->nv == NV && c->nc == NC) return launch_cv_fast<NV, NC>(c, w, q0, nq, B, proj);
+  BSE_FAST_CV(2, 2) BSE_FAST_CV(2, 4) BSE_FAST_CV(2, 6) BSE_FAST_CV(4, 2) BSE_FAST_CV(4, 4) BSE_FAST_CV(4, 6)
+  BSE_FAST_CV(6, 2) BSE_FAST_CV(6, 4) BSE_FAST_CV(6, 6)
+#undef BSE_FAST_CV
   return false;
 }
 
@@ -1227,6 +1427,7 @@ void set_attr() {
 template <int NV, int NC>
 void set_g2_attr() {
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 void set_all_attrs() {
   static bool done = false;
@@ -1519,10 +1720,11 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
       dim3 grid(nchunk * 2 * c->nc, nq, c->nk);
       size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
       bse_prof_begin(c, BSE_KP_PROJECT);
-      k_proj_cv32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na,
-                                                c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
-                                                c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem,
-                                                w->ApB, w->McB);
+      if (!fast_cv_kernels(c, w, q0, nq, B, true))
+        k_proj_cv32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na,
+                                                  c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
+                                                  c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem,
+                                                  w->ApB, w->McB);
       bse_prof_end(c, BSE_KP_PROJECT);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "proj_cv32");
@@ -1550,8 +1752,9 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
       dim3 grid(c->nk, nq);
       size_t sm = sizeof(float2) * 2 * c->nvc * G2CH;
       bse_prof_begin(c, BSE_KP_G2);
-      k_g2c_32<<<grid, 256, sm, c->stream>>>(w->TB, w->McB, c->nv, c->nc, na, c->mesh[0], c->mesh[1], c->mesh[2],
-                                             q0, c->d_qplus, w->rowsB, c->dim, B);
+      if (!fast_cv_kernels(c, w, q0, nq, B, false))
+        k_g2c_32<<<grid, 256, sm, c->stream>>>(w->TB, w->McB, c->nv, c->nc, na, c->mesh[0], c->mesh[1], c->mesh[2],
+                                               q0, c->d_qplus, w->rowsB, c->dim, B);
       bse_prof_end(c, BSE_KP_G2);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "g2c_32");

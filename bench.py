@@ -484,6 +484,8 @@ def main():
         "stages_ms": {"interp+per_k": statistics.mean(pre_ms), "assemble": statistics.mean(asm_ms),
                       "dipole+spectrum": statistics.mean(spec_ms)},
         "assembly_elements_per_s": asm_rate,
+        "spectrum_throughput": {"haydock_steps_per_s": nsteps / (statistics.mean(spec_ms) / 1000.0),
+                                "matvec_GBps": roof.get("achieved") if top == "matvec" else None},
         "kernels_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
         "roofline": roof, "tensor_roofline": tensor, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
     }

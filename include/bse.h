@@ -1,5 +1,6 @@
 /*
- * bse.h -- C ABI of the B300 (sm_103a) Tamm-Dancoff BSE hot path.
+ * bse.h -- C ABI of the B300 (sm_103a) Tamm-Dancoff BSE hot path and its extensions
+ * (full BSE, finite exciton momentum, matrix-free spectrum).
  *
  * The library builds the resonant block A of the BSE Hamiltonian on a dense k-mesh from
  * the unit-cell-indexed screened interaction W_mu,nu(R) and the localized-RI pair
@@ -19,6 +20,11 @@
  *                      abs_vel with the delta broadened to a Lorentzian -- by a Lanczos
  *                      recursion with full reorthogonalisation and a continued fraction.
  *   bse_lowest         lowest Ritz values of A by Lanczos (the TDA eigenvalues, §II.C).
+ *   bse_set_momentum   finite exciton momentum Q: pairs (v k, c k+Q) (the q != 0 extension, §V).
+ *   bse_assemble_coupling, bse_spectrum_full, bse_lowest_full
+ *                      full BSE: the coupling block B, eps2 with the Y amplitudes, the lowest
+ *                      paired +-Omega (§II.C, Eq. full_BSE_epsilon2).
+ *   bse_spectrum_matfree  the Haydock spectrum with H recomputed per Lanczos product.
  *
  * Conventions (all entry points):
  *  - Dense k-points are k = (n + k_offset)/N per axis, flattened (n1*N2 + n2)*N3 + n3.

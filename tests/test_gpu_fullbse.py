@@ -56,6 +56,24 @@ def test_coupling_block_split_matches_oracle(prec, name):
     assert np.abs(B - B.T).max() <= SPLIT_TOL[prec] * np.abs(Aref).max()
 
 
+def test_full_spectrum_split_odd_dim_matches_oracle():
+    """An odd dim (135) takes the single-pass full-read product (k_mmv, complex64) instead of
+    the tiled half reads."""
+    import dataclasses
+    import torch
+    spec = dataclasses.replace(RAGGED["ragged"], nv=3, nc=3, dense=(3, 1, 5))
+    inp = make_inputs(full_bse_spec(spec))
+    orc = O.BSEOracle(inp)
+    om = np.linspace(0.0, 12.0, 241)
+    ref = O.eps2_full_exact(orc.hamiltonian(), orc.coupling(), orc.dipoles(), om, ETA, orc.prefactor())
+    b, d, A, B = _gpu_AB(inp, precision="bf16x3")
+    assert b.dim % 2 == 1
+    u = b.dipole_vector(d["vel"], d["e_ks"])
+    eps = b.spectrum_full(A, B, u, 2 * b.dim, torch.from_numpy(om).cuda(), ETA, orc.prefactor())
+    b.sync()
+    assert np.linalg.norm(eps.cpu().numpy() - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
 def test_full_spectrum_split_matches_oracle():
     """bf16x3 A and B (complex64) with the FP64 recursion, full length."""
     import torch

@@ -1499,7 +1499,8 @@ void split_free(bse_ctx *c) {
   SplitWS *w = ws(c);
   if (!w) return;
   void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp, w->PHQ, w->PHK, w->WR32T, w->CR32, w->V032,
-                  w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq, w->ApB, w->XpB, w->McB, w->TB};
+                  w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq, w->ApB, w->XpB, w->McB, w->TB,
+                  w->mf_fwd, w->mf_bwd, w->mf_zp, w->mf_z2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;

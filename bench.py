@@ -564,9 +564,9 @@ def full_bse_report(spec, args, dev, nsteps, omega, pk):
                              "frac": achieved / pk["hbm_gbs"] if achieved else None,
                              "per_step_ms": per_step_ms, "launches_per_step": mv_n / (nsteps + 1),
                              "note": "product M r per Lanczos step: algorithmic bytes = the upper-triangle tiles "
-                                     "of A and of B once each; the half-read kernel runs four times per step "
-                                     "(A x, A conj(y), B y, B conj(x), three polarisations each), so each "
-                                     "matrix half is read twice"},
+                                     "of A and of B once each; the half-read kernel runs twice per step (A on "
+                                     "(x, conj y), B on (y, conj x), 2 x 3 polarisation vectors each), so each "
+                                     "matrix half is read once"},
     }
     del A, B
     ctx.close()

@@ -563,9 +563,9 @@ void launch_mmv(bse_ctx *c, const void *A, const void *B, const double2 *V, long
   k_mmv<T, NP, RPW><<<blocks, 256, 0, c->stream>>>((const T *)A, (const T *)B, c->dim, V, vs, S, 2 * c->dim);
 }
 
-// S [n_pol][2 dim] = M V, V[p] at V + p vs.  Complex64 A, B of even order: four half-read
-// products through the TDA's tiled TMA kernel (A x, A conj(y) Hermitian; B y, B conj(x)
-// symmetric), each reading the upper-triangle tiles once for all polarisations, so A and B
+// S [n_pol][2 dim] = M V, V[p] at V + p vs.  Complex64 A, B of even order: two half-read
+// products through the TDA's tiled TMA kernel, A on (x, conj(y)) (Hermitian) and B on
+// (y, conj(x)) (symmetric), 2 n_pol vectors each, so the upper-triangle tiles of A and of B
 // are each read once per step; otherwise one full-read pass (k_mmv).
 bse_status mmv(bse_ctx *c, FullScratch &s, int n_pol, const void *A, const void *B, const double2 *V, long long vs,
                double2 *S) {
@@ -574,9 +574,8 @@ bse_status mmv(bse_ctx *c, FullScratch &s, int n_pol, const void *A, const void 
     const dim3 g((unsigned)((dim + 255) / 256), n_pol);
     k_fl_pack<<<g, 256, 0, c->stream>>>(V, vs, dim, n_pol, s.Z);
     bse_count_launch();
-    bse_status r = BSE_OK;
-    for (int k = 0; k < 4 && r == BSE_OK; k++)
-      r = halfmv_run(c, s.hm, k < 2 ? A : B, k >= 2, s.Z + k * zs, n_pol, s.W + k * zs);
+    bse_status r = halfmv_run(c, s.hm, A, false, s.Z, 2 * n_pol, s.W);
+    if (r == BSE_OK) r = halfmv_run(c, s.hm, B, true, s.Z + 2 * zs, 2 * n_pol, s.W + 2 * zs);
     if (r != BSE_OK) return r;
     k_fl_combine<<<g, 256, 0, c->stream>>>(s.W, dim, n_pol, S, 2 * dim);
     bse_count_launch();

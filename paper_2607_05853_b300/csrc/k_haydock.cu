@@ -379,8 +379,9 @@ struct HmvSmem {
 
 // SYM = true: H is complex symmetric (H^T = H) instead of Hermitian; the mirrored tile then
 // contributes H_t^T y, which only changes how the row vector y is parked for the column sums.
+// More than three vectors (the full-BSE product's six) need more registers: two CTAs per SM.
 template <int NP, bool SYM = false>
-__global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
+__global__ void __launch_bounds__(128, (NP <= 3 ? MV_CTAS : 2)) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
                                                          int nb, const int2 *__restrict__ tiles, int ntiles,
                                                          const float2 *__restrict__ Q32, long long qs, int j,
                                                          float2 *__restrict__ part, const int *meff, int *err) {
@@ -563,27 +564,48 @@ __global__ void __launch_bounds__(128, MV_CTAS) k_hmv_tma(const __grid_constant_
           mine[k] = make_float4(a.x, a.y, b.x, b.y);
         }
         __syncwarp();
-        const int i = lane % (4 * NP), g = lane / (4 * NP);
-        unsigned long long s0 = 0ull, s1 = 0ull;
-        const unsigned long long one = pk2(1.f, 1.f);
-        if (lane < 8 * NP) {
-          const float *src = red + 16 * g * S::RSTR + 2 * i;
+        if constexpr (8 * NP <= 32) {
+          const int i = lane % (4 * NP), g = lane / (4 * NP);
+          unsigned long long s0 = 0ull, s1 = 0ull;
+          const unsigned long long one = pk2(1.f, 1.f);
+          if (lane < 8 * NP) {
+            const float *src = red + 16 * g * S::RSTR + 2 * i;
 #pragma unroll
-          for (int k = 0; k < 16; k += 2) {
-            const float2 v0 = *reinterpret_cast<const float2 *>(src + k * S::RSTR);
-            const float2 v1 = *reinterpret_cast<const float2 *>(src + (k + 1) * S::RSTR);
-            ffma2(s0, pk2(v0.x, v0.y), one);
-            ffma2(s1, pk2(v1.x, v1.y), one);
+            for (int k = 0; k < 16; k += 2) {
+              const float2 v0 = *reinterpret_cast<const float2 *>(src + k * S::RSTR);
+              const float2 v1 = *reinterpret_cast<const float2 *>(src + (k + 1) * S::RSTR);
+              ffma2(s0, pk2(v0.x, v0.y), one);
+              ffma2(s1, pk2(v1.x, v1.y), one);
+            }
           }
-        }
-        ffma2(s0, s1, one);
-        float2 tot = up2(s0);
-        tot.x += __shfl_down_sync(0xffffffffu, tot.x, 4 * NP);
-        tot.y += __shfl_down_sync(0xffffffffu, tot.y, 4 * NP);
-        if (lane < 4 * NP) {
-          const int rr = i / NP, p = i % NP;
-          const int lr = c * MV_CHUNK + warp * 4 + rr;
-          part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = tot;
+          ffma2(s0, s1, one);
+          float2 tot = up2(s0);
+          tot.x += __shfl_down_sync(0xffffffffu, tot.x, 4 * NP);
+          tot.y += __shfl_down_sync(0xffffffffu, tot.y, 4 * NP);
+          if (lane < 4 * NP) {
+            const int rr = i / NP, p = i % NP;
+            const int lr = c * MV_CHUNK + warp * 4 + rr;
+            part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = tot;
+          }
+        } else {
+          // more pairs (4 NP) than half-warps can cover: lane i < 4 NP sums pair i over all
+          // 32 lanes in two interleaved chains
+          for (int i = lane; i < 4 * NP; i += 32) {
+            const float *src = red + 2 * i;
+            unsigned long long s0 = 0ull, s1 = 0ull;
+            const unsigned long long one = pk2(1.f, 1.f);
+#pragma unroll
+            for (int k = 0; k < 32; k += 2) {
+              const float2 v0 = *reinterpret_cast<const float2 *>(src + k * S::RSTR);
+              const float2 v1 = *reinterpret_cast<const float2 *>(src + (k + 1) * S::RSTR);
+              ffma2(s0, pk2(v0.x, v0.y), one);
+              ffma2(s1, pk2(v1.x, v1.y), one);
+            }
+            ffma2(s0, s1, one);
+            const int rr = i / NP, p = i % NP;
+            const int lr = c * MV_CHUNK + warp * 4 + rr;
+            part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = up2(s0);
+          }
         }
         __syncwarp();
       }
@@ -634,8 +656,9 @@ constexpr int hmv_tma_smem() {
 // the two halves of the block's slot slab; each keeps a compensated (Kahan) FP32 sum, so the
 // result carries FP64-like accuracy without FP64 adds (B300's FP64 rate is ~1/60 of FP32),
 // and the two halves meet in FP64 in a fixed order.
-template <int NP>
-__global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__restrict__ part, long long dim,
+// HALVES = 1 (more than four vectors): one thread per output streams the whole slab.
+template <int NP, int HALVES = 2>
+__global__ void __launch_bounds__(HALVES * HT * NP, 1) k_hmv_reduce(const float2 *__restrict__ part, long long dim,
                                                                 int nb, double2 *__restrict__ W,
                                                                 const double2 *__restrict__ Q, long long qs, int j,
                                                                 const int *__restrict__ meff, double *__restrict__ apart) {
@@ -646,7 +669,7 @@ __global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__r
   const int l = o / NP, p = o % NP;
   const long long row = (long long)t * HT + l;
   const bool on = row < dim && j < meff[p];
-  const int s0 = h ? nb / 2 : 0, s1 = h ? nb : nb / 2;
+  const int s0 = h ? nb / 2 : 0, s1 = (h || HALVES == 1) ? nb : nb / 2;
   // Kahan: sum + (-comp) is the running total; each add is y = v - comp; t = sum + y;
   // comp = (t - sum) - y; sum = t
   float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
@@ -684,8 +707,10 @@ __global__ void __launch_bounds__(2 * HT * NP, 1) k_hmv_reduce(const float2 *__r
   if (!h) {
     double ar = 0.0;
     if (on) {
-      tx += hs[o].x;
-      ty += hs[o].y;
+      if (HALVES == 2) {
+        tx += hs[o].x;
+        ty += hs[o].y;
+      }
       W[(long long)p * dim + row] = make_double2(tx, ty);
       const double2 q = Q[p * qs + (long long)j * dim + row];
       ar = q.x * tx + q.y * ty;
@@ -1674,9 +1699,9 @@ __global__ void __launch_bounds__(256) k_real_cgemm(const double *__restrict__ A
 struct HalfMV {
   int nbt = 0, ntiles = 0;
   int2 *tiles = nullptr;
-  float2 *part = nullptr;   // [nbt][nbt][HT][3]
-  int *ones = nullptr;      // [3] recursion lengths for the kernels' liveness test (all live)
-  double *apart = nullptr;  // [3][nbt] (unused alpha partials of the reduction)
+  float2 *part = nullptr;   // [nbt][nbt][HT][6]
+  int *ones = nullptr;      // [6] recursion lengths for the kernels' liveness test (all live)
+  double *apart = nullptr;  // [6][nbt] (unused alpha partials of the reduction)
   double2 *Qdummy = nullptr;
 };
 
@@ -1690,16 +1715,16 @@ bse_status halfmv_alloc(bse_ctx *c, HalfMV **out) {
   for (int bi = 0; bi < h->nbt; bi++)
     for (int bj = bi; bj < h->nbt; bj++) tl.push_back(make_int2(bi, bj));
   h->ntiles = (int)tl.size();
-  const int ones[3] = {1, 1, 1};
+  const int ones[6] = {1, 1, 1, 1, 1, 1};
   cudaStream_t st = c->stream;
-  if (cudaMallocAsync((void **)&h->part, sizeof(float2) * (size_t)h->nbt * h->nbt * HT * 3, st) != cudaSuccess ||
+  if (cudaMallocAsync((void **)&h->part, sizeof(float2) * (size_t)h->nbt * h->nbt * HT * 6, st) != cudaSuccess ||
       cudaMallocAsync((void **)&h->tiles, sizeof(int2) * tl.size(), st) != cudaSuccess ||
-      cudaMallocAsync((void **)&h->ones, sizeof(int) * 3, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&h->apart, sizeof(double) * 3 * h->nbt, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&h->Qdummy, sizeof(double2) * 3 * dim, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->ones, sizeof(int) * 6, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->apart, sizeof(double) * 6 * h->nbt, st) != cudaSuccess ||
+      cudaMallocAsync((void **)&h->Qdummy, sizeof(double2) * 6 * dim, st) != cudaSuccess ||
       cudaMemcpyAsync(h->tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(h->ones, ones, sizeof(ones), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(h->Qdummy, 0, sizeof(double2) * 3 * dim, st) != cudaSuccess ||
+      cudaMemsetAsync(h->Qdummy, 0, sizeof(double2) * 6 * dim, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     halfmv_release(c, h);
@@ -1713,6 +1738,10 @@ bse_status halfmv_alloc(bse_ctx *c, HalfMV **out) {
     cudaFuncSetAttribute(k_hmv_tma<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
     cudaFuncSetAttribute(k_hmv_tma<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
     cudaFuncSetAttribute(k_hmv_tma<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
+    cudaFuncSetAttribute(k_hmv_tma<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<4>());
+    cudaFuncSetAttribute(k_hmv_tma<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<4>());
+    cudaFuncSetAttribute(k_hmv_tma<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<6>());
+    cudaFuncSetAttribute(k_hmv_tma<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<6>());
     attr = true;
   }
   *out = h;
@@ -1727,28 +1756,37 @@ void halfmv_release(bse_ctx *c, HalfMV *h) {
   delete h;
 }
 
-// W[p] = Hm Z[p] (p < np <= 3) for a complex64 Hm, Hermitian (sym = false) or complex
-// symmetric (sym = true), reading only its upper-triangle 128 x 128 tiles.  Z [np][dim]
-// complex64, W [np][dim] complex128.
+// W[p] = Hm Z[p] (np in 1, 2, 3, 4, 6) for a complex64 Hm, Hermitian (sym = false) or
+// complex symmetric (sym = true), reading only its upper-triangle 128 x 128 tiles once for
+// all np vectors.  Z [np][dim] complex64, W [np][dim] complex128.
 bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const float2 *Z, int np, double2 *W) {
   const long long dim = c->dim;
   CUtensorMap tm;
   if (!encode_rows_f32(&tm, Hm, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK))
     return bse_fail(c, BSE_ECUDA, "half-read product: tensor map encoding failed");
   cudaStream_t st = c->stream;
-  const int grid = std::min(h->ntiles, MV_CTAS * c->n_sm);
+  const int grid = std::min(h->ntiles, (np <= 3 ? MV_CTAS : 2) * c->n_sm);  // resident CTAs per SM
   bse_prof_begin(c, BSE_KP_MATVEC);
 #define HALF_LAUNCH(NPV, SYMV)                                                                                 \
   k_hmv_tma<NPV, SYMV><<<grid, 128, hmv_tma_smem<NPV>(), st>>>(tm, dim, h->nbt, h->tiles, h->ntiles, Z, dim, 0, \
                                                              h->part, h->ones, c->d_err)
+  if (np != 1 && np != 2 && np != 3 && np != 4 && np != 6)
+    return bse_fail(c, BSE_EINVAL, "half-read product: unsupported vector count");
   if (np == 1) { if (sym) HALF_LAUNCH(1, true); else HALF_LAUNCH(1, false); }
   else if (np == 2) { if (sym) HALF_LAUNCH(2, true); else HALF_LAUNCH(2, false); }
-  else { if (sym) HALF_LAUNCH(3, true); else HALF_LAUNCH(3, false); }
+  else if (np == 3) { if (sym) HALF_LAUNCH(3, true); else HALF_LAUNCH(3, false); }
+  else if (np == 4) { if (sym) HALF_LAUNCH(4, true); else HALF_LAUNCH(4, false); }
+  else { if (sym) HALF_LAUNCH(6, true); else HALF_LAUNCH(6, false); }
 #undef HALF_LAUNCH
   bse_prof_end(c, BSE_KP_MATVEC);
-  if (np == 1) k_hmv_reduce<1><<<h->nbt, 2 * HT * 1, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
-  else if (np == 2) k_hmv_reduce<2><<<h->nbt, 2 * HT * 2, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
-  else k_hmv_reduce<3><<<h->nbt, 2 * HT * 3, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart);
+#define HALF_REDUCE(NPV, HV) \
+  k_hmv_reduce<NPV, HV><<<h->nbt, HV * HT * NPV, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart)
+  if (np == 1) HALF_REDUCE(1, 2);
+  else if (np == 2) HALF_REDUCE(2, 2);
+  else if (np == 3) HALF_REDUCE(3, 2);
+  else if (np == 4) HALF_REDUCE(4, 2);
+  else HALF_REDUCE(6, 1);
+#undef HALF_REDUCE
   bse_count_launch(2);
   return bse_check_launch(c, "half-read product");
 }

@@ -86,3 +86,16 @@ def test_null_context_calls_are_safe(lib):
     assert lib.bse_sync(None) == _lib.BSE_EINVAL
     assert lib.bse_assemble(None, None) == _lib.BSE_EINVAL
     assert lib.bse_launch_count() >= 0
+
+
+def test_extension_entries_reject_null_context(lib):
+    """The full-BSE, finite-momentum, matrix-free and V(q) entries refuse a null context
+    before touching the device."""
+    from paper_2607_05853_b300 import _lib
+    q = (ctypes.c_int32 * 3)(1, 0, 0)
+    assert lib.bse_set_momentum(None, ctypes.cast(q, ctypes.c_void_p), None) == _lib.BSE_EINVAL
+    assert lib.bse_assemble_coupling(None, None) == _lib.BSE_EINVAL
+    assert lib.bse_spectrum_full(None, None, None, None, 1, 2, None, 1, 0.1, 1.0, None) == _lib.BSE_EINVAL
+    assert lib.bse_lowest_full(None, None, None, 1, 2, 1, None, None) == _lib.BSE_EINVAL
+    assert lib.bse_spectrum_matfree(None, None, 1, 2, None, 1, 0.1, 1.0, None, None) == _lib.BSE_EINVAL
+    assert lib.bse_interp_V(None, None, None) == _lib.BSE_EINVAL

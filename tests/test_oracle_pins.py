@@ -719,3 +719,16 @@ def test_full_bse_planted_coupling_mistake_is_caught(monkeypatch):
     p2 = (c[k1][:, nv + a], kf[k1], c[k2][:, j], kf[k2])
     bd = _brute_kernel(inp, kf, nk, mesh, p1, p2, inp["R_W"], inp["w_RW"], inp["W_R"])
     assert abs(bd - orc.coupling_direct(k1, k2)[i, a, j, b]) > 1e-6 * abs(bd)
+
+
+@pytest.mark.parametrize("Q", [(1, 0, 0), (1, 1, 0)])
+def test_finite_Q_time_reversal(Q):
+    """Real hoppings, real C(R), W(R), Vbar(R) and a mesh closed under k -> -k: time reversal
+    maps the pair (v k, c k+Q) to (v -k, c -k-Q), a pair of momentum -Q, so H(-Q) is
+    gauge-equivalent to conj H(Q) and the exciton dispersion is even, Omega_S(Q) = Omega_S(-Q)."""
+    spec = dataclasses.replace(tiny_spec(), k_offset=(0.0, 0.0, 0.0))
+    inp = make_inputs(spec)
+    mQ = tuple(int(x) for x in np.mod(-np.asarray(Q), np.asarray(spec.dense)))
+    e1 = np.linalg.eigvalsh(O.BSEOracle(inp, Q=Q).hamiltonian())
+    e2 = np.linalg.eigvalsh(O.BSEOracle(inp, Q=mQ).hamiltonian())
+    assert np.abs(e1 - e2).max() <= 1e-12 * np.abs(e1).max()

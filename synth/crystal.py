@@ -20,7 +20,8 @@ Recipe (seed = 20260000 + config unless given):
 * V0 = s_V L_V L_V^T / N_aux with L_V real Gaussian (symmetric positive semidefinite), and
   a bare V(R) on the R-set of W whose weighted sum is V0 (V(q) = V0 + a smooth PSD term
   that vanishes at q = 0);
-* velocities from the tight-binding derivative sum_R i R_cart h(R) e^{2 pi i k.R}.
+* velocities from the tight-binding derivative sum_R i R_cart h(R) e^{2 pi i k.R}; the
+  model itself (R_h, h_R, n_occ) is returned too, so that tests can rebuild h(k).
 
 None of the method's own arithmetic (dense-mesh interpolation, pair projection, kernel
 contraction, spectrum) is done here.
@@ -311,4 +312,5 @@ def make_inputs(spec: CrystalSpec, *, W_zero: bool = False, V_zero: bool = False
         R_C=R_C.astype(np.int32), C_R=C_R,
         R_W=R_W.astype(np.int32), w_RW=w_RW, W_R=W_R, W_q_coarse=Wq, q_coarse=qc,
         V0=V0, V_R=V_R, V_q_coarse=Vq, c_k=c_k, e_ks=e_ks, e_qp=e_qp, vel=vel,
+        R_h=R_h.astype(np.int32), h_R=hR, n_occ=n_occ,
     )

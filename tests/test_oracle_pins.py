@@ -198,6 +198,70 @@ def test_binding_energy_in_paper_range(cfg0):
     assert 0.1 <= eb <= 0.3
 
 
+def test_binding_energy_ipa_limit_and_definition():
+    """E_B = min_k (E_c - E_v) - Omega_1 (§IV): zero in the independent-particle limit, where
+    Omega_1 is the smallest pair energy (LAPACK on the W = V = 0 Hamiltonian), and it moves
+    by -delta when the lowest exciton alone is lowered by delta (a rank-one shift)."""
+    inp = make_inputs(config_spec(0), W_zero=True, V_zero=True)
+    H = O.BSEOracle(inp).hamiltonian()
+    w, X = np.linalg.eigh(H)
+    assert abs(O.binding_energy(inp["e_qp"], 4, w[0])) <= 1e-12
+    x = X[:, 0]
+    w2 = np.linalg.eigvalsh(H - 0.25 * np.outer(x, x.conj()))
+    assert abs(O.binding_energy(inp["e_qp"], 4, w2[0]) - 0.25) <= 1e-12
+
+
+def _tb_bands(inp, k, dK):
+    """Window bands of the generator's tight-binding h(k) at fractional k shifted by the
+    Cartesian dK (1/Angstrom): h = sum_R h(R) exp(i (2 pi k.R + dK.R_cart))."""
+    R = inp["R_h"].astype(np.float64)
+    ph = np.exp(1j * (TWO_PI * (R @ k) + (R @ inp["lattice"]) @ dK))
+    hk = np.einsum("r,rst->st", ph, inp["h_R"])
+    E, U = np.linalg.eigh(0.5 * (hk + hk.conj().T))
+    n_occ, nv, nc = int(inp["n_occ"]), int(inp["nv"]), int(inp["nc"])
+    cols = [n_occ - 1 - v for v in range(nv)] + [n_occ + c for c in range(nc)]
+    return E[cols], U[:, cols]
+
+
+@pytest.mark.parametrize("cfg", [0, 4])
+def test_dipoles_equal_band_derivative_overlaps(cfg):
+    """Eq. abs_vel's d = <ik|v|ak>/(E^KS_a - E^KS_i) with v = dh/dk is, by first-order
+    perturbation theory of h(k)|a> = E_a|a>, the overlap <i|d a/dk> of the valence state with
+    the k-derivative of the conduction state.  That derivative is taken here by central
+    differences of eigenvectors of the rebuilt h(k +- delta) in a parallel-transport gauge
+    (<a(k)|a(k +- delta)> real positive), so neither the velocity nor an energy denominator
+    enters: E^QP in place of E^KS in the denominator (a 0.5 eV scissor on 3-7 eV gaps) or
+    swapped band indices (<a|d i> = -conj <i|d a>) fail this."""
+    spec = config_spec(cfg)
+    if cfg == 4:
+        spec = dataclasses.replace(spec, dense=(5, 4, 1), nao=(3, 3, 3), naux=(4, 4, 4))
+    inp = make_inputs(spec)
+    orc = O.BSEOracle(inp)
+    d = orc.dipoles().reshape(3, orc.nk, orc.nv, orc.nc)
+    nv, h = orc.nv, 1e-5
+    worst = scale = 0.0
+    axes = (0, 1) if cfg == 4 else (0, 1, 2)
+    for ik in range(0, orc.nk, 3):
+        k = orc.kfrac[ik]
+        E0, U0 = _tb_bands(inp, k, np.zeros(3))
+        assert np.allclose(np.abs(np.einsum("sn,sn->n", U0.conj(), inp["c_k"][ik])), 1.0, atol=1e-10)
+        for a in axes:
+            e = np.zeros(3)
+            e[a] = h
+
+            def gauge(U):
+                ov = np.einsum("sn,sn->n", U0.conj(), U)
+                return U * (np.abs(ov) / ov)[None, :]
+            dU = (gauge(_tb_bands(inp, k, e)[1]) - gauge(_tb_bands(inp, k, -e)[1])) / (2 * h)
+            # <i|d a> in the gauge of the generator's c_k (its phases relative to U0)
+            ph = np.einsum("sn,sn->n", U0.conj(), inp["c_k"][ik])
+            fd = np.conj(ph[:nv])[:, None] * (U0[:, :nv].conj().T @ dU[:, nv:]) * ph[None, nv:]
+            worst = max(worst, np.abs(fd - d[a, ik]).max())
+            scale = max(scale, np.abs(d[a, ik]).max())
+    assert scale > 0.05
+    assert worst <= 1e-7 * scale, worst / scale
+
+
 # ---------------------------------------------------------------- a4 spectrum
 def test_haydock_full_length_equals_exact(cfg0):
     inp, orc, H = cfg0

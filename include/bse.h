@@ -229,7 +229,8 @@ bse_status bse_spectrum_add(bse_ctx *ctx, const void *H, const double *u, int n_
  * n_pol * (n_steps + 1) * dim * 24 bytes plus the matvec partials) return BSE_EINVAL with the
  * size in bse_last_error, before anything is enqueued.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  No call allocates or frees memory.  All calls
+ * first call before any stream capture.  No call allocates or frees memory, and none waits
+ * for the device: the work is enqueued on the context's stream as bse_spectrum's is.  All calls
  * share the one array and it keeps the last call's contents (every value the recursion
  * reads is written by the same call first); calls that overlap on the GPU -- two streams or
  * two contexts on one device at once -- race on it, so serialise them. */
@@ -251,7 +252,8 @@ bse_status bse_lowest(bse_ctx *ctx, const void *H, int n_eig, int n_steps, uint6
  *  vecs : [r][dim] complex128 (e.g. Ritz vectors from bse_lowest);  g : [r] float64. */
 bse_status bse_adjoint_seed(bse_ctx *ctx, const double *vecs, const double *g, int r, double *Gamma);
 
-/* Adjoint seed of the windowed absorption integral (scope row a8): with the Lorentzian of
+/* Adjoint seed of the windowed absorption integral (the spectrum of Eq. abs_vel, §II.C,
+ * integrated over a frequency window; differentiated through Eq. Hamiltonian): with the Lorentzian of
  * Eq. abs_vel (half width eta) integrated over [w_lo, w_hi],
  *   I = prefactor * sum_p u_p^dagger f(H) u_p,
  *   f(x) = (1/pi) [atan((w_hi - x)/eta) - atan((w_lo - x)/eta)],
@@ -299,8 +301,25 @@ void bse_batch_release(void);
  * (N_aux, rows per q, q per slab, pieces) for the life of the process.  Synchronous. */
 bse_status bse_autotune(bse_ctx *ctx, int *chosen_tile);
 
-/* Wait for the context's stream, then read and clear the device error word. */
-bse_status bse_sync(bse_ctx *ctx);
+/* Wait for the context's stream, then read and clear the device error word.
+ *  timeout_ms >= 0: poll the stream for at most that many milliseconds (host clock); if its
+ *                   work has not finished by then, return BSE_ETIMEOUT without touching the
+ *                   error word -- the work keeps running and bse_sync may be called again;
+ *  timeout_ms < 0 : wait without a limit.
+ * After the work is done: BSE_ETIMEOUT if a bounded device-side wait gave up, BSE_EDEVICE if a
+ * device-side check failed (see bse_last_error), BSE_ECUDA if the stream reported an error. */
+bse_status bse_sync(bse_ctx *ctx, int32_t timeout_ms);
+
+/* Failure-detection self tests (host-side and bounded; neither faults nor hangs the GPU):
+ *  bse_selftest_delay enqueues on the context's stream a host function that sleeps `ms`
+ *  (0..60000) milliseconds, so the stream stays busy for that long (a bse_sync with a shorter
+ *  timeout returns BSE_ETIMEOUT);
+ *  bse_selftest_wait launches one block that waits, through the same bounded mbarrier wait as
+ *  the tensor-core and matvec pipelines, on a barrier nothing completes; after `cycles`
+ *  (1..4e9) clock cycles it gives up and sets the error word, and the next bse_sync returns
+ *  BSE_ETIMEOUT with the context still usable.  The paper has no counterpart. */
+bse_status bse_selftest_delay(bse_ctx *ctx, int32_t ms);
+bse_status bse_selftest_wait(bse_ctx *ctx, int64_t cycles);
 
 /* Text of the last error on this context (never NULL; "" when none). */
 const char *bse_last_error(const bse_ctx *ctx);

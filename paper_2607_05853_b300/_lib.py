@@ -19,7 +19,7 @@ EXPORTS = ["bse_setup", "bse_interp_W", "bse_project_pairs", "bse_assemble", "bs
            "bse_spectrum_static", "bse_adjoint_seed", "bse_adjoint", "bse_batch_assemble",
            "bse_batch_release", "bse_autotune", "bse_window_seed", "bse_spectrum_add", "bse_interp_V",
            "bse_set_momentum", "bse_assemble_coupling", "bse_spectrum_full", "bse_lowest_full",
-           "bse_spectrum_matfree"]
+           "bse_spectrum_matfree", "bse_selftest_delay", "bse_selftest_wait"]
 KERNEL_IDS = {"interp": 0, "half": 1, "project": 2, "g1": 3, "g2": 4, "exch": 5, "matvec": 6, "reorth": 7}
 
 
@@ -84,7 +84,11 @@ def load() -> ctypes.CDLL:
     lib.bse_batch_release.restype = None
     lib.bse_autotune.argtypes = [vp, POINTER(c_int)]
     lib.bse_autotune.restype = c_int
-    lib.bse_sync.argtypes = [vp]
+    lib.bse_sync.argtypes = [vp, c_int32]
+    lib.bse_selftest_delay.argtypes = [vp, c_int32]
+    lib.bse_selftest_delay.restype = c_int
+    lib.bse_selftest_wait.argtypes = [vp, c_int64]
+    lib.bse_selftest_wait.restype = c_int
     lib.bse_last_error.argtypes = [vp]
     lib.bse_last_error.restype = ctypes.c_char_p
     lib.bse_dim.argtypes = [vp]

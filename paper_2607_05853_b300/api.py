@@ -296,8 +296,17 @@ class BSE:
         self._check(self._lib.bse_autotune(self._ctx, ctypes.byref(chosen)), "bse_autotune")
         return chosen.value
 
-    def sync(self):
-        self._check(self._lib.bse_sync(self._ctx), "bse_sync")
+    def sync(self, timeout_ms: int = 600_000):
+        """bse_sync: wait (at most timeout_ms; negative = no limit) and read the error word."""
+        self._check(self._lib.bse_sync(self._ctx, int(timeout_ms)), "bse_sync")
+
+    def selftest_delay(self, ms: int):
+        """bse_selftest_delay: keep the stream busy for ms milliseconds (a host function)."""
+        self._check(self._lib.bse_selftest_delay(self._ctx, int(ms)), "bse_selftest_delay")
+
+    def selftest_wait(self, cycles: int):
+        """bse_selftest_wait: one bounded device wait on a barrier nothing completes."""
+        self._check(self._lib.bse_selftest_wait(self._ctx, int(cycles)), "bse_selftest_wait")
 
 
 def batch_assemble(systems, Hs, stream=None, stamps: bool = False):

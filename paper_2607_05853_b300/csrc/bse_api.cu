@@ -2,14 +2,33 @@
 // and the q-slab loop of the FP64 assembly.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <thread>
+#include <utility>
 
 #include "bse_internal.cuh"
+#include "tc_ptx.cuh"
 
 static std::atomic<long long> g_launches{0};
 void bse_count_launch(int n) { g_launches += n; }
+
+static std::mutex g_once_mu;
+static std::set<std::pair<int, int>> g_once_done;
+
+void bse_once_per_device(const bse_ctx *c, int key, void (*fn)()) {
+  std::lock_guard<std::mutex> lk(g_once_mu);
+  if (!g_once_done.insert({c->device, key}).second) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != c->device) cudaSetDevice(c->device);
+  fn();
+  if (cur != c->device && cur >= 0) cudaSetDevice(cur);
+}
 
 bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg) {
   if (c) c->err = msg;
@@ -100,6 +119,19 @@ static void release(bse_ctx *c) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   split_free(c);
+}
+
+// One mbarrier that expects an arrival nothing makes: the bounded wait of the library's
+// tensor-core and matvec pipelines (tc::mbar_wait_bounded) runs out after `cycles` clock
+// cycles, and the kernel records BSE_DERR_TIMEOUT in the error word as they do.
+__global__ void k_selftest_wait(long long cycles, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait_bounded(&bar, 0, cycles)) atomicOr(err, BSE_DERR_TIMEOUT);
 }
 
 extern "C" {
@@ -502,10 +534,28 @@ bse_status bse_adjoint(bse_ctx *c, const double *Gamma, double *dW_R, double *de
   return run_adjoint(c, (const double2 *)Gamma, dW_R, de_qp);
 }
 
-bse_status bse_sync(bse_ctx *c) {
+bse_status bse_sync(bse_ctx *c, int32_t timeout_ms) {
   if (!c) return BSE_EINVAL;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return bse_fail(c, BSE_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+  if (timeout_ms < 0) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return bse_fail(c, BSE_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+  } else {
+    // poll the stream until its work is done or the host-side deadline passes; the work is
+    // left running on a timeout, so a later call can wait for it again
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      const cudaError_t e = cudaStreamQuery(c->stream);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return bse_fail(c, BSE_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+      const auto ms =
+          std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+      if (ms >= timeout_ms)
+        return bse_fail(c, BSE_ETIMEOUT,
+                        "sync: the stream's work did not finish within " + std::to_string(timeout_ms) +
+                            " ms (it keeps running; bse_sync may be called again)");
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
   int w = 0;
   if (cudaMemcpy(&w, c->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess)
@@ -515,6 +565,24 @@ bse_status bse_sync(bse_ctx *c) {
     return bse_fail(c, BSE_EDEVICE, "full BSE: [[A, B], [B*, A*]] is not positive definite (unstable excitations)");
   if (w) return bse_fail(c, BSE_EDEVICE, "device check failed, code " + std::to_string(w));
   return BSE_OK;
+}
+
+static void CUDART_CB host_delay(void *ms) { std::this_thread::sleep_for(std::chrono::milliseconds((intptr_t)ms)); }
+
+bse_status bse_selftest_delay(bse_ctx *c, int32_t ms) {
+  if (!c) return BSE_EINVAL;
+  if (ms < 0 || ms > 60000) return bse_fail(c, BSE_EINVAL, "selftest_delay: 0 <= ms <= 60000");
+  if (cudaLaunchHostFunc(c->stream, host_delay, (void *)(intptr_t)ms) != cudaSuccess)
+    return bse_fail(c, BSE_ECUDA, "selftest_delay: cudaLaunchHostFunc failed");
+  return BSE_OK;
+}
+
+bse_status bse_selftest_wait(bse_ctx *c, int64_t cycles) {
+  if (!c) return BSE_EINVAL;
+  if (cycles < 1 || cycles > 4000000000LL) return bse_fail(c, BSE_EINVAL, "selftest_wait: 1 <= cycles <= 4e9");
+  k_selftest_wait<<<1, 32, 0, c->stream>>>(cycles, c->d_err);
+  bse_count_launch();
+  return bse_check_launch(c, "selftest_wait");
 }
 
 bse_status bse_profile(bse_ctx *c, int enable) {

@@ -92,6 +92,11 @@ void bse_prof_end(bse_ctx *c, int id);
 
 // ---- helpers shared by the .cu files --------------------------------------------------
 void bse_count_launch(int n = 1);
+// Per-device one-time set-up (kernel attributes such as the dynamic shared-memory limit are
+// per device): the first call for (the context's device, key) in this process runs `fn`
+// with that device current; every call returns only after it has run (thread-safe).
+enum { BSE_ONCE_HMV_TDA = 0, BSE_ONCE_HMV_ALL = 1, BSE_ONCE_SPLIT = 2, BSE_ONCE_KEYS = 3 };
+void bse_once_per_device(const bse_ctx *c, int key, void (*fn)());
 bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg);
 bse_status bse_check_launch(bse_ctx *c, const char *what);
 

@@ -1166,6 +1166,21 @@ bool encode_rows_f32(CUtensorMap *m, const void *base, unsigned long long inner,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Upper-triangle tile list of the half-read matvec, (bi, bj) for bj >= bi in row order, written
+// on the device (no host copy, no stream synchronisation): thread bi writes its row, which
+// starts at bi nbt - bi (bi - 1) / 2.
+__global__ void k_fill_tiles(int nbt, int2 *__restrict__ tiles) {
+  const int bi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bi >= nbt) return;
+  const long long off = (long long)bi * nbt - (long long)bi * (bi - 1) / 2;
+  for (int bj = bi; bj < nbt; bj++) tiles[off + bj - bi] = make_int2(bi, bj);
+}
+
+void fill_tiles(bse_ctx *c, int nbt, int2 *tiles) {
+  k_fill_tiles<<<(nbt + 127) / 128, 128, 0, c->stream>>>(nbt, tiles);
+  bse_count_launch();
+}
+
 struct LanczosScratch {
   double2 *Q = nullptr, *W = nullptr, *coef = nullptr;
   float2 *Q32 = nullptr;  // FP32 shadow of Q (complex64 H only): reorthogonalisation projections
@@ -1214,16 +1229,12 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, 
       cudaGetLastError();
       return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
     }
-    std::vector<int2> tl;
-    for (int bi = 0; bi < s.nbt; bi++)
-      for (int bj = bi; bj < s.nbt; bj++) tl.push_back(make_int2(bi, bj));
-    s.ntiles = (int)tl.size();
-    if (cudaMallocAsync((void **)&s.tiles, sizeof(int2) * tl.size(), st) != cudaSuccess ||
-        cudaMemcpyAsync(s.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
+    s.ntiles = s.nbt * (s.nbt + 1) / 2;
+    if (cudaMallocAsync((void **)&s.tiles, sizeof(int2) * s.ntiles, st) != cudaSuccess) {
       cudaGetLastError();
       return bse_fail(c, BSE_ENOMEM, "spectrum: tile list allocation failed");
     }
+    fill_tiles(c, s.nbt, s.tiles);
   }
   return BSE_OK;
 }
@@ -1246,15 +1257,12 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const bool c64 = c->precision != BSE_FP64;
   if (c64 && s.hpart && s.tiles) {
     s.tma = encode_rows_f32(&s.tmH, H, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK);
-    if (s.tma) {
-      static bool attr = false;
-      if (!attr) {
+    if (s.tma)
+      bse_once_per_device(c, BSE_ONCE_HMV_TDA, [] {
         cudaFuncSetAttribute(k_hmv_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
         cudaFuncSetAttribute(k_hmv_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
         cudaFuncSetAttribute(k_hmv_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
-        attr = true;
-      }
-    }
+      });
   }
   // max |H| (matrix-free: twice the largest band energy)
   if (matfree) {
@@ -1730,8 +1738,7 @@ bse_status halfmv_alloc(bse_ctx *c, HalfMV **out) {
     halfmv_release(c, h);
     return bse_fail(c, BSE_ENOMEM, "half-read product scratch allocation failed");
   }
-  static bool attr = false;
-  if (!attr) {
+  bse_once_per_device(c, BSE_ONCE_HMV_ALL, [] {
     cudaFuncSetAttribute(k_hmv_tma<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<1>());
     cudaFuncSetAttribute(k_hmv_tma<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<2>());
     cudaFuncSetAttribute(k_hmv_tma<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<3>());
@@ -1742,8 +1749,7 @@ bse_status halfmv_alloc(bse_ctx *c, HalfMV **out) {
     cudaFuncSetAttribute(k_hmv_tma<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<4>());
     cudaFuncSetAttribute(k_hmv_tma<6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<6>());
     cudaFuncSetAttribute(k_hmv_tma<6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, hmv_tma_smem<6>());
-    attr = true;
-  }
+  });
   *out = h;
   return BSE_OK;
 }
@@ -1941,16 +1947,7 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
   if (r != BSE_OK) return r;
   LanczosScratch s;
   carve_scratch(c, s, n_pol, n_steps, base);
-  if (s.tiles) {
-    std::vector<int2> tl;
-    tl.reserve(s.ntiles);
-    for (int bi = 0; bi < s.nbt; bi++)
-      for (int bj = bi; bj < s.nbt; bj++) tl.push_back(make_int2(bi, bj));
-    if (cudaMemcpyAsync(s.tiles, tl.data(), sizeof(int2) * tl.size(), cudaMemcpyHostToDevice, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-      return bse_fail(c, BSE_ECUDA, "spectrum_static: tile list upload failed");
-  }
+  if (s.tiles) fill_tiles(c, s.nbt, s.tiles);
   r = lanczos_run(c, s, H, u, n_pol, n_steps);
   if (r != BSE_OK) return r;
   k_contfrac<<<(n_w + 127) / 128, 128, 0, c->stream>>>(s.a, s.b, n_steps + 1, s.beta0, s.meff, n_pol, omega, n_w, eta,

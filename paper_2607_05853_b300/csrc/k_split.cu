@@ -1429,16 +1429,14 @@ void set_g2_attr() {
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
-void set_all_attrs() {
-  static bool done = false;
-  if (done) return;
+void set_all_attrs_now() {
   set_g2_attr<2, 2>(); set_g2_attr<2, 4>(); set_g2_attr<2, 6>(); set_g2_attr<4, 2>(); set_g2_attr<4, 4>();
   set_g2_attr<4, 6>(); set_g2_attr<6, 2>(); set_g2_attr<6, 4>(); set_g2_attr<6, 6>();
   set_attr<1, 64>(); set_attr<1, 96>(); set_attr<1, 128>(); set_attr<1, 160>();
   set_attr<2, 64>(); set_attr<2, 96>(); set_attr<2, 128>(); set_attr<2, 160>();
   set_attr<3, 64>(); set_attr<3, 96>(); set_attr<3, 128>(); set_attr<3, 160>();
-  done = true;
 }
+void set_all_attrs(const bse_ctx *c) { bse_once_per_device(c, BSE_ONCE_SPLIT, set_all_attrs_now); }
 
 }  // namespace
 
@@ -1485,7 +1483,7 @@ bse_status split_setup(bse_ctx *c) {
         c->koff[1], c->koff[2], w->PHQ, w->PHK);
     bse_count_launch();
   }
-  set_all_attrs();
+  set_all_attrs(c);
   bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
             make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
             make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&

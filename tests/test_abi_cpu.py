@@ -83,7 +83,9 @@ def test_null_context_calls_are_safe(lib):
     lib.bse_free(None)
     assert lib.bse_last_error(None) == b"null context"
     assert lib.bse_dim(None) == -1
-    assert lib.bse_sync(None) == _lib.BSE_EINVAL
+    assert lib.bse_sync(None, 0) == _lib.BSE_EINVAL
+    assert lib.bse_selftest_delay(None, 1) == _lib.BSE_EINVAL
+    assert lib.bse_selftest_wait(None, 1) == _lib.BSE_EINVAL
     assert lib.bse_assemble(None, None) == _lib.BSE_EINVAL
     assert lib.bse_launch_count() >= 0
 

@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from synth import config_spec, make_inputs
 
-from helpers import to_dev
+from helpers import to_dev, assert_split_close
 from test_gpu_fp64 import RAGGED, REL
 
 pytestmark = pytest.mark.gpu
@@ -48,9 +48,8 @@ def test_finite_Q_hamiltonian_matches_oracle(name, Q):
     assert np.abs(H - H.conj().T).max() <= 1e-13 * scale
 
 
-# split precisions: the bound of the Q = 0 split tests (4e-6 x max|H| for bf16x3 and
-# bf16x2, 1e-4 for bf16x1); Q enters only through indices and the FP32 complex V
-SPLIT_TOL = {"bf16x3": 4e-6, "bf16x2": 4e-6, "bf16x1": 1e-4}
+# split precisions: the off-diagonal / diagonal bounds of the Q = 0 split tests
+# (tests/helpers.py); Q enters only through indices and the FP32 complex V
 
 
 @pytest.mark.parametrize("prec,name,Q", [("bf16x3", "cfg0", (1, 1, 0)), ("bf16x3", "cfg0", (2, 2, 2)),
@@ -60,9 +59,7 @@ def test_finite_Q_split_matches_oracle(prec, name, Q):
     inp = _inputs(name)
     ref = O.BSEOracle(inp, Q=Q).hamiltonian()
     b, d, H = _gpu_HQ(inp, Q, precision=prec)
-    H = H.cpu().numpy().astype(np.complex128)
-    scale = np.abs(ref).max()
-    assert np.abs(H - ref).max() <= SPLIT_TOL[prec] * scale
+    assert_split_close(H.cpu().numpy(), ref, prec)
 
 
 def test_finite_Q_triplet_without_V_R():

@@ -76,6 +76,27 @@ def test_window_seed_split_forward(cfg0):
     assert np.linalg.norm(de - de_ref) <= 1e-3 * np.linalg.norm(de_ref)
 
 
+def test_window_integral_autograd_matches_oracle(cfg0):
+    """WindowIntegral.apply(...).backward(): the forward's I and the gradients that reach W_R
+    and e_qp equal the oracle's exact integral and its Daleckii-Krein gradient (FP64 path,
+    Lanczos run to full length), scaled by the incoming gradient."""
+    import torch
+    from paper_2607_05853_b300.api import BSE
+    from paper_2607_05853_b300.grad import WindowIntegral
+    from helpers import to_dev
+    inp, orc, pref, G_ref, I_ref, dW_ref, de_ref = cfg0
+    b = BSE.from_inputs(inp, precision="fp64")
+    d = to_dev(inp)
+    u = b.dipole_vector(d["vel"], d["e_ks"])
+    W = d["W_R"].clone().requires_grad_(True)
+    e = d["e_qp"].clone().requires_grad_(True)
+    I = WindowIntegral.apply(W, e, b, d, u, b.dim, LO, HI, ETA, pref)
+    (2.5 * I).backward()
+    assert abs(I.item() - I_ref) <= 1e-10 * abs(I_ref)
+    assert _rel(W.grad.cpu().numpy(), 2.5 * dW_ref) <= 1e-8
+    assert _rel(e.grad.cpu().numpy(), 2.5 * de_ref) <= 1e-8
+
+
 @pytest.mark.parametrize("name", ["ragged", "two_d"])
 def test_window_seed_ragged_shapes(name):
     inp = make_inputs(RAGGED[name])

@@ -344,7 +344,7 @@ def test_planted_oracle_mistake_is_caught(mistake, monkeypatch):
     assert _brute_error(inp, bad) > 1e-6
 
 
-# ---------------------------------------------------------------- a8 gradients
+# ---------------------------------------------------------------- gradients (Hellmann-Feynman on Eq. Hamiltonian)
 def _grad_setup():
     spec = CrystalSpec("g", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25]]), (3, 4), (7, 6), (3, 1, 1),
                        (3, 2, 1), 2, 2, 5151, k_offset=(0.1, 0.2, 0.0), r_max=1.0, s_W=0.3, s_V=0.1)
@@ -419,7 +419,7 @@ def test_gradient_euler_identity():
     assert np.isclose(np.sum(inp["W_R"] * dW), np.vdot(x, direct @ x).real, rtol=1e-10)
 
 
-# ---- windowed absorption integral (scope row a8) -------------------------------------------
+# ---- windowed absorption integral (Eq. abs_vel over a window) -----------------------------
 WIN = (1.5, 3.0)
 
 

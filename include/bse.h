@@ -72,7 +72,9 @@ typedef enum {
  *  BSE_FP64  : everything in FP64 on CUDA cores; H is complex128.
  *  BSE_BF16X3: contractions on tcgen05 tensor cores with each FP32 operand split into
  *              three bf16 pieces (6 piece products kept), FP32 accumulation; phases
- *              and the E_c - E_v diagonal in FP64; H is complex64.
+ *              and the E_c - E_v diagonal in FP64; H is complex64, or complex128 with
+ *              bse_params.h_complex128 (then the spectrum, lowest-exciton and window entries
+ *              read it with the FP64 path's full-read products).
  *  BSE_BF16X2: as BF16X3 with two pieces (3 piece products).
  *  BSE_BF16X1: one bf16 piece (1 product) -- an accuracy ablation. */
 typedef enum { BSE_FP64 = 0, BSE_BF16X3 = 1, BSE_BF16X2 = 2, BSE_BF16X1 = 3 } bse_precision;
@@ -91,6 +93,8 @@ typedef struct {
   int32_t nv, nc;                /* band window, nv + nc <= total NAOs                 */
   double alpha;                  /* 2 singlet, 0 triplet (Eq. Hamiltonian)             */
   int32_t precision;             /* a bse_precision                                   */
+  int32_t h_complex128;          /* split precisions: 1 stores H as complex128 (the    */
+                                 /* E_c - E_v diagonal then exact in FP64), 0 complex64 */
 } bse_params;
 
 /* Validate p, copy its host arrays, allocate the workspace on the current CUDA device
@@ -141,8 +145,8 @@ bse_status bse_set_momentum(bse_ctx *ctx, const int32_t *Q, const double *V_R);
 bse_status bse_project_pairs(bse_ctx *ctx, const double *C_R, const double *c_k,
                              const double *e_qp);
 
-/* Steps (b)+(c): build H.  H : [dim][dim], complex128 for BSE_FP64, complex64 for the
- * split precisions.  Every element is written. */
+/* Steps (b)+(c): build H.  H : [dim][dim], complex128 for BSE_FP64 and for the split
+ * precisions with bse_params.h_complex128, complex64 otherwise.  Every element is written. */
 bse_status bse_assemble(bse_ctx *ctx, void *H);
 
 /* Full BSE (§II.C): the coupling block
@@ -151,7 +155,8 @@ bse_status bse_assemble(bse_ctx *ctx, void *H);
  * (1/N_k) C~_{b k2, i k1} W(k1 - k2) C~_{a k1, j k2}.  B is complex symmetric (B = B^T).
  *  B : [dim][dim], rows and columns ordered as H's; complex128 for BSE_FP64, complex64 for
  *      the split precisions (tensor-core contractions as in bse_assemble).  Every element is
- *      written.  Call after bse_project_pairs.  BSE_EINVAL at Q != 0.  Workspace for the
+ *      written.  Call after bse_project_pairs.  BSE_EINVAL at Q != 0 and for a split context
+ *      with h_complex128 (the full-BSE entries take complex64 A and B).  Workspace for the
  *      conduction-valence projections is allocated on the first call. */
 bse_status bse_assemble_coupling(bse_ctx *ctx, void *B);
 
@@ -284,22 +289,25 @@ bse_status bse_window_seed(bse_ctx *ctx, const void *H, const double *u, int n_p
 bse_status bse_adjoint(bse_ctx *ctx, const double *Gamma, double *dW_R, double *de_qp);
 
 /* Batching of several crystals (one context each, every one past bse_project_pairs): their
- * assemblies run as one CUDA graph, a branch per context forked from and joined into
- * `cuda_stream`, so the GPU interleaves systems of uneven size and the host issues one
- * launch.  The first call for a given list of (context, H) runs each assembly once eagerly,
+ * assemblies run as one CUDA graph forked from and joined into `cuda_stream`, so the host
+ * issues one launch; the systems are ordered by estimated work, smallest first, and dealt to
+ * two concurrent chains, so small systems finish early instead of queueing behind large ones.  The first call for a given list of (context, H) runs each assembly once eagerly,
  * then captures and instantiates the graph; later calls with the same list replay it.
  *  H : [n] device pointers as in bse_assemble;  stamps_ns : optional host [n] receiving, for
- *  each system, the nanoseconds from the start of this replay to the end of its branch
+ *  each system, the nanoseconds from the start of this replay to the end of its assembly
  *  (the call then waits for the stream), or NULL.  Contexts must not be freed while a graph
  *  that uses them is cached; bse_batch_release drops every cached graph. */
 bse_status bse_batch_assemble(bse_ctx **ctxs, void **H, int n, void *cuda_stream, int64_t *stamps_ns);
 void bse_batch_release(void);
 
-/* Autotuner: times the tensor-core GEMM of one q-slab (T = M_vv W(q)) for each candidate
- * N tile (64, 96, 128, 160 columns), keeps the fastest for this context and reports it in
- * *chosen_tile (0 for BSE_FP64, which has no tensor-core GEMM).  Results are cached per shape
- * (N_aux, rows per q, q per slab, pieces) for the life of the process.  Synchronous. */
-bse_status bse_autotune(bse_ctx *ctx, int *chosen_tile);
+/* Autotuner (call after bse_project_pairs): times one q-slab of the pair projections for each
+ * thread-block size (warp multiples up to 160 threads and the ABF count) and the tensor-core
+ * GEMM T = M_vv W(q) of the unfused direct term for each N tile (64, 96, 128, 160 columns),
+ * keeps the fastest of each for this context and reports them in *chosen_tile and
+ * *chosen_proj_threads (either pointer may be NULL; 0 for BSE_FP64, which has neither kernel,
+ * and for a projection without a register-blocked kernel).  Results are cached per shape for
+ * the life of the process.  Synchronous. */
+bse_status bse_autotune(bse_ctx *ctx, int *chosen_tile, int *chosen_proj_threads);
 
 /* Wait for the context's stream, then read and clear the device error word.
  *  timeout_ms >= 0: poll the stream for at most that many milliseconds (host clock); if its

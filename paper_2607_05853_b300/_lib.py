@@ -39,6 +39,7 @@ class BseParams(ctypes.Structure):
         ("nc", c_int32),
         ("alpha", c_double),
         ("precision", c_int32),
+        ("h_complex128", c_int32),
     ]
 
 
@@ -82,7 +83,7 @@ def load() -> ctypes.CDLL:
     lib.bse_batch_assemble.restype = c_int
     lib.bse_batch_release.argtypes = []
     lib.bse_batch_release.restype = None
-    lib.bse_autotune.argtypes = [vp, POINTER(c_int)]
+    lib.bse_autotune.argtypes = [vp, POINTER(c_int), POINTER(c_int)]
     lib.bse_autotune.restype = c_int
     lib.bse_sync.argtypes = [vp, c_int32]
     lib.bse_selftest_delay.argtypes = [vp, c_int32]

@@ -39,7 +39,7 @@ class BSE:
     """One crystal's TDA-BSE problem bound to the current CUDA device and stream."""
 
     def __init__(self, *, nao, naux, dense, R_C, R_W, w_RW, nv, nc, k_offset=(0.0, 0.0, 0.0),
-                 alpha=2.0, precision="fp64", stream: torch.cuda.Stream | None = None):
+                 alpha=2.0, precision="fp64", h_complex128: bool = False, stream: torch.cuda.Stream | None = None):
         lib = _lib.load()
         self._lib = lib
         nao = np.ascontiguousarray(nao, np.int32)
@@ -64,6 +64,7 @@ class BSE:
         p.nv, p.nc = int(nv), int(nc)
         p.alpha = float(alpha)
         p.precision = _lib.PRECISIONS[precision]
+        p.h_complex128 = 1 if h_complex128 else 0
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = ctypes.c_void_p()
         st = lib.bse_setup(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
@@ -78,7 +79,7 @@ class BSE:
         self.nao = int(lib.bse_nao(ctx))
         self.n_RW = len(R_W)
         self.n_RC = len(R_C)
-        self.h_dtype = torch.complex128 if precision == "fp64" else torch.complex64
+        self.h_dtype = torch.complex128 if (precision == "fp64" or h_complex128) else torch.complex64
 
     @classmethod
     def from_inputs(cls, inp: dict, **kw) -> "BSE":
@@ -291,10 +292,11 @@ class BSE:
                     "bse_profile_read")
         return ms.value, n.value
 
-    def autotune(self) -> int:
-        chosen = ctypes.c_int()
-        self._check(self._lib.bse_autotune(self._ctx, ctypes.byref(chosen)), "bse_autotune")
-        return chosen.value
+    def autotune(self, with_projection: bool = False):
+        """bse_autotune: the chosen GEMM N tile (and, if asked, the projection's threads per block)."""
+        chosen, proj = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.bse_autotune(self._ctx, ctypes.byref(chosen), ctypes.byref(proj)), "bse_autotune")
+        return (chosen.value, proj.value) if with_projection else chosen.value
 
     def sync(self, timeout_ms: int = 600_000):
         """bse_sync: wait (at most timeout_ms; negative = no limit) and read the error word."""

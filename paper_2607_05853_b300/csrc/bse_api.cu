@@ -201,6 +201,7 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
   c->nvc = p->nv * p->nc;
   c->alpha = p->alpha;
   c->precision = p->precision;
+  c->h64 = p->precision == BSE_FP64 || p->h_complex128 != 0;
   c->dim = nk * c->nvc;
   c->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&c->device);
@@ -400,6 +401,9 @@ bse_status bse_assemble_coupling(bse_ctx *c, void *B) {
   if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "assemble_coupling before project_pairs");
   if (!B) return bse_fail(c, BSE_EINVAL, "assemble_coupling: null B");
   if (c->qQ != 0) return bse_fail(c, BSE_EINVAL, "assemble_coupling: the full BSE is built at Q = 0");
+  if (c->precision != BSE_FP64 && c->h64)
+    return bse_fail(c, BSE_EINVAL, "assemble_coupling: the full BSE takes the complex64 split H (h_complex128 is for the TDA entries)");
+
   if (c->precision != BSE_FP64) return split_assemble_coupling(c, B);
   const int na = c->naux_tot;
   const long long rows = (long long)c->nk * c->nvc;
@@ -473,6 +477,9 @@ bse_status bse_spectrum_full(bse_ctx *c, const void *A, const void *B, const dou
                              const double *omega, int n_w, double eta, double prefactor, double *eps2) {
   if (!c) return BSE_EINVAL;
   if (!A || !B || !u || !omega || !eps2) return bse_fail(c, BSE_EINVAL, "spectrum_full: null argument");
+  if (c->precision != BSE_FP64 && c->h64)
+    return bse_fail(c, BSE_EINVAL, "spectrum_full: the full BSE takes the complex64 split H (h_complex128 is for the TDA entries)");
+
   if (n_pol < 1 || n_pol > 3 || n_steps < 2 || n_steps > 2 * c->dim || n_steps > BSE_FULL_MAX_STEPS || n_w < 1 ||
       !(eta > 0.0) || !std::isfinite(prefactor))
     return bse_fail(c, BSE_EINVAL, "spectrum_full: bad size or parameter");
@@ -483,6 +490,9 @@ bse_status bse_lowest_full(bse_ctx *c, const void *A, const void *B, int n_eig, 
                            double *omega_out, double *resid_out) {
   if (!c) return BSE_EINVAL;
   if (!A || !B || !omega_out) return bse_fail(c, BSE_EINVAL, "lowest_full: null argument");
+  if (c->precision != BSE_FP64 && c->h64)
+    return bse_fail(c, BSE_EINVAL, "lowest_full: the full BSE takes the complex64 split H (h_complex128 is for the TDA entries)");
+
   if (n_steps < 2 || n_steps > 2 * c->dim || n_steps > BSE_FULL_MAX_STEPS || n_eig < 1 || 2 * n_eig > n_steps)
     return bse_fail(c, BSE_EINVAL, "lowest_full: bad size");
   return run_lowest_full(c, A, B, n_eig, n_steps, seed, omega_out, resid_out);

@@ -1,10 +1,15 @@
-// Batched assembly of several crystals of uneven size as one CUDA graph: one branch per
-// context, forked from and joined back into the caller's stream, so the GPU interleaves the
-// systems' kernels and the host issues a single launch.  The graph is built on the first
-// call for a given list of (context, H) and replayed afterwards.  A device timestamp
-// (%globaltimer) is written when the graph starts and when each branch ends, which gives
-// per-system completion times inside the batch.
+// Batched assembly of several crystals of uneven size as one CUDA graph, built on the first
+// call for a given list of (context, H) and replayed afterwards, so the host issues a single
+// launch.  The systems are ordered by their estimated work, smallest first, and dealt in that
+// order to two chains that run concurrently (forked from and joined back into the caller's
+// stream): every system's kernels still get (most of) the GPU, small systems are not queued
+// behind large ones (shortest-job-first order minimises the mean completion time), and the
+// second chain fills the SMs a chain's small kernels leave idle.  A device timestamp
+// (%globaltimer) is written when the graph starts and when each system's assembly ends, which
+// gives per-system completion times inside the batch.
+#include <algorithm>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -63,10 +68,22 @@ bse_status build(BatchGraph *b, bse_ctx **ctxs, void **H, int n, cudaStream_t st
     cudaGetLastError();
     return bse_fail(c0, BSE_ENOMEM, "batch: timestamp allocation failed");
   }
-  b->branches.resize(n);
-  b->events.resize(n + 1);
-  for (int i = 0; i < n; i++) cudaStreamCreateWithFlags(&b->branches[i], cudaStreamNonBlocking);
-  for (int i = 0; i <= n; i++) cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming);
+  // estimated work of each assembly: the direct term's M_vv W(q) GEMM and second contraction
+  // over all pairs, the exchange over the full square (flops up to a common factor)
+  std::vector<double> work(n);
+  for (int i = 0; i < n; i++) {
+    const bse_ctx *c = ctxs[i];
+    const double nk = c->nk, na = c->naux_tot, nv = c->nv, nc = c->nc, dim = (double)c->dim;
+    work[i] = nk * nk * nv * nv * (na * na + nc * nc * na) + dim * dim * na;
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b2) { return work[a] < work[b2]; });
+  const int n_chains = std::min(n, 2);
+  b->branches.resize(n_chains);
+  b->events.resize(n_chains + 1);
+  for (int i = 0; i < n_chains; i++) cudaStreamCreateWithFlags(&b->branches[i], cudaStreamNonBlocking);
+  for (int i = 0; i <= n_chains; i++) cudaEventCreateWithFlags(&b->events[i], cudaEventDisableTiming);
   const long long launches0 = bse_launch_count();
   {
     const cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
@@ -76,21 +93,25 @@ bse_status build(BatchGraph *b, bse_ctx **ctxs, void **H, int n, cudaStream_t st
   bse_status s = BSE_OK;
   k_stamp<<<1, 32, 0, stream>>>(b->d_stamps);
   bse_count_launch();
-  cudaEventRecord(b->events[n], stream);
-  for (int i = 0; i < n && s == BSE_OK; i++) {
+  cudaEventRecord(b->events[n_chains], stream);
+  for (int ch = 0; ch < n_chains; ch++) cudaStreamWaitEvent(b->branches[ch], b->events[n_chains], 0);
+  for (int r = 0; r < n && s == BSE_OK; r++) {
+    const int i = order[r];
+    cudaStream_t br = b->branches[r % n_chains];
     bse_ctx *c = ctxs[i];
-    cudaStreamWaitEvent(b->branches[i], b->events[n], 0);
     cudaStream_t saved = c->stream;
     const bool prof = c->prof;
-    c->stream = b->branches[i];
+    c->stream = br;
     c->prof = false;
     s = bse_assemble(c, H[i]);
-    k_stamp<<<1, 32, 0, b->branches[i]>>>(b->d_stamps + i + 1);
+    k_stamp<<<1, 32, 0, br>>>(b->d_stamps + i + 1);
     bse_count_launch();
     c->stream = saved;
     c->prof = prof;
-    cudaEventRecord(b->events[i], b->branches[i]);
-    cudaStreamWaitEvent(stream, b->events[i], 0);
+  }
+  for (int ch = 0; ch < n_chains; ch++) {
+    cudaEventRecord(b->events[ch], b->branches[ch]);
+    cudaStreamWaitEvent(stream, b->events[ch], 0);
   }
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(stream, &graph);
@@ -165,13 +186,15 @@ void bse_batch_release(void) {
   g_batches.clear();
 }
 
-bse_status bse_autotune(bse_ctx *c, int *chosen_tile) {
+bse_status bse_autotune(bse_ctx *c, int *chosen_tile, int *chosen_proj_threads) {
   if (!c) return BSE_EINVAL;
   if (c->precision == BSE_FP64) {
     if (chosen_tile) *chosen_tile = 0;
+    if (chosen_proj_threads) *chosen_proj_threads = 0;
     return BSE_OK;
   }
-  return split_autotune(c, chosen_tile);
+  if (c->stage < 2) return bse_fail(c, BSE_ESTATE, "autotune before project_pairs");
+  return split_autotune(c, chosen_tile, chosen_proj_threads);
 }
 
 }  // extern "C"

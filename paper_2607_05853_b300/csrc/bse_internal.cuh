@@ -31,6 +31,7 @@ struct bse_ctx {
   int nv = 0, nc = 0, nb = 0, nvc = 0;
   double alpha = 2.0;
   int precision = BSE_FP64;
+  bool h64 = true;         // H is stored complex128 (BSE_FP64, or a split precision with h_complex128)
   // exciton momentum Q (mesh steps): qQ is the flattened index of Q, qmQ of -Q, so the
   // conduction point of the pairs at k is kdiff(k, qmQ) and k - Q is kdiff(k, qQ)
   int Qm[3] = {0, 0, 0};
@@ -164,7 +165,7 @@ bse_status run_spectrum_matfree(bse_ctx *c, const double2 *u, int n_pol, int n_s
                                 double eta, double pref, double *eps2, double *ab);
 bse_status split_project(bse_ctx *c, const double *C_R);
 bse_status split_y_to_fp64(bse_ctx *c);
-bse_status split_autotune(bse_ctx *c, int *chosen);
+bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj);
 void split_free(bse_ctx *c);
 
 // mesh helpers

@@ -361,31 +361,37 @@ __device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long lon
 
 // ---- TMA-fed Hermitian matvec (complex64 H), persistent ------------------------------------
 // Same tiles and partial slots as k_hmatvec_c64.  Each CTA (four warps, no dedicated
-// producer warp) walks its tiles in 16-row chunks through a 3-stage shared-memory ring
-// filled by TMA: lane 0 of warp 0 refills a stage as soon as all four warps have copied
-// their rows of it into registers, so two chunks are in flight while one is computed.
-// Three CTAs per SM (128 registers a thread).  A stage is 16 rows x 128 complex64 = 16 KB;
+// producer warp) walks its tiles in 16-row chunks through a shared-memory ring
+// filled by TMA: the last of the four warps to copy its rows of a stage into registers refills
+// it, so the other stages' chunks are in flight while one is computed (CTAs per SM and stages
+// in HmvSmem).  A stage is 16 rows x 128 complex64 = 16 KB;
 // rows/columns past dim arrive zero-filled.
-constexpr int MV_STAGES = 3, MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8, MV_CTAS = 3;
+constexpr int MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8;
 constexpr long long MV_WAIT = 4000000000LL;
 
+// Up to three vectors: four CTAs per SM (at most 128 registers a thread) with a two-stage ring
+// each, so 16 warps share an SM's FP32 pipes and eight 16 KB chunks are in flight per SM; more
+// vectors (the full-BSE product's four or six) need more registers: two CTAs, three stages.
 template <int NP>
 struct HmvSmem {
+  static constexpr int STAGES = NP <= 3 ? 2 : 3;
+  static constexpr int CTAS = NP <= 3 ? 4 : 2;
   static constexpr int RSTR = 8 * NP + 4;                 // floats per lane in the U-sum scratch
   static constexpr int XB = NP * HT * 24;                 // x vectors: (yr,-yr,yi,yi) + (xr,xi)
   static constexpr int USTR = (HT * NP * 8 > 32 * RSTR * 4) ? HT * NP * 8 : 32 * RSTR * 4;
-  static constexpr int BYTES = 128 + MV_STAGES * MV_STAGE_BYTES + XB + 4 * USTR;
+  static constexpr int BYTES = 128 + STAGES * MV_STAGE_BYTES + XB + 4 * USTR;
 };
 
 // SYM = true: H is complex symmetric (H^T = H) instead of Hermitian; the mirrored tile then
 // contributes H_t^T y, which only changes how the row vector y is parked for the column sums.
 // More than three vectors (the full-BSE product's six) need more registers: two CTAs per SM.
 template <int NP, bool SYM = false>
-__global__ void __launch_bounds__(128, (NP <= 3 ? MV_CTAS : 2)) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
+__global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid_constant__ CUtensorMap tmH, long long dim,
                                                          int nb, const int2 *__restrict__ tiles, int ntiles,
                                                          const float2 *__restrict__ Q32, long long qs, int j,
                                                          float2 *__restrict__ part, const int *meff, int *err) {
   using S = HmvSmem<NP>;
+  constexpr int MV_STAGES = S::STAGES;
   extern __shared__ __align__(128) uint8_t smv[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smv);
   uint64_t *empty = full + MV_STAGES;
@@ -1166,6 +1172,32 @@ bool encode_rows_f32(CUtensorMap *m, const void *base, unsigned long long inner,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Second reorthogonalisation pass only where it is needed (Daniel, Gragg, Kaufman and Stewart
+// 1976): when the first pass left more than half of the squared norm, |W'|^2 > |W|^2 / 2, W' is
+// orthogonal to the basis to working accuracy and a second pass would change nothing, so
+// meff2[p] = 0 makes the pass-two kernels skip polarisation p; otherwise meff2[p] = meff[p].
+__global__ void k_dgks(const double *__restrict__ n0part, const double *__restrict__ n1part, int nb,
+                       const int *__restrict__ meff, int *__restrict__ meff2) {
+  __shared__ double r0[32], r1[32];
+  const int p = blockIdx.x;
+  double a0 = 0.0, a1 = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) {
+    a0 += n0part[p * nb + i];
+    a1 += n1part[p * nb + i];
+  }
+  r0[threadIdx.x] = a0;
+  r1[threadIdx.x] = a1;
+  __syncwarp();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = 0; i < 32; i++) {
+      s0 += r0[i];
+      s1 += r1[i];
+    }
+    meff2[p] = (s1 > 0.5 * s0) ? 0 : meff[p];
+  }
+}
+
 // Upper-triangle tile list of the half-read matvec, (bi, bj) for bj >= bi in row order, written
 // on the device (no host copy, no stream synchronisation): thread bi writes its row, which
 // starts at bi nbt - bi (bi - 1) / 2.
@@ -1194,11 +1226,15 @@ struct LanczosScratch {
   bool tma = false;
   double *a = nullptr, *b = nullptr, *beta0 = nullptr, *hmax = nullptr, *part = nullptr;
   double *apart = nullptr, *npart = nullptr;  // per-row-block partials of alpha_j and |W|^2
+  double *n0part = nullptr;  // |W|^2 partials before the first reorthogonalisation pass
   int *meff = nullptr;
+  int *meff2 = nullptr;      // meff for the second pass, 0 where the DGKS test skips it
 };
 
 bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, bool matfree = false) {
   const long long dim = c->dim;
+  // FP32 shadow basis and half-read products for a complex64 H (and the matrix-free product)
+  const bool c64 = matfree || !c->h64;
   const size_t qbytes = sizeof(double2) * (size_t)n_pol * (n_steps + 1) * dim;
   cudaStream_t st = c->stream;
   if (cudaMallocAsync((void **)&s.Q, qbytes, st) != cudaSuccess ||
@@ -1210,21 +1246,23 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, 
       cudaMallocAsync((void **)&s.hmax, sizeof(double), st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.part, sizeof(double) * 1024, st) != cudaSuccess ||
       cudaMallocAsync((void **)&s.meff, sizeof(int) * n_pol, st) != cudaSuccess ||
-      cudaMallocAsync((void **)&s.apart, sizeof(double) * 2 * n_pol * ((dim + HT - 1) / HT), st) != cudaSuccess ||
-      (c->precision != BSE_FP64 &&
+      cudaMallocAsync((void **)&s.apart, sizeof(double) * 3 * n_pol * ((dim + HT - 1) / HT), st) != cudaSuccess ||
+      cudaMallocAsync((void **)&s.meff2, sizeof(int) * n_pol, st) != cudaSuccess ||
+      (c64 &&
        cudaMallocAsync((void **)&s.Q32, qbytes / 2, st) != cudaSuccess)) {
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
   }
   s.nbt = (int)((dim + HT - 1) / HT);
   s.npart = s.apart + (size_t)n_pol * s.nbt;
+  s.n0part = s.npart + (size_t)n_pol * s.nbt;
   s.nrch = (int)((dim + RCH - 1) / RCH);
-  if (c->precision != BSE_FP64 &&
+  if (c64 &&
       cudaMallocAsync((void **)&s.rpart, sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1), st) != cudaSuccess) {
     cudaGetLastError();
     return bse_fail(c, BSE_ENOMEM, "spectrum: reorthogonalisation scratch allocation failed");
   }
-  if (c->precision != BSE_FP64 && dim % 2 == 0 && !matfree) {
+  if (c64 && dim % 2 == 0 && !matfree) {
     if (cudaMallocAsync((void **)&s.hpart, sizeof(float2) * (size_t)s.nbt * s.nbt * HT * n_pol, st) != cudaSuccess) {
       cudaGetLastError();
       return bse_fail(c, BSE_ENOMEM, "spectrum: Krylov scratch allocation failed");
@@ -1240,7 +1278,8 @@ bse_status lanczos_alloc(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, 
 }
 
 void lanczos_release(bse_ctx *c, LanczosScratch &s) {
-  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.apart, s.Q32, s.hpart, s.tiles, s.rpart};
+  void *ptrs[] = {s.Q, s.W, s.coef, s.a, s.b, s.beta0, s.hmax, s.part, s.meff, s.meff2, s.apart, s.Q32, s.hpart,
+                  s.tiles, s.rpart};
   for (void *p : ptrs)
     if (p) cudaFreeAsync(p, c->stream);
 }
@@ -1254,7 +1293,7 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
   const long long qs = (long long)(n_steps + 1) * dim;
   const int ldab = n_steps + 1;
   cudaStream_t st = c->stream;
-  const bool c64 = c->precision != BSE_FP64;
+  const bool c64 = matfree || !c->h64;  // complex64 H (or the matrix-free product)
   if (c64 && s.hpart && s.tiles) {
     s.tma = encode_rows_f32(&s.tmH, H, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK);
     if (s.tma)
@@ -1289,7 +1328,7 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       r = split_matvec_free(c, s.Q + (long long)j * dim, qs, n_pol, s.W);
       if (r != BSE_OK) return r;
     } else if (c64 && s.tma) {
-      const int grid = std::min(s.ntiles, MV_CTAS * c->n_sm);
+      const int grid = std::min(s.ntiles, HmvSmem<3>::CTAS * c->n_sm);
       if (n_pol == 1) {
         k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
@@ -1337,12 +1376,21 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     }
     k_axpy<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff, s.nbt, s.apart);
     bse_prof_begin(c, BSE_KP_REORTH);
+    const bool proj32 = c64 && dim % 2 == 0;
+    if (proj32) k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.n0part);
     for (int pass = 0; pass < 2; pass++) {
-      if (c64 && dim % 2 == 0) {
+      if (proj32) {
+        // the second pass runs where the DGKS test asks for it (meff2)
+        if (pass == 1) {
+          k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.npart);
+          k_dgks<<<n_pol, 32, 0, st>>>(s.n0part, s.npart, s.nbt, s.meff, s.meff2);
+          bse_count_launch(2);
+        }
+        const int *mp = pass ? s.meff2 : s.meff;
         k_reorth_dots_chunk<<<dim3(s.nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart,
-                                                                                   s.nrch, ldab, s.meff);
-        k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab, s.meff);
-        k_reorth_update32<<<dim3(el2_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, s.meff);
+                                                                                   s.nrch, ldab, mp);
+        k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab, mp);
+        k_reorth_update32<<<dim3(el2_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, mp);
       } else {  // complex128 H, or an odd dim: FP64 projections on the FP64 basis
         k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
         k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
@@ -1352,7 +1400,7 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.npart);
     k_scale<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps, s.Q32,
                                                     s.nbt, s.npart);
-    bse_count_launch((c64 && dim % 2 == 0) ? 9 : 7);  // axpy, two reorthogonalisation passes, norm, scale
+    bse_count_launch(proj32 ? 10 : 7);  // axpy, two reorthogonalisation passes (+ the pass-one norm), norm, scale
     r = bse_check_launch(c, "lanczos step");
     if (r != BSE_OK) return r;
   }
@@ -1771,7 +1819,7 @@ bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const flo
   if (!encode_rows_f32(&tm, Hm, 2ull * dim, (unsigned long long)dim, 2 * HT, MV_CHUNK))
     return bse_fail(c, BSE_ECUDA, "half-read product: tensor map encoding failed");
   cudaStream_t st = c->stream;
-  const int grid = std::min(h->ntiles, (np <= 3 ? MV_CTAS : 2) * c->n_sm);  // resident CTAs per SM
+  const int grid = std::min(h->ntiles, (np <= 3 ? HmvSmem<3>::CTAS : HmvSmem<6>::CTAS) * c->n_sm);  // resident CTAs per SM
   bse_prof_begin(c, BSE_KP_MATVEC);
 #define HALF_LAUNCH(NPV, SYMV)                                                                                 \
   k_hmv_tma<NPV, SYMV><<<grid, 128, hmv_tma_smem<NPV>(), st>>>(tm, dim, h->nbt, h->tiles, h->ntiles, Z, dim, 0, \
@@ -1898,7 +1946,7 @@ bse_status static_scratch_base(bse_ctx *c, unsigned char **out) {
 // bytes it needs; with base == nullptr only the size is computed.
 size_t carve_scratch(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, unsigned char *base) {
   const long long dim = c->dim;
-  const bool c64 = c->precision != BSE_FP64;
+  const bool c64 = !c->h64;
   size_t off = 0;
   auto take = [&](size_t bytes) -> unsigned char * {
     off = (off + 255) & ~(size_t)255;
@@ -1916,9 +1964,11 @@ size_t carve_scratch(bse_ctx *c, LanczosScratch &s, int n_pol, int n_steps, unsi
   s.hmax = (double *)take(sizeof(double));
   s.part = (double *)take(sizeof(double) * 1024);
   s.meff = (int *)take(sizeof(int) * n_pol);
+  s.meff2 = (int *)take(sizeof(int) * n_pol);
   s.nbt = (int)((dim + HT - 1) / HT);
-  s.apart = (double *)take(sizeof(double) * 2 * n_pol * s.nbt);
+  s.apart = (double *)take(sizeof(double) * 3 * n_pol * s.nbt);
   s.npart = s.apart ? s.apart + (size_t)n_pol * s.nbt : nullptr;
+  s.n0part = s.apart ? s.apart + (size_t)2 * n_pol * s.nbt : nullptr;
   s.nrch = (int)((dim + RCH - 1) / RCH);
   s.Q32 = c64 ? (float2 *)take(sizeof(float2) * qn) : nullptr;
   s.rpart = c64 ? (float2 *)take(sizeof(float2) * (size_t)n_pol * s.nrch * (n_steps + 1)) : nullptr;

@@ -19,6 +19,7 @@
 #include <cstring>
 
 #include "bse_internal.cuh"
+#include "tc_direct.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -32,13 +33,21 @@ struct SplitWS {
   int nq = 1, rows = 0;
   __nv_bfloat16 *Wp = nullptr;   // [nk][PP][naux][kmem]   B[nu][mu] = W(q)[mu][nu]
   __nv_bfloat16 *Ap = nullptr;   // [nq][PP][rows][kmem]   M_vv pieces
-  float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux]
+  float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux], or [nq][nk][naux_pad][nc*nc] for the fused kernel
   float2 *T32 = nullptr;         // [nq][naux][rows]  (column nu of T = M_vv W(q) is contiguous)
   float2 *Y32 = nullptr;         // [nk][nao_max][nb][naux]
   __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V
   __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
   CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
   int bn_g1 = TC_BN;             // N tile of the M_vv W(q) GEMM (autotuned)
+  int proj_bs = 0;               // threads per block of the register-blocked projection (autotuned; 0 = default)
+  // fused direct term (T = M_vv W(q) and T M_cc^T in one kernel, T kept in tensor memory):
+  // used when N_aux fits one N tile and the window has a register-blocked projection
+  bool fused = false;
+  int bn_d = 0;                  // N tile of the fused kernel (>= N_aux)
+  int naux_pad = 0;              // M_cc row length (multiple of 16) in the fused layout
+  int pairs_d = 0, nui_d = 0;    // pairs per tile; M_cc columns per ring item
+  CUtensorMap tmB_d;
   // FP32 per-k stage
   float2 *PHQ = nullptr;         // [nk][n_RW]  w_R e^{-i q.R}
   float2 *PHK = nullptr;         // [nk][n_RC]  e^{+i k.R}
@@ -851,7 +860,7 @@ __global__ void __launch_bounds__(256) k_g2c_32(const float2 *__restrict__ T, co
 __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
                                                const double *__restrict__ eqp, int nv, int nc, int naux, int n1,
                                                int n2, int n3, int q0, const int *__restrict__ qlist, int rows,
-                                               long long dim, float2 *__restrict__ H) {
+                                               long long dim, float2 *__restrict__ H, double2 *__restrict__ H64) {
   extern __shared__ float2 sg[];
   const int nk = n1 * n2 * n3;
   const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
@@ -900,7 +909,23 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
     if (o < nout) {
       const int ia = o / nvc, jb = o % nvc;
       const int i = ia / nc, a = ia % nc;
-      float2 *hp = H + ((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb;
+      const long long ih = ((long long)k1 * nvc + ia) * dim + (long long)k2 * nvc + jb;
+      const long long im = ((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia;
+      if (H64) {  // complex128 H: the contribution and the diagonal added in FP64
+        double2 hv = H64[ih];
+        hv.x -= inv * (double)ad[t].x;
+        hv.y -= inv * (double)ad[t].y;
+        if (q == 0 && ia == jb) hv.x += eqp[(long long)k1 * nb + nv + a] - eqp[(long long)k1 * nb + i];
+        H64[ih] = hv;
+        if (mirror) {
+          double2 mv = H64[im];
+          mv.x -= inv * (double)ad[t].x;
+          mv.y += inv * (double)ad[t].y;
+          H64[im] = mv;
+        }
+        continue;
+      }
+      float2 *hp = H + ih;
       const float2 hx = *hp;
       float2 hv = make_float2(fmaf(-invf, ad[t].x, hx.x), fmaf(-invf, ad[t].y, hx.y));
       if (q == 0 && ia == jb)  // the diagonal sums in FP64 (one element per row)
@@ -908,7 +933,7 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
                        eqp[(long long)k1 * nb + i]);
       *hp = hv;
       if (mirror) {  // block (k2, k1) gets the conjugate of the direct contribution
-        float2 *hm = H + ((long long)k2 * nvc + jb) * dim + (long long)k1 * nvc + ia;
+        float2 *hm = H + im;
         const float2 mx = *hm;
         *hm = make_float2(fmaf(-invf, ad[t].x, mx.x), fmaf(invf, ad[t].y, mx.y));
       }
@@ -921,6 +946,9 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
 // M_cc element of that mu; both LRI terms go into one accumulator,
 //   M_vv[i][j] = sum_s conj(c2_sj) Y1_si + c1_si conj(Y2_sj),
 //   M_cc[a][b] = sum_s conj(c1_sa) Y2_sb + c2_sb conj(Y1_sa)   (band indices in the window).
+// M_cc is written [q][k1][a b][nu], or [q][k1][nu][a b] with nu padded to mc_pad (mc_pad > 0);
+// in the second layout a block's M_cc values go through shared memory ([mu][a b] after the
+// band tables) so that the stores of consecutive mu are one contiguous, coalesced run.
 // grid: x = q - q0, y = k1; block: mu chunk (blockDim >= 32), loop over mu.
 template <int NV, int NC>
 __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
@@ -928,7 +956,8 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
                                                   const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
                                                   const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
                                                   const int *__restrict__ qlist, int np, int rows, int kmem,
-                                                  __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc) {
+                                                  __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc,
+                                                  int mc_pad) {
   constexpr int NB = NV + NC;
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
@@ -942,7 +971,18 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   }
   __syncthreads();
   const long long plane = (long long)rows * kmem;
-  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
+  float2 *mstage = scf + 2 * nao_tot * NB;  // [blockDim][NC NC] (mc_pad > 0)
+  for (int mu_base = 0; mu_base < naux; mu_base += blockDim.x) {
+    const int mu = mu_base + threadIdx.x;
+    if (mu >= naux) {
+      if (mc_pad) {  // take part in the block's staged store
+        __syncthreads();
+        for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
+          Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
+        __syncthreads();
+      }
+      continue;
+    }
     const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
     const float2 *Y1 = Y + (long long)k1 * nao_max * NB * naux + mu;
     const float2 *Y2 = Y + (long long)k2 * nao_max * NB * naux + mu;
@@ -1010,11 +1050,22 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
           out[(2 * p + 1) * plane + r] = pi[p];
         }
       }
-    float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * naux + mu;
+    if (mc_pad) {  // [q][k1][nu][a b]: the fused direct kernel's layout (a pair's columns contiguous)
 #pragma unroll
-    for (int a = 0; a < NC; a++)
+      for (int a = 0; a < NC; a++)
 #pragma unroll
-      for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * naux] = mc[a][b];
+        for (int b = 0; b < NC; b++) mstage[threadIdx.x * (NC * NC) + a * NC + b] = mc[a][b];
+      __syncthreads();
+      for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
+        Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
+      __syncthreads();
+    } else {       // [q][k1][a b][nu]
+      float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * naux + mu;
+#pragma unroll
+      for (int a = 0; a < NC; a++)
+#pragma unroll
+        for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * naux] = mc[a][b];
+    }
   }
 }
 
@@ -1027,7 +1078,7 @@ template <int NV, int NC>
 __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
                                                  const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
                                                  int q0, const int *__restrict__ qlist, int rows, long long dim,
-                                                 float2 *__restrict__ H) {
+                                                 float2 *__restrict__ H, double2 *__restrict__ H64) {
   constexpr int R = NV * NV, C = NC * NC, TR = (R + 1) / 2, TCC = (C + 1) / 2, NVC = NV * NC, NB = NV + NC;
   extern __shared__ float2 sg2[];
   float2 *sT = sg2, *sM = sg2 + R * naux;
@@ -1088,7 +1139,23 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
         if (ij >= R || ab >= C) continue;
         const int i = ij / NV, j = ij % NV, a = ab / NC, b = ab % NC;
         const int ia = i * NC + a, jb = j * NC + b;
-        float2 *hp = H + ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
+        const long long ih = ((long long)k1 * NVC + ia) * dim + (long long)k2 * NVC + jb;
+        const long long im = ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
+        if (H64) {  // complex128 H: the contribution and the diagonal added in FP64
+          double2 hv = H64[ih];
+          hv.x -= inv * (double)acc[x][y].x;
+          hv.y -= inv * (double)acc[x][y].y;
+          if (q == 0 && ia == jb) hv.x += eqp[(long long)k1 * NB + NV + a] - eqp[(long long)k1 * NB + i];
+          H64[ih] = hv;
+          if (mirror) {
+            double2 mv = H64[im];
+            mv.x -= inv * (double)acc[x][y].x;
+            mv.y += inv * (double)acc[x][y].y;
+            H64[im] = mv;
+          }
+          continue;
+        }
+        float2 *hp = H + ih;
         const float2 hx = *hp;
         float2 hv = make_float2(fmaf(-invf, acc[x][y].x, hx.x), fmaf(-invf, acc[x][y].y, hx.y));
         if (q == 0 && ia == jb)  // the diagonal sums in FP64 (one element per row)
@@ -1096,7 +1163,7 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
                          eqp[(long long)k1 * NB + i]);
         *hp = hv;
         if (mirror) {
-          float2 *hm = H + ((long long)k2 * NVC + jb) * dim + (long long)k1 * NVC + ia;
+          float2 *hm = H + im;
           const float2 mx = *hm;
           *hm = make_float2(fmaf(-invf, acc[x][y].x, mx.x), fmaf(invf, acc[x][y].y, mx.y));
         }
@@ -1288,34 +1355,38 @@ const double2 *ck_tab(const bse_ctx *c, const SplitWS *w) { return w->shifted ? 
 const double *e_tab(const bse_ctx *c, const SplitWS *w) { return w->shifted ? w->eqpq : c->eqp; }
 
 template <int NV, int NC>
-void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq) {
+void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq, int mc_pad) {
   const int na = c->naux_tot;
-  const int bs = std::min(160, (na + 31) / 32 * 32);
-  const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
+  const int bs = w->proj_bs ? w->proj_bs : std::min(160, (na + 31) / 32 * 32);
+  const size_t sm = sizeof(float2) * (2 * c->nao_tot * (NV + NC) + (mc_pad ? (size_t)bs * NC * NC : 0));
   k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom,
                                                              c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
                                                              c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap,
-                                                             w->Mc32);
+                                                             w->Mc32, mc_pad);
 }
 
 template <int NV, int NC>
 bool launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  double2 *H64 = c->h64 ? reinterpret_cast<double2 *>(H) : nullptr;
+  if (H64) H = nullptr;
   constexpr int threads = ((NV * NV + 1) / 2) * ((NC * NC + 1) / 2);
   const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
   const size_t sm = sizeof(float2) * (size_t)(NV * NV + NC * NC) * c->naux_tot;
   if (sm > 200 * 1024) return false;  // the pair's rows do not fit: generic chunked kernel
   k_g2_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->naux_tot, c->mesh[0],
-                                                           c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
+                                                           c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H,
+                                                           H64);
   return true;
 }
 
 // Dispatch the register-blocked kernels for windows with Nv, Nc in {2, 4, 6}; false means
 // the caller falls back to the generic kernels.
-bool fast_pair_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H, bool proj) {
+// mc_pad > 0: the projection writes M_cc in the fused kernel's layout.
+bool fast_pair_kernels(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H, bool proj, int mc_pad = 0) {
 #define BSE_FAST(NV, NC)                                                       \
   if (c->nv == NV && c->nc == NC) {                                            \
     if (proj) {                                                                \
-      launch_proj_fast<NV, NC>(c, w, q0, nq);                                  \
+      launch_proj_fast<NV, NC>(c, w, q0, nq, mc_pad);                          \
       return true;                                                             \
     }                                                                          \
     return launch_g2_fast<NV, NC>(c, w, q0, nq, H);                            \
@@ -1418,6 +1489,45 @@ bse_status launch_tc_np(bse_ctx *c, int np, int bn, const CUtensorMap &A, const 
   return launch_tc_bn<1>(c, bn, A, B, args, grid, prof_id);
 }
 
+// ---- fused direct term -------------------------------------------------------------------
+template <int NP, int BN, int NC>
+bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  using Cf = tcd::DCfg<NP, BN>;
+  const long long total = (long long)a.tiles_m * a.tiles_b;
+  const int ctas = (int)std::min<long long>(total, c->n_sm);
+  bse_prof_begin(c, prof_id);
+  tcd::k_tc_direct<NP, BN, NC><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, a);
+  bse_prof_end(c, prof_id);
+  bse_count_launch();
+  return bse_check_launch(c, "tc_direct");
+}
+
+template <int NP, int BN>
+bse_status launch_direct_nc(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  switch (c->nc) {
+    case 2: return launch_direct_t<NP, BN, 2>(c, w, a, prof_id);
+    case 4: return launch_direct_t<NP, BN, 4>(c, w, a, prof_id);
+    default: return launch_direct_t<NP, BN, 6>(c, w, a, prof_id);
+  }
+}
+
+// N tiles of the fused kernel: T's N_aux columns in one tile (two ring stages of bf16x3 pieces
+// fit up to 160 columns), so the fused path takes N_aux <= 160.
+template <int NP>
+bse_status launch_direct_bn(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  if (w->bn_d == 64) return launch_direct_nc<NP, 64>(c, w, a, prof_id);
+  return launch_direct_nc<NP, 160>(c, w, a, prof_id);
+}
+
+bse_status launch_direct(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  if (w->np == 3) return launch_direct_bn<3>(c, w, a, prof_id);
+  if (w->np == 2) return launch_direct_bn<2>(c, w, a, prof_id);
+  return launch_direct_bn<1>(c, w, a, prof_id);
+}
+
+// Ring stage bytes of the fused kernel (operand pieces of one K chunk).
+int direct_stage_bytes(int np, int bn) { return 2 * np * (tcg::A_TILE + bn * tcg::ROWB); }
+
 // Shared-memory size attributes of every tensor-core instantiation, set once (outside any
 // stream capture).
 template <int NP, int BN>
@@ -1426,10 +1536,20 @@ void set_attr() {
 }
 template <int NV, int NC>
 void set_g2_attr() {
+  cudaFuncSetAttribute(k_proj32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
+template <int NP, int BN>
+void set_direct_attr() {
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
+}
 void set_all_attrs_now() {
+  set_direct_attr<1, 64>(); set_direct_attr<1, 160>();
+  set_direct_attr<2, 64>(); set_direct_attr<2, 160>();
+  set_direct_attr<3, 64>(); set_direct_attr<3, 160>();
   set_g2_attr<2, 2>(); set_g2_attr<2, 4>(); set_g2_attr<2, 6>(); set_g2_attr<4, 2>(); set_g2_attr<4, 4>();
   set_g2_attr<4, 6>(); set_g2_attr<6, 2>(); set_g2_attr<6, 4>(); set_g2_attr<6, 6>();
   set_attr<1, 64>(); set_attr<1, 96>(); set_attr<1, 128>(); set_attr<1, 160>();
@@ -1449,7 +1569,23 @@ bse_status split_setup(bse_ctx *c) {
   w->kmem = (na + 7) / 8 * 8;
   w->kchunks = (na + tcg::BK - 1) / tcg::BK;
   w->rows = c->nk * c->nv * c->nv;
-  const size_t per_q = (size_t)w->pp * w->rows * w->kmem * 2 + (size_t)c->nk * c->nc * c->nc * na * 8 +
+  // fused direct term: a window with register-blocked projections and T's columns in one tile
+  const bool win = (c->nv == 2 || c->nv == 4 || c->nv == 6) && (c->nc == 2 || c->nc == 4 || c->nc == 6);
+  w->fused = win && na <= 160;
+  w->naux_pad = (na + 15) / 16 * 16;
+  if (w->fused) {
+    w->bn_d = na <= 64 ? 64 : 160;
+    const int ncc = c->nc * c->nc, rpp = c->nv * c->nv;
+    const long long stage = direct_stage_bytes(w->np, w->bn_d);
+    w->pairs_d = 128 / rpp;
+    w->nui_d = (int)(stage / ((long long)w->pairs_d * ncc * 8)) / 16 * 16;
+    if (w->nui_d < 16) {  // wide conduction windows on Nv = 2: fewer pairs per tile
+      w->pairs_d = (int)(stage / (16LL * ncc * 8));
+      w->nui_d = 16;
+    }
+    w->nui_d = std::min(w->nui_d, w->naux_pad);
+  }
+  const size_t per_q = (size_t)w->pp * w->rows * w->kmem * 2 + (size_t)c->nk * c->nc * c->nc * w->naux_pad * 8 +
                        (size_t)w->rows * na * 8;
   const size_t budget = (size_t)1536 << 20;
   w->nq = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
@@ -1466,7 +1602,7 @@ bse_status split_setup(bse_ctx *c) {
       !alloc((void **)&w->X32, dimz * na * sizeof(float2)) ||
       !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * 2) ||
       !alloc((void **)&w->Ap, (size_t)w->nq * w->pp * w->rows * w->kmem * 2) ||
-      !alloc((void **)&w->Mc32, (size_t)w->nq * c->nk * c->nc * c->nc * na * 8) ||
+      !alloc((void **)&w->Mc32, (size_t)w->nq * c->nk * c->nc * c->nc * w->naux_pad * 8) ||
       !alloc((void **)&w->T32, (size_t)w->nq * w->rows * na * 8) ||
       !alloc((void **)&w->Y32, (size_t)c->nk * c->nao_max * c->nb * na * 8) ||
       !alloc((void **)&w->Pp, (size_t)w->pp * dimz * w->kmem * 2) ||
@@ -1474,6 +1610,7 @@ bse_status split_setup(bse_ctx *c) {
     return bse_fail(c, BSE_ENOMEM, "split workspace allocation failed");
   cudaMemset(w->Wp, 0, (size_t)c->nk * w->pp * na * w->kmem * 2);
   cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * 2);
+  cudaMemset(w->Mc32, 0, (size_t)w->nq * c->nk * c->nc * c->nc * w->naux_pad * 8);
   cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * 2);
   cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * 2);
   {
@@ -1486,6 +1623,7 @@ bse_status split_setup(bse_ctx *c) {
   set_all_attrs(c);
   bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
             make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
+            (!w->fused || make_map(&w->tmB_d, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_d)) &&
             make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&
             make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN);
   if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");
@@ -1596,6 +1734,7 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
     // the exchange block is Hermitian: element (r, c) is stored as conj at (c, r), so a lane's
     // row index runs along memory and the stores coalesce
     a.out = H;
+    a.out64 = c->h64 ? 1 : 0;
     a.ld_row = 1;
     a.ld_col = c->dim;
     a.conj_out = 1;
@@ -1612,6 +1751,42 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
   const int nqp = (int)c->qplus.size();
   for (int q0 = 0; q0 < nqp; q0 += w->nq) {
     const int nq = std::min(w->nq, nqp - q0);
+    if (w->fused) {
+      // projections (M_cc in the fused layout), then T = M_vv W(q) and H += -T M_cc^T / N_k
+      bse_prof_begin(c, BSE_KP_PROJECT);
+      fast_pair_kernels(c, w, q0, nq, H, true, w->naux_pad);
+      bse_prof_end(c, BSE_KP_PROJECT);
+      bse_count_launch();
+      bse_status s = bse_check_launch(c, "proj32");
+      if (s != BSE_OK) return s;
+      const int rpp = c->nv * c->nv;
+      tcd::DArgs a{};
+      a.nv = c->nv;
+      a.pairs = w->pairs_d;
+      a.rows = w->rows;
+      a.tiles_m = (c->nk + w->pairs_d - 1) / w->pairs_d;
+      a.tiles_b = nq;
+      a.k_chunks = w->kchunks;
+      a.naux = na;
+      a.naux_pad = w->naux_pad;
+      a.nui = w->nui_d;
+      a.n_mitems = (w->naux_pad + w->nui_d - 1) / w->nui_d;
+      a.Mc = w->Mc32;
+      a.qlist = c->d_qplus;
+      a.b_base = q0;
+      a.n1 = c->mesh[0];
+      a.n2 = c->mesh[1];
+      a.n3 = c->mesh[2];
+      a.eqp = e_tab(c, w);
+      a.dim = c->dim;
+      a.H = c->h64 ? nullptr : H;
+      a.H64 = c->h64 ? reinterpret_cast<double2 *>(H) : nullptr;
+      a.err = c->d_err;
+      (void)rpp;
+      s = launch_direct(c, w, a, BSE_KP_G1);
+      if (s != BSE_OK) return s;
+      continue;
+    }
     {
       dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
       size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
@@ -1649,7 +1824,8 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       bse_prof_begin(c, BSE_KP_G2);
       if (!fast_pair_kernels(c, w, q0, nq, H, false))
         k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->nv, c->nc, na, c->mesh[0], c->mesh[1],
-                                              c->mesh[2], q0, c->d_qplus, w->rows, c->dim, H);
+                                              c->mesh[2], q0, c->d_qplus, w->rows, c->dim, c->h64 ? nullptr : H,
+                                              c->h64 ? reinterpret_cast<double2 *>(H) : nullptr);
       bse_prof_end(c, BSE_KP_G2);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "g2_32");
@@ -1849,11 +2025,68 @@ bse_status split_matfree_hmax(bse_ctx *c, double *hmax) {
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int, int, int>, int> g_tune_proj;
+
+// Threads per block of the register-blocked projection: one slab of projections timed for each
+// candidate (a warp multiple up to the kernel's 160-thread bound and the ABF count); the
+// fastest is kept for this context and cached per shape.  0 when the window has no
+// register-blocked kernel.
+int tune_projection(bse_ctx *c, SplitWS *w) {
+  const int na = c->naux_tot;
+  const int nq = std::min(w->nq, (int)c->qplus.size());
+  const auto key = std::make_tuple(na, w->rows, nq, w->np, c->nv, c->nc);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_proj.find(key);
+    if (it != g_tune_proj.end()) return it->second;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_bs = 0;
+  const int cap = std::min(160, (na + 31) / 32 * 32);
+  for (int bs = 32; bs <= cap; bs += 32) {
+    w->proj_bs = bs;
+    if (!fast_pair_kernels(c, w, 0, nq, nullptr, true, w->fused ? w->naux_pad : 0)) break;  // warm-up
+    float t = 0.f;
+    for (int rep = 0; rep < 3; rep++) {
+      cudaEventRecord(e0, c->stream);
+      fast_pair_kernels(c, w, 0, nq, nullptr, true, w->fused ? w->naux_pad : 0);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t += ms;
+    }
+    bse_count_launch(4);
+    if (t < best) {
+      best = t;
+      best_bs = bs;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  w->proj_bs = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_proj[key] = best_bs;
+  }
+  return best_bs;
+}
 }  // namespace
 
-bse_status split_autotune(bse_ctx *c, int *chosen) {
+bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj) {
   SplitWS *w = ws(c);
   const int na = c->naux_tot;
+  {
+    const bool prof = c->prof;
+    c->prof = false;
+    const int pbs = tune_projection(c, w);
+    c->prof = prof;
+    w->proj_bs = pbs;
+    if (chosen_proj) *chosen_proj = pbs;
+  }
   const auto key = std::make_tuple(na, w->rows, std::min(w->nq, (int)c->qplus.size()), w->np);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -50,6 +50,7 @@ struct Args {
   long long ld_col;      //   (ld_row = 1 makes the epilogue's stores coalesced: a lane owns a row)
   long long out_bstride;
   int conj_out;          // store the conjugate of each element
+  int out64;             // out holds complex128 elements (same strides, in elements)
   int b_batch_planes;    // 0: B has no batch dimension (z = pp), else z = qlist[b_base + b]*PP + pp
   int b_base;
   const int *qlist;
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(192, 1)
       const int n0 = (t % args.tiles_n) * BN, m0 = ((t / args.tiles_n) % args.tiles_m) * BM;
       const int b = t / (args.tiles_n * args.tiles_m);
       const int row = m0 + quarter * 32 + lane;
-      float2 *orow = args.out + (long long)b * args.out_bstride + (long long)row * args.ld_row;
+      const long long orow = (long long)b * args.out_bstride + (long long)row * args.ld_row;
       const bool row_ok = row < args.rows;
       const float sim = args.conj_out ? -args.scale : args.scale;
 #pragma unroll 1
@@ -215,8 +216,13 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int j = 0; j < 16; j++) {
             const int col = n0 + c0 + j;
-            if (col < args.n_valid)
-              orow[col * args.ld_col] = make_float2(args.scale * __uint_as_float(rr[j]), sim * __uint_as_float(ri[j]));
+            if (col < args.n_valid) {
+              const float re = args.scale * __uint_as_float(rr[j]), im = sim * __uint_as_float(ri[j]);
+              if (args.out64)
+                reinterpret_cast<double2 *>(args.out)[orow + col * args.ld_col] = make_double2(re, im);
+              else
+                args.out[orow + col * args.ld_col] = make_float2(re, im);
+            }
           }
         }
       }

@@ -12,10 +12,10 @@ def to_dev(inp):
     return d
 
 
-def gpu_hamiltonian(inp, precision="fp64", alpha=2.0, Wq=False):
+def gpu_hamiltonian(inp, precision="fp64", alpha=2.0, Wq=False, **kw):
     import torch
     from paper_2607_05853_b300.api import BSE
-    b = BSE.from_inputs(inp, precision=precision, alpha=alpha)
+    b = BSE.from_inputs(inp, precision=precision, alpha=alpha, **kw)
     d = to_dev(inp)
     Wq_out = torch.empty((b.nk, b.naux, b.naux), dtype=torch.complex128, device="cuda") if Wq else None
     b.interp_W(d["W_R"], d["V0"], Wq_out)

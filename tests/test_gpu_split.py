@@ -85,6 +85,35 @@ def test_split_spectrum_close_to_fp64(cfg0):
     assert rel_l2 <= 1e-4, rel_l2
 
 
+def test_split_complex128_storage(cfg0):
+    """bse_params.h_complex128: the bf16x3 assembly stores H as complex128 -- the same kernel
+    contractions (the off-diagonal elements equal the complex64 H's to its rounding), the
+    E_c - E_v diagonal added in FP64 without the complex64 rounding -- and the spectrum reads
+    it with the FP64 path's products.  The full-BSE entries refuse such a context."""
+    import torch
+    from paper_2607_05853_b300 import _lib
+    inp, orc, Href = cfg0
+    b, d, H, _ = gpu_hamiltonian(inp, precision="bf16x3", h_complex128=True)
+    assert H.dtype == torch.complex128
+    Hn = H.cpu().numpy()
+    off, diag = offdiag_diag_errors(Hn, Href)
+    print(f"bf16x3 with complex128 H: off-diagonal {off:.3e}, diagonal {diag:.3e}")
+    assert off <= SPLIT_OFF["bf16x3"], off
+    assert diag <= 2e-8, diag
+    b32, _, H32, _ = gpu_hamiltonian(inp, precision="bf16x3")
+    H32 = H32.cpu().numpy().astype(np.complex128)
+    eye = np.eye(Hn.shape[0], dtype=bool)
+    assert np.abs(Hn - H32)[~eye].max() <= 2.0 ** -23 * np.abs(Href[~eye]).max()
+    u = b.dipole_vector(d["vel"], d["e_ks"])
+    om = torch.linspace(0, 10, 201, dtype=torch.float64, device="cuda")
+    eps = b.spectrum(H, u, b.dim, om, 0.1, orc.prefactor())
+    b.sync()
+    ref = O.eps2_exact(Href, orc.dipoles(), om.cpu().numpy(), 0.1, orc.prefactor())
+    assert np.linalg.norm(eps.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    with pytest.raises(_lib.BseError, match="EINVAL"):
+        b.assemble_coupling()
+
+
 @pytest.mark.slow
 def test_split_full_size_sampled_blocks_and_excitons():
     """The 27648-dim workload in the launch configuration the benchmark times: sampled

@@ -543,7 +543,7 @@ def main():
     if args.batch16:
         del H
         torch.cuda.empty_cache()
-        result["batched_uneven"] = batch16_report()
+        result["batched_uneven"] = batch16_report(world=world, rank=rank, dist=dist if world > 1 else None)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(inp, args.cpu_seconds)
     if rank == 0:
@@ -635,15 +635,21 @@ def _self_conj(q, dense):
     return all((2 * mi) % ni == 0 for mi, ni in zip(m, (n1, n2, n3)))
 
 
-def batch16_report(precision="bf16x3"):
+def batch16_report(precision="bf16x3", world=1, rank=0, dist=None):
     """16 seeded crystals of uneven size assembled as one CUDA graph: per-system throughput
     inside the batch, the isolated throughput of each system, aggregate speedup over running
-    them one after another, and Jain's fairness index of (batched / isolated) throughput."""
+    them one after another, and Jain's fairness index of (batched / isolated) throughput.
+    Under torchrun the systems are sharded across the ranks (longest-processing-time-first,
+    paper_2607_05853_b300.shard), each rank running its own batch graph; the report then
+    gathers every rank's systems (metadata only) and the job time is the slowest rank's."""
     import torch
     from paper_2607_05853_b300.api import BSE, batch_assemble, batch_release
+    from paper_2607_05853_b300.shard import assembly_work, assign_systems
     from synth import batched_specs, make_inputs
+    specs = batched_specs(16)
+    mine = assign_systems([assembly_work(sp.n_k, sp.n_aux, sp.nv, sp.nc) for sp in specs], world)[rank]
     systems, Hs, dims, tiles = [], [], [], []
-    for sp in batched_specs(16):
+    for sp in [specs[i] for i in mine]:
         inp = make_inputs(sp)
         b = BSE.from_inputs(inp, precision=precision)
         d = {k: torch.from_numpy(np.ascontiguousarray(inp[k])).cuda() for k in ("W_R", "V0", "C_R", "e_qp", "c_k")}
@@ -676,8 +682,16 @@ def batch16_report(precision="bf16x3"):
     done_ms = [x / 1e6 for x in stamps]
     x = [t_i / max(c_i, 1e-9) for t_i, c_i in zip(iso, done_ms)]   # batched / isolated throughput
     jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
+    if dist is not None:       # gather the ranks' per-system results (reporting only)
+        parts = [None] * world
+        dist.all_gather_object(parts, (t_batch, list(zip(dims, tiles, iso, done_ms))))
+        t_batch = max(p[0] for p in parts)
+        rows = [r for p in parts for r in p[1]]
+        dims, tiles, iso, done_ms = (list(c) for c in zip(*rows))
+        x = [t_i / max(c_i, 1e-9) for t_i, c_i in zip(iso, done_ms)]
+        jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
     el = [float(dm) ** 2 for dm in dims]
-    out = {"systems": 16, "precision": precision, "graph_ms": t_batch, "serial_ms": sum(iso),
+    out = {"systems": 16, "ranks": world, "precision": precision, "graph_ms": t_batch, "serial_ms": sum(iso),
            "aggregate_elements_per_s": sum(el) / (t_batch / 1e3),
            "serial_elements_per_s": sum(el) / (sum(iso) / 1e3),
            "batch_speedup_over_serial": sum(iso) / t_batch, "jain_fairness": jain,

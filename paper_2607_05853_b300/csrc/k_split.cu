@@ -972,17 +972,11 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   __syncthreads();
   const long long plane = (long long)rows * kmem;
   float2 *mstage = scf + 2 * nao_tot * NB;  // [blockDim][NC NC] (mc_pad > 0)
+  // every thread runs every iteration of this loop (the block-wide barriers of the staged
+  // store sit outside the per-mu branch)
   for (int mu_base = 0; mu_base < naux; mu_base += blockDim.x) {
     const int mu = mu_base + threadIdx.x;
-    if (mu >= naux) {
-      if (mc_pad) {  // take part in the block's staged store
-        __syncthreads();
-        for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
-          Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
-        __syncthreads();
-      }
-      continue;
-    }
+    if (mu < naux) {
     const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
     const float2 *Y1 = Y + (long long)k1 * nao_max * NB * naux + mu;
     const float2 *Y2 = Y + (long long)k2 * nao_max * NB * naux + mu;
@@ -1050,21 +1044,24 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
           out[(2 * p + 1) * plane + r] = pi[p];
         }
       }
-    if (mc_pad) {  // [q][k1][nu][a b]: the fused direct kernel's layout (a pair's columns contiguous)
+    if (mc_pad) {  // [q][k1][nu][a b]: the fused direct kernel's layout, staged below
 #pragma unroll
       for (int a = 0; a < NC; a++)
 #pragma unroll
         for (int b = 0; b < NC; b++) mstage[threadIdx.x * (NC * NC) + a * NC + b] = mc[a][b];
-      __syncthreads();
-      for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
-        Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
-      __syncthreads();
     } else {       // [q][k1][a b][nu]
       float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * naux + mu;
 #pragma unroll
       for (int a = 0; a < NC; a++)
 #pragma unroll
         for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * naux] = mc[a][b];
+    }
+    }  // mu < naux
+    if (mc_pad) {  // block-uniform: the staged values of this mu range as one contiguous run
+      __syncthreads();
+      for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
+        Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
+      __syncthreads();
     }
   }
 }

@@ -1,6 +1,7 @@
-"""Multi-rank host logic of bench.py on CPU (gloo, world size 2): the job's time is the
-slowest rank's, the value counts every rank's units, and the reference arm runs on rank 0
-only.  No GPU is touched."""
+"""Multi-rank host logic on CPU (gloo, world size 2): the job's time is the slowest rank's, the
+value counts every rank's units, the reference arm runs on rank 0 only, and the batched
+crystals are sharded across ranks (each rank computes the same longest-processing-time-first
+assignment; together the ranks cover every system exactly once).  No GPU is touched."""
 import os
 import socket
 import subprocess
@@ -53,3 +54,37 @@ def test_reference_arm_is_silent_on_nonzero_rank():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def _shard_rank(rank: int, world: int, port: int, q):
+    from paper_2607_05853_b300.shard import assembly_work, assign_systems
+    from synth import batched_specs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    works = [assembly_work(sp.n_k, sp.n_aux, sp.nv, sp.nc) for sp in batched_specs(16)]
+    mine = assign_systems(works, world)[rank]
+    everyone = [None] * world
+    dist.all_gather_object(everyone, mine)     # what each rank will assemble
+    q.put((rank, mine, everyone, works))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batched_systems_sharded_across_ranks_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    (_, m0, e0, works), (_, m1, e1, _) = out
+    assert e0 == e1 == [m0, m1]                               # both ranks agree without negotiating
+    assert sorted(m0 + m1) == list(range(16))                 # every system exactly once
+    assert all(works[a] <= works[b] for m in (m0, m1) for a, b in zip(m, m[1:]))   # SJF inside a rank
+    loads = [sum(works[i] for i in m) for m in (m0, m1)]
+    bound = max(sum(works) / 2, max(works))                   # no assignment beats this
+    assert max(loads) <= 4.0 / 3.0 * bound                    # the LPT guarantee

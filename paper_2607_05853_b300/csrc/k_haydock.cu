@@ -369,13 +369,13 @@ __device__ __forceinline__ void ffma2(unsigned long long &acc, unsigned long lon
 constexpr int MV_CHUNK = 16, MV_STAGE_BYTES = MV_CHUNK * HT * 8;
 constexpr long long MV_WAIT = 4000000000LL;
 
-// Up to three vectors: four CTAs per SM (at most 128 registers a thread) with a two-stage ring
-// each, so 16 warps share an SM's FP32 pipes and eight 16 KB chunks are in flight per SM; more
-// vectors (the full-BSE product's four or six) need more registers: two CTAs, three stages.
+// Three CTAs per SM for up to three vectors; more vectors (the full-BSE product's four or six)
+// need more registers: two CTAs.  (Four CTAs of 128 registers with two-stage rings measured
+// the same 0.63 ms per 27648-dim product as three: not latency-bound by warp count.)
 template <int NP>
 struct HmvSmem {
-  static constexpr int STAGES = NP <= 3 ? 2 : 3;
-  static constexpr int CTAS = NP <= 3 ? 4 : 2;
+  static constexpr int STAGES = 3;
+  static constexpr int CTAS = NP <= 3 ? 3 : 2;
   static constexpr int RSTR = 8 * NP + 4;                 // floats per lane in the U-sum scratch
   static constexpr int XB = NP * HT * 24;                 // x vectors: (yr,-yr,yi,yi) + (xr,xi)
   static constexpr int USTR = (HT * NP * 8 > 32 * RSTR * 4) ? HT * NP * 8 : 32 * RSTR * 4;

@@ -47,7 +47,7 @@ struct SplitWS {
   int bn_d = 0;                  // N tile of the fused kernel (>= N_aux)
   int naux_pad = 0;              // M_cc row length (multiple of 16) in the fused layout
   int pairs_d = 0, nui_d = 0;    // pairs per tile; M_cc columns per ring item
-  CUtensorMap tmB_d;
+  CUtensorMap tmB_d, tmM_d;      // W pieces with the fused N tile; M_cc {nu, ab, (q, k1)} per item
   // FP32 per-k stage
   float2 *PHQ = nullptr;         // [nk][n_RW]  w_R e^{-i q.R}
   float2 *PHK = nullptr;         // [nk][n_RC]  e^{+i k.R}
@@ -946,9 +946,8 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
 // M_cc element of that mu; both LRI terms go into one accumulator,
 //   M_vv[i][j] = sum_s conj(c2_sj) Y1_si + c1_si conj(Y2_sj),
 //   M_cc[a][b] = sum_s conj(c1_sa) Y2_sb + c2_sb conj(Y1_sa)   (band indices in the window).
-// M_cc is written [q][k1][a b][nu], or [q][k1][nu][a b] with nu padded to mc_pad (mc_pad > 0);
-// in the second layout a block's M_cc values go through shared memory ([mu][a b] after the
-// band tables) so that the stores of consecutive mu are one contiguous, coalesced run.
+// M_cc is written [q][k1][a b][nu] with rows of naux (mc_pad = 0) or of mc_pad (> naux, for the
+// fused kernel's tensor map) elements; the stores of one (a, b) over a warp's mu coalesce.
 // grid: x = q - q0, y = k1; block: mu chunk (blockDim >= 32), loop over mu.
 template <int NV, int NC>
 __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
@@ -971,12 +970,8 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   }
   __syncthreads();
   const long long plane = (long long)rows * kmem;
-  float2 *mstage = scf + 2 * nao_tot * NB;  // [blockDim][NC NC] (mc_pad > 0)
-  // every thread runs every iteration of this loop (the block-wide barriers of the staged
-  // store sit outside the per-mu branch)
-  for (int mu_base = 0; mu_base < naux; mu_base += blockDim.x) {
-    const int mu = mu_base + threadIdx.x;
-    if (mu < naux) {
+  const int mrow = mc_pad ? mc_pad : naux;  // M_cc row length
+  for (int mu = threadIdx.x; mu < naux; mu += blockDim.x) {
     const int A = aux_atom[mu], ao0 = ao_start[A], na = naoA[A];
     const float2 *Y1 = Y + (long long)k1 * nao_max * NB * naux + mu;
     const float2 *Y2 = Y + (long long)k2 * nao_max * NB * naux + mu;
@@ -1044,25 +1039,11 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
           out[(2 * p + 1) * plane + r] = pi[p];
         }
       }
-    if (mc_pad) {  // [q][k1][nu][a b]: the fused direct kernel's layout, staged below
+    float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * mrow + mu;
 #pragma unroll
-      for (int a = 0; a < NC; a++)
+    for (int a = 0; a < NC; a++)
 #pragma unroll
-        for (int b = 0; b < NC; b++) mstage[threadIdx.x * (NC * NC) + a * NC + b] = mc[a][b];
-    } else {       // [q][k1][a b][nu]
-      float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * naux + mu;
-#pragma unroll
-      for (int a = 0; a < NC; a++)
-#pragma unroll
-        for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * naux] = mc[a][b];
-    }
-    }  // mu < naux
-    if (mc_pad) {  // block-uniform: the staged values of this mu range as one contiguous run
-      __syncthreads();
-      for (int e = threadIdx.x; e < min((int)blockDim.x, naux - mu_base) * NC * NC; e += blockDim.x)
-        Mc[(((long long)qq * nk + k1) * mc_pad + mu_base) * (NC * NC) + e] = mstage[e];
-      __syncthreads();
-    }
+      for (int b = 0; b < NC; b++) mo[(long long)(a * NC + b) * mrow] = mc[a][b];
   }
 }
 
@@ -1355,7 +1336,7 @@ template <int NV, int NC>
 void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq, int mc_pad) {
   const int na = c->naux_tot;
   const int bs = w->proj_bs ? w->proj_bs : std::min(160, (na + 31) / 32 * 32);
-  const size_t sm = sizeof(float2) * (2 * c->nao_tot * (NV + NC) + (mc_pad ? (size_t)bs * NC * NC : 0));
+  const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
   k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom,
                                                              c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
                                                              c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap,
@@ -1451,6 +1432,22 @@ bool make_map(CUtensorMap *m, void *base, int k_extent, long long rows, long lon
   return r == CUDA_SUCCESS;
 }
 
+// 3-D tensor of 8-byte elements (complex64 values copied bit for bit) {x, y, z} with row pitch
+// x_pitch and plane pitch y * x_pitch elements, box {bx, by, bz}: M_cc of a slab for the fused
+// kernel, {nu, (a, b), (q, k1)}.
+bool make_map_c64_3d(CUtensorMap *m, void *base, long long x, long long y, long long z, long long x_pitch, int bx,
+                     int by, int bz) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)x, (cuuint64_t)y, (cuuint64_t)z};
+  cuuint64_t strides[2] = {(cuuint64_t)x_pitch * 8, (cuuint64_t)(y * x_pitch) * 8};
+  cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <int NP, int BN>
 bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
                      int prof_id) {
@@ -1493,7 +1490,7 @@ bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof
   const long long total = (long long)a.tiles_m * a.tiles_b;
   const int ctas = (int)std::min<long long>(total, c->n_sm);
   bse_prof_begin(c, prof_id);
-  tcd::k_tc_direct<NP, BN, NC><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, a);
+  tcd::k_tc_direct<NP, BN, NC><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, w->tmM_d, a);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_direct");
@@ -1533,7 +1530,6 @@ void set_attr() {
 }
 template <int NV, int NC>
 void set_g2_attr() {
-  cudaFuncSetAttribute(k_proj32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
@@ -1621,6 +1617,9 @@ bse_status split_setup(bse_ctx *c) {
   bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
             make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
             (!w->fused || make_map(&w->tmB_d, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_d)) &&
+            (!w->fused || make_map_c64_3d(&w->tmM_d, w->Mc32, w->naux_pad, (long long)c->nc * c->nc,
+                                          (long long)w->nq * c->nk, w->naux_pad, w->nui_d, c->nc * c->nc,
+                                          w->pairs_d)) &&
             make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&
             make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN);
   if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");

@@ -8,8 +8,8 @@
 // (BN >= N_aux), so the epilogue finishes D for those pairs from tensor memory alone.
 //
 // The shared-memory ring carries one sequence of items per tile: the tile's K chunks of the
-// GEMM operands (consumed by the MMA warp), then the tile's M_cc rows in slices of NUI columns
-// (consumed by the epilogue warps).  Each item takes stage it % S; the producer waits for the
+// GEMM operands (consumed by the MMA warp), then the tile's M_cc rows in slices of NUI columns,
+// one TMA box {NUI, Nc^2, P} each (consumed by the epilogue warps).  Each item takes stage it % S; the producer waits for the
 // stage to be released (by the MMA's commit or by one epilogue thread) before refilling it.
 // The epilogue releases the accumulators as soon as its last M_cc slice is done and then
 // adds D to H (read-modify-write: the exchange GEMM wrote every element first), so the next
@@ -31,14 +31,6 @@ using tcg::BK;
 using tcg::BM;
 using tcg::ROWB;
 using tcg::WAIT_LIMIT;
-
-// 1-D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size % 16 == 0).
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   tc::smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(tc::smem_u32(bar))
-               : "memory");
-}
 
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
@@ -67,7 +59,7 @@ struct DArgs {
   int naux, naux_pad;     // columns of T; M_cc row length in the slab buffer (multiple of 16)
   int nui;                // M_cc columns per ring item (multiple of 16)
   int n_mitems;           // ceil(naux_pad / nui)
-  const float2 *Mc;       // M_cc, [q][k1][nu (naux_pad)][a b] complex64
+  const float2 *Mc;       // M_cc, [q][k1][a b][nu (naux_pad)] complex64 (read through tmM)
   const int *qlist;       // transfer of batch b: qlist[b_base + b]
   int b_base;
   int n1, n2, n3;
@@ -94,10 +86,11 @@ __device__ __forceinline__ bool d_self_conj(int q, int n1, int n2, int n3) {
 
 template <int NP, int BN, int NC>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_direct(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DArgs args) {
+    k_tc_direct(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmM, DArgs args) {
   using C = DCfg<NP, BN>;
   constexpr int NCC = NC * NC, HALF = NCC / 2;  // D columns (a, b) per epilogue warp
-  static_assert(HALF % 2 == 0, "the warps' D halves are read from shared memory as float4 pairs");
+
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t *full = (uint64_t *)(smem + C::S * C::STAGE);
@@ -125,6 +118,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 0 && lane == 0) {
     tc::prefetch_tmap(&tmA);
     tc::prefetch_tmap(&tmB);
+    tc::prefetch_tmap(&tmM);
   }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -145,7 +139,6 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int m0 = m * args.pairs * rpp;
       const int q = args.qlist[args.b_base + b];
       const int k1_0 = m0 / rpp;
-      const int np_tile = min(args.pairs, args.rows / rpp - k1_0);  // pairs present in this tile
       for (int item = 0; item < items; item++, it++) {
         const int s = it % C::S;
         if (it >= C::S && !tc::mbar_wait_bounded(&empty[s], ((it / C::S) & 1) ^ 1, WAIT_LIMIT)) {
@@ -167,15 +160,11 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, 0, q * C::PP + pp);
           }
         } else {
-          // columns nu0 .. nu0 + nn - 1 of M_cc for the tile's pairs: smem [pair][nu][ab]
+          // columns nu0 .. nu0 + nui - 1 of M_cc for the tile's pairs, one TMA box
+          // {nui, Nc^2, pairs}: smem [pair][ab][nu] (columns or pairs past the tensor zero-filled)
           const int nu0 = (item - args.k_chunks) * args.nui;
-          const int nn = min(args.nui, args.naux_pad - nu0);
-          const uint32_t bytes = (uint32_t)nn * NCC * 8;
-          tc::mbar_arrive_expect_tx(&full[s], bytes * np_tile);
-          for (int pr = 0; pr < np_tile; pr++) {
-            const float2 *src = args.Mc + (((long long)b * (args.rows / rpp) + k1_0 + pr) * args.naux_pad + nu0) * NCC;
-            bulk_g2s(st + (size_t)pr * args.nui * NCC * 8, src, bytes, &full[s]);
-          }
+          tc::mbar_arrive_expect_tx(&full[s], (uint32_t)args.pairs * NCC * args.nui * 8);
+          tc::tma_load_3d(st, &tmM, &full[s], nu0, 0, b * (args.rows / rpp) + k1_0);
         }
       }
     }
@@ -275,29 +264,35 @@ __global__ void __launch_bounds__(THREADS, 1)
         ok = got;
         const int nu0 = mi * args.nui;
         const int nn = min(args.nui, args.naux - nu0);     // padded columns carry T = 0
-        const float2 *mcs = reinterpret_cast<const float2 *>(smem + s * C::STAGE) + (size_t)pr * args.nui * NCC +
-                            half * HALF;
+        // this warp's (a, b) rows of the pair: [ab][nu], nui columns each
+        const float2 *mcs = reinterpret_cast<const float2 *>(smem + s * C::STAGE) +
+                            ((size_t)pr * NCC + half * HALF) * args.nui;
         for (int c0 = 0; c0 < nn; c0 += 16) {
           uint32_t rr[16], ri[16];
           tc::tmem_ld16(tm_re + lane_off + nu0 + c0, rr);
           tc::tmem_ld16(tm_im + lane_off + nu0 + c0, ri);
           tc::tmem_ld_wait();
           if (ok && row_ok) {
+            // columns in pairs (nu, nu + 1); T is zero past N_aux, and the M_cc column paired
+            // with the last one of an odd N_aux is ignored
             const int cmax = min(16, nn - c0);
 #pragma unroll
-            for (int u = 0; u < 16; u++) {
+            for (int u = 0; u < 16; u += 2) {
               if (u >= cmax) break;
-              const float tr = __uint_as_float(rr[u]), ti = __uint_as_float(ri[u]);
-              const unsigned long long TR = tc::pk2(tr, tr), TI = tc::pk2(ti, ti);
-              const float4 *mrow = reinterpret_cast<const float4 *>(mcs + (size_t)(c0 + u) * NCC);
+              const float tr0 = __uint_as_float(rr[u]), ti0 = __uint_as_float(ri[u]);
+              const float tr1 = __uint_as_float(rr[u + 1]), ti1 = __uint_as_float(ri[u + 1]);
+              const unsigned long long TR0 = tc::pk2(tr0, tr0), TI0 = tc::pk2(ti0, ti0);
+              const unsigned long long TR1 = tc::pk2(tr1, tr1), TI1 = tc::pk2(ti1, ti1);
 #pragma unroll
-              for (int e2 = 0; e2 < HALF / 2; e2++) {
-                const float4 mm = mrow[e2];
-                const unsigned long long m0v = tc::pk2(mm.x, mm.y), m1v = tc::pk2(mm.z, mm.w);
-                tc::ffma2(acc1[2 * e2], m0v, TR);
-                tc::ffma2(acc2[2 * e2], m0v, TI);
-                tc::ffma2(acc1[2 * e2 + 1], m1v, TR);
-                tc::ffma2(acc2[2 * e2 + 1], m1v, TI);
+              for (int e = 0; e < HALF; e++) {
+                const float4 mm = *reinterpret_cast<const float4 *>(mcs + (size_t)e * args.nui + c0 + u);
+                const bool tail = u + 1 >= cmax;
+                const unsigned long long m0v = tc::pk2(mm.x, mm.y),
+                                         m1v = tc::pk2(tail ? 0.f : mm.z, tail ? 0.f : mm.w);
+                tc::ffma2(acc1[e], m0v, TR0);
+                tc::ffma2(acc2[e], m0v, TI0);
+                tc::ffma2(acc1[e], m1v, TR1);
+                tc::ffma2(acc2[e], m1v, TI1);
               }
             }
           }

@@ -33,6 +33,11 @@ METRIC = "H_BSE elements/s (split-prec TC vs FP64 GPU) at ≤1 meV lowest-excito
 # Hermitian matvec kernel, from one ncu capture of the 16000-dim case (7875 tiles):
 # 1.032880 GB read (the tiles themselves) + 45.80 MB written (the partial slots).
 MV_DRAM_BYTES_PER_TILE = (1.032880e9 + 45.800704e6) / 7875
+# DRAM bytes per transfer q of the split assembly's two slab kernels, from ncu captures of one
+# 20-q slab of the 16000-dim case (10^3 k-points, N_aux 150, Nv = Nc = 4): the projections
+# (313.4 MB read, 922.3 MB written: the M_vv bf16 pieces and M_cc) and the fused direct term
+# (1077.2 MB read, 70.9 MB written).  Both grow in proportion to the k-points per q.
+ASM_DRAM_BYTES_PER_Q_MESH10 = ((313.358848e6 + 922.320640e6) + (1077.169e6 + 70.853376e6)) / 20
 UNIT = "H elements/s"
 
 
@@ -161,6 +166,24 @@ def cpu_baseline(inp, seconds, rng_seed=5):
             "sample": f"{n} H blocks ({elems} elements) of the 27648-dim workload, W(q) and C(k) "
                       f"memoised per block as the oracle does, {dt:.1f} s on host cores (assembly only: "
                       f"the GPU line's value also includes the spectrum)"}
+
+
+def _qplus(mesh):
+    """One of each q / -q pair of the mesh (self-conjugate q once): the transfers the assembly
+    computes."""
+    n1, n2, n3 = (int(x) for x in mesh)
+    seen, out = set(), []
+    for a in range(n1):
+        for b in range(n2):
+            for c in range(n3):
+                q = (a, b, c)
+                if q in seen:
+                    continue
+                mq = ((n1 - a) % n1, (n2 - b) % n2, (n3 - c) % n3)
+                seen.add(q)
+                seen.add(mq)
+                out.append(q)
+    return out
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -538,6 +561,13 @@ def main():
                       "dipole vector and the 3-polarisation Haydock spectrum); the assembly-only rate "
                       "(interp + project + assemble) is assembly_elements_per_s",
         "assembly_elements_per_s": asm_rate,
+        "assembly_dram_bytes_est": (
+            {"slab_kernels": ASM_DRAM_BYTES_PER_Q_MESH10 * (spec.n_k / 1000.0) * len(_qplus(spec.dense)),
+             "H_bytes": float(ctx.dim) ** 2 * (16 if args.precision == "fp64" else 8),
+             "note": "projections + fused direct term: DRAM bytes per q from ncu on the 16000-dim case, "
+                     "scaled by k-points per q and the unique q of this mesh (the exchange GEMM's H write "
+                     "and the per-k stage come on top); H_bytes is what the assembly must write"}
+            if args.precision != "fp64" and spec.n_aux <= 160 else None),
         "spectrum_throughput": {"haydock_steps_per_s": nsteps / (statistics.mean(spec_ms) / 1000.0),
                                 "matvec_GBps": roof.get("achieved") if top == "matvec" else None},
         "kernels_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},

@@ -49,6 +49,14 @@ band minimum (counting up); k is flattened (n1*N2 + n2)*N3 + n3.
 Everything is FP64 / complex128, evaluated element block by element block from the
 definitions above; W(q) per q and C(k) per k are memoised (this does not change what
 is computed).  Nothing here is shared with, or imported from, the CUDA path.
+
+Pins (tests/test_oracle_pins.py) tie every function to something outside it: a real-space
+brute force of both kernels (A, B, finite Q), FFT and coarse-mesh identities of the
+interpolation, LAPACK, closed forms of the spectrum and of the full BSE, sum rules, central
+differences of the gradients, and for the dipoles the overlaps <i|d a/dk> from finite
+differences of the tight-binding eigenvectors.  Parity unpinned: the spin factor inside
+spectrum_prefactor (a reading of the paper's normalisation, shared by both sides) and
+absolute values against the paper's tables (its inputs are not available).
 """
 from __future__ import annotations
 

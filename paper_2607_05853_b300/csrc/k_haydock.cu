@@ -379,8 +379,7 @@ struct HmvSmem {
   static constexpr int RSTR = 8 * NP + 4;                 // floats per lane in the U-sum scratch
   static constexpr int XB = NP * HT * 24;                 // x vectors: (yr,-yr,yi,yi) + (xr,xi)
   static constexpr int USTR = (HT * NP * 8 > 32 * RSTR * 4) ? HT * NP * 8 : 32 * RSTR * 4;
-  static constexpr int UACC = HT * NP * 8;                // row sums of the CTA's current row run
-  static constexpr int BYTES = 128 + STAGES * MV_STAGE_BYTES + XB + 4 * USTR + UACC;
+  static constexpr int BYTES = 128 + STAGES * MV_STAGE_BYTES + XB + 4 * USTR;
 };
 
 // SYM = true: H is complex symmetric (H^T = H) instead of Hermitian; the mirrored tile then
@@ -402,11 +401,6 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
   float4 *yb = reinterpret_cast<float4 *>(ring + MV_STAGES * MV_STAGE_BYTES);  // [NP][HT] (yr,-yr,yi,yi)
   float2 *xc = reinterpret_cast<float2 *>(yb + NP * HT);                       // [NP][HT] (xr,xi)
   uint8_t *uni = reinterpret_cast<uint8_t *>(xc + NP * HT);  // per warp: U-sum scratch, then V partials
-  float2 *uacc = reinterpret_cast<float2 *>(uni + 4 * S::USTR);  // [HT][NP] row sums of the current run
-  // this CTA's tiles: one contiguous range of the row-ordered upper-triangle list, so consecutive
-  // tiles mostly share their block row and its row sums accumulate here across them
-  const int t_lo = (int)((long long)blockIdx.x * ntiles / gridDim.x);
-  const int t_hi = (int)((long long)(blockIdx.x + 1) * ntiles / gridDim.x);
   bool live = false;
   for (int p = 0; p < NP; p++) live |= (j < meff[p]);
   if (!live) return;
@@ -424,7 +418,7 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
   // ---- copies: chunk n of this CTA's sequence goes to stage n % MV_STAGES.  The first
   // MV_STAGES are issued here; afterwards the last warp to take a stage refills it ----
   constexpr int CPT = HT / MV_CHUNK;
-  const int n_chunks = (t_hi - t_lo) * CPT;
+  const int n_chunks = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * CPT;
   auto issue = [&](int n, int2 tl) {
     const int st = n % MV_STAGES;
     tc::mbar_arrive_expect_tx(&full[st], MV_STAGE_BYTES);
@@ -438,7 +432,7 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
   };
   if (threadIdx.x == 0) {
     tc::prefetch_tmap(&tmH);
-    const int2 tl0 = tiles[t_lo];
+    const int2 tl0 = tiles[blockIdx.x];
     for (int k = 0; k < MV_STAGES && k < n_chunks; k++) issue(k, tl0);
   }
   int it = 0;
@@ -471,19 +465,16 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
       }                                                                                           \
     }                                                                                             \
   } while (0)
-  for (int e = threadIdx.x; e < HT * NP; e += 128) uacc[e] = make_float2(0.f, 0.f);
-  int run_bj = 0;  // first block column of the current row run
-  if (t_lo < t_hi) {
-    HMV_FETCH(t_lo);
+  if (blockIdx.x < ntiles) {
+    HMV_FETCH(blockIdx.x);
     HMV_PARK();
   }
-  for (int t = t_lo; t < t_hi; t++) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int bi = tl_next.x, bj = tl_next.y;
     const bool diag = bi == bj;
     asm volatile("bar.sync 1, 128;" ::: "memory");  // this tile's x vectors are parked
-    if (t == t_lo || bj == bi) run_bj = bj;  // a row run starts at the range start or a diagonal tile
-    const bool has_next = t + 1 < t_hi;
-    if (has_next) HMV_FETCH(t + 1);
+    const bool has_next = t + (int)gridDim.x < ntiles;
+    if (has_next) HMV_FETCH(t + gridDim.x);
     // a lane owns columns 2f, 2f+1 (f = lane, lane + 32): x as (xr, xr) and (-xi, xi) pairs
     unsigned long long XA[4][NP], XB[4][NP], V[4][NP];
 #pragma unroll
@@ -600,8 +591,7 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
           if (lane < 4 * NP) {
             const int rr = i / NP, p = i % NP;
             const int lr = c * MV_CHUNK + warp * 4 + rr;
-            uacc[lr * NP + p].x += tot.x;
-            uacc[lr * NP + p].y += tot.y;
+            part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = tot;
           }
         } else {
           // more pairs (4 NP) than half-warps can cover: lane i < 4 NP sums pair i over all
@@ -620,9 +610,7 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
             ffma2(s0, s1, one);
             const int rr = i / NP, p = i % NP;
             const int lr = c * MV_CHUNK + warp * 4 + rr;
-            const float2 tot = up2(s0);
-            uacc[lr * NP + p].x += tot.x;
-            uacc[lr * NP + p].y += tot.y;
+            part[(((long long)bi * nb + bj) * HT + lr) * NP + p] = up2(s0);
           }
         }
         __syncwarp();
@@ -651,13 +639,6 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
         part[(((long long)bj * nb + bi) * HT + l) * NP + p] = acc;
       }
     }
-    // the row run ends with this tile: its row sums go to slot (bi, run_bj)
-    if (!has_next || tl_next.x != bi) {
-      for (int e = threadIdx.x; e < HT * NP; e += 128) {
-        part[((long long)bi * nb + run_bj) * HT * NP + e] = uacc[e];
-        uacc[e] = make_float2(0.f, 0.f);
-      }
-    }
     if (has_next) HMV_PARK();  // visible after the next tile's opening barrier
   }
   // chunks copied but never consumed (only after a timeout) must land before the CTA exits
@@ -676,22 +657,17 @@ constexpr int hmv_tma_smem() {
   return HmvSmem<NP>::BYTES;
 }
 
-// W[p][row] for the rows of block t from the slots k_hmv_tma wrote, and the block's share of
-// alpha_j = Re(Q_j^H W) per polarisation (apart[p][t]).  Row block t's slots are the column
-// sums of the tiles (s, t), s < t (slot (t, s)), and the row sums of each run of tiles (t, b..)
-// one CTA took in a row, kept in the slot of the run's first column b: the runs start at the
-// row's diagonal tile and wherever a CTA's contiguous tile range (the k_hmv_tma launch's
-// grid of mv_grid CTAs over ntiles tiles) begins inside the row.  Two threads per output
-// stream the column-sum slots in two halves (the second also takes the row-run slots); each
-// keeps a compensated (Kahan) FP32 sum, so the result carries FP64-like accuracy without FP64
-// adds (B300's FP64 rate is ~1/60 of FP32), and the two halves meet in FP64 in a fixed order.
-// HALVES = 1 (more than four vectors): one thread per output streams every slot.
+// W[p][row] = sum_s part[t][s][row_local][p] for the rows of block t, and the block's share
+// of alpha_j = Re(Q_j^H W) per polarisation (apart[p][t]).  Two threads per output stream
+// the two halves of the block's slot slab; each keeps a compensated (Kahan) FP32 sum, so the
+// result carries FP64-like accuracy without FP64 adds (B300's FP64 rate is ~1/60 of FP32),
+// and the two halves meet in FP64 in a fixed order.
+// HALVES = 1 (more than four vectors): one thread per output streams the whole slab.
 template <int NP, int HALVES = 2>
 __global__ void __launch_bounds__(HALVES * HT * NP, 1) k_hmv_reduce(const float2 *__restrict__ part, long long dim,
                                                                 int nb, double2 *__restrict__ W,
                                                                 const double2 *__restrict__ Q, long long qs, int j,
-                                                                const int *__restrict__ meff, double *__restrict__ apart,
-                                                                int mv_grid, int ntiles) {
+                                                                const int *__restrict__ meff, double *__restrict__ apart) {
   __shared__ double2 hs[HT * NP];
   __shared__ double av[HT * NP];
   const int t = blockIdx.x;
@@ -699,32 +675,13 @@ __global__ void __launch_bounds__(HALVES * HT * NP, 1) k_hmv_reduce(const float2
   const int l = o / NP, p = o % NP;
   const long long row = (long long)t * HT + l;
   const bool on = row < dim && j < meff[p];
-  const int s0 = h ? t / 2 : 0, s1 = (h || HALVES == 1) ? t : t / 2;  // column-sum slots (t, s), s < t
+  const int s0 = h ? nb / 2 : 0, s1 = (h || HALVES == 1) ? nb : nb / 2;
   // Kahan: sum + (-comp) is the running total; each add is y = v - comp; t = sum + y;
   // comp = (t - sum) - y; sum = t
   float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
   if (on) {
     const float2 *src = part + ((long long)t * nb * HT + l) * NP + p;
     const long long step = (long long)HT * NP;
-    if (h || HALVES == 1) {
-      // row-run slots: the row's tiles are list entries r0 .. r0 + nb - t - 1; CTA c's range
-      // starts at floor(c ntiles / mv_grid)
-      const long long r0 = (long long)t * nb - (long long)t * (t - 1) / 2, r1 = r0 + nb - t;
-      long long c = ((r0 + 1) * mv_grid - 1) / ntiles + 1;  // first CTA starting after r0
-      long long start = r0;
-      while (start < r1) {
-        const float2 v = src[(t + (start - r0)) * step];
-        const float yx = v.x - cx, tx = sx + yx;
-        cx = (tx - sx) - yx;
-        sx = tx;
-        const float yy = v.y - cy, ty = sy + yy;
-        cy = (ty - sy) - yy;
-        sy = ty;
-        if (c >= mv_grid) break;
-        start = c * ntiles / mv_grid;
-        c++;
-      }
-    }
     int s = s0;
     for (; s + 8 <= s1; s += 8) {
       float2 v[8];
@@ -1375,18 +1332,15 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       if (n_pol == 1) {
         k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       grid, s.ntiles);
+        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmv_tma<2><<<grid, 128, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       grid, s.ntiles);
+        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmv_tma<3><<<grid, 128, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       grid, s.ntiles);
+        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
       bse_count_launch(2);
     } else if (c64 && s.hpart) {
@@ -1394,18 +1348,15 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       if (n_pol == 1) {
         k_hmatvec_c64<1><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       s.ntiles, s.ntiles);
+        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else if (n_pol == 2) {
         k_hmatvec_c64<2><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       s.ntiles, s.ntiles);
+        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       } else {
         k_hmatvec_c64<3><<<g, 128, 0, st>>>((const float2 *)H, dim, s.nbt, s.Q32, qs, j, s.hpart, s.meff);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart,
-                                                       s.ntiles, s.ntiles);
+        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
       }
       bse_count_launch(2);
     } else if (c64) {
@@ -1883,8 +1834,7 @@ bse_status halfmv_run(bse_ctx *c, HalfMV *h, const void *Hm, bool sym, const flo
 #undef HALF_LAUNCH
   bse_prof_end(c, BSE_KP_MATVEC);
 #define HALF_REDUCE(NPV, HV) \
-  k_hmv_reduce<NPV, HV><<<h->nbt, HV * HT * NPV, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart, \
-                                                          grid, h->ntiles)
+  k_hmv_reduce<NPV, HV><<<h->nbt, HV * HT * NPV, 0, st>>>(h->part, dim, h->nbt, W, h->Qdummy, dim, 0, h->ones, h->apart)
   if (np == 1) HALF_REDUCE(1, 2);
   else if (np == 2) HALF_REDUCE(2, 2);
   else if (np == 3) HALF_REDUCE(3, 2);

@@ -10,7 +10,7 @@ value = H elements (dim^2) per second of whole step; the assembly-only rate, the
 GPU path, the accuracy against the FP64 path and the stage breakdown are extra keys.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision bf16x3|bf16x2|bf16x1|fp64]
+                  [--precision bf16x3|bf16x2|bf16x1|tf32x2|fp64]
 """
 from __future__ import annotations
 
@@ -65,6 +65,68 @@ def parse():
     ap.add_argument("--batch16", action="store_true",
                     help="add the 16-uneven-crystal batch (one CUDA graph) report under 'batched_uneven'")
     return ap.parse_args()
+
+
+# Nominal dense tensor rates of the part (B300: tf32 1.1, bf16 2.25 PFLOP/s): a tf32 contraction
+# takes the measured bf16 peak times their ratio.
+TF32_PER_BF16 = 1.1 / 2.25
+PIECE_PRODUCTS = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1, "tf32x2": 3}
+
+
+def tensor_peak(pk, precision, key="bf16_tflops_sustained"):
+    return pk[key] * (TF32_PER_BF16 if precision == "tf32x2" else 1.0)
+
+
+def tf32x2_report(inp, d, spec, ctx, H64, w_d, prof, pk, args):
+    """The same workload assembled with two tf32 pieces per operand (BSE_TF32X2: 3 kind::tf32
+    products instead of bf16x3's 6 bf16 ones): assembly time, the M_vv W(q) kernel's tensor
+    rate against bf16x3's, and its errors against the FP64 GPU path (outside the timed region)."""
+    import torch
+    from paper_2607_05853_b300.api import BSE
+    st = torch.cuda.current_stream()
+    dim2 = float(ctx.dim) ** 2
+    c3 = BSE.from_inputs(inp, precision="tf32x2")
+    H3 = torch.empty((ctx.dim, ctx.dim), dtype=torch.complex64, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rep in range(2):                      # the first pass warms up
+        if rep == 1:
+            c3.profile(True)
+        a.record(st)
+        c3.interp_W(d["W_R"], d["V0"])
+        c3.project_pairs(d["C_R"], d["c_k"], d["e_qp"])
+        c3.assemble(H3)
+        b.record(st)
+        c3.sync()
+    tf_ms = a.elapsed_time(b)
+    g1_tf, _ = c3.profile_read("g1")
+    ex_tf, _ = c3.profile_read("exch")
+    c3.profile(False)
+    diff = H3.to(torch.complex128) - H64
+    dmax = diff.abs().max().item()
+    del diff
+    w_t, r_t = c3.lowest(H3, 10, 300)
+    c3.sync()
+    nk, naux, nv = spec.n_k, spec.n_aux, spec.nv
+    nq_half = (nk + sum(1 for q in range(nk) if _self_conj(q, spec.dense))) // 2
+    g1_mac = 8.0 * nq_half * nk * nv * nv * naux * naux
+    per = max(1, args.steps)
+    g1_bf = prof["g1"][0] / per
+    tf_peak, bf_peak = tensor_peak(pk, "tf32x2"), tensor_peak(pk, "bf16x3")
+    out = {"assembly_ms": tf_ms, "elements_per_s": dim2 / (tf_ms / 1000.0),
+           "g1_ms": g1_tf, "g1_ms_bf16x3": g1_bf, "exchange_ms": ex_tf,
+           "g1_tensor_tflops": g1_mac * 3 / (g1_tf * 1e-3) / 1e12,
+           "g1_tensor_frac": g1_mac * 3 / (g1_tf * 1e-3) / 1e12 / tf_peak,
+           "g1_tensor_tflops_bf16x3": g1_mac * 6 / (g1_bf * 1e-3) / 1e12,
+           "g1_tensor_frac_bf16x3": g1_mac * 6 / (g1_bf * 1e-3) / 1e12 / bf_peak,
+           "tensor_peak_tf32": tf_peak,
+           "peak_source": pk["source"] + " (sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25)",
+           "max_abs_dH_eV": dmax, "lowest10_abs_err_meV": (1000.0 * (w_t - w_d).abs()).tolist(),
+           "note": "the bench workload with two tf32 pieces per FP32 operand (3 kind::tf32 products) instead of "
+                   "bf16x3 (6 bf16 products); g1 = the M_vv W(q) kernel (fused with the second contraction "
+                   "where N_aux <= 160); errors against the FP64 GPU path"}
+    del H3
+    c3.close()
+    return out
 
 
 def workload(small, mesh=0):
@@ -356,11 +418,11 @@ def main():
         if args.precision != "fp64" and ctx.dim % 2 == 0:
             roof["traffic"] = MV_DRAM_BYTES_PER_TILE * ntiles
     elif top == "g1" and args.precision != "fp64":
-        pieces = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1}[args.precision]
+        pieces = PIECE_PRODUCTS[args.precision]
         alg = 8.0 * nk * nv * nv * naux * naux * pieces * (ctx_slab_q(ctx, spec))
         roof = {"bound": "tensor", "achieved": alg / (per_launch_ms * 1e-3) / 1e12,
-                "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s"}
-        roof_note = "M_vv W(q): executed bf16 tensor flops (8 N_k Nv^2 Naux^2 x split products) per launch"
+                "peak": tensor_peak(pk, args.precision), "unit": "TFLOP/s"}
+        roof_note = "M_vv W(q): executed tensor flops (8 N_k Nv^2 Naux^2 x split products) per launch"
     else:
         alg = None
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s"}
@@ -376,7 +438,7 @@ def main():
     # each q/-q pair, the exchange over the full square)
     tensor = None
     if args.precision != "fp64":
-        pieces = {"bf16x3": 6, "bf16x2": 3, "bf16x1": 1}[args.precision]
+        pieces = PIECE_PRODUCTS[args.precision]
         nq_half = (nk + sum(1 for q in range(nk) if _self_conj(q, spec.dense))) // 2
         g1_flops = 8.0 * nq_half * nk * nv * nv * naux * naux * pieces
         ex_flops = 8.0 * float(ctx.dim) ** 2 * naux * pieces
@@ -388,16 +450,17 @@ def main():
             a_g1 = g1_flops / ((g1_ms / per) * 1e-3) / 1e12
             a_ex = ex_flops / ((ex_ms / per) * 1e-3) / 1e12
             asm_s = statistics.mean([p + a for p, a in zip(pre_ms, asm_ms)]) * 1e-3
-            sus = pk["bf16_tflops_sustained"]
+            sus = tensor_peak(pk, args.precision)
             fused = g2_n == 0
             tensor = {"bound": "tensor", "unit": "TFLOP/s", "peak": sus,
-                      "peak_source": pk["source"] + " (sustained bf16)",
+                      "peak_source": pk["source"] + (" (sustained bf16 x nominal tf32/bf16 ratio 1.1/2.25)"
+                                                     if args.precision == "tf32x2" else " (sustained bf16)"),
                       "g1_achieved": a_g1, "g1_frac": a_g1 / sus,
                       "exchange_achieved": a_ex, "exchange_frac": a_ex / sus,
                       "assembly_achieved": (g1_flops + ex_flops) / asm_s / 1e12,
                       "assembly_frac": (g1_flops + ex_flops) / asm_s / 1e12 / sus,
                       "direct_fused": fused,
-                      "note": "executed bf16 flops per step = 8 x complex MACs x piece products; g1 = the M_vv W(q) "
+                      "note": "executed tensor flops per step = 8 x complex MACs x piece products; g1 = the M_vv W(q) "
                               "GEMM" + (" fused with the second contraction T M_cc^T and the H update (its time "
                                         "includes that CUDA-core epilogue)" if fused else "") +
                               "; assembly = per-k stage + projections + every GEMM, with the tensor-core flops of "
@@ -469,6 +532,8 @@ def main():
                     f"over {n_mv} Lanczos steps; errors against the FP64 GPU path"}
         del H2, diff
         c2.close()
+        if args.precision == "bf16x3":
+            extra["split_tf32x2"] = tf32x2_report(inp, d, spec, ctx, H64, w_d, prof, pk, args)
         del H64
         ref.close()
 
@@ -546,7 +611,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64"}.get(args.precision, f"{args.precision} (assembly: bf16-piece tensor-core GEMMs with f32 "
+        "dtype": {"fp64": "f64"}.get(args.precision, f"{args.precision} (assembly: {'tf32' if args.precision == 'tf32x2' else 'bf16'}-piece tensor-core GEMMs with f32 "
                                                      "accumulation, f32 projections, f64 phases and diagonal; H "
                                                      "stored complex64; Lanczos: f64 recursion and basis, f32 "
                                                      "products on the complex64 H with compensated sums)"),

@@ -76,8 +76,11 @@ typedef enum {
  *              bse_params.h_complex128 (then the spectrum, lowest-exciton and window entries
  *              read it with the FP64 path's full-read products).
  *  BSE_BF16X2: as BF16X3 with two pieces (3 piece products).
- *  BSE_BF16X1: one bf16 piece (1 product) -- an accuracy ablation. */
-typedef enum { BSE_FP64 = 0, BSE_BF16X3 = 1, BSE_BF16X2 = 2, BSE_BF16X1 = 3 } bse_precision;
+ *  BSE_BF16X1: one bf16 piece (1 product) -- an accuracy ablation.
+ *  BSE_TF32X2: as BF16X3 with two tf32 pieces per FP32 operand, x ~ tf32(x) + tf32(x - tf32(x))
+ *              (about 22 significant bits), the 3 products of order <= 1 on tcgen05 kind::tf32
+ *              MMAs (half the bf16 rate); H as for the bf16 splits. */
+typedef enum { BSE_FP64 = 0, BSE_BF16X3 = 1, BSE_BF16X2 = 2, BSE_BF16X1 = 3, BSE_TF32X2 = 4 } bse_precision;
 
 typedef struct {
   int32_t n_atoms;
@@ -95,10 +98,29 @@ typedef struct {
   int32_t precision;             /* a bse_precision                                   */
   int32_t h_complex128;          /* split precisions: 1 stores H as complex128 (the    */
                                  /* E_c - E_v diagonal then exact in FP64), 0 complex64 */
+  /* Optional consistency data of W's R-set (§III.B: W(R) is the Fourier transform of W on
+   * the coarse mesh, folded into the Wigner-Seitz cell).  The arithmetic needs neither: phases
+   * use integer R, and the coarse mesh enters only through R_W and w_RW.  When given they are
+   * checked at setup (BSE_EINVAL on a mismatch):
+   *  coarse  : the coarse (GW) mesh, or {0,0,0}: the weights w_RW of the images of each coarse
+   *            Born-von Karman class (R mod coarse, per axis) sum to 1 (within 1e-9), every
+   *            class included, and no image's weight is <= 0;
+   *  lattice : host [3][3] float64 lattice vectors a_i as rows (any length unit), or NULL;
+   *            with coarse, every image is a shortest member of its class under this metric
+   *            (|sum_i R_i a_i| <= |sum_i (R_i + m_i coarse_i) a_i| (1 + 1e-9) + 1e-9 for all
+   *            m in {-1,0,1}^3).
+   * Atom positions and the occupied-band count do not enter the method's arithmetic (C(R) and
+   * the band window's coefficients are inputs), so bse_params does not take them. */
+  int32_t coarse[3];
+  const double *lattice;
 } bse_params;
 
-/* Validate p, copy its host arrays, allocate the workspace on the current CUDA device
- * and bind the context to `cuda_stream` (a cudaStream_t, NULL = default stream).
+/* The host-side checks of bse_setup alone (argument ranges, sizes and the optional coarse /
+ * lattice consistency above); touches no device.  BSE_OK or BSE_EINVAL. */
+bse_status bse_check_params(const bse_params *p);
+
+/* Validate p (bse_check_params), copy its host arrays, allocate the workspace on the current
+ * CUDA device and bind the context to `cuda_stream` (a cudaStream_t, NULL = default stream).
  * On success *out receives the context; on failure *out is NULL.  Synchronous. */
 bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out);
 

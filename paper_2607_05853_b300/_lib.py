@@ -10,10 +10,10 @@ LIB_PATH = os.path.join(HERE, "libbse.so")
 
 BSE_OK, BSE_EINVAL, BSE_ENOMEM, BSE_ECUDA, BSE_ETIMEOUT, BSE_ESTATE, BSE_EDEVICE = range(7)
 STATUS_NAMES = ["BSE_OK", "BSE_EINVAL", "BSE_ENOMEM", "BSE_ECUDA", "BSE_ETIMEOUT", "BSE_ESTATE", "BSE_EDEVICE"]
-PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x2": 2, "bf16x1": 3}
+PRECISIONS = {"fp64": 0, "bf16x3": 1, "bf16x2": 2, "bf16x1": 3, "tf32x2": 4}
 
 # Every symbol include/bse.h declares.
-EXPORTS = ["bse_setup", "bse_interp_W", "bse_project_pairs", "bse_assemble", "bse_dipole_vector",
+EXPORTS = ["bse_check_params", "bse_setup", "bse_interp_W", "bse_project_pairs", "bse_assemble", "bse_dipole_vector",
            "bse_spectrum", "bse_lowest", "bse_sync", "bse_last_error", "bse_dim", "bse_naux",
            "bse_nao", "bse_launch_count", "bse_free", "bse_profile", "bse_profile_read",
            "bse_spectrum_static", "bse_adjoint_seed", "bse_adjoint", "bse_batch_assemble",
@@ -40,6 +40,8 @@ class BseParams(ctypes.Structure):
         ("alpha", c_double),
         ("precision", c_int32),
         ("h_complex128", c_int32),
+        ("coarse", c_int32 * 3),
+        ("lattice", POINTER(c_double)),
     ]
 
 
@@ -62,6 +64,8 @@ def load() -> ctypes.CDLL:
     lib = ctypes.CDLL(LIB_PATH)
     vp = c_void_p
     lib.bse_setup.argtypes = [POINTER(BseParams), vp, POINTER(vp)]
+    lib.bse_check_params.argtypes = [POINTER(BseParams)]
+    lib.bse_check_params.restype = c_int
     lib.bse_interp_W.argtypes = [vp, vp, vp, vp]
     lib.bse_interp_V.argtypes = [vp, vp, vp]
     lib.bse_set_momentum.argtypes = [vp, vp, vp]

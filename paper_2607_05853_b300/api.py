@@ -39,7 +39,8 @@ class BSE:
     """One crystal's TDA-BSE problem bound to the current CUDA device and stream."""
 
     def __init__(self, *, nao, naux, dense, R_C, R_W, w_RW, nv, nc, k_offset=(0.0, 0.0, 0.0),
-                 alpha=2.0, precision="fp64", h_complex128: bool = False, stream: torch.cuda.Stream | None = None):
+                 alpha=2.0, precision="fp64", h_complex128: bool = False, coarse=None, lattice=None,
+                 stream: torch.cuda.Stream | None = None):
         lib = _lib.load()
         self._lib = lib
         nao = np.ascontiguousarray(nao, np.int32)
@@ -65,6 +66,11 @@ class BSE:
         p.alpha = float(alpha)
         p.precision = _lib.PRECISIONS[precision]
         p.h_complex128 = 1 if h_complex128 else 0
+        if coarse is not None:            # optional R-set checks (bse_params.coarse / lattice)
+            p.coarse[:] = [int(x) for x in coarse]
+        self._lattice = None if lattice is None else np.ascontiguousarray(lattice, np.float64).reshape(3, 3)
+        if self._lattice is not None:
+            p.lattice = self._lattice.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         ctx = ctypes.c_void_p()
         st = lib.bse_setup(ctypes.byref(p), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx))
@@ -83,6 +89,8 @@ class BSE:
 
     @classmethod
     def from_inputs(cls, inp: dict, **kw) -> "BSE":
+        kw.setdefault("coarse", inp.get("coarse"))
+        kw.setdefault("lattice", inp.get("lattice"))
         return cls(nao=inp["nao"], naux=inp["naux"], dense=inp["dense"], R_C=inp["R_C"], R_W=inp["R_W"],
                    w_RW=inp["w_RW"], nv=inp["nv"], nc=inp["nc"], k_offset=inp["k_offset"], **kw)
 

@@ -143,9 +143,51 @@ int64_t bse_dim(const bse_ctx *ctx) { return ctx ? ctx->dim : -1; }
 int32_t bse_naux(const bse_ctx *ctx) { return ctx ? ctx->naux_tot : -1; }
 int32_t bse_nao(const bse_ctx *ctx) { return ctx ? ctx->nao_tot : -1; }
 
-bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
-  if (!out) return BSE_EINVAL;
-  *out = nullptr;
+// The optional coarse-mesh checks of W's R-set: per Born-von Karman class of the coarse mesh
+// the image weights sum to one, and (with the lattice) each image is a shortest member of its
+// class, i.e. the set is the Wigner-Seitz folding the interpolation of §III.B assumes.
+static bool check_coarse(const bse_params *p) {
+  const int *N = p->coarse;
+  if (N[0] == 0 && N[1] == 0 && N[2] == 0) return true;
+  for (int i = 0; i < 3; i++)
+    if (N[i] < 1 || N[i] > 4096) return false;
+  const long long ncls = (long long)N[0] * N[1] * N[2];
+  if (ncls > (1 << 24)) return false;
+  std::vector<double> wsum((size_t)ncls, 0.0);
+  for (int r = 0; r < p->n_RW; r++) {
+    const int *R = p->R_W + 3 * r;
+    if (!(p->w_RW[r] > 0.0)) return false;
+    long long idx = 0;
+    for (int i = 0; i < 3; i++) idx = idx * N[i] + ((R[i] % N[i]) + N[i]) % N[i];
+    wsum[(size_t)idx] += p->w_RW[r];
+  }
+  for (double w : wsum)
+    if (std::fabs(w - 1.0) > 1e-9) return false;
+  if (!p->lattice) return true;
+  for (int i = 0; i < 9; i++)
+    if (!std::isfinite(p->lattice[i])) return false;
+  auto len = [&](double r0, double r1, double r2) {
+    double s = 0.0;
+    for (int j = 0; j < 3; j++) {
+      const double x = r0 * p->lattice[j] + r1 * p->lattice[3 + j] + r2 * p->lattice[6 + j];
+      s += x * x;
+    }
+    return std::sqrt(s);
+  };
+  for (int r = 0; r < p->n_RW; r++) {
+    const int *R = p->R_W + 3 * r;
+    const double l0 = len(R[0], R[1], R[2]);
+    for (int m0 = -1; m0 <= 1; m0++)
+      for (int m1 = -1; m1 <= 1; m1++)
+        for (int m2 = -1; m2 <= 1; m2++) {
+          const double l = len(R[0] + (double)m0 * N[0], R[1] + (double)m1 * N[1], R[2] + (double)m2 * N[2]);
+          if (l0 > l * (1.0 + 1e-9) + 1e-9) return false;
+        }
+  }
+  return true;
+}
+
+bse_status bse_check_params(const bse_params *p) {
   if (!p) return BSE_EINVAL;
   if (p->n_atoms < 1 || p->n_atoms > 4096 || !p->nao_per_atom || !p->naux_per_atom) return BSE_EINVAL;
   for (int i = 0; i < 3; i++) {
@@ -154,20 +196,35 @@ bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
   }
   if (p->n_RC < 1 || !p->R_C || p->n_RW < 1 || !p->R_W || !p->w_RW) return BSE_EINVAL;
   if (p->nv < 1 || p->nc < 1 || p->nv > 8 || p->nc > 8) return BSE_EINVAL;
-  if (p->precision < BSE_FP64 || p->precision > BSE_BF16X1) return BSE_EINVAL;
+  if (p->precision < BSE_FP64 || p->precision > BSE_TF32X2) return BSE_EINVAL;
   if (!std::isfinite(p->alpha)) return BSE_EINVAL;
   long long nk = (long long)p->dense[0] * p->dense[1] * p->dense[2];
   if (nk > 65535) return BSE_EINVAL;
-  int nao_tot = 0, naux_tot = 0, nao_max = 0;
+  int nao_tot = 0, naux_tot = 0;
   for (int a = 0; a < p->n_atoms; a++) {
     if (p->nao_per_atom[a] < 1 || p->naux_per_atom[a] < 1) return BSE_EINVAL;
     nao_tot += p->nao_per_atom[a];
     naux_tot += p->naux_per_atom[a];
-    nao_max = std::max(nao_max, p->nao_per_atom[a]);
   }
   if (p->nv + p->nc > nao_tot || naux_tot > 8192 || nao_tot > 4096) return BSE_EINVAL;
   for (int r = 0; r < p->n_RW; r++)
     if (!std::isfinite(p->w_RW[r])) return BSE_EINVAL;
+  if (!check_coarse(p)) return BSE_EINVAL;
+  return BSE_OK;
+}
+
+bse_status bse_setup(const bse_params *p, void *cuda_stream, bse_ctx **out) {
+  if (!out) return BSE_EINVAL;
+  *out = nullptr;
+  const bse_status chk = bse_check_params(p);
+  if (chk != BSE_OK) return chk;
+  const long long nk = (long long)p->dense[0] * p->dense[1] * p->dense[2];
+  int nao_tot = 0, naux_tot = 0, nao_max = 0;
+  for (int a = 0; a < p->n_atoms; a++) {
+    nao_tot += p->nao_per_atom[a];
+    naux_tot += p->naux_per_atom[a];
+    nao_max = std::max(nao_max, p->nao_per_atom[a]);
+  }
 
   bse_ctx *c = new bse_ctx();
   c->n_atoms = p->n_atoms;

@@ -1,6 +1,7 @@
-// Split-precision assembly of H (BSE_BF16X3 / X2 / X1): the bulk complex contractions
-// run on tcgen05 tensor cores with bf16 operand pieces and FP32 accumulation; phases,
-// the per-k stage and the E_c - E_v diagonal stay FP64; H is stored as complex64.
+// Split-precision assembly of H (BSE_BF16X3 / X2 / X1, BSE_TF32X2): the bulk complex
+// contractions run on tcgen05 tensor cores with bf16 (or tf32) operand pieces and FP32
+// accumulation; phases and the E_c - E_v diagonal stay FP64; H is stored as complex64 (or
+// complex128 on request).
 //
 // Per q-slab (q = k1 - k2, §III.A Eq. W_LRI):
 //   k_proj32      M_vv(k1,q) and M_cc(k1,q) in FP32 from Y (F(k',k) + conj F(k,k')^T),
@@ -31,13 +32,16 @@ struct SplitWS {
   int np = 3, pp = 6;
   int kmem = 0, kchunks = 0;
   int nq = 1, rows = 0;
-  __nv_bfloat16 *Wp = nullptr;   // [nk][PP][naux][kmem]   B[nu][mu] = W(q)[mu][nu]
-  __nv_bfloat16 *Ap = nullptr;   // [nq][PP][rows][kmem]   M_vv pieces
+  bool tf32 = false;             // pieces are tf32 values in FP32 words (two per value)
+  int pbytes = 2;                // bytes per piece element (2 bf16, 4 tf32)
+  // piece buffers (PP = 2 x pieces planes, elements of pbytes bytes)
+  void *Wp = nullptr;            // [nk][PP][naux][kmem]   B[nu][mu] = W(q)[mu][nu]
+  void *Ap = nullptr;            // [nq][PP][rows][kmem]   M_vv pieces
   float2 *Mc32 = nullptr;        // [nq][nk][nc*nc][naux], or [nq][nk][naux_pad][nc*nc] for the fused kernel
   float2 *T32 = nullptr;         // [nq][naux][rows]  (column nu of T = M_vv W(q) is contiguous)
   float2 *Y32 = nullptr;         // [nk][nao_max][nb][naux]
-  __nv_bfloat16 *Pp = nullptr;   // [PP][dim][kmem]        pieces of X V
-  __nv_bfloat16 *Xp = nullptr;   // [PP][dim][kmem]        pieces of conj(X)
+  void *Pp = nullptr;            // [PP][dim][kmem]        pieces of X V
+  void *Xp = nullptr;            // [PP][dim][kmem]        pieces of conj(X)
   CUtensorMap tmA_g1, tmB_g1, tmA_x, tmB_x;
   int bn_g1 = TC_BN;             // N tile of the M_vv W(q) GEMM (autotuned)
   int proj_bs = 0;               // threads per block of the register-blocked projection (autotuned; 0 = default)
@@ -64,8 +68,8 @@ struct SplitWS {
   float2 *X32 = nullptr;         // [dim][naux]  exchange factors
   // coupling block B of the full BSE (allocated on first use)
   int nqB = 0, rowsB = 0;        // q per slab; rows (k1, b, i) of M1 per q
-  __nv_bfloat16 *ApB = nullptr;  // [nqB][PP][rowsB][kmem]  M1 pieces
-  __nv_bfloat16 *XpB = nullptr;  // [PP][dim][kmem]         pieces of X (no conjugate)
+  void *ApB = nullptr;           // [nqB][PP][rowsB][kmem]  M1 pieces
+  void *XpB = nullptr;           // [PP][dim][kmem]         pieces of X (no conjugate)
   float2 *McB = nullptr;         // [nqB][nk][nc*nv][naux]   M2
   float2 *TB = nullptr;          // [nqB][naux][rowsB]       T1 = M1 W(q)
   CUtensorMap tmA_B, tmB_xB;
@@ -95,48 +99,39 @@ __device__ __forceinline__ void split_pieces(R x, int np, __nv_bfloat16 *p) {
   }
 }
 
-// Wp[q][pp][nu][mu] from W(q)[mu][nu] (FP64).
-__global__ void k_split_W(const double2 *__restrict__ Wq, int nk, int naux, int kmem, int np,
-                          __nv_bfloat16 *__restrict__ Wp) {
-  const long long nn = (long long)naux * naux;
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int q = blockIdx.y;
-  if (e >= nn) return;
-  const int nu = (int)(e / naux), mu = (int)(e % naux);
-  const double2 w = Wq[(long long)q * nn + (long long)mu * naux + nu];
-  __nv_bfloat16 pr[3], pi[3];
-  split_pieces<double>(w.x, np, pr);
-  split_pieces<double>(w.y, np, pi);
-  const long long plane = (long long)naux * kmem;
-  __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
+// A tensor-core operand as planes of pieces, [piece * 2 + (re, im)][...]: bf16 pieces (np of
+// them, split_pieces) or, with tf32 set, two tf32 pieces in FP32 words (x ~ tf32(x) +
+// tf32(x - tf32(x)), the residual exact in the source precision).  Offsets and plane pitches
+// count elements of the piece type.
+struct PieceBuf {
+  void *p;
+  int np;
+  int tf32;
+  template <class R>
+  __device__ __forceinline__ void put(long long plane, long long off, R re, R im) const {
+    if (tf32) {
+      float *b = static_cast<float *>(p) + off;
+      const float hr = tc::tf32_rna((float)re), hi = tc::tf32_rna((float)im);
+      b[0] = hr;
+      b[plane] = hi;
+      b[2 * plane] = tc::tf32_rna((float)(re - (R)hr));
+      b[3 * plane] = tc::tf32_rna((float)(im - (R)hi));
+    } else {
+      __nv_bfloat16 pr[3], pi[3];
+      split_pieces<R>(re, np, pr);
+      split_pieces<R>(im, np, pi);
+      __nv_bfloat16 *b = static_cast<__nv_bfloat16 *>(p) + off;
 #pragma unroll
-  for (int p = 0; p < 3; p++) {
-    if (p >= np) break;
-    base[(2 * p) * plane] = pr[p];
-    base[(2 * p + 1) * plane] = pi[p];
+      for (int k = 0; k < 3; k++) {
+        if (k >= np) break;
+        b[(2 * k) * plane] = pr[k];
+        b[(2 * k + 1) * plane] = pi[k];
+      }
+    }
   }
-}
+};
 
-// dst[pp][r][k] pieces of (conj ? conj(src) : src), src [rows][naux] FP64 complex.
-__global__ void k_split_rows(const double2 *__restrict__ src, long long rows, int naux, int kmem, int np,
-                             int conj, __nv_bfloat16 *__restrict__ dst) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= rows * naux) return;
-  const long long r = e / naux;
-  const int k = (int)(e % naux);
-  double2 v = src[e];
-  if (conj) v.y = -v.y;
-  __nv_bfloat16 pr[3], pi[3];
-  split_pieces<double>(v.x, np, pr);
-  split_pieces<double>(v.y, np, pi);
-  const long long plane = rows * kmem;
-#pragma unroll
-  for (int p = 0; p < 3; p++) {
-    if (p >= np) break;
-    dst[(2 * p) * plane + r * kmem + k] = pr[p];
-    dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
-  }
-}
+PieceBuf pieces(const SplitWS *w, void *p) { return PieceBuf{p, w->np, w->tf32 ? 1 : 0}; }
 
 // ---- FP32 per-k stage (split precisions): phases in FP64, sums in FP32 -------------------
 // The products feed bf16 pieces whose sum carries ~2^-24 relative precision, so FP32 sums
@@ -185,8 +180,8 @@ __global__ void k_f2d(const float *__restrict__ src, long long n, double *__rest
 // asked, as complex128 W(q)[mu][nu].
 constexpr int IQB = 16;
 __global__ void __launch_bounds__(256) k_interp_W32(const float *__restrict__ WR32T, const float2 *__restrict__ PHQ,
-                                                    int nRW, int naux, int nk, int kmem, int np,
-                                                    __nv_bfloat16 *__restrict__ Wp, double2 *__restrict__ Wq_out) {
+                                                    int nRW, int naux, int nk, int kmem, PieceBuf Wp,
+                                                    double2 *__restrict__ Wq_out) {
   extern __shared__ float2 phs[];  // [IQB][nRW]
   const int q0 = blockIdx.y * IQB;
   for (int t = threadIdx.x; t < IQB * nRW; t += blockDim.x) {
@@ -213,16 +208,7 @@ __global__ void __launch_bounds__(256) k_interp_W32(const float *__restrict__ WR
     for (int j = 0; j < IQB; j++) {
       const int q = q0 + j;
       if (q >= nk) break;
-      __nv_bfloat16 pr[3], pi[3];
-      split_pieces<float>(acc[j].x, np, pr);
-      split_pieces<float>(acc[j].y, np, pi);
-      __nv_bfloat16 *base = Wp + (long long)q * 2 * np * plane + (long long)nu * kmem + mu;
-#pragma unroll
-      for (int p = 0; p < 3; p++) {
-        if (p >= np) break;
-        base[(2 * p) * plane] = pr[p];
-        base[(2 * p + 1) * plane] = pi[p];
-      }
+      Wp.put<float>(plane, (long long)q * 2 * Wp.np * plane + (long long)nu * kmem + mu, acc[j].x, acc[j].y);
       if (Wq_out) Wq_out[(long long)q * nn + (long long)mu * naux + nu] = make_double2(acc[j].x, acc[j].y);
     }
   }
@@ -288,7 +274,7 @@ __global__ void k_half_transform32(const float *__restrict__ CR, const float2 *_
 __global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__restrict__ ck, int nao_tot, int nb,
                                int nv, int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
                                const int *__restrict__ ao_start, const int *__restrict__ naoA, long long dim,
-                               int kmem, int np, float2 *__restrict__ X, __nv_bfloat16 *__restrict__ Xp) {
+                               int kmem, float2 *__restrict__ X, PieceBuf Xp) {
   const int k = blockIdx.y;
   const int mu = blockIdx.x * blockDim.x + threadIdx.x;
   if (mu >= naux) return;
@@ -310,15 +296,7 @@ __global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__res
       const float2 x = make_float2(f1.x + f2.x, f1.y - f2.y);
       const long long r = ((long long)k * nv + i) * nc + a;
       X[r * naux + mu] = x;
-      __nv_bfloat16 pr[3], pi[3];
-      split_pieces<float>(x.x, np, pr);
-      split_pieces<float>(-x.y, np, pi);
-#pragma unroll
-      for (int p = 0; p < 3; p++) {
-        if (p >= np) break;
-        Xp[(2 * p) * plane + r * kmem + mu] = pr[p];
-        Xp[(2 * p + 1) * plane + r * kmem + mu] = pi[p];
-      }
+      Xp.put<float>(plane, r * kmem + mu, x.x, -x.y);
     }
 }
 
@@ -327,8 +305,7 @@ __global__ void k_exchange_X32(const float2 *__restrict__ Y, const float2 *__res
 // Hermitian sum_R w_R Vbar(R) e^{+iQ.R} otherwise.
 template <bool CPLX>
 __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *__restrict__ X,
-                                                    const float2 *__restrict__ V0, int kmem, int np,
-                                                    __nv_bfloat16 *__restrict__ Pp) {
+                                                    const float2 *__restrict__ V0, int kmem, PieceBuf Pp) {
   __shared__ float2 As[16][64];
   __shared__ float2 Bs[16][64];
   const int K = N;
@@ -375,15 +352,7 @@ __global__ void __launch_bounds__(256) k_xv0_pieces(int M, int N, const float2 *
     for (int j = 0; j < 4; j++) {
       const int r = row0 + ty + 16 * i, cc = col0 + tx + 16 * j;
       if (r >= M || cc >= N) continue;
-      __nv_bfloat16 pr[3], pi[3];
-      split_pieces<float>(acc[i][j].x, np, pr);
-      split_pieces<float>(acc[i][j].y, np, pi);
-#pragma unroll
-      for (int p = 0; p < 3; p++) {
-        if (p >= np) break;
-        Pp[(2 * p) * plane + (long long)r * kmem + cc] = pr[p];
-        Pp[(2 * p + 1) * plane + (long long)r * kmem + cc] = pi[p];
-      }
+      Pp.put<float>(plane, (long long)r * kmem + cc, acc[i][j].x, acc[i][j].y);
     }
 }
 
@@ -433,8 +402,8 @@ constexpr int MAXB = 8;
 __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot, int nb, int nv,
                          int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
                          const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1, int n2, int n3,
-                         int q0, const int *__restrict__ qlist, int np, int rows, int kmem,
-                         __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc) {
+                         int q0, const int *__restrict__ qlist, int rows, int kmem, PieceBuf Ap,
+                         float2 *__restrict__ Mc) {
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
   const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
@@ -471,21 +440,10 @@ __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict
         }
     }
     const long long plane = (long long)rows * kmem;
-    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)(k1 * nv + i) * nv * kmem + mu;
+    const long long out = (long long)qq * 2 * Ap.np * plane + (long long)(k1 * nv + i) * nv * kmem + mu;
 #pragma unroll
     for (int j = 0; j < MAXB; j++)
-      if (j < nv) {
-        const float vr = acc1[j].x + acc2[j].x, vi = acc1[j].y - acc2[j].y;
-        __nv_bfloat16 pr[3], pi[3];
-        split_pieces<float>(vr, np, pr);
-        split_pieces<float>(vi, np, pi);
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-          if (p >= np) break;
-          out[(2 * p) * plane + (long long)j * kmem] = pr[p];
-          out[(2 * p + 1) * plane + (long long)j * kmem] = pi[p];
-        }
-      }
+      if (j < nv) Ap.put<float>(plane, out + (long long)j * kmem, acc1[j].x + acc2[j].x, acc1[j].y - acc2[j].y);
   } else {
     const int a = row - nv;
     for (int s = 0; s < na; s++) {
@@ -514,8 +472,8 @@ __global__ void k_proj32(const float2 *__restrict__ Y, const double2 *__restrict
 __global__ void k_proj_cv32(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot, int nb, int nv,
                             int nc, int naux, int nao_max, const int *__restrict__ aux_atom,
                             const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1, int n2, int n3,
-                            int q0, const int *__restrict__ qlist, int np, int rowsB, int kmem,
-                            __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ M2) {
+                            int q0, const int *__restrict__ qlist, int rowsB, int kmem, PieceBuf Ap,
+                            float2 *__restrict__ M2) {
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
   const int nchunk = (naux + blockDim.x - 1) / blockDim.x;
@@ -555,20 +513,10 @@ __global__ void k_proj_cv32(const float2 *__restrict__ Y, const double2 *__restr
   }
   if (first) {
     const long long plane = (long long)rowsB * kmem;
-    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + ((long long)(k1 * nc + row) * nv) * kmem + mu;
+    const long long out = (long long)qq * 2 * Ap.np * plane + ((long long)(k1 * nc + row) * nv) * kmem + mu;
 #pragma unroll
     for (int j = 0; j < MAXB; j++)
-      if (j < nv) {
-        __nv_bfloat16 pr[3], pi[3];
-        split_pieces<float>(acc1[j].x + acc2[j].x, np, pr);
-        split_pieces<float>(acc1[j].y - acc2[j].y, np, pi);
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-          if (p >= np) break;
-          out[(2 * p) * plane + (long long)j * kmem] = pr[p];
-          out[(2 * p + 1) * plane + (long long)j * kmem] = pi[p];
-        }
-      }
+      if (j < nv) Ap.put<float>(plane, out + (long long)j * kmem, acc1[j].x + acc2[j].x, acc1[j].y - acc2[j].y);
   } else {
     float2 *out = M2 + ((((long long)qq * nk + k1) * nc + (row - nc)) * nv) * naux + mu;
 #pragma unroll
@@ -578,23 +526,13 @@ __global__ void k_proj_cv32(const float2 *__restrict__ Y, const double2 *__restr
 }
 
 // dst[pp][r][k] pieces of src [rows][naux] (FP32 complex, no conjugate).
-__global__ void k_pieces_f32(const float2 *__restrict__ src, long long rows, int naux, int kmem, int np,
-                             __nv_bfloat16 *__restrict__ dst) {
+__global__ void k_pieces_f32(const float2 *__restrict__ src, long long rows, int naux, int kmem, PieceBuf dst) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * naux) return;
   const long long r = e / naux;
   const int k = (int)(e % naux);
   const float2 v = src[e];
-  __nv_bfloat16 pr[3], pi[3];
-  split_pieces<float>(v.x, np, pr);
-  split_pieces<float>(v.y, np, pi);
-  const long long plane = rows * kmem;
-#pragma unroll
-  for (int p = 0; p < 3; p++) {
-    if (p >= np) break;
-    dst[(2 * p) * plane + r * kmem + k] = pr[p];
-    dst[(2 * p + 1) * plane + r * kmem + k] = pi[p];
-  }
+  dst.put<float>(rows * kmem, r * kmem + k, v.x, v.y);
 }
 
 // ---- matrix-free products H x (no H stored) ---------------------------------------------
@@ -954,9 +892,8 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
                                                   int nao_tot, int naux, int nao_max,
                                                   const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
                                                   const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
-                                                  const int *__restrict__ qlist, int np, int rows, int kmem,
-                                                  __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ Mc,
-                                                  int mc_pad) {
+                                                  const int *__restrict__ qlist, int rows, int kmem, PieceBuf Ap,
+                                                  float2 *__restrict__ Mc, int mc_pad) {
   constexpr int NB = NV + NC;
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
@@ -1023,22 +960,12 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
         }
       }
     }
-    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)k1 * NV * NV * kmem + mu;
+    const long long out = (long long)qq * 2 * Ap.np * plane + (long long)k1 * NV * NV * kmem + mu;
 #pragma unroll
     for (int i = 0; i < NV; i++)
 #pragma unroll
-      for (int j = 0; j < NV; j++) {
-        __nv_bfloat16 pr[3], pi[3];
-        split_pieces<float>(mv[i][j].x, np, pr);
-        split_pieces<float>(mv[i][j].y, np, pi);
-        const long long r = (long long)(i * NV + j) * kmem;
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-          if (p >= np) break;
-          out[(2 * p) * plane + r] = pr[p];
-          out[(2 * p + 1) * plane + r] = pi[p];
-        }
-      }
+      for (int j = 0; j < NV; j++)
+        Ap.put<float>(plane, out + (long long)(i * NV + j) * kmem, mv[i][j].x, mv[i][j].y);
     float2 *mo = Mc + (((long long)qq * nk + k1) * NC * NC) * mrow + mu;
 #pragma unroll
     for (int a = 0; a < NC; a++)
@@ -1160,8 +1087,8 @@ __global__ void __launch_bounds__(160) k_proj_cv32_t(const float2 *__restrict__ 
                                                      int nao_tot, int naux, int nao_max,
                                                      const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
                                                      const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
-                                                     const int *__restrict__ qlist, int np, int rowsB, int kmem,
-                                                     __nv_bfloat16 *__restrict__ Ap, float2 *__restrict__ M2) {
+                                                     const int *__restrict__ qlist, int rowsB, int kmem, PieceBuf Ap,
+                                                     float2 *__restrict__ M2) {
   constexpr int NB = NV + NC, NVC = NV * NC;
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
@@ -1216,22 +1143,12 @@ __global__ void __launch_bounds__(160) k_proj_cv32_t(const float2 *__restrict__ 
         }
       }
     }
-    __nv_bfloat16 *out = Ap + (long long)qq * 2 * np * plane + (long long)k1 * NVC * kmem + mu;
+    const long long out = (long long)qq * 2 * Ap.np * plane + (long long)k1 * NVC * kmem + mu;
 #pragma unroll
     for (int b = 0; b < NC; b++)
 #pragma unroll
-      for (int i = 0; i < NV; i++) {
-        __nv_bfloat16 pr[3], pi[3];
-        split_pieces<float>(m1[b][i].x, np, pr);
-        split_pieces<float>(m1[b][i].y, np, pi);
-        const long long r = (long long)(b * NV + i) * kmem;
-#pragma unroll
-        for (int p = 0; p < 3; p++) {
-          if (p >= np) break;
-          out[(2 * p) * plane + r] = pr[p];
-          out[(2 * p + 1) * plane + r] = pi[p];
-        }
-      }
+      for (int i = 0; i < NV; i++)
+        Ap.put<float>(plane, out + (long long)(b * NV + i) * kmem, m1[b][i].x, m1[b][i].y);
     float2 *mo = M2 + (((long long)qq * nk + k1) * NVC) * naux + mu;
 #pragma unroll
     for (int a = 0; a < NC; a++)
@@ -1339,8 +1256,8 @@ void launch_proj_fast(bse_ctx *c, SplitWS *w, int q0, int nq, int mc_pad) {
   const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
   k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom,
                                                              c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
-                                                             c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap,
-                                                             w->Mc32, mc_pad);
+                                                             c->mesh[2], q0, c->d_qplus, w->rows, w->kmem,
+                                                             pieces(w, w->Ap), w->Mc32, mc_pad);
 }
 
 template <int NV, int NC>
@@ -1385,7 +1302,7 @@ bool launch_cv_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *B, bool proj
     const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
     k_proj_cv32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(
         y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
-        c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem, w->ApB, w->McB);
+        c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rowsB, w->kmem, pieces(w, w->ApB), w->McB);
     return true;
   }
   constexpr int threads = ((NV * NC + 1) / 2) * ((NV * NC + 1) / 2);
@@ -1419,15 +1336,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3-D bf16 tensor {K = k_extent, rows, planes} with row pitch kmem elements.
-bool make_map(CUtensorMap *m, void *base, int k_extent, long long rows, long long planes, int kmem, int box_rows) {
+// 3-D tensor of pieces {K = k_extent, rows, planes} with row pitch kmem elements: bf16, or FP32
+// words holding tf32 pieces (tf32); the box is one 64-byte row of K by box_rows rows.
+bool make_map(CUtensorMap *m, void *base, int k_extent, long long rows, long long planes, int kmem, int box_rows,
+              bool tf32) {
   auto fn = encode_fn();
   if (!fn) return false;
+  const cuuint64_t eb = tf32 ? 4 : 2;
   cuuint64_t dims[3] = {(cuuint64_t)k_extent, (cuuint64_t)rows, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)kmem * 2, (cuuint64_t)rows * kmem * 2};
-  cuuint32_t box[3] = {(cuuint32_t)tcg::BK, (cuuint32_t)box_rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)kmem * eb, (cuuint64_t)rows * kmem * eb};
+  cuuint32_t box[3] = {(cuuint32_t)(tf32 ? tcg::BK_TF32 : tcg::BK), (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+  CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides,
+                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -1448,7 +1369,7 @@ bool make_map_c64_3d(CUtensorMap *m, void *base, long long x, long long y, long 
   return r == CUDA_SUCCESS;
 }
 
-template <int NP, int BN>
+template <int NP, int BN, bool TF>
 bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
                      int prof_id) {
   using Cf = tcg::Cfg<NP, BN>;
@@ -1459,61 +1380,64 @@ bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, con
   const long long total = (long long)grid.x * grid.y * grid.z;
   const int ctas = (int)std::min<long long>(total, c->n_sm);
   bse_prof_begin(c, prof_id);
-  tcg::k_tc_zgemm<NP, BN><<<ctas, 192, Cf::SMEM, c->stream>>>(A, B, a);
+  tcg::k_tc_zgemm<NP, BN, TF><<<ctas, 192, Cf::SMEM, c->stream>>>(A, B, a);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_zgemm");
 }
 
-template <int NP>
+template <int NP, bool TF = false>
 bse_status launch_tc_bn(bse_ctx *c, int bn, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args,
                         dim3 grid, int prof_id) {
   switch (bn) {
-    case 64: return launch_tc<NP, 64>(c, A, B, args, grid, prof_id);
-    case 96: return launch_tc<NP, 96>(c, A, B, args, grid, prof_id);
-    case 128: return launch_tc<NP, 128>(c, A, B, args, grid, prof_id);
-    default: return launch_tc<NP, 160>(c, A, B, args, grid, prof_id);
+    case 64: return launch_tc<NP, 64, TF>(c, A, B, args, grid, prof_id);
+    case 96: return launch_tc<NP, 96, TF>(c, A, B, args, grid, prof_id);
+    case 128: return launch_tc<NP, 128, TF>(c, A, B, args, grid, prof_id);
+    default: return launch_tc<NP, 160, TF>(c, A, B, args, grid, prof_id);
   }
 }
 
+// The context's piece kind picks the instantiation: tf32 pieces (two of them) or np bf16 pieces.
 bse_status launch_tc_np(bse_ctx *c, int np, int bn, const CUtensorMap &A, const CUtensorMap &B,
                         const tcg::Args &args, dim3 grid, int prof_id) {
+  if (ws(c)->tf32) return launch_tc_bn<2, true>(c, bn, A, B, args, grid, prof_id);
   if (np == 3) return launch_tc_bn<3>(c, bn, A, B, args, grid, prof_id);
   if (np == 2) return launch_tc_bn<2>(c, bn, A, B, args, grid, prof_id);
   return launch_tc_bn<1>(c, bn, A, B, args, grid, prof_id);
 }
 
 // ---- fused direct term -------------------------------------------------------------------
-template <int NP, int BN, int NC>
+template <int NP, int BN, int NC, bool TF>
 bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
   using Cf = tcd::DCfg<NP, BN>;
   const long long total = (long long)a.tiles_m * a.tiles_b;
   const int ctas = (int)std::min<long long>(total, c->n_sm);
   bse_prof_begin(c, prof_id);
-  tcd::k_tc_direct<NP, BN, NC><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, w->tmM_d, a);
+  tcd::k_tc_direct<NP, BN, NC, TF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, w->tmM_d, a);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_direct");
 }
 
-template <int NP, int BN>
+template <int NP, int BN, bool TF>
 bse_status launch_direct_nc(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
   switch (c->nc) {
-    case 2: return launch_direct_t<NP, BN, 2>(c, w, a, prof_id);
-    case 4: return launch_direct_t<NP, BN, 4>(c, w, a, prof_id);
-    default: return launch_direct_t<NP, BN, 6>(c, w, a, prof_id);
+    case 2: return launch_direct_t<NP, BN, 2, TF>(c, w, a, prof_id);
+    case 4: return launch_direct_t<NP, BN, 4, TF>(c, w, a, prof_id);
+    default: return launch_direct_t<NP, BN, 6, TF>(c, w, a, prof_id);
   }
 }
 
 // N tiles of the fused kernel: T's N_aux columns in one tile (two ring stages of bf16x3 pieces
 // fit up to 160 columns), so the fused path takes N_aux <= 160.
-template <int NP>
+template <int NP, bool TF = false>
 bse_status launch_direct_bn(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
-  if (w->bn_d == 64) return launch_direct_nc<NP, 64>(c, w, a, prof_id);
-  return launch_direct_nc<NP, 160>(c, w, a, prof_id);
+  if (w->bn_d == 64) return launch_direct_nc<NP, 64, TF>(c, w, a, prof_id);
+  return launch_direct_nc<NP, 160, TF>(c, w, a, prof_id);
 }
 
 bse_status launch_direct(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  if (w->tf32) return launch_direct_bn<2, true>(c, w, a, prof_id);
   if (w->np == 3) return launch_direct_bn<3>(c, w, a, prof_id);
   if (w->np == 2) return launch_direct_bn<2>(c, w, a, prof_id);
   return launch_direct_bn<1>(c, w, a, prof_id);
@@ -1524,20 +1448,22 @@ int direct_stage_bytes(int np, int bn) { return 2 * np * (tcg::A_TILE + bn * tcg
 
 // Shared-memory size attributes of every tensor-core instantiation, set once (outside any
 // stream capture).
-template <int NP, int BN>
+template <int NP, int BN, bool TF = false>
 void set_attr() {
-  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcg::Cfg<NP, BN>::SMEM);
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, BN, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcg::Cfg<NP, BN>::SMEM);
 }
 template <int NV, int NC>
 void set_g2_attr() {
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
-template <int NP, int BN>
+template <int NP, int BN, bool TF = false>
 void set_direct_attr() {
-  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
-  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
-  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, tcd::DCfg<NP, BN>::SMEM);
+  constexpr int sm = tcd::DCfg<NP, BN>::SMEM;
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 void set_all_attrs_now() {
   set_direct_attr<1, 64>(); set_direct_attr<1, 160>();
@@ -1548,6 +1474,8 @@ void set_all_attrs_now() {
   set_attr<1, 64>(); set_attr<1, 96>(); set_attr<1, 128>(); set_attr<1, 160>();
   set_attr<2, 64>(); set_attr<2, 96>(); set_attr<2, 128>(); set_attr<2, 160>();
   set_attr<3, 64>(); set_attr<3, 96>(); set_attr<3, 128>(); set_attr<3, 160>();
+  set_direct_attr<2, 64, true>(); set_direct_attr<2, 160, true>();
+  set_attr<2, 64, true>(); set_attr<2, 96, true>(); set_attr<2, 128, true>(); set_attr<2, 160, true>();
 }
 void set_all_attrs(const bse_ctx *c) { bse_once_per_device(c, BSE_ONCE_SPLIT, set_all_attrs_now); }
 
@@ -1556,11 +1484,14 @@ void set_all_attrs(const bse_ctx *c) { bse_once_per_device(c, BSE_ONCE_SPLIT, se
 bse_status split_setup(bse_ctx *c) {
   SplitWS *w = new SplitWS();
   c->tc = w;
-  w->np = c->precision == BSE_BF16X3 ? 3 : c->precision == BSE_BF16X2 ? 2 : 1;
+  w->tf32 = c->precision == BSE_TF32X2;
+  w->pbytes = w->tf32 ? 4 : 2;
+  w->np = c->precision == BSE_BF16X3 ? 3 : (c->precision == BSE_BF16X2 || w->tf32) ? 2 : 1;
   w->pp = 2 * w->np;
   const int na = c->naux_tot;
   w->kmem = (na + 7) / 8 * 8;
-  w->kchunks = (na + tcg::BK - 1) / tcg::BK;
+  const int bk = w->tf32 ? tcg::BK_TF32 : tcg::BK;
+  w->kchunks = (na + bk - 1) / bk;
   w->rows = c->nk * c->nv * c->nv;
   // fused direct term: a window with register-blocked projections and T's columns in one tile
   const bool win = (c->nv == 2 || c->nv == 4 || c->nv == 6) && (c->nc == 2 || c->nc == 4 || c->nc == 6);
@@ -1578,7 +1509,8 @@ bse_status split_setup(bse_ctx *c) {
     }
     w->nui_d = std::min(w->nui_d, w->naux_pad);
   }
-  const size_t per_q = (size_t)w->pp * w->rows * w->kmem * 2 + (size_t)c->nk * c->nc * c->nc * w->naux_pad * 8 +
+  const size_t pb = (size_t)w->pbytes;
+  const size_t per_q = (size_t)w->pp * w->rows * w->kmem * pb + (size_t)c->nk * c->nc * c->nc * w->naux_pad * 8 +
                        (size_t)w->rows * na * 8;
   const size_t budget = (size_t)1536 << 20;
   w->nq = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
@@ -1593,19 +1525,19 @@ bse_status split_setup(bse_ctx *c) {
       !alloc((void **)&w->V032, nn * sizeof(float2)) ||
       !alloc((void **)&w->ck32, (size_t)c->nk * c->nao_tot * c->nb * sizeof(float2)) ||
       !alloc((void **)&w->X32, dimz * na * sizeof(float2)) ||
-      !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * 2) ||
-      !alloc((void **)&w->Ap, (size_t)w->nq * w->pp * w->rows * w->kmem * 2) ||
+      !alloc((void **)&w->Wp, (size_t)c->nk * w->pp * na * w->kmem * pb) ||
+      !alloc((void **)&w->Ap, (size_t)w->nq * w->pp * w->rows * w->kmem * pb) ||
       !alloc((void **)&w->Mc32, (size_t)w->nq * c->nk * c->nc * c->nc * w->naux_pad * 8) ||
       !alloc((void **)&w->T32, (size_t)w->nq * w->rows * na * 8) ||
       !alloc((void **)&w->Y32, (size_t)c->nk * c->nao_max * c->nb * na * 8) ||
-      !alloc((void **)&w->Pp, (size_t)w->pp * dimz * w->kmem * 2) ||
-      !alloc((void **)&w->Xp, (size_t)w->pp * dimz * w->kmem * 2))
+      !alloc((void **)&w->Pp, (size_t)w->pp * dimz * w->kmem * pb) ||
+      !alloc((void **)&w->Xp, (size_t)w->pp * dimz * w->kmem * pb))
     return bse_fail(c, BSE_ENOMEM, "split workspace allocation failed");
-  cudaMemset(w->Wp, 0, (size_t)c->nk * w->pp * na * w->kmem * 2);
-  cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * 2);
+  cudaMemset(w->Wp, 0, (size_t)c->nk * w->pp * na * w->kmem * pb);
+  cudaMemset(w->Ap, 0, (size_t)w->nq * w->pp * w->rows * w->kmem * pb);
   cudaMemset(w->Mc32, 0, (size_t)w->nq * c->nk * c->nc * c->nc * w->naux_pad * 8);
-  cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * 2);
-  cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * 2);
+  cudaMemset(w->Pp, 0, (size_t)w->pp * dimz * w->kmem * pb);
+  cudaMemset(w->Xp, 0, (size_t)w->pp * dimz * w->kmem * pb);
   {
     const long long nph = (long long)c->nk * (c->n_RW + c->n_RC);
     k_phase_tables<<<(unsigned)((nph + 255) / 256), 256, 0, c->stream>>>(
@@ -1614,14 +1546,15 @@ bse_status split_setup(bse_ctx *c) {
     bse_count_launch();
   }
   set_all_attrs(c);
-  bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM) &&
-            make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1) &&
-            (!w->fused || make_map(&w->tmB_d, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_d)) &&
+  const bool tf = w->tf32;
+  bool ok = make_map(&w->tmA_g1, w->Ap, na, w->rows, (long long)w->pp * w->nq, w->kmem, tcg::BM, tf) &&
+            make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1, tf) &&
+            (!w->fused || make_map(&w->tmB_d, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_d, tf)) &&
             (!w->fused || make_map_c64_3d(&w->tmM_d, w->Mc32, w->naux_pad, (long long)c->nc * c->nc,
                                           (long long)w->nq * c->nk, w->naux_pad, w->nui_d, c->nc * c->nc,
                                           w->pairs_d)) &&
-            make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM) &&
-            make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN);
+            make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM, tf) &&
+            make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN, tf);
   if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");
   if (cudaGetLastError() != cudaSuccess) return bse_fail(c, BSE_ECUDA, "split workspace initialisation failed");
   return BSE_OK;
@@ -1650,7 +1583,8 @@ bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out) {
     return bse_fail(c, BSE_EINVAL, "interp_W: too many W(R) images for one block");
   dim3 grid((unsigned)std::min<long long>((nn + 255) / 256, 1024), (c->nk + IQB - 1) / IQB);
   bse_prof_begin(c, BSE_KP_INTERP);
-  k_interp_W32<<<grid, 256, sm, c->stream>>>(w->WR32T, w->PHQ, c->n_RW, na, c->nk, w->kmem, w->np, w->Wp, Wq_out);
+  k_interp_W32<<<grid, 256, sm, c->stream>>>(w->WR32T, w->PHQ, c->n_RW, na, c->nk, w->kmem, pieces(w, w->Wp),
+                                              Wq_out);
   bse_prof_end(c, BSE_KP_INTERP);
   bse_count_launch(2);
   return bse_check_launch(c, "split interp_W");
@@ -1691,15 +1625,15 @@ bse_status split_project(bse_ctx *c, const double *C_R) {
   }
   k_exchange_X32<<<dim3((na + 127) / 128, c->nk), 128, 0, c->stream>>>(
       w->shifted ? w->Y32q : w->Y32, w->shifted ? w->ck32q : w->ck32, c->nao_tot, c->nb, c->nv, c->nc, na,
-      c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->dim, w->kmem, w->np, w->X32, w->Xp);
+      c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->dim, w->kmem, w->X32, pieces(w, w->Xp));
   const long long nn = (long long)na * na;
   k_to_f32<<<(unsigned)((nn + 255) / 256), 256, 0, c->stream>>>(c->V0c, nn, w->V032);
   dim3 g((na + 63) / 64, (unsigned)((c->dim + 63) / 64));
   if (g.y > 65535) return bse_fail(c, BSE_EINVAL, "exchange factors: dim too large for the P grid");
   if (c->vx_from_R)
-    k_xv0_pieces<true><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
+    k_xv0_pieces<true><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, pieces(w, w->Pp));
   else
-    k_xv0_pieces<false><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, w->np, w->Pp);
+    k_xv0_pieces<false><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, pieces(w, w->Pp));
   bse_count_launch(6);
   c->y64_valid = false;
   return bse_check_launch(c, "split project");
@@ -1790,7 +1724,8 @@ bse_status split_assemble(bse_ctx *c, void *Hv) {
       if (!fast_pair_kernels(c, w, q0, nq, H, true))
         k_proj32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
                                                c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
-                                               c->mesh[2], q0, c->d_qplus, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
+                                               c->mesh[2], q0, c->d_qplus, w->rows, w->kmem, pieces(w, w->Ap),
+                                               w->Mc32);
       bse_prof_end(c, BSE_KP_PROJECT);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "proj32");
@@ -1843,13 +1778,14 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
   if (c->nv > MAXB || c->nvc > 64) return bse_fail(c, BSE_EINVAL, "assemble_coupling: band window too wide");
   if (!w->ApB) {
     w->rowsB = c->nk * c->nc * c->nv;
-    const size_t per_q = (size_t)w->pp * w->rowsB * w->kmem * 2 + (size_t)c->nk * c->nvc * na * 8 +
+    const size_t per_q = (size_t)w->pp * w->rowsB * w->kmem * w->pbytes + (size_t)c->nk * c->nvc * na * 8 +
                          (size_t)w->rowsB * na * 8;
     const size_t budget = (size_t)1536 << 20;
     w->nqB = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
     w->nqB = std::min(w->nqB, 65535);
     if (c->mesh[2] > 1 && w->nqB >= c->mesh[2]) w->nqB = w->nqB / c->mesh[2] * c->mesh[2];
-    const size_t apb = (size_t)w->nqB * w->pp * w->rowsB * w->kmem * 2, xpb = (size_t)w->pp * c->dim * w->kmem * 2;
+    const size_t apb = (size_t)w->nqB * w->pp * w->rowsB * w->kmem * w->pbytes,
+                 xpb = (size_t)w->pp * c->dim * w->kmem * w->pbytes;
     if (!alloc((void **)&w->ApB, apb) || !alloc((void **)&w->XpB, xpb) ||
         !alloc((void **)&w->McB, (size_t)w->nqB * c->nk * c->nvc * na * 8) ||
         !alloc((void **)&w->TB, (size_t)w->nqB * w->rowsB * na * 8))
@@ -1857,13 +1793,14 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
     if (cudaMemsetAsync(w->ApB, 0, apb, c->stream) != cudaSuccess ||
         cudaMemsetAsync(w->XpB, 0, xpb, c->stream) != cudaSuccess)
       return bse_fail(c, BSE_ECUDA, "assemble_coupling: workspace initialisation failed");
-    if (!make_map(&w->tmA_B, w->ApB, na, w->rowsB, (long long)w->pp * w->nqB, w->kmem, tcg::BM) ||
-        !make_map(&w->tmB_xB, w->XpB, na, c->dim, w->pp, w->kmem, TC_BN))
+    if (!make_map(&w->tmA_B, w->ApB, na, w->rowsB, (long long)w->pp * w->nqB, w->kmem, tcg::BM, w->tf32) ||
+        !make_map(&w->tmB_xB, w->XpB, na, c->dim, w->pp, w->kmem, TC_BN, w->tf32))
       return bse_fail(c, BSE_ECUDA, "assemble_coupling: tensor map encoding failed");
   }
   {
     const long long n = c->dim * na;
-    k_pieces_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(w->X32, c->dim, na, w->kmem, w->np, w->XpB);
+    k_pieces_f32<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(w->X32, c->dim, na, w->kmem,
+                                                                      pieces(w, w->XpB));
     bse_count_launch();
     tcg::Args a{};
     a.rows = (int)c->dim;
@@ -1894,8 +1831,8 @@ bse_status split_assemble_coupling(bse_ctx *c, void *Bv) {
       if (!fast_cv_kernels(c, w, q0, nq, B, true))
         k_proj_cv32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na,
                                                   c->nao_max, c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
-                                                  c->mesh[1], c->mesh[2], q0, c->d_qplus, w->np, w->rowsB, w->kmem,
-                                                  w->ApB, w->McB);
+                                                  c->mesh[1], c->mesh[2], q0, c->d_qplus, w->rowsB, w->kmem,
+                                                  pieces(w, w->ApB), w->McB);
       bse_prof_end(c, BSE_KP_PROJECT);
       bse_count_launch();
       bse_status s = bse_check_launch(c, "proj_cv32");
@@ -1967,7 +1904,7 @@ bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_p
       if (!fast_pair_kernels(c, w, q0, nq, nullptr, true))
         k_proj32<<<grid, 128, sm, st>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
                                         c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2], q0,
-                                        c->d_qplus, w->np, w->rows, w->kmem, w->Ap, w->Mc32);
+                                        c->d_qplus, w->rows, w->kmem, pieces(w, w->Ap), w->Mc32);
       bse_count_launch();
     }
     {
@@ -2030,7 +1967,7 @@ std::map<std::tuple<int, int, int, int, int, int>, int> g_tune_proj;
 int tune_projection(bse_ctx *c, SplitWS *w) {
   const int na = c->naux_tot;
   const int nq = std::min(w->nq, (int)c->qplus.size());
-  const auto key = std::make_tuple(na, w->rows, nq, w->np, c->nv, c->nc);
+  const auto key = std::make_tuple(na, w->rows, nq, w->np + (w->tf32 ? 10 : 0), c->nv, c->nc);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_proj.find(key);
@@ -2083,13 +2020,13 @@ bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj) {
     w->proj_bs = pbs;
     if (chosen_proj) *chosen_proj = pbs;
   }
-  const auto key = std::make_tuple(na, w->rows, std::min(w->nq, (int)c->qplus.size()), w->np);
+  const auto key = std::make_tuple(na, w->rows, std::min(w->nq, (int)c->qplus.size()), w->np + (w->tf32 ? 10 : 0));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       w->bn_g1 = it->second;
-      if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1))
+      if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1, w->tf32))
         return bse_fail(c, BSE_ECUDA, "autotune: tensor map encoding failed");
       if (chosen) *chosen = w->bn_g1;
       return BSE_OK;
@@ -2105,7 +2042,7 @@ bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj) {
   int best_bn = TC_BN;
   for (int bn : TC_BN_CAND) {
     CUtensorMap tB;
-    if (!make_map(&tB, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, bn)) continue;
+    if (!make_map(&tB, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, bn, w->tf32)) continue;
     tcg::Args a{};
     a.rows = w->rows;
     a.n_valid = na;
@@ -2140,7 +2077,7 @@ bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   w->bn_g1 = best_bn;
-  if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1))
+  if (!make_map(&w->tmB_g1, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, w->bn_g1, w->tf32))
     return bse_fail(c, BSE_ECUDA, "autotune: tensor map encoding failed");
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

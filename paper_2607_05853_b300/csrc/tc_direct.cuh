@@ -1,6 +1,6 @@
 // Direct term of the Hamiltonian in one persistent tensor-core kernel (sm_103a):
 //
-//   T = M_vv W(q)                      (tcgen05, bf16 pieces, FP32 accumulation in tensor memory)
+//   T = M_vv W(q)                      (tcgen05, bf16 or tf32 pieces, FP32 accumulation in tensor memory)
 //   D = T M_cc^T   per pair (k1, k2 = k1 - q),   H block (k1, k2) += -D / N_k   (and its mirror)
 //
 // the two contractions of Eq. W_LRI's direct kernel, with T never leaving the SM.  One tile
@@ -27,7 +27,6 @@
 namespace tcd {
 
 using tcg::A_TILE;
-using tcg::BK;
 using tcg::BM;
 using tcg::ROWB;
 using tcg::WAIT_LIMIT;
@@ -55,7 +54,7 @@ struct DArgs {
   int pairs;              // pairs per tile; a tile covers rows m0 .. m0 + pairs nv^2 - 1
   int rows;               // rows of M_vv per q (N_k nv^2)
   int tiles_m, tiles_b;   // tiles per q, q values in this launch
-  int k_chunks;           // ceil(N_aux / BK)
+  int k_chunks;           // ceil(N_aux / K per stage): 32 bf16 or 16 tf32 (TF)
   int naux, naux_pad;     // columns of T; M_cc row length in the slab buffer (multiple of 16)
   int nui;                // M_cc columns per ring item (multiple of 16)
   int n_mitems;           // ceil(naux_pad / nui)
@@ -84,7 +83,7 @@ __device__ __forceinline__ bool d_self_conj(int q, int n1, int n2, int n3) {
   return (n1 - a1) % n1 == a1 && (n2 - a2) % n2 == a2 && (n3 - a3) % n3 == a3;
 }
 
-template <int NP, int BN, int NC>
+template <int NP, int BN, int NC, bool TF = false>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_direct(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmM, DArgs args) {
@@ -156,8 +155,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int kc = item;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
           for (int pp = 0; pp < C::PP; pp++) {
-            tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
-            tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, 0, q * C::PP + pp);
+            tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * tcg::bk_elems<TF>(), m0, b * C::PP + pp);
+            tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * tcg::bk_elems<TF>(), 0, q * C::PP + pp);
           }
         } else {
           // columns nu0 .. nu0 + nui - 1 of M_cc for the tile's pairs, one TMA box
@@ -173,8 +172,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t IPOS = tc::idesc_bf16(BM, BN, false);
-    constexpr uint32_t INEG = tc::idesc_bf16(BM, BN, true);
+    constexpr uint32_t IPOS = tc::idesc<TF>(BM, BN, false);
+    constexpr uint32_t INEG = tc::idesc<TF>(BM, BN, true);
     int it = 0, tcount = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
@@ -202,7 +201,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t sa = tc::smem_u32(smem + s * C::STAGE);
         const uint32_t sb = sa + C::PP * A_TILE;
 #pragma unroll
-        for (int k16 = 0; k16 < BK / 16; k16++) {
+        for (int k16 = 0; k16 < ROWB / 32; k16++) {  // two MMAs (32 bytes of K each) per row
 #pragma unroll
           for (int pa = 0; pa < NP; pa++) {
 #pragma unroll
@@ -212,12 +211,12 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
               const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
               const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-              tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
+              tc::mma<TF>(tm_re, ar, br, IPOS, acc_r);
               acc_r = 1;
-              tc::mma_bf16(tm_re, ai, bi, INEG, 1);
-              tc::mma_bf16(tm_im, ar, bi, IPOS, acc_i);
+              tc::mma<TF>(tm_re, ai, bi, INEG, 1);
+              tc::mma<TF>(tm_im, ar, bi, IPOS, acc_i);
               acc_i = 1;
-              tc::mma_bf16(tm_im, ai, br, IPOS, 1);
+              tc::mma<TF>(tm_im, ai, br, IPOS, 1);
             }
           }
         }

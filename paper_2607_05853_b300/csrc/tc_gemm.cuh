@@ -9,8 +9,12 @@
 // MMAs: Re += Ar Br^T - Ai Bi^T (the minus through the A-negate bit of the instruction
 // descriptor), Im += Ar Bi^T + Ai Br^T.
 //
+// With TF = true the pieces are tf32 values in FP32 words instead (x ~ p0 + p1, p0 = tf32(x),
+// p1 = tf32(x - p0), NP = 2: 3 products of kind::tf32 MMAs); everything else is the same.
+//
 // Operands arrive by TMA as 3-D tensors {K, rows, plane-piece(-batch)} with 64-byte
-// swizzled rows (32 bf16 of K per stage); rows and K beyond the tensor are zero-filled.
+// swizzled rows (32 bf16 or 16 tf32 of K per stage); rows and K beyond the tensor are
+// zero-filled.
 // Persistent CTAs (one per SM) walk the 128 x BN output tiles: warp 0 issues TMA, warp 1
 // allocates tensor memory and issues the MMAs from one thread, warps 2-5 drain the
 // accumulators of one tile while the next tile's operands stream in.  Every barrier wait
@@ -23,6 +27,9 @@ namespace tcg {
 
 constexpr int BM = 128;
 constexpr int BK = 32;                // bf16 elements of K per stage (64-byte rows)
+constexpr int BK_TF32 = 16;           // tf32 elements of K per stage (the same 64-byte rows)
+template <bool TF>
+__host__ __device__ constexpr int bk_elems() { return TF ? BK_TF32 : BK; }
 constexpr int ROWB = BK * 2;          // bytes per smem row
 constexpr int A_TILE = BM * ROWB;     // 8 KB
 constexpr int SMEM_BUDGET = 221184;   // stage bytes per CTA
@@ -58,7 +65,7 @@ struct Args {
   int tiles_n, tiles_m, tiles_b;  // output tiles along N, M and the batch (set by the launcher)
 };
 
-template <int NP, int BN>
+template <int NP, int BN, bool TF = false>
 __global__ void __launch_bounds__(192, 1)
     k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args args) {
   using C = Cfg<NP, BN>;
@@ -125,8 +132,8 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t *st = smem + s * C::STAGE;
         tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
         for (int pp = 0; pp < C::PP; pp++) {
-          tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * BK, m0, b * C::PP + pp);
-          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * BK, n0, zb + pp);
+          tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * bk_elems<TF>(), m0, b * C::PP + pp);
+          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * bk_elems<TF>(), n0, zb + pp);
         }
       }
     }
@@ -135,8 +142,8 @@ __global__ void __launch_bounds__(192, 1)
       if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    constexpr uint32_t IPOS = tc::idesc_bf16(BM, BN, false);
-    constexpr uint32_t INEG = tc::idesc_bf16(BM, BN, true);
+    constexpr uint32_t IPOS = tc::idesc<TF>(BM, BN, false);
+    constexpr uint32_t INEG = tc::idesc<TF>(BM, BN, true);
     int it = 0, tcount = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
@@ -163,8 +170,9 @@ __global__ void __launch_bounds__(192, 1)
         tc::tc_fence_after();
         const uint32_t sa = tc::smem_u32(smem + s * C::STAGE);
         const uint32_t sb = sa + C::PP * A_TILE;
+        // two MMAs per 64-byte row: K = 16 bf16 or 8 tf32 each (32 bytes)
 #pragma unroll
-        for (int k16 = 0; k16 < BK / 16; k16++) {
+        for (int k16 = 0; k16 < ROWB / 32; k16++) {
 #pragma unroll
           for (int pa = 0; pa < NP; pa++) {
 #pragma unroll
@@ -174,12 +182,12 @@ __global__ void __launch_bounds__(192, 1)
               const uint64_t ai = tc::smem_desc(sa + (2 * pa + 1) * A_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
               const uint64_t br = tc::smem_desc(sb + (2 * pb) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
               const uint64_t bi = tc::smem_desc(sb + (2 * pb + 1) * C::B_TILE + k16 * 32, 16, 8 * ROWB, tc::SWZ_64B);
-              tc::mma_bf16(tm_re, ar, br, IPOS, acc_r);
+              tc::mma<TF>(tm_re, ar, br, IPOS, acc_r);
               acc_r = 1;
-              tc::mma_bf16(tm_re, ai, bi, INEG, 1);
-              tc::mma_bf16(tm_im, ar, bi, IPOS, acc_i);
+              tc::mma<TF>(tm_re, ai, bi, INEG, 1);
+              tc::mma<TF>(tm_im, ar, bi, IPOS, acc_i);
               acc_i = 1;
-              tc::mma_bf16(tm_im, ai, br, IPOS, 1);
+              tc::mma<TF>(tm_im, ai, br, IPOS, 1);
             }
           }
         }

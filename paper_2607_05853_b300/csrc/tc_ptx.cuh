@@ -104,6 +104,27 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same with tf32 inputs (kind::tf32): the operands are FP32 words of which the tensor core
+// uses the sign, exponent and the 10 leading mantissa bits.
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+template <bool TF>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (TF)
+    mma_tf32(d_tmem, adesc, bdesc, idesc, accumulate);
+  else
+    mma_bf16(d_tmem, adesc, bdesc, idesc, accumulate);
+}
 // Arrive (once) on an mbarrier when all previously issued tcgen05 ops of this thread complete.
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -138,6 +159,25 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool negA) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::tf32 (A and B format field 2 = tf32), fp32 D, both operands
+// K-major; the same M, N and negate fields as kind::f16.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N, bool negA) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+template <bool TF>
+__host__ __device__ constexpr uint32_t idesc(int M, int N, bool negA) {
+  return TF ? idesc_tf32(M, N, negA) : idesc_bf16(M, N, negA);
+}
+
+// x = hi + lo with hi and lo tf32 values (round to nearest, ties away from zero, through the
+// cvt.rna.tf32.f32 conversion); the residual x - hi is exact in FP32.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
 }
 
 }  // namespace tc

@@ -34,16 +34,23 @@ def gpu_hamiltonian(inp, precision="fp64", alpha=2.0, Wq=False, **kw):
 #   off-diagonal  bf16x3 5.0e-7 .. 1.7e-6   bf16x2 3.8e-6 .. 1.1e-5   bf16x1 1.9e-3 .. 3.6e-3
 #   diagonal      bf16x3 <= 4.7e-8          bf16x2 <= 2.6e-7          bf16x1 <= 9.0e-5
 #   coupling B    bf16x3 4.9e-7 .. 6.1e-7   bf16x2 3.1e-6 .. 5.2e-6   bf16x1 1.4e-3 .. 2.7e-3
-# and on the 27648-dim sampled blocks: H bf16x3 1.7e-6 (bf16x2 3.8e-6), H(Q) 2.3e-6, B 1.5e-6;
+#   tf32x2        off-diagonal 4.0e-7 .. 7.4e-7, diagonal <= 4.7e-8, B 3.9e-7 .. 5.7e-7
+# and on the 27648-dim sampled blocks: H bf16x3 1.7e-6 (bf16x2 3.8e-6, tf32x2 1.5e-6),
+# H(Q) 2.3e-6, B 1.5e-6.  With N_aux = 185 (the unfused GEMM path) the off-diagonal errors are
+# 1.1e-6 (bf16x3, tf32x2) and the diagonal ones 1.3e-7 .. 1.5e-7: there the diagonal's kernel
+# terms, not its storage rounding, set its error, so the diagonal bound is the larger of the
+# storage bound and the off-diagonal bound scaled to absolute (assert_split_close);
 # the larger cell's blocks sum more ABFs, so the full-size bound is the wider SPLIT_OFF_FULL.
 # The bf16x3 bounds sit between the bf16x3 and bf16x2 errors, so a build whose tensor-core
 # GEMMs kept only bf16x2's three piece products fails them (tests/test_gpu_split.py checks
 # that on the real bf16x2 path).  The diagonal bound is the complex64 storage rounding
 # (2^-23 of the value) for bf16x3; the order-one kernel error of bf16x1 dominates its own.
-SPLIT_OFF = {"bf16x3": 3e-6, "bf16x2": 3e-5, "bf16x1": 1e-2}
-SPLIT_OFF_FULL = {"bf16x3": 3e-6}            # the 27648-dim sampled blocks of H, H(Q) and B
-SPLIT_DIAG = {"bf16x3": 1.2e-7, "bf16x2": 5e-7, "bf16x1": 1e-3}
-SPLIT_B = {"bf16x3": 1.5e-6, "bf16x2": 2e-5, "bf16x1": 1e-2}
+# tf32x2 (two tf32 pieces, ~22 bits) carries the FP32 stages' error as bf16x3 does and takes its
+# bounds; a tf32x2 GEMM that kept only the hi x hi product would be off by ~2^-11.
+SPLIT_OFF = {"bf16x3": 3e-6, "bf16x2": 3e-5, "bf16x1": 1e-2, "tf32x2": 3e-6}
+SPLIT_OFF_FULL = {"bf16x3": 3e-6, "tf32x2": 3e-6}   # the 27648-dim sampled blocks of H, H(Q) and B
+SPLIT_DIAG = {"bf16x3": 1.2e-7, "bf16x2": 5e-7, "bf16x1": 1e-3, "tf32x2": 1.2e-7}
+SPLIT_B = {"bf16x3": 1.5e-6, "bf16x2": 2e-5, "bf16x1": 1e-2, "tf32x2": 1.5e-6}
 
 
 def offdiag_diag_errors(got, ref):
@@ -59,8 +66,16 @@ def offdiag_diag_errors(got, ref):
 
 
 def assert_split_close(got, ref, prec, off_tol=None):
-    """H parity of a split precision with the bounds above."""
+    """H parity of a split precision with the bounds above: the off-diagonal relative to its
+    largest reference element; the diagonal within the larger of its storage bound (relative
+    to the largest diagonal element) and the off-diagonal bound in absolute terms (the
+    diagonal carries the same kernel terms)."""
     off, diag = offdiag_diag_errors(got, ref)
-    assert off <= (off_tol if off_tol is not None else SPLIT_OFF[prec]), (prec, "off-diagonal", off)
-    assert diag <= SPLIT_DIAG[prec], (prec, "diagonal", diag)
+    ot = off_tol if off_tol is not None else SPLIT_OFF[prec]
+    assert off <= ot, (prec, "off-diagonal", off)
+    ref = np.asarray(ref, np.complex128)
+    eye = np.eye(ref.shape[0], dtype=bool)
+    dmax = np.abs(ref[eye]).max()
+    omax = np.abs(ref[~eye]).max() if ref.shape[0] > 1 else 0.0
+    assert diag * dmax <= max(SPLIT_DIAG[prec] * dmax, ot * omax), (prec, "diagonal", diag)
     return off, diag

@@ -101,3 +101,72 @@ def test_extension_entries_reject_null_context(lib):
     assert lib.bse_lowest_full(None, None, None, 1, 2, 1, None, None) == _lib.BSE_EINVAL
     assert lib.bse_spectrum_matfree(None, None, 1, 2, None, 1, 0.1, 1.0, None, None) == _lib.BSE_EINVAL
     assert lib.bse_interp_V(None, None, None) == _lib.BSE_EINVAL
+
+
+def _params_from(inp, coarse=True, lattice=True):
+    from paper_2607_05853_b300 import _lib
+    keep = {k: np.ascontiguousarray(inp[k], dt) for k, dt in
+            (("nao", np.int32), ("naux", np.int32), ("R_C", np.int32), ("R_W", np.int32), ("w_RW", np.float64),
+             ("lattice", np.float64))}
+    p = _lib.BseParams()
+    p.n_atoms = len(keep["nao"])
+    p.nao_per_atom = keep["nao"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.naux_per_atom = keep["naux"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.dense[:] = [int(x) for x in inp["dense"]]
+    p.k_offset[:] = [float(x) for x in inp["k_offset"]]
+    p.n_RC, p.R_C = len(keep["R_C"]), keep["R_C"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.n_RW, p.R_W = len(keep["R_W"]), keep["R_W"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    p.w_RW = keep["w_RW"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p.nv, p.nc, p.alpha, p.precision = int(inp["nv"]), int(inp["nc"]), 2.0, 1
+    if coarse:
+        p.coarse[:] = [int(x) for x in inp["coarse"]]
+    if lattice:
+        p.lattice = keep["lattice"].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return p, keep
+
+
+def _inputs(which):
+    from synth import config_spec, make_inputs, batched_specs
+    from synth.crystal import CrystalSpec, _hex
+    if which == "tiny":
+        return make_inputs(config_spec(0))
+    if which == "batch":
+        return make_inputs(batched_specs(16)[3])
+    return make_inputs(CrystalSpec("2d", _hex(3.19, 20.0), np.array([[0, 0, 0], [1 / 3, 2 / 3, 0.08]]),
+                                   (3, 4), (7, 6), (3, 3, 1), (6, 6, 1), 2, 2, 1717, two_d=True))
+
+
+@pytest.mark.parametrize("which", ["tiny", "batch", "two_d"])
+def test_coarse_mesh_and_lattice_checks(lib, which):
+    """The R-set of W is the Wigner-Seitz folding of the coarse mesh (§III.B): the generator's
+    sets pass bse_check_params with the coarse mesh and lattice given; a weight changed, a
+    class left out or an image moved to a longer member of its class are rejected."""
+    from paper_2607_05853_b300 import _lib
+    inp = _inputs(which)
+    p, keep = _params_from(inp)
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_OK
+    # a weight off by 10 %
+    keep["w_RW"][0] *= 0.9
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_EINVAL
+    keep["w_RW"][0] /= 0.9
+    # one class missing
+    p.n_RW = len(keep["R_W"]) - 1
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_EINVAL
+    p.n_RW = len(keep["R_W"])
+    # the longest image moved by one coarse period along a periodic axis: weights still sum to
+    # one per class (it stays in its class), but it is no longer a shortest member
+    lat = keep["lattice"]
+    lens = np.linalg.norm(keep["R_W"] @ lat, axis=1)
+    i = int(np.argmax(lens))
+    ax = 0
+    step = np.zeros(3, np.int32)
+    step[ax] = int(inp["coarse"][ax]) * (1 if (keep["R_W"][i] @ lat) @ lat[ax] >= 0 else -1)
+    keep["R_W"][i] += step
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_EINVAL
+    p.lattice = None                       # without the lattice only the weights are checked
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_OK
+    keep["R_W"][i] -= step
+    p.coarse[:] = [int(inp["coarse"][0]) + 1, int(inp["coarse"][1]), int(inp["coarse"][2])]
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_EINVAL   # the wrong coarse mesh
+    p.coarse[:] = [0, 0, 0]
+    assert lib.bse_check_params(ctypes.byref(p)) == _lib.BSE_OK       # not given: not checked

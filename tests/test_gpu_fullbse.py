@@ -44,7 +44,8 @@ def test_coupling_block_matches_oracle(name):
 
 
 @pytest.mark.parametrize("prec,name", [("bf16x3", "cfg0"), ("bf16x2", "ragged"), ("bf16x3", "wide"),
-                                       ("bf16x1", "cfg0"), ("bf16x3", "two_d")])
+                                       ("bf16x1", "cfg0"), ("bf16x3", "two_d"), ("tf32x2", "cfg0"),
+                                       ("tf32x2", "two_d")])
 def test_coupling_block_split_matches_oracle(prec, name):
     inp = make_inputs(config_spec(0) if name == "cfg0" else RAGGED[name])
     ref = O.BSEOracle(inp).coupling()

@@ -54,7 +54,7 @@ def test_finite_Q_hamiltonian_matches_oracle(name, Q):
 
 @pytest.mark.parametrize("prec,name,Q", [("bf16x3", "cfg0", (1, 1, 0)), ("bf16x3", "cfg0", (2, 2, 2)),
                                          ("bf16x2", "ragged", (1, 1, 3)), ("bf16x3", "two_d", (1, 2, 0)),
-                                         ("bf16x1", "cfg0", (3, 0, 1))])
+                                         ("bf16x1", "cfg0", (3, 0, 1)), ("tf32x2", "ragged", (1, 1, 2))])
 def test_finite_Q_split_matches_oracle(prec, name, Q):
     inp = _inputs(name)
     ref = O.BSEOracle(inp, Q=Q).hamiltonian()

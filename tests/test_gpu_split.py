@@ -1,5 +1,5 @@
-"""GPU parity of the split-precision tensor-core path (bf16 pieces, FP32 accumulation,
-complex64 H) against the FP64 oracle, via the C ABI.
+"""GPU parity of the split-precision tensor-core path (bf16 or tf32 pieces, FP32
+accumulation, complex64 H) against the FP64 oracle, via the C ABI.
 
 Tolerances (tests/helpers.py): the off-diagonal kernel terms relative to the largest
 off-diagonal reference element, the diagonal relative to the largest diagonal one, with the
@@ -14,9 +14,16 @@ import oracle as O
 from synth import config_spec, make_inputs
 
 from helpers import SPLIT_OFF, SPLIT_OFF_FULL, assert_split_close, gpu_hamiltonian, offdiag_diag_errors
+from synth import CrystalSpec
+from synth.crystal import _fcc
 from test_gpu_fp64 import RAGGED
 
 pytestmark = pytest.mark.gpu
+
+# N_aux = 185 > 160: T = M_vv W(q) through the unfused tensor-core GEMM (two N tiles) and the
+# register-blocked second contraction instead of the fused direct kernel
+BIG_AUX = CrystalSpec("bigaux", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25], [0.5, 0.5, 0.5]]),
+                      (5, 6, 5), (60, 70, 55), (2, 1, 1), (2, 2, 2), 2, 2, 777, r_max=1.0)
 
 
 @pytest.fixture(scope="module")
@@ -26,7 +33,7 @@ def cfg0():
     return inp, orc, orc.hamiltonian()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16x1"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16x1", "tf32x2"])
 def test_split_H_matches_oracle(cfg0, prec):
     inp, orc, Href = cfg0
     b, d, H, _ = gpu_hamiltonian(inp, precision=prec)
@@ -64,12 +71,24 @@ def test_split_direct_only(cfg0):
     assert_split_close(H.cpu().numpy(), ref, "bf16x3")
 
 
-@pytest.mark.parametrize("name", list(RAGGED))
-def test_split_ragged_shapes(name):
-    inp = make_inputs(RAGGED[name])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x2"])
+@pytest.mark.parametrize("name", list(RAGGED) + ["bigaux"])
+def test_split_ragged_shapes(name, prec):
+    inp = make_inputs(BIG_AUX if name == "bigaux" else RAGGED[name])
     ref = O.BSEOracle(inp).hamiltonian()
-    b, d, H, _ = gpu_hamiltonian(inp, precision="bf16x3")
-    assert_split_close(H.cpu().numpy(), ref, "bf16x3")
+    b, d, H, _ = gpu_hamiltonian(inp, precision=prec)
+    assert_split_close(H.cpu().numpy(), ref, prec)
+
+
+def test_split_tf32x2_bound_separates_bf16x2(cfg0):
+    """tf32x2 (three kind::tf32 products) sits with bf16x3 below the bf16x3 bound, which the
+    bf16x2 path exceeds."""
+    inp, orc, Href = cfg0
+    b, d, H, _ = gpu_hamiltonian(inp, precision="tf32x2")
+    off_t = offdiag_diag_errors(H.cpu().numpy(), Href)[0]
+    b2, d2, H2, _ = gpu_hamiltonian(inp, precision="bf16x2")
+    off_2 = offdiag_diag_errors(H2.cpu().numpy(), Href)[0]
+    assert off_t <= SPLIT_OFF["tf32x2"] < off_2, (off_t, off_2)
 
 
 def test_split_spectrum_close_to_fp64(cfg0):
@@ -118,7 +137,8 @@ def test_split_complex128_storage(cfg0):
 def test_split_full_size_sampled_blocks_and_excitons():
     """The 27648-dim workload in the launch configuration the benchmark times: sampled
     blocks against the oracle (off-diagonal and diagonal bounds as above; the bf16x2 path
-    on the same blocks exceeds the bf16x3 bound), and the lowest 10 excitons against the FP64
+    on the same blocks exceeds the bf16x3 bound, the tf32x2 path stays within it), and the
+    lowest 10 excitons against the FP64
     GPU path (Lanczos on both matrices from the same start vector) within 1 meV."""
     import torch
     inp = make_inputs(config_spec(2))
@@ -151,6 +171,12 @@ def test_split_full_size_sampled_blocks_and_excitons():
     assert off2 > SPLIT_OFF_FULL["bf16x3"], off2
     del H2
     b2.close()
+    torch.cuda.empty_cache()
+    bt, _, Ht, _ = gpu_hamiltonian(inp, precision="tf32x2")
+    offt, diagt = sampled_errors(Ht)
+    assert offt <= SPLIT_OFF_FULL["tf32x2"] and diagt <= 1.2e-7, (offt, diagt)
+    del Ht
+    bt.close()
     torch.cuda.empty_cache()
     b64, _, H64, _ = gpu_hamiltonian(inp, precision="fp64")
     w_d, r_d = b64.lowest(H64, 10, 300)

@@ -769,34 +769,41 @@ def batch16_report(precision="bf16x3", world=1, rank=0, dist=None):
         e.record(st)
         torch.cuda.synchronize()
         iso.append(a.elapsed_time(e))
-    batch_assemble(systems, Hs)  # build + first replay
-    torch.cuda.synchronize()
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(st)
-    batch_assemble(systems, Hs)
-    e.record(st)
-    torch.cuda.synchronize()
-    t_batch = a.elapsed_time(e)
-    stamps = batch_assemble(systems, Hs, stamps=True)
-    done_ms = [x / 1e6 for x in stamps]
-    x = [t_i / max(c_i, 1e-9) for t_i, c_i in zip(iso, done_ms)]   # batched / isolated throughput
-    jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
-    if dist is not None:       # gather the ranks' per-system results (reporting only)
-        parts = [None] * world
-        dist.all_gather_object(parts, (t_batch, list(zip(dims, tiles, iso, done_ms))))
-        t_batch = max(p[0] for p in parts)
-        rows = [r for p in parts for r in p[1]]
-        dims, tiles, iso, done_ms = (list(c) for c in zip(*rows))
-        x = [t_i / max(c_i, 1e-9) for t_i, c_i in zip(iso, done_ms)]
-        jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
     el = [float(dm) ** 2 for dm in dims]
-    out = {"systems": 16, "ranks": world, "precision": precision, "graph_ms": t_batch, "serial_ms": sum(iso),
-           "aggregate_elements_per_s": sum(el) / (t_batch / 1e3),
-           "serial_elements_per_s": sum(el) / (sum(iso) / 1e3),
-           "batch_speedup_over_serial": sum(iso) / t_batch, "jain_fairness": jain,
-           "per_system": [{"dim": dm, "tile": tl, "isolated_ms": round(ti, 3), "done_in_batch_ms": round(c, 3),
-                           "elements_per_s_isolated": e2 / (ti / 1e3)}
-                          for dm, tl, ti, c, e2 in zip(dims, tiles, iso, done_ms, el)]}
+    out = {"systems": 16, "ranks": world, "precision": precision, "serial_ms": sum(iso),
+           "serial_elements_per_s": sum(el) / (sum(iso) / 1e3)}
+    for schedule in ("worklist", "chains"):
+        batch_assemble(systems, Hs, schedule=schedule)  # build + first replay
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        batch_assemble(systems, Hs, schedule=schedule)
+        e.record(st)
+        torch.cuda.synchronize()
+        t_batch = a.elapsed_time(e)
+        stamps = batch_assemble(systems, Hs, stamps=True, schedule=schedule)
+        done_ms = [x / 1e6 for x in stamps]
+        rows = list(zip(dims, tiles, iso, done_ms))
+        if dist is not None:       # gather the ranks' per-system results (reporting only)
+            parts = [None] * world
+            dist.all_gather_object(parts, (t_batch, rows))
+            t_batch = max(p[0] for p in parts)
+            rows = [r for p in parts for r in p[1]]
+        x = [t_i / max(c_i, 1e-9) for _, _, t_i, c_i in rows]   # batched / isolated throughput
+        jain = sum(x) ** 2 / (len(x) * sum(v * v for v in x))
+        elr = [float(r[0]) ** 2 for r in rows]
+        res = {"graph_ms": t_batch, "aggregate_elements_per_s": sum(elr) / (t_batch / 1e3),
+               "batch_speedup_over_serial": sum(r[2] for r in rows) / t_batch, "jain_fairness": jain,
+               "per_system": [{"dim": dm, "tile": tl, "isolated_ms": round(ti, 3), "done_in_batch_ms": round(c, 3),
+                               "elements_per_s_isolated": float(dm) ** 2 / (ti / 1e3)}
+                              for dm, tl, ti, c in rows]}
+        if schedule == "worklist":
+            out["serial_ms"] = sum(r[2] for r in rows)
+            out["serial_elements_per_s"] = sum(elr) / (out["serial_ms"] / 1e3)
+            out.update(res)
+            out["schedule"] = "worklist: grouped tensor-core launches over the (system, q-slab, tile) work list"
+        else:
+            out["chains"] = res
     batch_release()
     for b in systems:
         b.close()

@@ -312,14 +312,25 @@ bse_status bse_adjoint(bse_ctx *ctx, const double *Gamma, double *dW_R, double *
 
 /* Batching of several crystals (one context each, every one past bse_project_pairs): their
  * assemblies run as one CUDA graph forked from and joined into `cuda_stream`, so the host
- * issues one launch; the systems are ordered by estimated work, smallest first, and dealt to
- * two concurrent chains, so small systems finish early instead of queueing behind large ones.  The first call for a given list of (context, H) runs each assembly once eagerly,
- * then captures and instantiates the graph; later calls with the same list replay it.
+ * issues one launch.  The systems are ordered by estimated work, smallest first (so small
+ * systems finish early instead of queueing behind large ones), and dealt in that order to two
+ * concurrent chains.  Per chain, schedule
+ *  BSE_BATCH_WORKLIST: the chain's (system, q-slab) units are packed into steps (the next slab
+ *    of each unfinished system in order, at most one per system, until the step's M_vv W(q)
+ *    tiles fill two waves of the SMs); each step's tensor-core GEMMs of all its systems (the
+ *    exchange GEMMs of systems starting there, then M_vv W(q) per N tile) run as one persistent
+ *    launch over a work list of (system, q, tile), the projections and second contractions per
+ *    system.  Every system must use the same split precision (BSE_EINVAL otherwise).
+ *  BSE_BATCH_CHAINS: each system's own assembly in turn.
+ * The first call for a given list of (context, H) and schedule runs the assemblies once
+ * eagerly, then captures and instantiates the graph; later calls with the same list replay it.
  *  H : [n] device pointers as in bse_assemble;  stamps_ns : optional host [n] receiving, for
  *  each system, the nanoseconds from the start of this replay to the end of its assembly
  *  (the call then waits for the stream), or NULL.  Contexts must not be freed while a graph
  *  that uses them is cached; bse_batch_release drops every cached graph. */
-bse_status bse_batch_assemble(bse_ctx **ctxs, void **H, int n, void *cuda_stream, int64_t *stamps_ns);
+typedef enum { BSE_BATCH_WORKLIST = 0, BSE_BATCH_CHAINS = 1 } bse_batch_schedule;
+bse_status bse_batch_assemble(bse_ctx **ctxs, void **H, int n, void *cuda_stream, int32_t schedule,
+                              int64_t *stamps_ns);
 void bse_batch_release(void);
 
 /* Autotuner (call after bse_project_pairs): times one q-slab of the pair projections for each

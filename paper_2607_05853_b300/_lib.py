@@ -20,6 +20,7 @@ EXPORTS = ["bse_check_params", "bse_setup", "bse_interp_W", "bse_project_pairs",
            "bse_batch_release", "bse_autotune", "bse_window_seed", "bse_spectrum_add", "bse_interp_V",
            "bse_set_momentum", "bse_assemble_coupling", "bse_spectrum_full", "bse_lowest_full",
            "bse_spectrum_matfree", "bse_selftest_delay", "bse_selftest_wait"]
+BATCH_SCHEDULES = {"worklist": 0, "chains": 1}
 KERNEL_IDS = {"interp": 0, "half": 1, "project": 2, "g1": 3, "g2": 4, "exch": 5, "matvec": 6, "reorth": 7}
 
 
@@ -83,7 +84,7 @@ def load() -> ctypes.CDLL:
     lib.bse_adjoint_seed.argtypes = [vp, vp, vp, c_int, vp]
     lib.bse_adjoint.argtypes = [vp, vp, vp, vp]
     lib.bse_window_seed.argtypes = [vp, vp, vp, c_int, c_int, c_double, c_double, c_double, c_double, vp, vp]
-    lib.bse_batch_assemble.argtypes = [POINTER(vp), POINTER(vp), c_int, vp, POINTER(c_int64)]
+    lib.bse_batch_assemble.argtypes = [POINTER(vp), POINTER(vp), c_int, vp, c_int32, POINTER(c_int64)]
     lib.bse_batch_assemble.restype = c_int
     lib.bse_batch_release.argtypes = []
     lib.bse_batch_release.restype = None

@@ -319,10 +319,12 @@ class BSE:
         self._check(self._lib.bse_selftest_wait(self._ctx, int(cycles)), "bse_selftest_wait")
 
 
-def batch_assemble(systems, Hs, stream=None, stamps: bool = False):
-    """bse_batch_assemble: assemble several crystals as one CUDA graph (one branch each).
+def batch_assemble(systems, Hs, stream=None, stamps: bool = False, schedule: str = "worklist"):
+    """bse_batch_assemble: assemble several crystals as one CUDA graph.
 
-    systems: list of BSE contexts (each past project_pairs); Hs: matching H tensors.
+    systems: list of BSE contexts (each past project_pairs); Hs: matching H tensors;
+    schedule: "worklist" (grouped tensor-core launches over the systems' tiles, one split
+    precision for all) or "chains" (each system's assembly on one of two concurrent chains).
     Returns per-system completion times in ns from the replay start when stamps=True."""
     lib = _lib.load()
     n = len(systems)
@@ -332,7 +334,9 @@ def batch_assemble(systems, Hs, stream=None, stamps: bool = False):
     hp = (ctypes.c_void_p * n)(*[H.data_ptr() for H in Hs])
     st = stream if stream is not None else torch.cuda.current_stream()
     out = (ctypes.c_int64 * n)() if stamps else None
-    r = lib.bse_batch_assemble(ctxs, hp, n, ctypes.c_void_p(st.cuda_stream), out)
+    if schedule not in _lib.BATCH_SCHEDULES:
+        raise ValueError(f"schedule must be one of {list(_lib.BATCH_SCHEDULES)}")
+    r = lib.bse_batch_assemble(ctxs, hp, n, ctypes.c_void_p(st.cuda_stream), _lib.BATCH_SCHEDULES[schedule], out)
     if r != _lib.BSE_OK:
         raise BseError(r, "bse_batch_assemble: " + lib.bse_last_error(systems[0]._ctx).decode())
     return [int(x) for x in out] if stamps else None

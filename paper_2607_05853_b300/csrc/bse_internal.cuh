@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -96,7 +97,7 @@ void bse_count_launch(int n = 1);
 // Per-device one-time set-up (kernel attributes such as the dynamic shared-memory limit are
 // per device): the first call for (the context's device, key) in this process runs `fn`
 // with that device current; every call returns only after it has run (thread-safe).
-enum { BSE_ONCE_HMV_TDA = 0, BSE_ONCE_HMV_ALL = 1, BSE_ONCE_SPLIT = 2, BSE_ONCE_KEYS = 3 };
+enum { BSE_ONCE_HMV_TDA = 0, BSE_ONCE_HMV_ALL = 1, BSE_ONCE_SPLIT = 2, BSE_ONCE_GROUPED = 3, BSE_ONCE_KEYS = 4 };
 void bse_once_per_device(const bse_ctx *c, int key, void (*fn)());
 bse_status bse_fail(bse_ctx *c, bse_status s, const std::string &msg);
 bse_status bse_check_launch(bse_ctx *c, const char *what);
@@ -156,6 +157,11 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
 bse_status split_setup(bse_ctx *c);
 bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
+// Batched assembly of the n split-precision systems ctxs[order[0..n-1]] (smallest first) as a
+// work list of grouped launches on their (common) stream; stamp(i) runs when system i's last
+// launch is enqueued.
+bse_status split_batch_worklist(bse_ctx **ctxs, void **H, const int *order, int n,
+                                const std::function<void(int)> &stamp);
 bse_status split_assemble_coupling(bse_ctx *c, void *B);
 // W[p] = H x[p] (x[p] at x + p xs, W [n_pol][dim]) without H (split precisions), and the
 // early-stop scale of the matrix-free recursion

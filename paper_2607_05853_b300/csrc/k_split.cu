@@ -17,7 +17,10 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
+#include <functional>
+#include <vector>
 
 #include "bse_internal.cuh"
 #include "tc_direct.cuh"
@@ -1373,14 +1376,20 @@ template <int NP, int BN, bool TF>
 bse_status launch_tc(bse_ctx *c, const CUtensorMap &A, const CUtensorMap &B, const tcg::Args &args, dim3 grid,
                      int prof_id) {
   using Cf = tcg::Cfg<NP, BN>;
-  tcg::Args a = args;
-  a.tiles_n = (int)grid.x;
-  a.tiles_m = (int)grid.y;
-  a.tiles_b = (int)grid.z;
+  tcg::Groups<1> G;
+  G.A[0] = A;
+  G.B[0] = B;
+  G.a[0] = args;
+  G.a[0].tiles_n = (int)grid.x;
+  G.a[0].tiles_m = (int)grid.y;
+  G.a[0].tiles_b = (int)grid.z;
   const long long total = (long long)grid.x * grid.y * grid.z;
+  G.tile0[0] = 0;
+  G.tile0[1] = total;
+  G.n = 1;
   const int ctas = (int)std::min<long long>(total, c->n_sm);
   bse_prof_begin(c, prof_id);
-  tcg::k_tc_zgemm<NP, BN, TF><<<ctas, 192, Cf::SMEM, c->stream>>>(A, B, a);
+  tcg::k_tc_zgemm<NP, BN, TF><<<ctas, 192, Cf::SMEM, c->stream>>>(G);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_zgemm");
@@ -1650,117 +1659,316 @@ bse_status split_y_to_fp64(bse_ctx *c) {
   return bse_check_launch(c, "pair table to FP64");
 }
 
+namespace {
+
+// ---- the assembly's stages (one system) ----------------------------------------------------
+// The exchange GEMM: H = alpha/N_k (X V) conj(X)^T, writing every element.
+void exchange_gemm(const bse_ctx *c, const SplitWS *w, float2 *H, tcg::Args &a, dim3 &grid) {
+  a = tcg::Args{};
+  a.rows = (int)c->dim;
+  a.n_valid = (int)c->dim;
+  a.k_chunks = w->kchunks;
+  a.scale = (float)(c->alpha / c->nk);
+  // the exchange block is Hermitian: element (r, c) is stored as conj at (c, r), so a lane's
+  // row index runs along memory and the stores coalesce
+  a.out = H;
+  a.out64 = c->h64 ? 1 : 0;
+  a.ld_row = 1;
+  a.ld_col = c->dim;
+  a.conj_out = 1;
+  a.out_bstride = 0;
+  a.b_batch_planes = 0;
+  a.b_base = 0;
+  a.qlist = nullptr;
+  a.err = c->d_err;
+  grid = dim3((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
+}
+
+// The pair projections of q-slab [q0, q0 + nq) (M_cc in the fused layout on the fused path).
+bse_status slab_project(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  const int na = c->naux_tot;
+  bse_prof_begin(c, BSE_KP_PROJECT);
+  if (w->fused) {
+    fast_pair_kernels(c, w, q0, nq, H, true, w->naux_pad);
+  } else if (!fast_pair_kernels(c, w, q0, nq, H, true)) {
+    const int nchunk = (na + 127) / 128;
+    dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
+    size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
+    k_proj32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+                                           c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
+                                           c->mesh[2], q0, c->d_qplus, w->rows, w->kmem, pieces(w, w->Ap), w->Mc32);
+  }
+  bse_prof_end(c, BSE_KP_PROJECT);
+  bse_count_launch();
+  return bse_check_launch(c, "proj32");
+}
+
+// Fused path: T = M_vv W(q) and H += -T M_cc^T / N_k for the slab in one kernel.
+bse_status slab_direct(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  tcd::DArgs a{};
+  a.nv = c->nv;
+  a.pairs = w->pairs_d;
+  a.rows = w->rows;
+  a.tiles_m = (c->nk + w->pairs_d - 1) / w->pairs_d;
+  a.tiles_b = nq;
+  a.k_chunks = w->kchunks;
+  a.naux = c->naux_tot;
+  a.naux_pad = w->naux_pad;
+  a.nui = w->nui_d;
+  a.n_mitems = (w->naux_pad + w->nui_d - 1) / w->nui_d;
+  a.Mc = w->Mc32;
+  a.qlist = c->d_qplus;
+  a.b_base = q0;
+  a.n1 = c->mesh[0];
+  a.n2 = c->mesh[1];
+  a.n3 = c->mesh[2];
+  a.eqp = e_tab(c, w);
+  a.dim = c->dim;
+  a.H = c->h64 ? nullptr : H;
+  a.H64 = c->h64 ? reinterpret_cast<double2 *>(H) : nullptr;
+  a.err = c->d_err;
+  return launch_direct(c, w, a, BSE_KP_G1);
+}
+
+// Unfused path, first contraction: T = M_vv W(q) (tensor cores) for the slab.
+void slab_g1(const bse_ctx *c, const SplitWS *w, int q0, int nq, tcg::Args &a, dim3 &grid) {
+  const int na = c->naux_tot;
+  a = tcg::Args{};
+  a.rows = w->rows;
+  a.n_valid = na;
+  a.k_chunks = w->kchunks;
+  a.scale = 1.0f;
+  a.out = w->T32;
+  a.ld_row = 1;
+  a.ld_col = w->rows;
+  a.out_bstride = (long long)w->rows * na;
+  a.b_batch_planes = 1;
+  a.b_base = q0;
+  a.qlist = c->d_qplus;
+  a.err = c->d_err;
+  grid = dim3((unsigned)((na + w->bn_g1 - 1) / w->bn_g1), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
+}
+
+// Unfused path, second contraction: H block += -(1/N_k) T M_cc^T (+ the diagonal).
+bse_status slab_g2(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  const int na = c->naux_tot;
+  dim3 grid(c->nk, nq);
+  size_t sm = sizeof(float2) * (c->nv * c->nv + c->nc * c->nc) * G2CH;
+  bse_prof_begin(c, BSE_KP_G2);
+  if (!fast_pair_kernels(c, w, q0, nq, H, false))
+    k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                          c->mesh[2], q0, c->d_qplus, w->rows, c->dim, c->h64 ? nullptr : H,
+                                          c->h64 ? reinterpret_cast<double2 *>(H) : nullptr);
+  bse_prof_end(c, BSE_KP_G2);
+  bse_count_launch();
+  return bse_check_launch(c, "g2_32");
+}
+
+}  // namespace
+
 bse_status split_assemble(bse_ctx *c, void *Hv) {
   SplitWS *w = ws(c);
   float2 *H = (float2 *)Hv;
-  const int na = c->naux_tot;
-  // exchange: H = alpha/N_k (X V) conj(X)^T  -- writes every element
   {
-    tcg::Args a{};
-    a.rows = (int)c->dim;
-    a.n_valid = (int)c->dim;
-    a.k_chunks = w->kchunks;
-    a.scale = (float)(c->alpha / c->nk);
-    // the exchange block is Hermitian: element (r, c) is stored as conj at (c, r), so a lane's
-    // row index runs along memory and the stores coalesce
-    a.out = H;
-    a.out64 = c->h64 ? 1 : 0;
-    a.ld_row = 1;
-    a.ld_col = c->dim;
-    a.conj_out = 1;
-    a.out_bstride = 0;
-    a.b_batch_planes = 0;
-    a.b_base = 0;
-    a.qlist = nullptr;
-    a.err = c->d_err;
-    dim3 grid((unsigned)((c->dim + TC_BN - 1) / TC_BN), (unsigned)((c->dim + tcg::BM - 1) / tcg::BM), 1);
+    tcg::Args a;
+    dim3 grid;
+    exchange_gemm(c, w, H, a, grid);
     bse_status s = launch_tc_np(c, w->np, TC_BN, w->tmA_x, w->tmB_x, a, grid, BSE_KP_EXCH);
     if (s != BSE_OK) return s;
   }
-  const int nchunk = (na + 127) / 128;
   const int nqp = (int)c->qplus.size();
   for (int q0 = 0; q0 < nqp; q0 += w->nq) {
     const int nq = std::min(w->nq, nqp - q0);
-    if (w->fused) {
-      // projections (M_cc in the fused layout), then T = M_vv W(q) and H += -T M_cc^T / N_k
-      bse_prof_begin(c, BSE_KP_PROJECT);
-      fast_pair_kernels(c, w, q0, nq, H, true, w->naux_pad);
-      bse_prof_end(c, BSE_KP_PROJECT);
-      bse_count_launch();
-      bse_status s = bse_check_launch(c, "proj32");
-      if (s != BSE_OK) return s;
-      const int rpp = c->nv * c->nv;
-      tcd::DArgs a{};
-      a.nv = c->nv;
-      a.pairs = w->pairs_d;
-      a.rows = w->rows;
-      a.tiles_m = (c->nk + w->pairs_d - 1) / w->pairs_d;
-      a.tiles_b = nq;
-      a.k_chunks = w->kchunks;
-      a.naux = na;
-      a.naux_pad = w->naux_pad;
-      a.nui = w->nui_d;
-      a.n_mitems = (w->naux_pad + w->nui_d - 1) / w->nui_d;
-      a.Mc = w->Mc32;
-      a.qlist = c->d_qplus;
-      a.b_base = q0;
-      a.n1 = c->mesh[0];
-      a.n2 = c->mesh[1];
-      a.n3 = c->mesh[2];
-      a.eqp = e_tab(c, w);
-      a.dim = c->dim;
-      a.H = c->h64 ? nullptr : H;
-      a.H64 = c->h64 ? reinterpret_cast<double2 *>(H) : nullptr;
-      a.err = c->d_err;
-      (void)rpp;
-      s = launch_direct(c, w, a, BSE_KP_G1);
-      if (s != BSE_OK) return s;
-      continue;
+    bse_status s = slab_project(c, w, q0, nq, H);
+    if (s == BSE_OK) {
+      if (w->fused) {
+        s = slab_direct(c, w, q0, nq, H);
+      } else {
+        tcg::Args a;
+        dim3 grid;
+        slab_g1(c, w, q0, nq, a, grid);
+        s = launch_tc_np(c, w->np, w->bn_g1, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
+        if (s == BSE_OK) s = slab_g2(c, w, q0, nq, H);
+      }
     }
-    {
-      dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);
-      size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
-      bse_prof_begin(c, BSE_KP_PROJECT);
-      if (!fast_pair_kernels(c, w, q0, nq, H, true))
-        k_proj32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
-                                               c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1],
-                                               c->mesh[2], q0, c->d_qplus, w->rows, w->kmem, pieces(w, w->Ap),
-                                               w->Mc32);
-      bse_prof_end(c, BSE_KP_PROJECT);
-      bse_count_launch();
-      bse_status s = bse_check_launch(c, "proj32");
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+namespace {
+
+// ---- batched assembly of several systems as a work list ----------------------------------
+// One grouped tensor-core launch per step and N tile: every (system, q-slab) GEMM of the step
+// is a group of the launch's work list (Groups), so the persistent CTAs stream the tiles of
+// all of them (smallest system first) instead of one launch per system.
+constexpr int MAXG = 16;
+struct GemmItem {
+  const CUtensorMap *A, *B;
+  tcg::Args a;
+  dim3 grid;
+};
+
+template <int NP, int BN, bool TF>
+bse_status launch_grouped_t(bse_ctx *c, const std::vector<GemmItem> &items, int prof_id) {
+  using Cf = tcg::Cfg<NP, BN>;
+  for (size_t i0 = 0; i0 < items.size(); i0 += MAXG) {
+    const int n = (int)std::min<size_t>(MAXG, items.size() - i0);
+    tcg::Groups<MAXG> G;
+    long long t0 = 0;
+    for (int g = 0; g < n; g++) {
+      const GemmItem &it = items[i0 + g];
+      G.A[g] = *it.A;
+      G.B[g] = *it.B;
+      G.a[g] = it.a;
+      G.a[g].tiles_n = (int)it.grid.x;
+      G.a[g].tiles_m = (int)it.grid.y;
+      G.a[g].tiles_b = (int)it.grid.z;
+      G.tile0[g] = t0;
+      t0 += (long long)it.grid.x * it.grid.y * it.grid.z;
+    }
+    for (int g = n; g <= MAXG; g++) G.tile0[g] = t0;
+    G.n = n;
+    if (t0 == 0) continue;
+    const int ctas = (int)std::min<long long>(t0, c->n_sm);
+    bse_prof_begin(c, prof_id);
+    tcg::k_tc_zgemm<NP, BN, TF, MAXG><<<ctas, 192, Cf::SMEM, c->stream>>>(G);
+    bse_prof_end(c, prof_id);
+    bse_count_launch();
+    const bse_status s = bse_check_launch(c, "tc_zgemm (grouped)");
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+template <int NP, bool TF>
+bse_status launch_grouped_bn(bse_ctx *c, int bn, const std::vector<GemmItem> &items, int prof_id) {
+  switch (bn) {
+    case 64: return launch_grouped_t<NP, 64, TF>(c, items, prof_id);
+    case 96: return launch_grouped_t<NP, 96, TF>(c, items, prof_id);
+    case 128: return launch_grouped_t<NP, 128, TF>(c, items, prof_id);
+    default: return launch_grouped_t<NP, 160, TF>(c, items, prof_id);
+  }
+}
+
+bse_status launch_grouped(bse_ctx *c, const SplitWS *w, int bn, const std::vector<GemmItem> &items, int prof_id) {
+  if (items.empty()) return BSE_OK;
+  if (w->tf32) return launch_grouped_bn<2, true>(c, bn, items, prof_id);
+  if (w->np == 3) return launch_grouped_bn<3, false>(c, bn, items, prof_id);
+  if (w->np == 2) return launch_grouped_bn<2, false>(c, bn, items, prof_id);
+  return launch_grouped_bn<1, false>(c, bn, items, prof_id);
+}
+
+template <int NP, bool TF>
+void set_grouped_attr() {
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, 64, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcg::Cfg<NP, 64>::SMEM);
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, 96, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcg::Cfg<NP, 96>::SMEM);
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, 128, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcg::Cfg<NP, 128>::SMEM);
+  cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, 160, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcg::Cfg<NP, 160>::SMEM);
+}
+void set_grouped_attrs_now() {
+  set_grouped_attr<1, false>();
+  set_grouped_attr<2, false>();
+  set_grouped_attr<3, false>();
+  set_grouped_attr<2, true>();
+}
+
+}  // namespace
+
+// The work-list schedule of a batch: the systems ctxs[order[0]], ctxs[order[1]], ...
+// (smallest first).  Their (system, q-slab) units are dealt into steps: a step takes the next
+// slab of each unfinished system in order, at most one per system (each system has one slab
+// buffer), until its M_vv W(q) tiles fill two waves of the SMs; a system's exchange GEMM joins
+// the step of its first slab.  Per step: one grouped exchange launch, the systems'
+// projections, one grouped M_vv W(q) launch per N tile (unfused systems), then each system's
+// second contraction or fused direct kernel.  Every launch goes to the first system's
+// stream; stamp(i) is called once system i's work is enqueued.
+bse_status split_batch_worklist(bse_ctx **ctxs, void **Hv, const int *order, int n,
+                                const std::function<void(int)> &stamp) {
+  bse_ctx *c0 = ctxs[order[0]];
+  const SplitWS *w0 = ws(c0);
+  for (int r = 0; r < n; r++) {
+    const bse_ctx *c = ctxs[order[r]];
+    const SplitWS *w = ws(ctxs[order[r]]);
+    if (c->precision == BSE_FP64 || !w || w->np != w0->np || w->tf32 != w0->tf32)
+      return bse_fail(c0, BSE_EINVAL, "batch work list: every system needs the same split precision");
+    if (c->stream != c0->stream) return bse_fail(c0, BSE_EINVAL, "batch work list: streams differ");
+  }
+  bse_once_per_device(c0, BSE_ONCE_GROUPED, set_grouped_attrs_now);
+  std::vector<int> next(n, 0), nslab(n);   // by position in order
+  for (int r = 0; r < n; r++) {
+    const bse_ctx *c = ctxs[order[r]];
+    const int nqp = (int)c->qplus.size(), nq = ws(ctxs[order[r]])->nq;
+    nslab[r] = (nqp + nq - 1) / nq;
+  }
+  const long long fill = 2LL * c0->n_sm;
+  int left = 0;
+  for (int r = 0; r < n; r++) left += nslab[r] > 0;
+  struct Unit {
+    int r, q0, nq;
+  };
+  while (left > 0) {
+    std::vector<Unit> step;
+    long long tiles = 0;
+    for (int r = 0; r < n && tiles < fill && (int)step.size() < MAXG; r++) {
+      if (next[r] >= nslab[r]) continue;
+      const bse_ctx *c = ctxs[order[r]];
+      const SplitWS *w = ws(ctxs[order[r]]);
+      const int q0 = next[r] * w->nq, nq = std::min(w->nq, (int)c->qplus.size() - q0);
+      step.push_back({r, q0, nq});
+      const long long mt = w->fused ? (c->nk + w->pairs_d - 1) / w->pairs_d
+                                    : (long long)((c->naux_tot + w->bn_g1 - 1) / w->bn_g1) *
+                                          ((w->rows + tcg::BM - 1) / tcg::BM);
+      tiles += mt * nq;
+    }
+    {  // exchange GEMMs of the systems starting here
+      std::vector<GemmItem> ex;
+      for (const Unit &u : step)
+        if (u.q0 == 0) {
+          const int i = order[u.r];
+          GemmItem it;
+          it.A = &ws(ctxs[i])->tmA_x;
+          it.B = &ws(ctxs[i])->tmB_x;
+          exchange_gemm(ctxs[i], ws(ctxs[i]), (float2 *)Hv[i], it.a, it.grid);
+          ex.push_back(it);
+        }
+      const bse_status s = launch_grouped(c0, w0, TC_BN, ex, BSE_KP_EXCH);
       if (s != BSE_OK) return s;
     }
-    {
-      tcg::Args a{};
-      a.rows = w->rows;
-      a.n_valid = na;
-      a.k_chunks = w->kchunks;
-      a.scale = 1.0f;
-      a.out = w->T32;
-      a.ld_row = 1;
-      a.ld_col = w->rows;
-      a.out_bstride = (long long)w->rows * na;
-      a.b_batch_planes = 1;
-      a.b_base = q0;
-      a.qlist = c->d_qplus;
-      a.err = c->d_err;
-      dim3 grid((unsigned)((na + w->bn_g1 - 1) / w->bn_g1), (unsigned)((w->rows + tcg::BM - 1) / tcg::BM), nq);
-      bse_status s = launch_tc_np(c, w->np, w->bn_g1, w->tmA_g1, w->tmB_g1, a, grid, BSE_KP_G1);
+    for (const Unit &u : step) {
+      const int i = order[u.r];
+      const bse_status s = slab_project(ctxs[i], ws(ctxs[i]), u.q0, u.nq, (float2 *)Hv[i]);
       if (s != BSE_OK) return s;
     }
-    {
-      dim3 grid(c->nk, nq);
-      size_t sm = sizeof(float2) * (c->nv * c->nv + c->nc * c->nc) * G2CH;
-      bse_prof_begin(c, BSE_KP_G2);
-      if (!fast_pair_kernels(c, w, q0, nq, H, false))
-        k_g2_32<<<grid, 256, sm, c->stream>>>(w->T32, w->Mc32, e_tab(c, w), c->nv, c->nc, na, c->mesh[0], c->mesh[1],
-                                              c->mesh[2], q0, c->d_qplus, w->rows, c->dim, c->h64 ? nullptr : H,
-                                              c->h64 ? reinterpret_cast<double2 *>(H) : nullptr);
-      bse_prof_end(c, BSE_KP_G2);
-      bse_count_launch();
-      bse_status s = bse_check_launch(c, "g2_32");
+    for (int bn : TC_BN_CAND) {
+      std::vector<GemmItem> g1;
+      for (const Unit &u : step) {
+        const int i = order[u.r];
+        SplitWS *w = ws(ctxs[i]);
+        if (w->fused || w->bn_g1 != bn) continue;
+        GemmItem it;
+        it.A = &w->tmA_g1;
+        it.B = &w->tmB_g1;
+        slab_g1(ctxs[i], w, u.q0, u.nq, it.a, it.grid);
+        g1.push_back(it);
+      }
+      const bse_status s = launch_grouped(c0, w0, bn, g1, BSE_KP_G1);
       if (s != BSE_OK) return s;
+    }
+    for (const Unit &u : step) {
+      const int i = order[u.r];
+      SplitWS *w = ws(ctxs[i]);
+      const bse_status s = w->fused ? slab_direct(ctxs[i], w, u.q0, u.nq, (float2 *)Hv[i])
+                                    : slab_g2(ctxs[i], w, u.q0, u.nq, (float2 *)Hv[i]);
+      if (s != BSE_OK) return s;
+      if (++next[u.r] == nslab[u.r]) {
+        left--;
+        stamp(i);
+      }
     }
   }
   return BSE_OK;

@@ -15,7 +15,8 @@
 // Operands arrive by TMA as 3-D tensors {K, rows, plane-piece(-batch)} with 64-byte
 // swizzled rows (32 bf16 or 16 tf32 of K per stage); rows and K beyond the tensor are
 // zero-filled.
-// Persistent CTAs (one per SM) walk the 128 x BN output tiles: warp 0 issues TMA, warp 1
+// Persistent CTAs (one per SM) walk the 128 x BN output tiles of a work list (one GEMM, or
+// several independent ones of a batch, Groups below): warp 0 issues TMA, warp 1
 // allocates tensor memory and issues the MMAs from one thread, warps 2-5 drain the
 // accumulators of one tile while the next tile's operands stream in.  Every barrier wait
 // is bounded; a timeout sets the device error word and the CTA winds down.
@@ -65,9 +66,20 @@ struct Args {
   int tiles_n, tiles_m, tiles_b;  // output tiles along N, M and the batch (set by the launcher)
 };
 
-template <int NP, int BN, bool TF = false>
-__global__ void __launch_bounds__(192, 1)
-    k_tc_zgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Args args) {
+// The work list of one launch: NG independent GEMMs (operand tensor maps and output
+// arguments each), their output tiles numbered consecutively, group g owning tiles
+// tile0[g] .. tile0[g + 1] - 1 (n of them in use).  A single GEMM is the list with NG = 1; the
+// batched assembly of several systems puts each system's GEMM of one step in a group.
+template <int NG>
+struct Groups {
+  CUtensorMap A[NG], B[NG];
+  Args a[NG];
+  long long tile0[NG + 1];
+  int n;
+};
+
+template <int NP, int BN, bool TF = false, int NG = 1>
+__global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Groups<NG> G) {
   using C = Cfg<NP, BN>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -79,7 +91,11 @@ __global__ void __launch_bounds__(192, 1)
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int total = args.tiles_n * args.tiles_m * args.tiles_b;
+  const long long total = G.tile0[G.n];
+  // group of work-list tile t; a CTA's tiles only grow, so its group index only advances
+  auto group_of = [&](long long t, int &g) {
+    while (g + 1 < G.n && t >= G.tile0[g + 1]) g++;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::S; s++) {
@@ -91,10 +107,11 @@ __global__ void __launch_bounds__(192, 1)
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 0 && lane == 0) {
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
-  }
+  if (warp == 0 && lane == 0)
+    for (int g = 0; g < G.n; g++) {
+      tc::prefetch_tmap(&G.A[g]);
+      tc::prefetch_tmap(&G.B[g]);
+    }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
     tc::tmem_relinquish();
@@ -111,11 +128,14 @@ __global__ void __launch_bounds__(192, 1)
   // of tile t drains the accumulators while the producer already loads tile t + gridDim.x.
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer ----------------
-    int it = 0;
+    int it = 0, g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int n0 = (t % args.tiles_n) * BN, m0 = ((t / args.tiles_n) % args.tiles_m) * BM;
-      const int b = t / (args.tiles_n * args.tiles_m);
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      group_of(t, g);
+      const Args &args = G.a[g];
+      const int lt = (int)(t - G.tile0[g]);
+      const int n0 = (lt % args.tiles_n) * BN, m0 = ((lt / args.tiles_n) % args.tiles_m) * BM;
+      const int b = lt / (args.tiles_n * args.tiles_m);
       const int zb = args.b_batch_planes ? args.qlist[args.b_base + b] * C::PP : 0;
       for (int kc = 0; kc < args.k_chunks; kc++, it++) {
         const int s = it % C::S;
@@ -132,21 +152,24 @@ __global__ void __launch_bounds__(192, 1)
         uint8_t *st = smem + s * C::STAGE;
         tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
         for (int pp = 0; pp < C::PP; pp++) {
-          tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * bk_elems<TF>(), m0, b * C::PP + pp);
-          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * bk_elems<TF>(), n0, zb + pp);
+          tc::tma_load_3d(st + pp * A_TILE, &G.A[g], &full[s], kc * bk_elems<TF>(), m0, b * C::PP + pp);
+          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &G.B[g], &full[s], kc * bk_elems<TF>(), n0,
+                          zb + pp);
         }
       }
     }
     // every copy this CTA started lands before the CTA can exit
     for (int k = it - C::S < 0 ? 0 : it - C::S; k < it; k++)
-      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
+      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(G.a[g].err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t IPOS = tc::idesc<TF>(BM, BN, false);
     constexpr uint32_t INEG = tc::idesc<TF>(BM, BN, true);
-    int it = 0, tcount = 0;
+    int it = 0, tcount = 0, g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
+      group_of(t, g);
+      const Args &args = G.a[g];
       if (*abort_flag) break;
       if (tcount > 0 && !tc::mbar_wait_bounded(tempty, (tcount - 1) & 1, 4 * WAIT_LIMIT)) {
         atomicOr(args.err, 2);
@@ -199,8 +222,10 @@ __global__ void __launch_bounds__(192, 1)
     // ---------------- epilogue: TMEM -> registers -> global ----------------
     const int quarter = warp % 4;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    int tcount = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
+    int tcount = 0, g = 0;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
+      group_of(t, g);
+      const Args &args = G.a[g];
       const bool ok = !*abort_flag && tc::mbar_wait_bounded(tfull, tcount & 1, 4 * WAIT_LIMIT);
       if (!ok) {
         atomicOr(args.err, 2);
@@ -208,8 +233,9 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       tc::tc_fence_after();
-      const int n0 = (t % args.tiles_n) * BN, m0 = ((t / args.tiles_n) % args.tiles_m) * BM;
-      const int b = t / (args.tiles_n * args.tiles_m);
+      const int lt = (int)(t - G.tile0[g]);
+      const int n0 = (lt % args.tiles_n) * BN, m0 = ((lt / args.tiles_n) % args.tiles_m) * BM;
+      const int b = lt / (args.tiles_n * args.tiles_m);
       const int row = m0 + quarter * 32 + lane;
       const long long orow = (long long)b * args.out_bstride + (long long)row * args.ld_row;
       const bool row_ok = row < args.rows;

@@ -28,7 +28,8 @@ def offset_average(systems, Hs, dipoles, omega: torch.Tensor, n_steps: int, eta:
     if not (len(systems) == len(Hs) == len(dipoles) == len(prefactors) == len(weights)):
         raise ValueError("offset_average: one system, H, dipole vector, prefactor and weight per offset")
     if batched:
-        batch_assemble(systems, Hs)
+        split = all(b.precision != "fp64" and b.precision == systems[0].precision for b in systems)
+        batch_assemble(systems, Hs, schedule="worklist" if split else "chains")
     else:
         for b, H in zip(systems, Hs):
             b.assemble(H)

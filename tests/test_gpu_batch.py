@@ -1,6 +1,8 @@
-"""Batching of uneven crystals as one CUDA graph (bse_batch_assemble) and the tile autotuner
+"""Batching of uneven crystals as one CUDA graph (bse_batch_assemble, both schedules: the work
+list of grouped tensor-core launches and the two concurrent chains) and the tile autotuner
 (bse_autotune): each system's H must equal its unbatched assembly exactly (same kernels, same
-tiles), match the oracle within the split tolerance, and stay the same on graph replay."""
+tiles, same order of the updates of each element), match the oracle within the split
+tolerance, and stay the same on graph replay."""
 import numpy as np
 import pytest
 
@@ -41,7 +43,8 @@ def _setup(specs, prec="bf16x3"):
     return systems
 
 
-def test_batch_graph_matches_unbatched_and_oracle():
+@pytest.mark.parametrize("schedule", ["worklist", "chains"])
+def test_batch_graph_matches_unbatched_and_oracle(schedule):
     import torch
     from paper_2607_05853_b300.api import batch_assemble, batch_release
     systems = _setup(SMALL)
@@ -51,14 +54,14 @@ def test_batch_graph_matches_unbatched_and_oracle():
     ref = [b.assemble() for _, b, _ in systems]
     torch.cuda.synchronize()
     Hs = [torch.zeros_like(r) for r in ref]
-    stamps = batch_assemble([b for _, b, _ in systems], Hs, stamps=True)
+    stamps = batch_assemble([b for _, b, _ in systems], Hs, stamps=True, schedule=schedule)
     assert all(s > 0 for s in stamps)
     for (inp, b, _), H, R in zip(systems, Hs, ref):
         assert torch.equal(H, R), inp["name"]
         assert_split_close(H.cpu().numpy(), O.BSEOracle(inp).hamiltonian(), "bf16x3")
     for H in Hs:
         H.zero_()
-    batch_assemble([b for _, b, _ in systems], Hs)   # replay of the cached graph
+    batch_assemble([b for _, b, _ in systems], Hs, schedule=schedule)   # replay of the cached graph
     torch.cuda.synchronize()
     for H, R in zip(Hs, ref):
         assert torch.equal(H, R)
@@ -66,21 +69,25 @@ def test_batch_graph_matches_unbatched_and_oracle():
 
 
 def test_batch_mixed_precisions():
-    """An FP64 and a split context in the same graph."""
+    """An FP64 and a split context in the same graph (the chains schedule; the work list
+    needs one split precision and refuses the pair)."""
     import torch
-    from paper_2607_05853_b300.api import batch_assemble, batch_release
+    from paper_2607_05853_b300.api import BseError, batch_assemble, batch_release
     a = _setup(SMALL[:1], "fp64")[0]
     b = _setup(SMALL[1:2], "bf16x2")[0]
     ra, rb = a[1].assemble(), b[1].assemble()
     Ha, Hb = torch.zeros_like(ra), torch.zeros_like(rb)
-    batch_assemble([a[1], b[1]], [Ha, Hb])
+    with pytest.raises(BseError, match="EINVAL"):
+        batch_assemble([a[1], b[1]], [Ha, Hb], schedule="worklist")
+    batch_assemble([a[1], b[1]], [Ha, Hb], schedule="chains")
     torch.cuda.synchronize()
     assert torch.equal(Ha, ra) and torch.equal(Hb, rb)
     batch_release()
 
 
 @pytest.mark.slow
-def test_sixteen_uneven_crystals_batch():
+@pytest.mark.parametrize("schedule", ["worklist", "chains"])
+def test_sixteen_uneven_crystals_batch(schedule):
     """The 16-crystal batch (1-8 atoms, N_aux 86-579, meshes 6^3-10^3, Nv,Nc in {2,4,6}),
     complex64 split path, autotuned, one graph: per-system sampled blocks against the oracle
     for the smaller systems, exact equality with the unbatched assembly for all."""
@@ -91,7 +98,7 @@ def test_sixteen_uneven_crystals_batch():
     for _, b, _ in systems:
         b.autotune()
     Hs = [torch.empty((b.dim, b.dim), dtype=b.h_dtype, device="cuda") for _, b, _ in systems]
-    stamps = batch_assemble([b for _, b, _ in systems], Hs, stamps=True)
+    stamps = batch_assemble([b for _, b, _ in systems], Hs, stamps=True, schedule=schedule)
     rng = np.random.default_rng(1)
     for (inp, b, _), H in zip(systems, Hs):
         ref = b.assemble()

@@ -344,6 +344,25 @@ __global__ void __launch_bounds__(128, 4) k_hmatvec_c64(const float2 *__restrict
 
 
 
+// Launch with programmatic stream serialization: the kernel may be scheduled while its
+// predecessor in the stream drains (hiding the launch latency of the Lanczos step's short
+// kernels); every kernel launched this way opens with tc::griddep_wait().  Launch errors
+// surface through cudaGetLastError as for <<<>>>.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Packed FP32 pairs (Blackwell fma.rn.f32x2): one instruction performs two FP32 FMAs.
 __device__ __forceinline__ unsigned long long pk2(float a, float b) {
   unsigned long long r;
@@ -401,6 +420,8 @@ __global__ void __launch_bounds__(128, HmvSmem<NP>::CTAS) k_hmv_tma(const __grid
   float4 *yb = reinterpret_cast<float4 *>(ring + MV_STAGES * MV_STAGE_BYTES);  // [NP][HT] (yr,-yr,yi,yi)
   float2 *xc = reinterpret_cast<float2 *>(yb + NP * HT);                       // [NP][HT] (xr,xi)
   uint8_t *uni = reinterpret_cast<uint8_t *>(xc + NP * HT);  // per warp: U-sum scratch, then V partials
+  tc::griddep_wait();
+  tc::griddep_launch();
   bool live = false;
   for (int p = 0; p < NP; p++) live |= (j < meff[p]);
   if (!live) return;
@@ -668,6 +689,8 @@ __global__ void __launch_bounds__(HALVES * HT * NP, 1) k_hmv_reduce(const float2
                                                                 int nb, double2 *__restrict__ W,
                                                                 const double2 *__restrict__ Q, long long qs, int j,
                                                                 const int *__restrict__ meff, double *__restrict__ apart) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ double2 hs[HT * NP];
   __shared__ double av[HT * NP];
   const int t = blockIdx.x;
@@ -755,11 +778,27 @@ __global__ void k_alpha_part(const double2 *__restrict__ W, long long dim, const
   if (threadIdx.x == 0) apart[p * nb + t] = ar;
 }
 
-// alpha_j = sum_t apart[p][t] (same order in every block); W -= alpha_j Q_j + b_{j-1} Q_{j-1}
+// Per 128-row block sums of v (one value per thread, blockDim = 256, rows in thread order):
+// out[2 blockIdx.x + h] for the block's two halves h (those below nb).
+__device__ __forceinline__ void half_block_sums(double v, double *red, double *out, int nb) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  if (threadIdx.x < 2 && 2 * (int)blockIdx.x + (int)threadIdx.x < nb) {
+    const double *r = red + 4 * threadIdx.x;
+    out[2 * blockIdx.x + threadIdx.x] = ((r[0] + r[1]) + r[2]) + r[3];
+  }
+}
+
+// alpha_j = sum_t apart[p][t] (same order in every block); W -= alpha_j Q_j + b_{j-1} Q_{j-1};
+// with n0part, also the per-row-block sums of |W|^2 of the result (n0part[p][t]).
 __global__ void __launch_bounds__(256) k_axpy(double2 *__restrict__ W, long long dim, const double2 *__restrict__ Q,
                                               long long qs, int j, double *__restrict__ a, const double *__restrict__ b,
                                               int ldab, const int *__restrict__ meff, int nb,
-                                              const double *__restrict__ apart) {
+                                              const double *__restrict__ apart, double *__restrict__ n0part) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ double red[32];
   __shared__ double sa;
   const int p = blockIdx.y;
@@ -770,19 +809,25 @@ __global__ void __launch_bounds__(256) k_axpy(double2 *__restrict__ W, long long
   if (blockIdx.x == 0 && threadIdx.x == 0) a[p * ldab + j] = aj;
   const double bj = j > 0 ? b[p * ldab + j - 1] : 0.0;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= dim) return;
-  const double2 *qj = Q + p * qs + (long long)j * dim;
-  const double2 *qm = j > 0 ? qj - dim : qj;
-  double2 v = W[(long long)p * dim + e];
-  const double2 x = qj[e], y = qm[e];
-  v.x -= aj * x.x + bj * y.x;
-  v.y -= aj * x.y + bj * y.y;
-  W[(long long)p * dim + e] = v;
+  double nv = 0.0;
+  if (e < dim) {
+    const double2 *qj = Q + p * qs + (long long)j * dim;
+    const double2 *qm = j > 0 ? qj - dim : qj;
+    double2 v = W[(long long)p * dim + e];
+    const double2 x = qj[e], y = qm[e];
+    v.x -= aj * x.x + bj * y.x;
+    v.y -= aj * x.y + bj * y.y;
+    W[(long long)p * dim + e] = v;
+    nv = v.x * v.x + v.y * v.y;
+  }
+  if (n0part) half_block_sums(nv, red, n0part + (long long)p * nb, nb);
 }
 
 // npart[p][t] = sum over the rows of block t of |W|^2
 __global__ void k_norm_part(const double2 *__restrict__ W, long long dim, int j, const int *__restrict__ meff, int nb,
                             double *__restrict__ npart) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ double red[32];
   const int t = blockIdx.x, p = blockIdx.y;
   const long long row = (long long)t * HT + threadIdx.x;
@@ -801,6 +846,8 @@ __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ W, lo
                                                long long qs, int j, double *__restrict__ b, int ldab, int *meff,
                                                const double *__restrict__ hmax, int n_steps, float2 *__restrict__ Q32,
                                                int nb, const double *__restrict__ npart) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ double red[32];
   __shared__ double sb;
   const int p = blockIdx.y;
@@ -895,6 +942,8 @@ __global__ void __launch_bounds__(256, 2) k_reorth_dots_chunk(const double2 *__r
                                                               const float2 *__restrict__ Q32, long long qs, int j,
                                                               float2 *__restrict__ partial, int nchunk, int ldp,
                                                               const int *__restrict__ meff) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ float4 ws[RCH / 2];
   const int chunk = blockIdx.x, p = blockIdx.y;
   if (j >= meff[p]) return;
@@ -952,6 +1001,8 @@ __global__ void __launch_bounds__(256, 2) k_reorth_dots_chunk(const double2 *__r
 // coef[p][i] = sum over chunks of partial[p][i][chunk] (FP64): one warp per (i, p)
 __global__ void __launch_bounds__(256) k_reorth_coef(const float2 *__restrict__ partial, int nchunk, int ldp, int j,
                                                      double2 *__restrict__ coef, int ldc, const int *__restrict__ meff) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   const int i = blockIdx.x * 8 + threadIdx.x / 32, lane = threadIdx.x % 32, p = blockIdx.y;
   if (j >= meff[p] || i > j) return;
   const float2 *src = partial + ((long long)p * ldp + i) * nchunk;
@@ -970,11 +1021,16 @@ __global__ void __launch_bounds__(256) k_reorth_coef(const float2 *__restrict__ 
 
 // W -= sum_i coef_i Q32_i for two elements per thread (float4 loads, 16 basis rows in flight
 // per thread); FP32 products and sums, subtracted from the FP64 vector.  Needs an even dim.
+// With npart, also the per-row-block sums of |W|^2 of the result (npart[p][t], four 128-row
+// blocks per 256-thread block).
 constexpr int RUN = 16;
 __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict__ W, long long dim,
                                                             const float2 *__restrict__ Q32, long long qs, int j,
                                                             const double2 *__restrict__ coef, int ldc,
-                                                            const int *__restrict__ meff) {
+                                                            const int *__restrict__ meff, int nb,
+                                                            double *__restrict__ npart) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ float2 cs[1024];
   const int p = blockIdx.y;
   if (j >= meff[p]) return;
@@ -1016,6 +1072,7 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
       }
     }
   }
+  double nv = 0.0;
   if (in) {
     double2 *wp = W + (long long)p * dim + e;
     double2 v0 = wp[0], v1 = wp[1];
@@ -1025,6 +1082,15 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
     v1.y -= (double)a1i;
     wp[0] = v0;
     wp[1] = v1;
+    nv = (v0.x * v0.x + v0.y * v0.y) + (v1.x * v1.x + v1.y * v1.y);
+  }
+  if (npart) {
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = nv;
+    __syncthreads();
+    const int t = 4 * blockIdx.x + threadIdx.x;  // 128-row block of warps 2 threadIdx.x, +1
+    if (threadIdx.x < 4 && t < nb) npart[(long long)p * nb + t] = red[2 * threadIdx.x] + red[2 * threadIdx.x + 1];
   }
 }
 
@@ -1178,6 +1244,8 @@ bool encode_rows_f32(CUtensorMap *m, const void *base, unsigned long long inner,
 // meff2[p] = 0 makes the pass-two kernels skip polarisation p; otherwise meff2[p] = meff[p].
 __global__ void k_dgks(const double *__restrict__ n0part, const double *__restrict__ n1part, int nb,
                        const int *__restrict__ meff, int *__restrict__ meff2) {
+  tc::griddep_wait();
+  tc::griddep_launch();
   __shared__ double r0[32], r1[32];
   const int p = blockIdx.x;
   double a0 = 0.0, a1 = 0.0;
@@ -1330,17 +1398,23 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
     } else if (c64 && s.tma) {
       const int grid = std::min(s.ntiles, HmvSmem<3>::CTAS * c->n_sm);
       if (n_pol == 1) {
-        k_hmv_tma<1><<<grid, 128, hmv_tma_smem<1>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        launch_pdl(k_hmv_tma<1>, dim3(grid), dim3(128), hmv_tma_smem<1>(), st, s.tmH, dim, s.nbt, s.tiles,
+                   s.ntiles, (const float2 *)s.Q32, qs, j, s.hpart, (const int *)s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<1><<<s.nbt, 2 * HT * 1, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
+        launch_pdl(k_hmv_reduce<1>, dim3(s.nbt), dim3(2 * HT * 1), 0, st, (const float2 *)s.hpart, dim, s.nbt,
+                   s.W, (const double2 *)s.Q, qs, j, (const int *)s.meff, s.apart);
       } else if (n_pol == 2) {
-        k_hmv_tma<2><<<grid, 128, hmv_tma_smem<2>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        launch_pdl(k_hmv_tma<2>, dim3(grid), dim3(128), hmv_tma_smem<2>(), st, s.tmH, dim, s.nbt, s.tiles,
+                   s.ntiles, (const float2 *)s.Q32, qs, j, s.hpart, (const int *)s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<2><<<s.nbt, 2 * HT * 2, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
+        launch_pdl(k_hmv_reduce<2>, dim3(s.nbt), dim3(2 * HT * 2), 0, st, (const float2 *)s.hpart, dim, s.nbt,
+                   s.W, (const double2 *)s.Q, qs, j, (const int *)s.meff, s.apart);
       } else {
-        k_hmv_tma<3><<<grid, 128, hmv_tma_smem<3>(), st>>>(s.tmH, dim, s.nbt, s.tiles, s.ntiles, s.Q32, qs, j, s.hpart, s.meff, c->d_err);
+        launch_pdl(k_hmv_tma<3>, dim3(grid), dim3(128), hmv_tma_smem<3>(), st, s.tmH, dim, s.nbt, s.tiles,
+                   s.ntiles, (const float2 *)s.Q32, qs, j, s.hpart, (const int *)s.meff, c->d_err);
         bse_prof_end(c, BSE_KP_MATVEC);
-        k_hmv_reduce<3><<<s.nbt, 2 * HT * 3, 0, st>>>(s.hpart, dim, s.nbt, s.W, s.Q, qs, j, s.meff, s.apart);
+        launch_pdl(k_hmv_reduce<3>, dim3(s.nbt), dim3(2 * HT * 3), 0, st, (const float2 *)s.hpart, dim, s.nbt,
+                   s.W, (const double2 *)s.Q, qs, j, (const int *)s.meff, s.apart);
       }
       bse_count_launch(2);
     } else if (c64 && s.hpart) {
@@ -1374,33 +1448,41 @@ bse_status lanczos_run(bse_ctx *c, LanczosScratch &s, const void *H, const doubl
       k_alpha_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, s.Q, qs, j, s.meff, s.nbt, s.apart);
       bse_count_launch();
     }
-    k_axpy<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.a, s.b, ldab, s.meff, s.nbt, s.apart);
-    bse_prof_begin(c, BSE_KP_REORTH);
     const bool proj32 = c64 && dim % 2 == 0;
-    if (proj32) k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.n0part);
+    // |W|^2 per row block before the reorthogonalisation (the DGKS test's reference)
+    launch_pdl(k_axpy, dim3(el_blocks, n_pol), dim3(256), 0, st, s.W, dim, (const double2 *)s.Q, qs, j, s.a,
+               (const double *)s.b, ldab, (const int *)s.meff, s.nbt, (const double *)s.apart,
+               proj32 ? s.n0part : (double *)nullptr);
+    bse_prof_begin(c, BSE_KP_REORTH);
     for (int pass = 0; pass < 2; pass++) {
       if (proj32) {
-        // the second pass runs where the DGKS test asks for it (meff2)
+        // the second pass runs where the DGKS test asks for it (meff2); the first pass left the
+        // norms of its result in npart, and the second overwrites them where it runs, so npart
+        // holds the final norms either way
         if (pass == 1) {
-          k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.npart);
-          k_dgks<<<n_pol, 32, 0, st>>>(s.n0part, s.npart, s.nbt, s.meff, s.meff2);
-          bse_count_launch(2);
+          launch_pdl(k_dgks, dim3(n_pol), dim3(32), 0, st, (const double *)s.n0part, (const double *)s.npart, s.nbt,
+                     (const int *)s.meff, s.meff2);
+          bse_count_launch();
         }
         const int *mp = pass ? s.meff2 : s.meff;
-        k_reorth_dots_chunk<<<dim3(s.nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.rpart,
-                                                                                   s.nrch, ldab, mp);
-        k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(s.rpart, s.nrch, ldab, j, s.coef, ldab, mp);
-        k_reorth_update32<<<dim3(el2_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q32, qs, j, s.coef, ldab, mp);
+        launch_pdl(k_reorth_dots_chunk, dim3(s.nrch, n_pol, (j + RROWS) / RROWS), dim3(256), 0, st,
+                   (const double2 *)s.W, dim, (const float2 *)s.Q32, qs, j, s.rpart, s.nrch, ldab, mp);
+        launch_pdl(k_reorth_coef, dim3((j + 1 + 7) / 8, n_pol), dim3(256), 0, st, (const float2 *)s.rpart, s.nrch,
+                   ldab, j, s.coef, ldab, mp);
+        launch_pdl(k_reorth_update32, dim3(el2_blocks, n_pol), dim3(256), 0, st, s.W, dim, (const float2 *)s.Q32, qs,
+                   j, (const double2 *)s.coef, ldab, mp, s.nbt, s.npart);
       } else {  // complex128 H, or an odd dim: FP64 projections on the FP64 basis
         k_reorth_dots<<<dim3(j + 1, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
         k_reorth_update<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.coef, ldab, s.meff);
       }
     }
     bse_prof_end(c, BSE_KP_REORTH);
-    k_norm_part<<<dim3(s.nbt, n_pol), HT, 0, st>>>(s.W, dim, j, s.meff, s.nbt, s.npart);
-    k_scale<<<dim3(el_blocks, n_pol), 256, 0, st>>>(s.W, dim, s.Q, qs, j, s.b, ldab, s.meff, s.hmax, n_steps, s.Q32,
-                                                    s.nbt, s.npart);
-    bse_count_launch(proj32 ? 10 : 7);  // axpy, two reorthogonalisation passes (+ the pass-one norm), norm, scale
+    if (!proj32)
+      launch_pdl(k_norm_part, dim3(s.nbt, n_pol), dim3(HT), 0, st, (const double2 *)s.W, dim, j, (const int *)s.meff,
+                 s.nbt, s.npart);
+    launch_pdl(k_scale, dim3(el_blocks, n_pol), dim3(256), 0, st, (const double2 *)s.W, dim, s.Q, qs, j, s.b, ldab,
+               s.meff, (const double *)s.hmax, n_steps, s.Q32, s.nbt, (const double *)s.npart);
+    bse_count_launch(proj32 ? 8 : 7);  // axpy, two reorthogonalisation passes (+ the DGKS test), (norm,) scale
     r = bse_check_launch(c, "lanczos step");
     if (r != BSE_OK) return r;
   }
@@ -1858,7 +1940,8 @@ bse_status launch_reorth32_pass(bse_ctx *c, double2 *W, long long n, const float
   k_reorth_dots_chunk<<<dim3(nrch, n_pol, (j + RROWS) / RROWS), 256, 0, st>>>(W, n, D32, qs, j, rpart, nrch, ldp,
                                                                              meff);
   k_reorth_coef<<<dim3((j + 1 + 7) / 8, n_pol), 256, 0, st>>>(rpart, nrch, ldp, j, coef, ldp, meff);
-  k_reorth_update32<<<dim3((unsigned)((n / 2 + 255) / 256), n_pol), 256, 0, st>>>(W, n, U32, qs, j, coef, ldp, meff);
+  k_reorth_update32<<<dim3((unsigned)((n / 2 + 255) / 256), n_pol), 256, 0, st>>>(W, n, U32, qs, j, coef, ldp, meff, 0,
+                                                                                  nullptr);
   bse_count_launch(3);
   return BSE_OK;
 }

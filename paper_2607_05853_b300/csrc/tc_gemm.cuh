@@ -93,8 +93,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const long long total = G.tile0[G.n];
   // group of work-list tile t; a CTA's tiles only grow, so its group index only advances
+  // (a single GEMM, NG = 1, indexes its arguments with a constant)
   auto group_of = [&](long long t, int &g) {
-    while (g + 1 < G.n && t >= G.tile0[g + 1]) g++;
+    if constexpr (NG > 1)
+      while (g + 1 < G.n && t >= G.tile0[g + 1]) g++;
   };
 
   if (threadIdx.x == 0) {
@@ -132,8 +134,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
     bool ok = true;
     for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
       group_of(t, g);
-      const Args &args = G.a[g];
-      const int lt = (int)(t - G.tile0[g]);
+      const Args args = G.a[NG == 1 ? 0 : g];  // a register copy: the stores below cannot alias it
+      const int lt = (int)(t - G.tile0[NG == 1 ? 0 : g]);
       const int n0 = (lt % args.tiles_n) * BN, m0 = ((lt / args.tiles_n) % args.tiles_m) * BM;
       const int b = lt / (args.tiles_n * args.tiles_m);
       const int zb = args.b_batch_planes ? args.qlist[args.b_base + b] * C::PP : 0;
@@ -152,15 +154,15 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
         uint8_t *st = smem + s * C::STAGE;
         tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
         for (int pp = 0; pp < C::PP; pp++) {
-          tc::tma_load_3d(st + pp * A_TILE, &G.A[g], &full[s], kc * bk_elems<TF>(), m0, b * C::PP + pp);
-          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &G.B[g], &full[s], kc * bk_elems<TF>(), n0,
+          tc::tma_load_3d(st + pp * A_TILE, &G.A[NG == 1 ? 0 : g], &full[s], kc * bk_elems<TF>(), m0, b * C::PP + pp);
+          tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &G.B[NG == 1 ? 0 : g], &full[s], kc * bk_elems<TF>(), n0,
                           zb + pp);
         }
       }
     }
     // every copy this CTA started lands before the CTA can exit
     for (int k = it - C::S < 0 ? 0 : it - C::S; k < it; k++)
-      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(G.a[g].err, 2);
+      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(G.a[NG == 1 ? 0 : g].err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t IPOS = tc::idesc<TF>(BM, BN, false);
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
     bool ok = true;
     for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
       group_of(t, g);
-      const Args &args = G.a[g];
+      const Args args = G.a[NG == 1 ? 0 : g];  // a register copy: the stores below cannot alias it
       if (*abort_flag) break;
       if (tcount > 0 && !tc::mbar_wait_bounded(tempty, (tcount - 1) & 1, 4 * WAIT_LIMIT)) {
         atomicOr(args.err, 2);
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
     int tcount = 0, g = 0;
     for (long long t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
       group_of(t, g);
-      const Args &args = G.a[g];
+      const Args args = G.a[NG == 1 ? 0 : g];  // a register copy: the stores below cannot alias it
       const bool ok = !*abort_flag && tc::mbar_wait_bounded(tfull, tcount & 1, 4 * WAIT_LIMIT);
       if (!ok) {
         atomicOr(args.err, 2);
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_zgemm(const __grid_constant__ Gro
         break;
       }
       tc::tc_fence_after();
-      const int lt = (int)(t - G.tile0[g]);
+      const int lt = (int)(t - G.tile0[NG == 1 ? 0 : g]);
       const int n0 = (lt % args.tiles_n) * BN, m0 = ((lt / args.tiles_n) % args.tiles_m) * BM;
       const int b = lt / (args.tiles_n * args.tiles_m);
       const int row = m0 + quarter * 32 + lane;

@@ -172,6 +172,16 @@ __host__ __device__ constexpr uint32_t idesc(int M, int N, bool negA) {
   return TF ? idesc_tf32(M, N, negA) : idesc_bf16(M, N, negA);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream finishes; this wait (first in the kernel, before
+// any global memory access) returns once the predecessor has completed and its writes are
+// visible.  For an ordinary launch there is nothing to wait for and it returns at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the stream (if launched programmatically) start being scheduled once
+// every block of this grid has executed it or exited; it still waits (griddep_wait) for this
+// grid to complete before touching memory.
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // x = hi + lo with hi and lo tf32 values (round to nearest, ties away from zero, through the
 // cvt.rna.tf32.f32 conversion); the residual x - hi is exact in FP32.
 __device__ __forceinline__ float tf32_rna(float x) {

@@ -1079,6 +1079,105 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
   }
 }
 
+// Matrix-free form of k_g2_32_t: the pair's block D = -(1/N_k) T M_cc^T is formed the same way
+// (the pair's rows staged by asynchronous copies, 2 x 2 register blocks) and applied as soon as
+// it is formed: its rows to x[k2] (fwd[p][qq][k1]) and, for a mirrored transfer, D^dagger to
+// x[k1] (bwd[p][qq][k2]), as k_g2mv_32 does with the generic blocking.
+template <int NV, int NC>
+__global__ void __launch_bounds__(256) k_g2mv_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                                   int naux, int n1, int n2, int n3, int q0,
+                                                   const int *__restrict__ qlist, int rows,
+                                                   const double2 *__restrict__ x, long long xs, int n_pol, int nqs,
+                                                   double2 *__restrict__ fwd, double2 *__restrict__ bwd) {
+  constexpr int R = NV * NV, C = NC * NC, TR = (R + 1) / 2, TCC = (C + 1) / 2, NVC = NV * NC;
+  extern __shared__ float2 sg2[];
+  float2 *sT = sg2, *sM = sg2 + R * naux, *sD = sM + C * naux;
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const bool mirror = !q_self_conjugate(q, n1, n2, n3);
+  static_assert(R % 2 == 0, "the pair's T rows are copied in 16-byte pieces");
+  const float2 *Tq = T + (long long)qq * rows * naux + (long long)k1 * R;
+  const float2 *Mk = Mc + ((long long)qq * nk + k1) * C * naux;
+  {
+    float4 *st4 = reinterpret_cast<float4 *>(sT);
+    for (int e = threadIdx.x; e < naux * (R / 2); e += blockDim.x) {
+      const int nu = e / (R / 2), h = e % (R / 2);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(st4 + e)),
+                   "l"(reinterpret_cast<const float4 *>(Tq + (long long)nu * rows) + h)
+                   : "memory");
+    }
+  }
+  if ((naux & 1) == 0) {
+    const float4 *m4 = reinterpret_cast<const float4 *>(Mk);
+    float4 *sm4 = reinterpret_cast<float4 *>(sM);
+    for (int e = threadIdx.x; e < C * naux / 2; e += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(sm4 + e)), "l"(m4 + e) : "memory");
+  } else {
+    for (int e = threadIdx.x; e < C * naux; e += blockDim.x) sM[e] = Mk[e];
+  }
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+  __syncthreads();
+  const float invf = 1.0f / nk;
+  for (int w = threadIdx.x; w < TR * TCC; w += blockDim.x) {
+    const int tr = w / TCC, tc = w % TCC;
+    const int r0 = 2 * tr, r1 = min(2 * tr + 1, R - 1), m0 = 2 * tc, m1 = min(2 * tc + 1, C - 1);
+    const float2 *pt0 = sT + r0, *pt1 = sT + r1, *pm0 = sM + m0 * naux, *pm1 = sM + m1 * naux;
+    float2 acc[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int b = 0; b < 2; b++) acc[a][b] = make_float2(0.f, 0.f);
+    for (int u = 0; u < naux; u++) {
+      const float2 tt[2] = {pt0[u * R], pt1[u * R]}, mm[2] = {pm0[u], pm1[u]};
+#pragma unroll
+      for (int a = 0; a < 2; a++)
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+          acc[a][b].x = fmaf(tt[a].x, mm[b].x, fmaf(-tt[a].y, mm[b].y, acc[a][b].x));
+          acc[a][b].y = fmaf(tt[a].x, mm[b].y, fmaf(tt[a].y, mm[b].x, acc[a][b].y));
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; a++)
+#pragma unroll
+      for (int b = 0; b < 2; b++) {
+        const int ij = 2 * tr + a, ab = 2 * tc + b;
+        if (ij >= R || ab >= C) continue;
+        const int i = ij / NV, j = ij % NV, ca = ab / NC, cb = ab % NC;
+        sD[(i * NC + ca) * NVC + j * NC + cb] = make_float2(-invf * acc[a][b].x, -invf * acc[a][b].y);
+      }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 2 * n_pol * NVC; e += blockDim.x) {
+    const int side = e / (n_pol * NVC), p = (e / NVC) % n_pol, r = e % NVC;
+    double sr = 0.0, si = 0.0;
+    if (side == 0) {  // row ia = r of D times x[k2]
+      const double2 *xv = x + p * xs + (long long)k2 * NVC;
+#pragma unroll 4
+      for (int jb = 0; jb < NVC; jb++) {
+        const float2 d = sD[r * NVC + jb];
+        const double2 v = xv[jb];
+        sr += (double)d.x * v.x - (double)d.y * v.y;
+        si += (double)d.x * v.y + (double)d.y * v.x;
+      }
+      fwd[(((long long)p * nqs + qq) * nk + k1) * NVC + r] = make_double2(sr, si);
+    } else {          // column jb = r of D, conjugated, times x[k1]
+      if (mirror) {
+        const double2 *xv = x + p * xs + (long long)k1 * NVC;
+#pragma unroll 4
+        for (int ia = 0; ia < NVC; ia++) {
+          const float2 d = sD[ia * NVC + r];
+          const double2 v = xv[ia];
+          sr += (double)d.x * v.x + (double)d.y * v.y;
+          si += (double)d.x * v.y - (double)d.y * v.x;
+        }
+      }
+      bwd[(((long long)p * nqs + qq) * nk + k2) * NVC + r] = make_double2(sr, si);
+    }
+  }
+}
+
 // Register-blocked conduction-valence projections for the coupling block (windows with Nv, Nc
 // in {2, 4, 6}): per mu the bands of k1 and k2 are loaded once and
 //   M1[b][i] = sum_s conj(c2_s,nv+b) y1_s,i + c1_s,i conj(y2_s,nv+b)   (C~_{b k2, i k1}),
@@ -1277,6 +1376,29 @@ bool launch_g2_fast(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
   return true;
 }
 
+// The register-blocked matrix-free second contraction for windows with Nv, Nc in {2, 4, 6};
+// false means the caller runs the generic k_g2mv_32.
+template <int NV, int NC>
+bool launch_g2mv_t(bse_ctx *c, SplitWS *w, int q0, int nq, const double2 *x, long long xs, int n_pol) {
+  constexpr int threads = ((NV * NV + 1) / 2) * ((NC * NC + 1) / 2);
+  const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
+  const size_t sm = sizeof(float2) * ((size_t)(NV * NV + NC * NC) * c->naux_tot + (size_t)(NV * NC) * (NV * NC));
+  if (sm > 200 * 1024) return false;
+  k_g2mv_32_t<NV, NC><<<dim3(c->nk, nq), bs, sm, c->stream>>>(w->T32, w->Mc32, c->naux_tot, c->mesh[0], c->mesh[1],
+                                                             c->mesh[2], q0, c->d_qplus, w->rows, x, xs, n_pol, w->nq,
+                                                             w->mf_fwd, w->mf_bwd);
+  return true;
+}
+
+bool fast_g2mv(bse_ctx *c, SplitWS *w, int q0, int nq, const double2 *x, long long xs, int n_pol) {
+#define BSE_FAST_MV(NV, NC) \
+  if (c->nv == NV && c->nc == NC) return launch_g2mv_t<NV, NC>(c, w, q0, nq, x, xs, n_pol);
+  BSE_FAST_MV(2, 2) BSE_FAST_MV(2, 4) BSE_FAST_MV(2, 6) BSE_FAST_MV(4, 2) BSE_FAST_MV(4, 4) BSE_FAST_MV(4, 6)
+  BSE_FAST_MV(6, 2) BSE_FAST_MV(6, 4) BSE_FAST_MV(6, 6)
+#undef BSE_FAST_MV
+  return false;
+}
+
 // Dispatch the register-blocked kernels for windows with Nv, Nc in {2, 4, 6}; false means
 // the caller falls back to the generic kernels.
 // mc_pad > 0: the projection writes M_cc in the fused kernel's layout.
@@ -1465,6 +1587,7 @@ void set_attr() {
 template <int NV, int NC>
 void set_g2_attr() {
   cudaFuncSetAttribute(k_g2_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_g2mv_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_g2c_32_t<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 template <int NP, int BN, bool TF = false>
@@ -2135,9 +2258,10 @@ bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_p
     }
     {
       const size_t sm = sizeof(float2) * ((size_t)(c->nv * c->nv + c->nc * c->nc) * G2CH + (size_t)c->nvc * c->nvc);
-      k_g2mv_32<<<dim3(c->nk, nq), 256, sm, st>>>(w->T32, w->Mc32, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
-                                                  c->mesh[2], q0, c->d_qplus, w->rows, x, xs, n_pol, w->nq, w->mf_fwd,
-                                                  w->mf_bwd);
+      if (!fast_g2mv(c, w, q0, nq, x, xs, n_pol))
+        k_g2mv_32<<<dim3(c->nk, nq), 256, sm, st>>>(w->T32, w->Mc32, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                                    c->mesh[2], q0, c->d_qplus, w->rows, x, xs, n_pol, w->nq, w->mf_fwd,
+                                                    w->mf_bwd);
       const long long n = (long long)n_pol * c->nk * c->nvc;
       k_mf_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w->mf_fwd, w->mf_bwd, nq, w->nq, c->nk, c->nvc, n_pol,
                                                                W);

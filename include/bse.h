@@ -317,10 +317,11 @@ bse_status bse_adjoint(bse_ctx *ctx, const double *Gamma, double *dW_R, double *
  * concurrent chains.  Per chain, schedule
  *  BSE_BATCH_WORKLIST: the chain's (system, q-slab) units are packed into steps (the next slab
  *    of each unfinished system in order, at most one per system, until the step's M_vv W(q)
- *    tiles fill two waves of the SMs); each step's tensor-core GEMMs of all its systems (the
- *    exchange GEMMs of systems starting there, then M_vv W(q) per N tile) run as one persistent
- *    launch over a work list of (system, q, tile), the projections and second contractions per
- *    system.  Every system must use the same split precision (BSE_EINVAL otherwise).
+ *    tiles fill two waves of the SMs); each stage of a step (the exchange GEMMs of systems
+ *    starting there, the pair projections, M_vv W(q), the second contraction or the fused
+ *    direct term) runs as one launch over the work list of its (system, q, tile) units, per
+ *    kernel instantiation (window, N tile, block size; the tensor-core ones persistent).
+ *    Every system must use the same split precision (BSE_EINVAL otherwise).
  *  BSE_BATCH_CHAINS: each system's own assembly in turn.
  * The first call for a given list of (context, H) and schedule runs the assemblies once
  * eagerly, then captures and instantiates the graph; later calls with the same list replay it.

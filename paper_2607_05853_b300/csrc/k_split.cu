@@ -18,6 +18,9 @@
 
 #include <algorithm>
 #include <array>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 #include <functional>
 #include <vector>
@@ -891,16 +894,16 @@ __global__ void __launch_bounds__(256) k_g2_32(const float2 *__restrict__ T, con
 // fused kernel's tensor map) elements; the stores of one (a, b) over a warp's mu coalesce.
 // grid: x = q - q0, y = k1; block: mu chunk (blockDim >= 32), loop over mu.
 template <int NV, int NC>
-__global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
-                                                  int nao_tot, int naux, int nao_max,
-                                                  const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
-                                                  const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
-                                                  const int *__restrict__ qlist, int rows, int kmem, PieceBuf Ap,
-                                                  float2 *__restrict__ Mc, int mc_pad) {
+__device__ __forceinline__ void proj_t_body(const float2 *__restrict__ Y, const double2 *__restrict__ ck, int nao_tot,
+                                            int naux, int nao_max, const int *__restrict__ aux_atom,
+                                            const int *__restrict__ ao_start, const int *__restrict__ naoA, int n1,
+                                            int n2, int n3, int q0, const int *__restrict__ qlist, int rows,
+                                            int kmem, PieceBuf Ap, float2 *__restrict__ Mc, int mc_pad, int qq,
+                                            int k1) {
   constexpr int NB = NV + NC;
   extern __shared__ float2 scf[];
   const int nk = n1 * n2 * n3;
-  const int qq = blockIdx.x, q = qlist[q0 + qq], k1 = blockIdx.y;
+  const int q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
   float2 *c1 = scf, *c2 = scf + nao_tot * NB;
   for (int e = threadIdx.x; e < nao_tot * NB; e += blockDim.x) {
@@ -977,21 +980,65 @@ __global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, 
   }
 }
 
+template <int NV, int NC>
+__global__ void __launch_bounds__(160) k_proj32_t(const float2 *__restrict__ Y, const double2 *__restrict__ ck,
+                                                  int nao_tot, int naux, int nao_max,
+                                                  const int *__restrict__ aux_atom, const int *__restrict__ ao_start,
+                                                  const int *__restrict__ naoA, int n1, int n2, int n3, int q0,
+                                                  const int *__restrict__ qlist, int rows, int kmem, PieceBuf Ap,
+                                                  float2 *__restrict__ Mc, int mc_pad) {
+  proj_t_body<NV, NC>(Y, ck, nao_tot, naux, nao_max, aux_atom, ao_start, naoA, n1, n2, n3, q0, qlist, rows, kmem, Ap,
+                      Mc, mc_pad, blockIdx.x, blockIdx.y);
+}
+
+// The projections of several systems' q-slabs in one launch (the batched assembly's work
+// list): group g owns blocks blk0[g] .. blk0[g + 1] - 1, block b of a group being the pair
+// block (qq = b % nq, k1 = b / nq) of that system's slab.
+constexpr int MAXPG = 16;
+struct ProjGroup {
+  const float2 *Y;
+  const double2 *ck;
+  int nao_tot, naux, nao_max;
+  const int *aux_atom, *ao_start, *naoA;
+  int n1, n2, n3, q0;
+  const int *qlist;
+  int rows, kmem;
+  PieceBuf Ap;
+  float2 *Mc;
+  int mc_pad, nq;
+};
+struct ProjGroups {
+  ProjGroup g[MAXPG];
+  long long blk0[MAXPG + 1];
+  int n;
+};
+
+template <int NV, int NC>
+__global__ void __launch_bounds__(160) k_proj32_t_grouped(const __grid_constant__ ProjGroups G) {
+  int g = 0;
+  const long long b = blockIdx.x;
+  while (g + 1 < G.n && b >= G.blk0[g + 1]) g++;
+  const ProjGroup a = G.g[g];
+  const long long lb = b - G.blk0[g];
+  proj_t_body<NV, NC>(a.Y, a.ck, a.nao_tot, a.naux, a.nao_max, a.aux_atom, a.ao_start, a.naoA, a.n1, a.n2, a.n3, a.q0,
+                      a.qlist, a.rows, a.kmem, a.Ap, a.Mc, a.mc_pad, (int)(lb % a.nq), (int)(lb / a.nq));
+}
+
 // Second contraction per pair: the pair's T rows (R consecutive elements per column nu of the
 // column-major T) and M_cc rows (C x N_aux, contiguous) are copied to shared memory in one
 // vectorised asynchronous sweep; thread
 // (r, c) then owns the 2x2 outputs rows (i,j) in {2r, 2r+1}, columns (a,b) in {2c, 2c+1}
 // of D = T M_cc^T.  H gets D's contribution at (k1, k2) and its conjugate at (k2, k1).
 template <int NV, int NC>
-__global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
-                                                 const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
-                                                 int q0, const int *__restrict__ qlist, int rows, long long dim,
-                                                 float2 *__restrict__ H, double2 *__restrict__ H64) {
+__device__ __forceinline__ void g2_t_body(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                          const double *__restrict__ eqp, int naux, int n1, int n2, int n3, int q0,
+                                          const int *__restrict__ qlist, int rows, long long dim,
+                                          float2 *__restrict__ H, double2 *__restrict__ H64, int k1, int qq) {
   constexpr int R = NV * NV, C = NC * NC, TR = (R + 1) / 2, TCC = (C + 1) / 2, NVC = NV * NC, NB = NV + NC;
   extern __shared__ float2 sg2[];
   float2 *sT = sg2, *sM = sg2 + R * naux;
   const int nk = n1 * n2 * n3;
-  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int q = qlist[q0 + qq];
   const int k2 = kdiff(k1, q, n1, n2, n3);
   const bool mirror = !q_self_conjugate(q, n1, n2, n3);
   static_assert(R % 2 == 0, "the pair's T rows are copied in 16-byte pieces");
@@ -1077,6 +1124,45 @@ __global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, c
         }
       }
   }
+}
+
+template <int NV, int NC>
+__global__ void __launch_bounds__(256) k_g2_32_t(const float2 *__restrict__ T, const float2 *__restrict__ Mc,
+                                                 const double *__restrict__ eqp, int naux, int n1, int n2, int n3,
+                                                 int q0, const int *__restrict__ qlist, int rows, long long dim,
+                                                 float2 *__restrict__ H, double2 *__restrict__ H64) {
+  g2_t_body<NV, NC>(T, Mc, eqp, naux, n1, n2, n3, q0, qlist, rows, dim, H, H64, blockIdx.x, blockIdx.y);
+}
+
+// The second contractions of several systems' q-slabs in one launch (the batched assembly's
+// work list): group g owns blocks blk0[g] .. blk0[g + 1] - 1, block b being the pair block
+// (k1 = b % nk, qq = b / nk) of that system's slab.
+struct G2Group {
+  const float2 *T, *Mc;
+  const double *eqp;
+  int naux, n1, n2, n3, q0;
+  const int *qlist;
+  int rows;
+  long long dim;
+  float2 *H;
+  double2 *H64;
+};
+struct G2Groups {
+  G2Group g[MAXPG];
+  long long blk0[MAXPG + 1];
+  int n;
+};
+
+template <int NV, int NC>
+__global__ void __launch_bounds__(256) k_g2_32_t_grouped(const __grid_constant__ G2Groups G) {
+  int g = 0;
+  const long long b = blockIdx.x;
+  while (g + 1 < G.n && b >= G.blk0[g + 1]) g++;
+  const G2Group a = G.g[g];
+  const int nk = a.n1 * a.n2 * a.n3;
+  const long long lb = b - G.blk0[g];
+  g2_t_body<NV, NC>(a.T, a.Mc, a.eqp, a.naux, a.n1, a.n2, a.n3, a.q0, a.qlist, a.rows, a.dim, a.H, a.H64,
+                    (int)(lb % nk), (int)(lb / nk));
 }
 
 // Matrix-free form of k_g2_32_t: the pair's block D = -(1/N_k) T M_cc^T is formed the same way
@@ -1543,8 +1629,16 @@ bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof
   using Cf = tcd::DCfg<NP, BN>;
   const long long total = (long long)a.tiles_m * a.tiles_b;
   const int ctas = (int)std::min<long long>(total, c->n_sm);
+  tcd::DGroups<1> G;
+  G.A[0] = w->tmA_g1;
+  G.B[0] = w->tmB_d;
+  G.M[0] = w->tmM_d;
+  G.a[0] = a;
+  G.tile0[0] = 0;
+  G.tile0[1] = total;
+  G.n = 1;
   bse_prof_begin(c, prof_id);
-  tcd::k_tc_direct<NP, BN, NC, TF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(w->tmA_g1, w->tmB_d, w->tmM_d, a);
+  tcd::k_tc_direct<NP, BN, NC, TF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(G);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_direct");
@@ -1827,8 +1921,8 @@ bse_status slab_project(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
 }
 
 // Fused path: T = M_vv W(q) and H += -T M_cc^T / N_k for the slab in one kernel.
-bse_status slab_direct(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
-  tcd::DArgs a{};
+void direct_args(const bse_ctx *c, const SplitWS *w, int q0, int nq, float2 *H, tcd::DArgs &a) {
+  a = tcd::DArgs{};
   a.nv = c->nv;
   a.pairs = w->pairs_d;
   a.rows = w->rows;
@@ -1850,6 +1944,11 @@ bse_status slab_direct(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
   a.H = c->h64 ? nullptr : H;
   a.H64 = c->h64 ? reinterpret_cast<double2 *>(H) : nullptr;
   a.err = c->d_err;
+}
+
+bse_status slab_direct(bse_ctx *c, SplitWS *w, int q0, int nq, float2 *H) {
+  tcd::DArgs a;
+  direct_args(c, w, q0, nq, H, a);
   return launch_direct(c, w, a, BSE_KP_G1);
 }
 
@@ -1993,11 +2092,207 @@ void set_grouped_attr() {
   cudaFuncSetAttribute(tcg::k_tc_zgemm<NP, 160, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        tcg::Cfg<NP, 160>::SMEM);
 }
+template <int NP, bool TF>
+void set_grouped_direct_attr() {
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 64, 2, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 64>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 64, 4, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 64>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 64, 6, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 64>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 160, 2, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 160>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 160, 4, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 160>::SMEM);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, 160, 6, TF, MAXG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       tcd::DCfg<NP, 160>::SMEM);
+}
+template <int NV, int NC>
+void set_grouped_g2_attr() {
+  cudaFuncSetAttribute(k_g2_32_t_grouped<NV, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
 void set_grouped_attrs_now() {
   set_grouped_attr<1, false>();
   set_grouped_attr<2, false>();
   set_grouped_attr<3, false>();
   set_grouped_attr<2, true>();
+  set_grouped_direct_attr<1, false>();
+  set_grouped_direct_attr<2, false>();
+  set_grouped_direct_attr<3, false>();
+  set_grouped_direct_attr<2, true>();
+  set_grouped_g2_attr<2, 2>(); set_grouped_g2_attr<2, 4>(); set_grouped_g2_attr<2, 6>();
+  set_grouped_g2_attr<4, 2>(); set_grouped_g2_attr<4, 4>(); set_grouped_g2_attr<4, 6>();
+  set_grouped_g2_attr<6, 2>(); set_grouped_g2_attr<6, 4>(); set_grouped_g2_attr<6, 6>();
+}
+
+// A (system, q-slab) unit of a batch step.
+struct BUnit {
+  bse_ctx *c;
+  float2 *H;
+  int q0, nq;
+};
+
+bool window_blocked(const bse_ctx *c) {
+  return (c->nv == 2 || c->nv == 4 || c->nv == 6) && (c->nc == 2 || c->nc == 4 || c->nc == 6);
+}
+
+// Register-blocked projections of units with one window and block size, MAXPG per launch.
+template <int NV, int NC>
+bse_status launch_proj_grouped_t(bse_ctx *c0, const std::vector<BUnit> &us, int bs) {
+  for (size_t i0 = 0; i0 < us.size(); i0 += MAXPG) {
+    const int n = (int)std::min<size_t>(MAXPG, us.size() - i0);
+    ProjGroups G;
+    long long b0 = 0;
+    size_t sm = 0;
+    for (int g = 0; g < n; g++) {
+      const BUnit &u = us[i0 + g];
+      bse_ctx *c = u.c;
+      SplitWS *w = ws(c);
+      ProjGroup &a = G.g[g];
+      a.Y = y_tab(w);
+      a.ck = ck_tab(c, w);
+      a.nao_tot = c->nao_tot;
+      a.naux = c->naux_tot;
+      a.nao_max = c->nao_max;
+      a.aux_atom = c->d_aux_atom;
+      a.ao_start = c->d_ao_start;
+      a.naoA = c->d_nao;
+      a.n1 = c->mesh[0];
+      a.n2 = c->mesh[1];
+      a.n3 = c->mesh[2];
+      a.q0 = u.q0;
+      a.qlist = c->d_qplus;
+      a.rows = w->rows;
+      a.kmem = w->kmem;
+      a.Ap = pieces(w, w->Ap);
+      a.Mc = w->Mc32;
+      a.mc_pad = w->fused ? w->naux_pad : 0;
+      a.nq = u.nq;
+      G.blk0[g] = b0;
+      b0 += (long long)u.nq * c->nk;
+      sm = std::max(sm, sizeof(float2) * 2 * c->nao_tot * (NV + NC));
+    }
+    for (int g = n; g <= MAXPG; g++) G.blk0[g] = b0;
+    G.n = n;
+    if (b0 > 0x7fffffffLL) return bse_fail(c0, BSE_EINVAL, "batch: projection grid too large");
+    bse_prof_begin(c0, BSE_KP_PROJECT);
+    k_proj32_t_grouped<NV, NC><<<(unsigned)b0, bs, sm, c0->stream>>>(G);
+    bse_prof_end(c0, BSE_KP_PROJECT);
+    bse_count_launch();
+    const bse_status s = bse_check_launch(c0, "proj32 (grouped)");
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+// Register-blocked second contractions of unfused units with one window, MAXPG per launch.
+template <int NV, int NC>
+bse_status launch_g2_grouped_t(bse_ctx *c0, const std::vector<BUnit> &us) {
+  constexpr int threads = ((NV * NV + 1) / 2) * ((NC * NC + 1) / 2);
+  const int bs = std::max(128, std::min(256, (threads + 31) / 32 * 32));
+  for (size_t i0 = 0; i0 < us.size(); i0 += MAXPG) {
+    const int n = (int)std::min<size_t>(MAXPG, us.size() - i0);
+    G2Groups G;
+    long long b0 = 0;
+    size_t sm = 0;
+    for (int g = 0; g < n; g++) {
+      const BUnit &u = us[i0 + g];
+      bse_ctx *c = u.c;
+      SplitWS *w = ws(c);
+      G2Group &a = G.g[g];
+      a.T = w->T32;
+      a.Mc = w->Mc32;
+      a.eqp = e_tab(c, w);
+      a.naux = c->naux_tot;
+      a.n1 = c->mesh[0];
+      a.n2 = c->mesh[1];
+      a.n3 = c->mesh[2];
+      a.q0 = u.q0;
+      a.qlist = c->d_qplus;
+      a.rows = w->rows;
+      a.dim = c->dim;
+      a.H = c->h64 ? nullptr : u.H;
+      a.H64 = c->h64 ? reinterpret_cast<double2 *>(u.H) : nullptr;
+      G.blk0[g] = b0;
+      b0 += (long long)u.nq * c->nk;
+      sm = std::max(sm, sizeof(float2) * (size_t)(NV * NV + NC * NC) * c->naux_tot);
+    }
+    for (int g = n; g <= MAXPG; g++) G.blk0[g] = b0;
+    G.n = n;
+    if (b0 > 0x7fffffffLL) return bse_fail(c0, BSE_EINVAL, "batch: second-contraction grid too large");
+    bse_prof_begin(c0, BSE_KP_G2);
+    k_g2_32_t_grouped<NV, NC><<<(unsigned)b0, bs, sm, c0->stream>>>(G);
+    bse_prof_end(c0, BSE_KP_G2);
+    bse_count_launch();
+    const bse_status s = bse_check_launch(c0, "g2_32 (grouped)");
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+// Fused direct term of fused units with one N tile and conduction window, MAXG per launch.
+template <int NP, int BN, int NC, bool TF>
+bse_status launch_direct_grouped_t(bse_ctx *c0, const std::vector<BUnit> &us) {
+  using Cf = tcd::DCfg<NP, BN>;
+  for (size_t i0 = 0; i0 < us.size(); i0 += MAXG) {
+    const int n = (int)std::min<size_t>(MAXG, us.size() - i0);
+    tcd::DGroups<MAXG> G;
+    long long t0 = 0;
+    for (int g = 0; g < n; g++) {
+      const BUnit &u = us[i0 + g];
+      SplitWS *w = ws(u.c);
+      G.A[g] = w->tmA_g1;
+      G.B[g] = w->tmB_d;
+      G.M[g] = w->tmM_d;
+      direct_args(u.c, w, u.q0, u.nq, u.H, G.a[g]);
+      G.tile0[g] = t0;
+      t0 += (long long)G.a[g].tiles_m * G.a[g].tiles_b;
+    }
+    for (int g = n; g <= MAXG; g++) G.tile0[g] = t0;
+    G.n = n;
+    if (t0 == 0) continue;
+    const int ctas = (int)std::min<long long>(t0, c0->n_sm);
+    bse_prof_begin(c0, BSE_KP_G1);
+    tcd::k_tc_direct<NP, BN, NC, TF, MAXG><<<ctas, tcd::THREADS, Cf::SMEM, c0->stream>>>(G);
+    bse_prof_end(c0, BSE_KP_G1);
+    bse_count_launch();
+    const bse_status s = bse_check_launch(c0, "tc_direct (grouped)");
+    if (s != BSE_OK) return s;
+  }
+  return BSE_OK;
+}
+
+template <int NP, bool TF>
+bse_status launch_direct_grouped_nc(bse_ctx *c0, int bn, int nc, const std::vector<BUnit> &us) {
+#define BSE_DG(BN_, NC_) \
+  if (bn == BN_ && nc == NC_) return launch_direct_grouped_t<NP, BN_, NC_, TF>(c0, us);
+  BSE_DG(64, 2) BSE_DG(64, 4) BSE_DG(64, 6) BSE_DG(160, 2) BSE_DG(160, 4) BSE_DG(160, 6)
+#undef BSE_DG
+  return bse_fail(c0, BSE_EINVAL, "batch: no fused kernel for this tile");
+}
+
+bse_status launch_direct_grouped(bse_ctx *c0, const SplitWS *w0, int bn, int nc, const std::vector<BUnit> &us) {
+  if (us.empty()) return BSE_OK;
+  if (w0->tf32) return launch_direct_grouped_nc<2, true>(c0, bn, nc, us);
+  if (w0->np == 3) return launch_direct_grouped_nc<3, false>(c0, bn, nc, us);
+  if (w0->np == 2) return launch_direct_grouped_nc<2, false>(c0, bn, nc, us);
+  return launch_direct_grouped_nc<1, false>(c0, bn, nc, us);
+}
+
+bse_status launch_proj_grouped(bse_ctx *c0, int nv, int nc, int bs, const std::vector<BUnit> &us) {
+#define BSE_PG(NV_, NC_) \
+  if (nv == NV_ && nc == NC_) return launch_proj_grouped_t<NV_, NC_>(c0, us, bs);
+  BSE_PG(2, 2) BSE_PG(2, 4) BSE_PG(2, 6) BSE_PG(4, 2) BSE_PG(4, 4) BSE_PG(4, 6) BSE_PG(6, 2) BSE_PG(6, 4) BSE_PG(6, 6)
+#undef BSE_PG
+  return bse_fail(c0, BSE_EINVAL, "batch: no register-blocked projection for this window");
+}
+
+bse_status launch_g2_grouped(bse_ctx *c0, int nv, int nc, const std::vector<BUnit> &us) {
+#define BSE_GG(NV_, NC_) \
+  if (nv == NV_ && nc == NC_) return launch_g2_grouped_t<NV_, NC_>(c0, us);
+  BSE_GG(2, 2) BSE_GG(2, 4) BSE_GG(2, 6) BSE_GG(4, 2) BSE_GG(4, 4) BSE_GG(4, 6) BSE_GG(6, 2) BSE_GG(6, 4) BSE_GG(6, 6)
+#undef BSE_GG
+  return bse_fail(c0, BSE_EINVAL, "batch: no register-blocked second contraction for this window");
 }
 
 }  // namespace
@@ -2006,10 +2301,11 @@ void set_grouped_attrs_now() {
 // (smallest first).  Their (system, q-slab) units are dealt into steps: a step takes the next
 // slab of each unfinished system in order, at most one per system (each system has one slab
 // buffer), until its M_vv W(q) tiles fill two waves of the SMs; a system's exchange GEMM joins
-// the step of its first slab.  Per step: one grouped exchange launch, the systems'
-// projections, one grouped M_vv W(q) launch per N tile (unfused systems), then each system's
-// second contraction or fused direct kernel.  Every launch goes to the first system's
-// stream; stamp(i) is called once system i's work is enqueued.
+// the step of its first slab.  Per step, every stage is one launch over the work list of its
+// units (per kernel instantiation: window, N tile, block size): the exchange GEMMs, the
+// projections, M_vv W(q) of unfused systems, then the second contractions of unfused systems
+// and the fused direct term of fused ones.  Every launch goes to the first system's stream;
+// stamp(i) is called once system i's work is enqueued.
 bse_status split_batch_worklist(bse_ctx **ctxs, void **Hv, const int *order, int n,
                                 const std::function<void(int)> &stamp) {
   bse_ctx *c0 = ctxs[order[0]];
@@ -2062,10 +2358,25 @@ bse_status split_batch_worklist(bse_ctx **ctxs, void **Hv, const int *order, int
       const bse_status s = launch_grouped(c0, w0, TC_BN, ex, BSE_KP_EXCH);
       if (s != BSE_OK) return s;
     }
-    for (const Unit &u : step) {
-      const int i = order[u.r];
-      const bse_status s = slab_project(ctxs[i], ws(ctxs[i]), u.q0, u.nq, (float2 *)Hv[i]);
-      if (s != BSE_OK) return s;
+    {  // projections: register-blocked windows grouped by (Nv, Nc, block size), others one by one
+      std::map<std::tuple<int, int, int>, std::vector<BUnit>> pg;
+      for (const Unit &u : step) {
+        const int i = order[u.r];
+        bse_ctx *c = ctxs[i];
+        SplitWS *w = ws(c);
+        if (window_blocked(c)) {
+          const int bs = w->proj_bs ? w->proj_bs : std::min(160, (c->naux_tot + 31) / 32 * 32);
+          pg[std::make_tuple(c->nv, c->nc, bs)].push_back({c, (float2 *)Hv[i], u.q0, u.nq});
+        } else {
+          const bse_status s = slab_project(c, w, u.q0, u.nq, (float2 *)Hv[i]);
+          if (s != BSE_OK) return s;
+        }
+      }
+      for (const auto &kv : pg) {
+        const bse_status s =
+            launch_proj_grouped(c0, std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), kv.second);
+        if (s != BSE_OK) return s;
+      }
     }
     for (int bn : TC_BN_CAND) {
       std::vector<GemmItem> g1;
@@ -2082,17 +2393,38 @@ bse_status split_batch_worklist(bse_ctx **ctxs, void **Hv, const int *order, int
       const bse_status s = launch_grouped(c0, w0, bn, g1, BSE_KP_G1);
       if (s != BSE_OK) return s;
     }
-    for (const Unit &u : step) {
-      const int i = order[u.r];
-      SplitWS *w = ws(ctxs[i]);
-      const bse_status s = w->fused ? slab_direct(ctxs[i], w, u.q0, u.nq, (float2 *)Hv[i])
-                                    : slab_g2(ctxs[i], w, u.q0, u.nq, (float2 *)Hv[i]);
-      if (s != BSE_OK) return s;
-      if (++next[u.r] == nslab[u.r]) {
-        left--;
-        stamp(i);
+    {  // the fused direct term grouped by (N tile, Nc); the unfused second contraction grouped
+       // by window where the pair's rows fit shared memory, else one by one
+      std::map<std::pair<int, int>, std::vector<BUnit>> dg, gg;
+      for (const Unit &u : step) {
+        const int i = order[u.r];
+        bse_ctx *c = ctxs[i];
+        SplitWS *w = ws(c);
+        const BUnit bu{c, (float2 *)Hv[i], u.q0, u.nq};
+        if (w->fused) {
+          dg[std::make_pair(w->bn_d, c->nc)].push_back(bu);
+        } else if (window_blocked(c) &&
+                   sizeof(float2) * (size_t)(c->nv * c->nv + c->nc * c->nc) * c->naux_tot <= 200 * 1024) {
+          gg[std::make_pair(c->nv, c->nc)].push_back(bu);
+        } else {
+          const bse_status s = slab_g2(c, w, u.q0, u.nq, (float2 *)Hv[i]);
+          if (s != BSE_OK) return s;
+        }
+      }
+      for (const auto &kv : dg) {
+        const bse_status s = launch_direct_grouped(c0, w0, kv.first.first, kv.first.second, kv.second);
+        if (s != BSE_OK) return s;
+      }
+      for (const auto &kv : gg) {
+        const bse_status s = launch_g2_grouped(c0, kv.first.first, kv.first.second, kv.second);
+        if (s != BSE_OK) return s;
       }
     }
+    for (const Unit &u : step)
+      if (++next[u.r] == nslab[u.r]) {
+        left--;
+        stamp(order[u.r]);
+      }
   }
   return BSE_OK;
 }
@@ -2284,9 +2616,6 @@ bse_status split_matfree_hmax(bse_ctx *c, double *hmax) {
 // Picks the N tile of the T = M_vv W(q) tensor-core GEMM by timing one q-slab launch per
 // candidate (values do not change the timing, so no inputs are needed), keeps the fastest,
 // and re-encodes the B-operand tensor map.  Results are cached per shape in the process.
-#include <map>
-#include <mutex>
-#include <tuple>
 namespace {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tune_cache;

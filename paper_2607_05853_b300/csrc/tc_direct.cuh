@@ -83,10 +83,19 @@ __device__ __forceinline__ bool d_self_conj(int q, int n1, int n2, int n3) {
   return (n1 - a1) % n1 == a1 && (n2 - a2) % n2 == a2 && (n3 - a3) % n3 == a3;
 }
 
-template <int NP, int BN, int NC, bool TF = false>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_tc_direct(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const __grid_constant__ CUtensorMap tmM, DArgs args) {
+// The work list of one launch: NG systems' q-slabs (operand, W and M_cc tensor maps and
+// arguments each), their tiles numbered consecutively, group g owning tiles tile0[g] ..
+// tile0[g + 1] - 1 (n groups in use); a single slab is the list with NG = 1.
+template <int NG>
+struct DGroups {
+  CUtensorMap A[NG], B[NG], M[NG];
+  DArgs a[NG];
+  long long tile0[NG + 1];
+  int n;
+};
+
+template <int NP, int BN, int NC, bool TF = false, int NG = 1>
+__global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant__ DGroups<NG> G) {
   using C = DCfg<NP, BN>;
   constexpr int NCC = NC * NC, HALF = NCC / 2;  // D columns (a, b) per epilogue warp
 
@@ -100,9 +109,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int total = args.tiles_m * args.tiles_b;
-  const int items = args.k_chunks + args.n_mitems;  // ring items per tile
-  const int rpp = args.nv * args.nv;                // rows per pair
+  const long long total = G.tile0[G.n];
+  // group of work-list tile t (a CTA's tiles only grow; a single slab indexes with a constant)
+  auto group_of = [&](long long t, int &g) {
+    if constexpr (NG > 1)
+      while (g + 1 < G.n && t >= G.tile0[g + 1]) g++;
+  };
+#define GI (NG == 1 ? 0 : g)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::S; s++) {
@@ -114,11 +127,12 @@ __global__ void __launch_bounds__(THREADS, 1)
     *abort_flag = 0;
     tc::fence_barrier_init();
   }
-  if (warp == 0 && lane == 0) {
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
-    tc::prefetch_tmap(&tmM);
-  }
+  if (warp == 0 && lane == 0)
+    for (int g = 0; g < G.n; g++) {
+      tc::prefetch_tmap(&G.A[g]);
+      tc::prefetch_tmap(&G.B[g]);
+      tc::prefetch_tmap(&G.M[g]);
+    }
   if (warp == 1) {
     tc::tmem_alloc(tmem_slot, C::TMEM_COLS);
     tc::tmem_relinquish();
@@ -131,10 +145,15 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer: operand K chunks, then the tile's M_cc slices ----------------
-    int it = 0;
+    int it = 0, g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const int m = t % args.tiles_m, b = t / args.tiles_m;
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      group_of(t, g);
+      const DArgs args = G.a[GI];  // a register copy: the stores below cannot alias it
+      const int items = args.k_chunks + args.n_mitems;  // ring items per tile
+      const int rpp = args.nv * args.nv;                // rows per pair
+      const int lt = (int)(t - G.tile0[GI]);
+      const int m = lt % args.tiles_m, b = lt / args.tiles_m;
       const int m0 = m * args.pairs * rpp;
       const int q = args.qlist[args.b_base + b];
       const int k1_0 = m0 / rpp;
@@ -155,28 +174,31 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int kc = item;
           tc::mbar_arrive_expect_tx(&full[s], C::STAGE);
           for (int pp = 0; pp < C::PP; pp++) {
-            tc::tma_load_3d(st + pp * A_TILE, &tmA, &full[s], kc * tcg::bk_elems<TF>(), m0, b * C::PP + pp);
-            tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &tmB, &full[s], kc * tcg::bk_elems<TF>(), 0, q * C::PP + pp);
+            tc::tma_load_3d(st + pp * A_TILE, &G.A[GI], &full[s], kc * tcg::bk_elems<TF>(), m0, b * C::PP + pp);
+            tc::tma_load_3d(st + C::PP * A_TILE + pp * C::B_TILE, &G.B[GI], &full[s], kc * tcg::bk_elems<TF>(), 0,
+                            q * C::PP + pp);
           }
         } else {
           // columns nu0 .. nu0 + nui - 1 of M_cc for the tile's pairs, one TMA box
           // {nui, Nc^2, pairs}: smem [pair][ab][nu] (columns or pairs past the tensor zero-filled)
           const int nu0 = (item - args.k_chunks) * args.nui;
           tc::mbar_arrive_expect_tx(&full[s], (uint32_t)args.pairs * NCC * args.nui * 8);
-          tc::tma_load_3d(st, &tmM, &full[s], nu0, 0, b * (args.rows / rpp) + k1_0);
+          tc::tma_load_3d(st, &G.M[GI], &full[s], nu0, 0, b * (args.rows / rpp) + k1_0);
         }
       }
     }
     // every copy this CTA started lands before the CTA can exit
     for (int k = it - C::S < 0 ? 0 : it - C::S; k < it; k++)
-      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(args.err, 2);
+      if (!tc::mbar_wait_bounded(&full[k % C::S], (k / C::S) & 1, WAIT_LIMIT)) atomicOr(G.a[GI].err, 2);
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     constexpr uint32_t IPOS = tc::idesc<TF>(BM, BN, false);
     constexpr uint32_t INEG = tc::idesc<TF>(BM, BN, true);
-    int it = 0, tcount = 0;
+    int it = 0, tcount = 0, g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
+    for (long long t = blockIdx.x; t < total && ok; t += gridDim.x, tcount++) {
+      group_of(t, g);
+      const DArgs args = G.a[GI];
       if (*abort_flag) break;
       if (tcount > 0 && !tc::mbar_wait_bounded(tempty, (tcount - 1) & 1, 4 * WAIT_LIMIT)) {
         atomicOr(args.err, 2);
@@ -229,13 +251,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ---------------- epilogue: D = T M_cc^T from tensor memory and the staged M_cc ----------
     const int quarter = warp % 4, half = (warp - 2) / 4;   // lane quarter; which half of D's columns
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const double inv = 1.0 / ((double)args.n1 * args.n2 * args.n3);
-    const float invf = (float)inv;
-    const int nb = args.nv + NC;
-    int tcount = 0, it = 0;
+    int tcount = 0, it = 0, g = 0;
     // Control flow is the same in every epilogue thread whatever the waits return (each tile's
     // items each end in the warps' named barrier); after an abort the waits are skipped.
-    for (int t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
+    for (long long t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
+      group_of(t, g);
+      const DArgs args = G.a[GI];  // a register copy: the H stores below cannot alias it
+      const double inv = 1.0 / ((double)args.n1 * args.n2 * args.n3);
+      const float invf = (float)inv;
+      const int nb = args.nv + NC;
+      const int rpp = args.nv * args.nv;
       it += args.k_chunks;
       bool ok = !*abort_flag && tc::mbar_wait_bounded(tfull, tcount & 1, 4 * WAIT_LIMIT);
       if (!ok) {
@@ -243,7 +268,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         *abort_flag = 1;
       }
       tc::tc_fence_after();
-      const int m = t % args.tiles_m, b = t / args.tiles_m;
+      const int lt = (int)(t - G.tile0[GI]);
+      const int m = lt % args.tiles_m, b = lt / args.tiles_m;
       const int m0 = m * args.pairs * rpp;
       const int lrow = quarter * 32 + lane;                 // row of the tile (tensor-memory lane)
       const int row = m0 + lrow;                            // (k1, i, j) within this q
@@ -354,6 +380,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, C::TMEM_COLS);
   }
+#undef GI
 }
 
 }  // namespace tcd

@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 METRIC = "H_BSE elements/s (split-prec TC vs FP64 GPU) at ≤1 meV lowest-exciton error"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 128x128 tile of the current
 # Hermitian matvec kernel, from one ncu capture of the 16000-dim case (7875 tiles):
-# 1.032880 GB read (the tiles themselves) + 45.80 MB written (the partial slots).
-MV_DRAM_BYTES_PER_TILE = (1.032880e9 + 45.800704e6) / 7875
+# 1.032827 GB read (the tiles themselves) + 45.72 MB written (the partial slots).
+MV_DRAM_BYTES_PER_TILE = (1.032827e9 + 45.723136e6) / 7875
 # DRAM bytes per transfer q of the split assembly's two slab kernels, from ncu captures of one
 # 20-q slab of the 16000-dim case (10^3 k-points, N_aux 150, Nv = Nc = 4): the projections
 # (313.4 MB read, 922.3 MB written: the M_vv bf16 pieces and M_cc) and the fused direct term

@@ -43,7 +43,6 @@ struct bse_ctx {
   int device = 0;
   int n_sm = 148;
   int stage = 0;  // 0 setup, 1 interp_W done, 2 project_pairs done
-  bool y64_valid = true;  // c->Y holds the pair table (split precisions keep it in FP32)
   std::string err;
 
   // small device tables
@@ -157,6 +156,9 @@ bse_status run_spectrum_static(bse_ctx *c, const void *H, const double2 *u, int 
 bse_status split_setup(bse_ctx *c);
 bse_status split_interp_W(bse_ctx *c, const double *W_R, double2 *Wq_out);
 bse_status split_assemble(bse_ctx *c, void *H);
+// dL/dW(q) of every transfer into c->Aq from the split contexts' FP32 pair table (the
+// adjoint's slab loop; the Fourier adjoint and the diagonal follow in k_adjoint.cu).
+bse_status split_adjoint_slabs(bse_ctx *c, const double2 *Gamma);
 // Batched assembly of the n split-precision systems ctxs[order[0..n-1]] (smallest first) as a
 // work list of grouped launches on their (common) stream; stamp(i) runs when system i's last
 // launch is enqueued.
@@ -170,7 +172,6 @@ bse_status split_matfree_hmax(bse_ctx *c, double *hmax);
 bse_status run_spectrum_matfree(bse_ctx *c, const double2 *u, int n_pol, int n_steps, const double *omega, int n_w,
                                 double eta, double pref, double *eps2, double *ab);
 bse_status split_project(bse_ctx *c, const double *C_R);
-bse_status split_y_to_fp64(bse_ctx *c);
 bse_status split_autotune(bse_ctx *c, int *chosen, int *chosen_proj);
 void split_free(bse_ctx *c);
 

@@ -4,7 +4,10 @@
 // (the direct term of Eq. W_LRI is the only place W enters), then the adjoint of
 // W(q) = sum_R w_R W(R) e^{-i q.R} gives dL/dW_mu,nu(R) = w_R Re sum_q e^{-i q.R} dL/dW(q)_mu,nu,
 // and the E_c - E_v diagonal (Eq. Hamiltonian) gives dL/dE^QP.  The pair projections are
-// recomputed one q-slab at a time, never stored for all pairs; everything is FP64.
+// recomputed one q-slab at a time, never stored for all pairs; everything is FP64 for an FP64
+// context.  A split-precision context runs the slab loop from its FP32 pair table with FP32
+// sums (k_split.cu:split_adjoint_slabs; its error is the split forward's own) and the same
+// FP64 Fourier adjoint and diagonal.
 #include <algorithm>
 
 #include "bse_internal.cuh"
@@ -201,7 +204,7 @@ bse_status adjoint_workspace(bse_ctx *c) {
       return bse_fail(c, BSE_ENOMEM, "adjoint: workspace allocation failed");
     }
   }
-  if (!c->Mv) {
+  if (!c->Mv && c->precision == BSE_FP64) {  // the split precisions use their own slab buffers
     const size_t per_q = (size_t)c->nk * (2 * c->nv * c->nv + c->nc * c->nc) * c->naux_tot * sizeof(double2);
     const size_t budget = (size_t)768 << 20;
     c->slab = (int)std::max<size_t>(1, std::min<size_t>((size_t)c->nk, budget / std::max<size_t>(per_q, 1)));
@@ -221,13 +224,13 @@ bse_status adjoint_workspace(bse_ctx *c) {
 bse_status run_adjoint(bse_ctx *c, const double2 *Gamma, double *dW_R, double *de_qp) {
   bse_status s = adjoint_workspace(c);
   if (s != BSE_OK) return s;
-  if (!c->y64_valid) {  // split-precision context: widen its FP32 pair table once
-    s = split_y_to_fp64(c);
-    if (s != BSE_OK) return s;
-  }
   const int na = c->naux_tot;
   const long long rows = (long long)c->nk * c->nv * c->nv;
-  for (int q0 = 0; q0 < c->nk; q0 += c->slab) {
+  if (c->precision != BSE_FP64) {  // the split precisions: FP32 slabs from their pair table
+    s = split_adjoint_slabs(c, Gamma);
+    if (s != BSE_OK) return s;
+  }
+  for (int q0 = 0; c->precision == BSE_FP64 && q0 < c->nk; q0 += c->slab) {
     const int nq = std::min(c->slab, c->nk - q0);
     s = launch_project_slab_fp64(c, q0, nq, c->d_qall);
     if (s != BSE_OK) return s;

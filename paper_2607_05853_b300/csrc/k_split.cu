@@ -83,6 +83,8 @@ struct SplitWS {
   double2 *mf_fwd = nullptr, *mf_bwd = nullptr;  // [3][nq][nk][nvc]
   double2 *mf_zp = nullptr;                      // [3][nchunk][naux] partial X^dagger x
   double2 *mf_z2 = nullptr;                      // [3][naux]         V X^dagger x
+  // adjoint (allocated on first use): M_vv of a slab of transfers in plain FP32, two planes
+  float *adjMv = nullptr;                        // [nq][2][rows][kmem]
   int mf_nch = 0;
 };
 
@@ -106,16 +108,21 @@ __device__ __forceinline__ void split_pieces(R x, int np, __nv_bfloat16 *p) {
 }
 
 // A tensor-core operand as planes of pieces, [piece * 2 + (re, im)][...]: bf16 pieces (np of
-// them, split_pieces) or, with tf32 set, two tf32 pieces in FP32 words (x ~ tf32(x) +
-// tf32(x - tf32(x)), the residual exact in the source precision).  Offsets and plane pitches
-// count elements of the piece type.
+// them, split_pieces) or, with tf32 = 1, two tf32 pieces in FP32 words (x ~ tf32(x) +
+// tf32(x - tf32(x)), the residual exact in the source precision); tf32 = 2 (with np = 1): the
+// plain FP32 value in two planes (re, im), for the adjoint's CUDA-core GEMM.  Offsets and plane
+// pitches count elements of the piece type.
 struct PieceBuf {
   void *p;
   int np;
   int tf32;
   template <class R>
   __device__ __forceinline__ void put(long long plane, long long off, R re, R im) const {
-    if (tf32) {
+    if (tf32 == 2) {
+      float *b = static_cast<float *>(p) + off;
+      b[0] = (float)re;
+      b[plane] = (float)im;
+    } else if (tf32) {
       float *b = static_cast<float *>(p) + off;
       const float hr = tc::tf32_rna((float)re), hi = tc::tf32_rna((float)im);
       b[0] = hr;
@@ -174,11 +181,6 @@ __global__ void k_wr_f32t(const double *__restrict__ WR, int nRW, int naux, floa
 __global__ void k_d2f(const double *__restrict__ src, long long n, float *__restrict__ dst) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     dst[e] = (float)src[e];
-}
-
-__global__ void k_f2d(const float *__restrict__ src, long long n, double *__restrict__ dst) {
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-    dst[e] = (double)src[e];
 }
 
 // W(q) = sum_R w_R e^{-i q.R} W(R) (R-sum of Eq. W_LRI) for IQB transfers per block, written
@@ -1791,7 +1793,7 @@ void split_free(bse_ctx *c) {
   if (!w) return;
   void *ptrs[] = {w->Wp, w->Ap, w->Mc32, w->T32, w->Y32, w->Pp, w->Xp, w->PHQ, w->PHK, w->WR32T, w->CR32, w->V032,
                   w->ck32, w->X32, w->Y32q, w->ck32q, w->ckq, w->eqpq, w->ApB, w->XpB, w->McB, w->TB,
-                  w->mf_fwd, w->mf_bwd, w->mf_zp, w->mf_z2};
+                  w->mf_fwd, w->mf_bwd, w->mf_zp, w->mf_z2, w->adjMv};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete w;
@@ -1861,19 +1863,7 @@ bse_status split_project(bse_ctx *c, const double *C_R) {
   else
     k_xv0_pieces<false><<<g, 256, 0, c->stream>>>((int)c->dim, na, w->X32, w->V032, w->kmem, pieces(w, w->Pp));
   bse_count_launch(6);
-  c->y64_valid = false;
   return bse_check_launch(c, "split project");
-}
-
-// The FP64 pair table for the adjoint of a split-precision context: the FP32 table widened.
-bse_status split_y_to_fp64(bse_ctx *c) {
-  SplitWS *w = ws(c);
-  const long long ny = 2LL * c->nk * c->nao_max * c->nb * c->naux_tot;
-  k_f2d<<<(unsigned)std::min<long long>((ny + 255) / 256, 8192), 256, 0, c->stream>>>((const float *)w->Y32, ny,
-                                                                                       (double *)c->Y);
-  bse_count_launch();
-  c->y64_valid = true;
-  return bse_check_launch(c, "pair table to FP64");
 }
 
 namespace {
@@ -2601,6 +2591,168 @@ bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_p
       s = bse_check_launch(c, "matrix-free direct slab");
       if (s != BSE_OK) return s;
     }
+  }
+  return BSE_OK;
+}
+
+// ---- adjoint of the split-precision assembly --------------------------------------------
+// dL/dW(q) = -(1/N_k) M_vv(q)^T U(q) with U[(k1,i,j)][nu] = sum_ab Gamma_(k2 j b),(k1 i a)
+// M_cc(k1,q)^nu_ab (the same contraction as the FP64 adjoint, k_adjoint.cu), for every q one
+// slab at a time: the projections from the FP32 pair table (M_vv written as plain FP32 planes,
+// M_cc as the assembly writes it), U in FP32 and the product on CUDA cores with FP32 sums over
+// the pairs, each dL/dW(q) stored in FP64 for the FP64 Fourier adjoint.  Its error (~1e-6 of
+// the gradient) is the split forward's own.
+namespace {
+
+constexpr int APCH = 64;  // nu chunk of the Gamma contraction
+
+__global__ void __launch_bounds__(256) k_adj_phi_mc32(const double2 *__restrict__ Gamma, const float2 *__restrict__ Mc,
+                                                      int nv, int nc, int naux, int n1, int n2, int n3, int q0,
+                                                      const int *__restrict__ qlist, long long dim,
+                                                      float2 *__restrict__ U) {
+  extern __shared__ float2 sa32[];
+  const int nk = n1 * n2 * n3;
+  const int k1 = blockIdx.x, qq = blockIdx.y, q = qlist[q0 + qq];
+  const int k2 = kdiff(k1, q, n1, n2, n3);
+  const int nvv = nv * nv, ncc = nc * nc, nvc = nv * nc;
+  float2 *phi = sa32;                // [nvv][ncc]
+  float2 *mcs = sa32 + nvv * ncc;    // [ncc][APCH]
+  for (int e = threadIdx.x; e < nvv * ncc; e += blockDim.x) {
+    const int ij = e / ncc, ab = e % ncc;
+    const int i = ij / nv, j = ij % nv, a = ab / nc, b = ab % nc;
+    const double2 g = Gamma[((long long)k2 * nvc + j * nc + b) * dim + (long long)k1 * nvc + i * nc + a];
+    phi[e] = make_float2((float)g.x, (float)g.y);
+  }
+  const float2 *Mk = Mc + ((long long)qq * nk + k1) * ncc * naux;
+  float2 *Uk = U + ((long long)qq * nk + k1) * nvv * naux;
+  for (int n0 = 0; n0 < naux; n0 += APCH) {
+    const int nn = min(APCH, naux - n0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < ncc * APCH; e += blockDim.x) {
+      const int ab = e / APCH, u = e % APCH;
+      mcs[e] = u < nn ? Mk[(long long)ab * naux + n0 + u] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nvv * APCH; e += blockDim.x) {
+      const int ij = e / APCH, u = e % APCH;
+      if (u >= nn) continue;
+      float xr = 0.f, xi = 0.f;
+      for (int ab = 0; ab < ncc; ab++) {
+        const float2 f = phi[ij * ncc + ab], m = mcs[ab * APCH + u];
+        xr = fmaf(f.x, m.x, fmaf(-f.y, m.y, xr));
+        xi = fmaf(f.x, m.y, fmaf(f.y, m.x, xi));
+      }
+      Uk[(long long)ij * naux + n0 + u] = make_float2(xr, xi);
+    }
+  }
+}
+
+// C[cidx[q0 + b]] = alpha A[b]^T B[b] for complex A [K x M] in two FP32 planes (row pitch lda,
+// plane pitch `plane`, batch pitch 2 plane) and B [K x N] complex64 (batch pitch sB): FP32
+// products and sums, stored as FP64.  64 x 64 output tiles, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_cgemm_tn32(int M, int N, int K, const float *__restrict__ A, long long plane,
+                                                    int lda, const float2 *__restrict__ B, long long sB,
+                                                    double2 *__restrict__ C, long long sC, const int *__restrict__ cidx,
+                                                    int q0, double alpha) {
+  __shared__ float2 As[16][64];
+  __shared__ float2 Bs[16][64];
+  const int bz = blockIdx.z;
+  const float *Are = A + (long long)bz * 2 * plane, *Aim = Are + plane;
+  B += (long long)bz * sB;
+  C += (long long)cidx[q0 + bz] * sC;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int row0 = blockIdx.y * 64, col0 = blockIdx.x * 64;
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[i][j] = make_float2(0.f, 0.f);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int kk = e / 64, r = e % 64, gk = k0 + kk;
+      const long long ia = (long long)gk * lda + row0 + r;
+      As[kk][r] = (gk < K && row0 + r < M) ? make_float2(Are[ia], Aim[ia]) : make_float2(0.f, 0.f);
+      Bs[kk][r] = (gk < K && col0 + r < N) ? B[(long long)gk * N + col0 + r] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; kk++) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; j++) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          acc[i][j].x = fmaf(a[i].x, b[j].x, fmaf(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fmaf(a[i].x, b[j].y, fmaf(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++)
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = row0 + ty + 16 * i, cc = col0 + tx + 16 * j;
+      if (r < M && cc < N) C[(long long)r * N + cc] = make_double2(alpha * acc[i][j].x, alpha * acc[i][j].y);
+    }
+}
+
+// The projections of transfers qlist[q0 ..] into the given M_vv buffer (register-blocked
+// windows, else the generic kernel), M_cc as the unfused assembly writes it.
+template <int NV, int NC>
+void launch_proj_list(bse_ctx *c, SplitWS *w, int q0, int nq, const int *qlist, PieceBuf Av) {
+  const int na = c->naux_tot;
+  const int bs = w->proj_bs ? w->proj_bs : std::min(160, (na + 31) / 32 * 32);
+  const size_t sm = sizeof(float2) * 2 * c->nao_tot * (NV + NC);
+  k_proj32_t<NV, NC><<<dim3(nq, c->nk), bs, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, na, c->nao_max,
+                                                             c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0],
+                                                             c->mesh[1], c->mesh[2], q0, qlist, w->rows, w->kmem, Av,
+                                                             w->Mc32, 0);
+}
+
+void project_list(bse_ctx *c, SplitWS *w, int q0, int nq, const int *qlist, PieceBuf Av) {
+#define BSE_PL(NV, NC)                                   \
+  if (c->nv == NV && c->nc == NC) {                      \
+    launch_proj_list<NV, NC>(c, w, q0, nq, qlist, Av);   \
+    return;                                              \
+  }
+  BSE_PL(2, 2) BSE_PL(2, 4) BSE_PL(2, 6) BSE_PL(4, 2) BSE_PL(4, 4) BSE_PL(4, 6) BSE_PL(6, 2) BSE_PL(6, 4) BSE_PL(6, 6)
+#undef BSE_PL
+  const int na = c->naux_tot;
+  dim3 grid(((na + 127) / 128) * (c->nv + c->nc), nq, c->nk);
+  const size_t sm = sizeof(float2) * 2 * c->nao_tot * c->nb;
+  k_proj32<<<grid, 128, sm, c->stream>>>(y_tab(w), ck_tab(c, w), c->nao_tot, c->nb, c->nv, c->nc, na, c->nao_max,
+                                         c->d_aux_atom, c->d_ao_start, c->d_nao, c->mesh[0], c->mesh[1], c->mesh[2],
+                                         q0, qlist, w->rows, w->kmem, Av, w->Mc32);
+}
+
+}  // namespace
+
+bse_status split_adjoint_slabs(bse_ctx *c, const double2 *Gamma) {
+  SplitWS *w = ws(c);
+  const int na = c->naux_tot;
+  if (!w->adjMv && !alloc((void **)&w->adjMv, sizeof(float) * 2 * (size_t)w->nq * w->rows * w->kmem))
+    return bse_fail(c, BSE_ENOMEM, "adjoint: slab allocation failed");
+  const size_t sm = sizeof(float2) * (c->nv * c->nv * c->nc * c->nc + c->nc * c->nc * APCH);
+  if (sm > 200 * 1024) return bse_fail(c, BSE_EINVAL, "adjoint: band window too wide");
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_adj_phi_mc32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const long long plane = (long long)w->rows * w->kmem;
+  for (int q0 = 0; q0 < c->nk; q0 += w->nq) {
+    const int nq = std::min(w->nq, c->nk - q0);
+    project_list(c, w, q0, nq, c->d_qall, PieceBuf{w->adjMv, 1, 2});
+    k_adj_phi_mc32<<<dim3(c->nk, nq), 256, sm, c->stream>>>(Gamma, w->Mc32, c->nv, c->nc, na, c->mesh[0], c->mesh[1],
+                                                          c->mesh[2], q0, c->d_qall, c->dim, w->T32);
+    dim3 grid((na + 63) / 64, (na + 63) / 64, nq);
+    k_cgemm_tn32<<<grid, 256, 0, c->stream>>>(na, na, w->rows, w->adjMv, plane, w->kmem, w->T32,
+                                              (long long)w->rows * na, c->Aq, (long long)na * na, c->d_qall, q0,
+                                              -1.0 / c->nk);
+    bse_count_launch(3);
+    const bse_status s = bse_check_launch(c, "adjoint slab (split)");
+    if (s != BSE_OK) return s;
   }
   return BSE_OK;
 }

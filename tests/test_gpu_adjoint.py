@@ -42,6 +42,23 @@ def test_adjoint_fp64_matches_oracle(cfg0):
     assert np.isclose(de[:, 4:].sum(), 1.0, atol=1e-10) and np.isclose(de[:, :4].sum(), -1.0, atol=1e-10)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x2"])
+def test_adjoint_split_exact_seed_matches_oracle(cfg0, prec):
+    """The split-precision adjoint (FP32 projections, contraction and sums over the pairs,
+    FP64 Fourier adjoint) with the oracle's exact seed x x^dagger: dW within 1e-5 of the
+    gradient's scale (the FP32 sums over ~N_k Nv^2 pairs carry ~1e-6), dE^QP (the FP64 diagonal
+    of the seed) to 1e-12."""
+    import torch
+    inp, orc, w, X = cfg0
+    G = np.outer(X[:, 0], X[:, 0].conj())
+    ref_dW, ref_de = O.grad_from_seed(orc, G)
+    b, d, H, _ = gpu_hamiltonian(inp, precision=prec)
+    dW, de = b.adjoint(torch.from_numpy(G).cuda())
+    b.sync()
+    assert _rel(dW.cpu().numpy(), ref_dW) <= 1e-5
+    assert np.abs(de.cpu().numpy() - ref_de).max() <= 1e-12
+
+
 def test_autograd_function_backward(cfg0):
     import torch
     from paper_2607_05853_b300.api import BSE

@@ -1626,7 +1626,7 @@ bse_status launch_tc_np(bse_ctx *c, int np, int bn, const CUtensorMap &A, const 
 }
 
 // ---- fused direct term -------------------------------------------------------------------
-template <int NP, int BN, int NC, bool TF>
+template <int NP, int BN, int NC, bool TF, bool MF = false>
 bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
   using Cf = tcd::DCfg<NP, BN>;
   const long long total = (long long)a.tiles_m * a.tiles_b;
@@ -1640,27 +1640,27 @@ bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof
   G.tile0[1] = total;
   G.n = 1;
   bse_prof_begin(c, prof_id);
-  tcd::k_tc_direct<NP, BN, NC, TF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(G);
+  tcd::k_tc_direct<NP, BN, NC, TF, 1, MF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(G);
   bse_prof_end(c, prof_id);
   bse_count_launch();
   return bse_check_launch(c, "tc_direct");
 }
 
-template <int NP, int BN, bool TF>
+template <int NP, int BN, bool TF, bool MF = false>
 bse_status launch_direct_nc(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
   switch (c->nc) {
-    case 2: return launch_direct_t<NP, BN, 2, TF>(c, w, a, prof_id);
-    case 4: return launch_direct_t<NP, BN, 4, TF>(c, w, a, prof_id);
-    default: return launch_direct_t<NP, BN, 6, TF>(c, w, a, prof_id);
+    case 2: return launch_direct_t<NP, BN, 2, TF, MF>(c, w, a, prof_id);
+    case 4: return launch_direct_t<NP, BN, 4, TF, MF>(c, w, a, prof_id);
+    default: return launch_direct_t<NP, BN, 6, TF, MF>(c, w, a, prof_id);
   }
 }
 
 // N tiles of the fused kernel: T's N_aux columns in one tile (two ring stages of bf16x3 pieces
 // fit up to 160 columns), so the fused path takes N_aux <= 160.
-template <int NP, bool TF = false>
+template <int NP, bool TF = false, bool MF = false>
 bse_status launch_direct_bn(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
-  if (w->bn_d == 64) return launch_direct_nc<NP, 64, TF>(c, w, a, prof_id);
-  return launch_direct_nc<NP, 160, TF>(c, w, a, prof_id);
+  if (w->bn_d == 64) return launch_direct_nc<NP, 64, TF, MF>(c, w, a, prof_id);
+  return launch_direct_nc<NP, 160, TF, MF>(c, w, a, prof_id);
 }
 
 bse_status launch_direct(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
@@ -1668,6 +1668,14 @@ bse_status launch_direct(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_i
   if (w->np == 3) return launch_direct_bn<3>(c, w, a, prof_id);
   if (w->np == 2) return launch_direct_bn<2>(c, w, a, prof_id);
   return launch_direct_bn<1>(c, w, a, prof_id);
+}
+
+// The matrix-free form of the fused kernel (a.x, a.fwd, a.bwd set; Nv = 2 or 4).
+bse_status launch_direct_mf(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof_id) {
+  if (w->tf32) return launch_direct_bn<2, true, true>(c, w, a, prof_id);
+  if (w->np == 3) return launch_direct_bn<3, false, true>(c, w, a, prof_id);
+  if (w->np == 2) return launch_direct_bn<2, false, true>(c, w, a, prof_id);
+  return launch_direct_bn<1, false, true>(c, w, a, prof_id);
 }
 
 // Ring stage bytes of the fused kernel (operand pieces of one K chunk).
@@ -1692,6 +1700,9 @@ void set_direct_attr() {
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 void set_all_attrs_now() {
   set_direct_attr<1, 64>(); set_direct_attr<1, 160>();
@@ -2549,7 +2560,34 @@ bse_status split_matvec_free(bse_ctx *c, const double2 *x, long long xs, int n_p
   if (s != BSE_OK) return s;
   const int nqp = (int)c->qplus.size();
   const int nchunk = (na + 127) / 128;
-  for (int q0 = 0; q0 < nqp; q0 += w->nq) {
+  // fused path (Nv = 2, 4): T stays in tensor memory and each block is applied from the
+  // fused kernel's epilogue (fwd / bwd summed into by atomic adds, so zeroed per slab)
+  const bool fused_mf = w->fused && (c->nv == 2 || c->nv == 4);
+  const size_t mf_bytes = sizeof(double2) * (size_t)n_pol * w->nq * c->nk * c->nvc;
+  for (int q0 = 0; fused_mf && q0 < nqp; q0 += w->nq) {
+    const int nq = std::min(w->nq, nqp - q0);
+    s = slab_project(c, w, q0, nq, nullptr);
+    if (s != BSE_OK) return s;
+    if (cudaMemsetAsync(w->mf_fwd, 0, mf_bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(w->mf_bwd, 0, mf_bytes, st) != cudaSuccess)
+      return bse_fail(c, BSE_ECUDA, "matrix-free product: clearing the slab partials failed");
+    tcd::DArgs a;
+    direct_args(c, w, q0, nq, nullptr, a);
+    a.x = x;
+    a.xs = xs;
+    a.n_pol = n_pol;
+    a.nqs = w->nq;
+    a.fwd = w->mf_fwd;
+    a.bwd = w->mf_bwd;
+    s = launch_direct_mf(c, w, a, -1);
+    if (s != BSE_OK) return s;
+    const long long n = (long long)n_pol * c->nk * c->nvc;
+    k_mf_reduce<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(w->mf_fwd, w->mf_bwd, nq, w->nq, c->nk, c->nvc, n_pol, W);
+    bse_count_launch();
+    s = bse_check_launch(c, "matrix-free direct slab");
+    if (s != BSE_OK) return s;
+  }
+  for (int q0 = 0; !fused_mf && q0 < nqp; q0 += w->nq) {
     const int nq = std::min(w->nq, nqp - q0);
     {
       dim3 grid(nchunk * (c->nv + c->nc), nq, c->nk);

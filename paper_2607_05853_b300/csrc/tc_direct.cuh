@@ -67,6 +67,11 @@ struct DArgs {
   float2 *H;              // complex64 H, or
   double2 *H64;           // complex128 H (then H is null)
   int *err;
+  // matrix-free form (MF): the block is applied to x instead of added to H
+  const double2 *x;       // [n_pol][..] complex128, polarisation p at x + p xs
+  long long xs;
+  int n_pol, nqs;         // vectors; q stride of fwd / bwd
+  double2 *fwd, *bwd;     // [n_pol][nqs][N_k][nv nc], summed into (zeroed before the launch)
 };
 
 __device__ __forceinline__ int d_kdiff(int k1, int q, int n1, int n2, int n3) {
@@ -94,7 +99,12 @@ struct DGroups {
   int n;
 };
 
-template <int NP, int BN, int NC, bool TF = false, int NG = 1>
+// MF: the matrix-free product's form.  Each pair block D is applied as soon as it is formed,
+// fwd[p][qq][k1] += D x_p[k2] and, for a mirrored transfer, bwd[p][qq][k2] += D^dagger x_p[k1],
+// with no H; for Nv = 2 or 4, whose pairs are rpp consecutive lanes of one warp, so that the
+// sums over j and over i are warp shuffles (the two column halves and the q-slab's pairs meet
+// in FP64 atomic adds).
+template <int NP, int BN, int NC, bool TF = false, int NG = 1, bool MF = false>
 __global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant__ DGroups<NG> G) {
   using C = DCfg<NP, BN>;
   constexpr int NCC = NC * NC, HALF = NCC / 2;  // D columns (a, b) per epilogue warp
@@ -329,6 +339,67 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant_
       // accumulators drained: the next tile's MMAs may start while H is updated
       tc::tc_fence_before();
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(tempty)) : "memory");
+      if constexpr (MF) {
+        // every lane takes part in the shuffles; dead rows contribute zero and add nothing
+        const bool live = ok && row_ok;
+        const int rowc = live ? row : 0;
+        const int q = args.qlist[args.b_base + b];
+        const int k1 = rowc / rpp, ij = rowc % rpp, i = ij / args.nv, j = ij % args.nv;
+        const int k2 = d_kdiff(k1, q, args.n1, args.n2, args.n3);
+        const bool mirror = !d_self_conj(q, args.n1, args.n2, args.n3);
+        const int nvc = args.nv * NC, nk = args.n1 * args.n2 * args.n3;
+        float2 dv[HALF];
+#pragma unroll
+        for (int e = 0; e < HALF; e++) {
+          const float2 x1 = tc::up2(acc1[e]), x2 = tc::up2(acc2[e]);
+          dv[e] = live ? make_float2(-invf * (x1.x - x2.y), -invf * (x1.y + x2.x)) : make_float2(0.f, 0.f);
+        }
+        for (int p = 0; p < args.n_pol; p++) {
+          const double2 *xk2 = args.x + p * args.xs + (long long)k2 * nvc + j * NC;  // x[k2][(j, b)]
+          const double2 *xk1 = args.x + p * args.xs + (long long)k1 * nvc + i * NC;  // x[k1][(i, a)]
+          double2 *fw = args.fwd + (((long long)p * args.nqs + b) * nk + k1) * nvc + i * NC + half * (NC / 2);
+          double2 *bw = args.bwd + (((long long)p * args.nqs + b) * nk + k2) * nvc + j * NC;
+#pragma unroll
+          for (int aa = 0; aa < NC / 2; aa++) {  // row (i, a = half NC/2 + aa) of D times x[k2]
+            double fr = 0.0, fi = 0.0;
+#pragma unroll
+            for (int bb = 0; bb < NC; bb++) {
+              const float2 d = dv[aa * NC + bb];
+              const double2 xv = xk2[bb];
+              fr += (double)d.x * xv.x - (double)d.y * xv.y;
+              fi += (double)d.x * xv.y + (double)d.y * xv.x;
+            }
+            for (int o = 1; o < args.nv; o <<= 1) {  // sum over j
+              fr += __shfl_xor_sync(0xffffffffu, fr, o);
+              fi += __shfl_xor_sync(0xffffffffu, fi, o);
+            }
+            if (live && j == 0) {
+              atomicAdd(&fw[aa].x, fr);
+              atomicAdd(&fw[aa].y, fi);
+            }
+          }
+#pragma unroll
+          for (int bb = 0; bb < NC; bb++) {  // column (j, b) of D, conjugated, times x[k1]
+            double gr = 0.0, gi = 0.0;
+#pragma unroll
+            for (int aa = 0; aa < NC / 2; aa++) {
+              const float2 d = dv[aa * NC + bb];
+              const double2 xv = xk1[half * (NC / 2) + aa];
+              gr += (double)d.x * xv.x + (double)d.y * xv.y;
+              gi += (double)d.x * xv.y - (double)d.y * xv.x;
+            }
+            for (int o = args.nv; o < rpp; o <<= 1) {  // sum over i
+              gr += __shfl_xor_sync(0xffffffffu, gr, o);
+              gi += __shfl_xor_sync(0xffffffffu, gi, o);
+            }
+            if (live && mirror && i == 0) {
+              atomicAdd(&bw[bb].x, gr);
+              atomicAdd(&bw[bb].y, gi);
+            }
+          }
+        }
+        continue;
+      }
       if (!ok || !row_ok) continue;
       // H block (k1, k2) += -D / N_k, its mirror (k2, k1) += conj(-D / N_k); the q = 0 diagonal
       // sums in FP64 with E_c - E_v

@@ -8,11 +8,18 @@ import oracle as O
 from synth import config_spec, make_inputs
 
 from helpers import to_dev
+from synth import CrystalSpec
+from synth.crystal import _fcc
 from test_gpu_fp64 import RAGGED
 
 pytestmark = pytest.mark.gpu
 
 ETA = 0.1
+
+# Nv = 2 with N_aux <= 160: the fused kernel's matrix-free form with two-lane j sums (cfg0 has
+# Nv = 4; ragged, two_d and wide take the unfused block application)
+NV2 = CrystalSpec("nv2", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25]]), (7, 7), (11, 13), (2, 1, 1),
+                  (3, 2, 2), 2, 6, 2718, r_max=1.0)
 
 
 def _ctx(inp, precision="bf16x3", Q=None):
@@ -29,12 +36,12 @@ def _ctx(inp, precision="bf16x3", Q=None):
     return b, d
 
 
-@pytest.mark.parametrize("name", ["cfg0", "ragged", "wide", "two_d"])
+@pytest.mark.parametrize("name", ["cfg0", "nv2", "ragged", "wide", "two_d"])
 def test_matfree_lanczos_matches_stored_H(name):
     """Same recursion coefficients (a_j, b_j) as the stored complex64 H: the two differ only in
     where the FP32-accurate elements are rounded."""
     import torch
-    inp = make_inputs(config_spec(0) if name == "cfg0" else RAGGED[name])
+    inp = make_inputs(config_spec(0) if name == "cfg0" else NV2 if name == "nv2" else RAGGED[name])
     b, d = _ctx(inp)
     H = b.assemble()
     u = b.dipole_vector(d["vel"], d["e_ks"])

@@ -5,8 +5,12 @@
 //
 // The matrix-vector product reads H once per Lanczos step for all polarisations.  For a
 // complex128 H the products are FP64; for a complex64 H (split-precision assembly) the
-// products and the per-lane partial sums are FP32 (H itself carries FP32 rounding) and
-// the cross-lane sums, dots, norms, updates and the reorthogonalisation are FP64.
+// products are FP32 (H itself carries FP32 rounding), read through the upper-triangle tiles
+// (k_hmv_tma) and summed across tiles with compensated FP32 sums (k_hmv_reduce); the
+// recursion scalars, the basis, the norms and the three-term update are FP64, and the
+// reorthogonalisation projects on an FP32 shadow of the basis (FP32 products, FP64 chunk
+// sums) and subtracts from the FP64 vector.  The short kernels of a step are launched with
+// programmatic stream serialization (launch_pdl).
 #include <algorithm>
 #include <cmath>
 #include <mutex>

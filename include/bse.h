@@ -226,7 +226,8 @@ bse_status bse_dipole_vector(bse_ctx *ctx, const double *vel, const double *e_ks
 
 /* Step (d): Haydock spectrum.  For each of n_pol (1..3) start vectors u[p] (complex128
  * [n_pol][dim]) run n_steps (1..dim) Lanczos steps on H (type as in bse_assemble) in
- * FP64 with full reorthogonalisation (twice), stopping early when b_j < 1e-14 max|H|,
+ * FP64 with full reorthogonalisation (a second pass where the DGKS test asks for it),
+ * stopping early when b_j < 1e-14 max|H|,
  * then eps2[w] = prefactor * sum_p -(1/pi) Im g_p(omega[w] + i eta), with
  * g = |u|^2/(z - a1 - b1^2/(z - a2 - ...)).  eps2 : [n_w] float64.  ab : optional
  * [n_pol][3][n_steps] float64 receiving a_j, b_j and (in [p][2][0]) |u|, or NULL.

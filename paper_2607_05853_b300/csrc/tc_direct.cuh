@@ -302,34 +302,61 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant_
         // this warp's (a, b) rows of the pair: [ab][nu], nui columns each
         const float2 *mcs = reinterpret_cast<const float2 *>(smem + s * C::STAGE) +
                             ((size_t)pr * NCC + half * HALF) * args.nui;
-        for (int c0 = 0; c0 < nn; c0 += 16) {
-          uint32_t rr[16], ri[16];
-          tc::tmem_ld16(tm_re + lane_off + nu0 + c0, rr);
-          tc::tmem_ld16(tm_im + lane_off + nu0 + c0, ri);
-          tc::tmem_ld_wait();
-          if (ok && row_ok) {
-            // columns in pairs (nu, nu + 1); T is zero past N_aux, and the M_cc column paired
-            // with the last one of an odd N_aux is ignored
-            const int cmax = min(16, nn - c0);
+        // T columns c0 .. c0 + 15 of this slice times the pair's M_cc rows: columns in pairs
+        // (nu, nu + 1); T is zero past N_aux, and the M_cc column paired with the last one of an
+        // odd N_aux is ignored
+        auto fma_group = [&](const uint32_t (&rr)[16], const uint32_t (&ri)[16], int c0) {
+          const int cmax = min(16, nn - c0);
 #pragma unroll
-            for (int u = 0; u < 16; u += 2) {
-              if (u >= cmax) break;
-              const float tr0 = __uint_as_float(rr[u]), ti0 = __uint_as_float(ri[u]);
-              const float tr1 = __uint_as_float(rr[u + 1]), ti1 = __uint_as_float(ri[u + 1]);
-              const unsigned long long TR0 = tc::pk2(tr0, tr0), TI0 = tc::pk2(ti0, ti0);
-              const unsigned long long TR1 = tc::pk2(tr1, tr1), TI1 = tc::pk2(ti1, ti1);
+          for (int u = 0; u < 16; u += 2) {
+            if (u >= cmax) break;
+            const float tr0 = __uint_as_float(rr[u]), ti0 = __uint_as_float(ri[u]);
+            const float tr1 = __uint_as_float(rr[u + 1]), ti1 = __uint_as_float(ri[u + 1]);
+            const unsigned long long TR0 = tc::pk2(tr0, tr0), TI0 = tc::pk2(ti0, ti0);
+            const unsigned long long TR1 = tc::pk2(tr1, tr1), TI1 = tc::pk2(ti1, ti1);
 #pragma unroll
-              for (int e = 0; e < HALF; e++) {
-                const float4 mm = *reinterpret_cast<const float4 *>(mcs + (size_t)e * args.nui + c0 + u);
-                const bool tail = u + 1 >= cmax;
-                const unsigned long long m0v = tc::pk2(mm.x, mm.y),
-                                         m1v = tc::pk2(tail ? 0.f : mm.z, tail ? 0.f : mm.w);
-                tc::ffma2(acc1[e], m0v, TR0);
-                tc::ffma2(acc2[e], m0v, TI0);
-                tc::ffma2(acc1[e], m1v, TR1);
-                tc::ffma2(acc2[e], m1v, TI1);
-              }
+            for (int e = 0; e < HALF; e++) {
+              const float4 mm = *reinterpret_cast<const float4 *>(mcs + (size_t)e * args.nui + c0 + u);
+              const bool tail = u + 1 >= cmax;
+              const unsigned long long m0v = tc::pk2(mm.x, mm.y),
+                                       m1v = tc::pk2(tail ? 0.f : mm.z, tail ? 0.f : mm.w);
+              tc::ffma2(acc1[e], m0v, TR0);
+              tc::ffma2(acc2[e], m0v, TI0);
+              tc::ffma2(acc1[e], m1v, TR1);
+              tc::ffma2(acc2[e], m1v, TI1);
             }
+          }
+        };
+        if constexpr (NC <= 4 && NG == 1) {
+          // tensor-memory loads one 16-column group ahead of the FMAs that use them (the wait
+          // covers every load the thread issued before it); Nc = 6 and the batched work list
+          // keep one group in flight (their accumulators and group arguments leave no
+          // registers for a second)
+          uint32_t ra[16], ia[16], rb[16], ib[16];
+          tc::tmem_ld16(tm_re + lane_off + nu0, ra);
+          tc::tmem_ld16(tm_im + lane_off + nu0, ia);
+          for (int c0 = 0; c0 < nn; c0 += 32) {
+            tc::tmem_ld_wait();
+            const bool next1 = c0 + 16 < nn, next2 = c0 + 32 < nn;
+            if (next1) {
+              tc::tmem_ld16(tm_re + lane_off + nu0 + c0 + 16, rb);
+              tc::tmem_ld16(tm_im + lane_off + nu0 + c0 + 16, ib);
+            }
+            if (ok && row_ok) fma_group(ra, ia, c0);
+            tc::tmem_ld_wait();
+            if (next2) {
+              tc::tmem_ld16(tm_re + lane_off + nu0 + c0 + 32, ra);
+              tc::tmem_ld16(tm_im + lane_off + nu0 + c0 + 32, ia);
+            }
+            if (next1 && ok && row_ok) fma_group(rb, ib, c0 + 16);
+          }
+        } else {
+          for (int c0 = 0; c0 < nn; c0 += 16) {
+            uint32_t rr[16], ri[16];
+            tc::tmem_ld16(tm_re + lane_off + nu0 + c0, rr);
+            tc::tmem_ld16(tm_im + lane_off + nu0 + c0, ri);
+            tc::tmem_ld_wait();
+            if (ok && row_ok) fma_group(rr, ri, c0);
           }
         }
         // the epilogue warps are done with this slice: one thread releases the stage

@@ -1043,7 +1043,9 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
   const float4 *qp = reinterpret_cast<const float4 *>(Q32 + p * qs + e);
   const long long rs = dim / 2;
   float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
-  for (int i0 = 0; i0 <= j; i0 += 1024) {
+  // basis rows are taken from j down to 0: the dots pass that precedes this one read them
+  // upwards, so its most recent rows (the ones still in L2) come first here
+  for (int i0 = (j / 1024) * 1024; i0 >= 0; i0 -= 1024) {
     const int n = min(1024, j + 1 - i0);
     __syncthreads();
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -1052,21 +1054,22 @@ __global__ void __launch_bounds__(256, 2) k_reorth_update32(double2 *__restrict_
     }
     __syncthreads();
     if (in) {
-      int i = 0;
-      for (; i + RUN <= n; i += RUN) {
+      int i = n;
+      for (; i >= RUN; i -= RUN) {
         float4 q[RUN];
 #pragma unroll
-        for (int u = 0; u < RUN; u++) q[u] = __ldg(qp + (long long)(i0 + i + u) * rs);
+        for (int u = 0; u < RUN; u++) q[u] = __ldg(qp + (long long)(i0 + i - 1 - u) * rs);
 #pragma unroll
         for (int u = 0; u < RUN; u++) {
-          const float2 c = cs[i + u];
+          const float2 c = cs[i - 1 - u];
           a0r = fmaf(c.x, q[u].x, fmaf(-c.y, q[u].y, a0r));
           a0i = fmaf(c.x, q[u].y, fmaf(c.y, q[u].x, a0i));
           a1r = fmaf(c.x, q[u].z, fmaf(-c.y, q[u].w, a1r));
           a1i = fmaf(c.x, q[u].w, fmaf(c.y, q[u].z, a1i));
         }
       }
-      for (; i < n; i++) {
+      while (i > 0) {
+        i--;
         const float2 c = cs[i];
         const float4 q = __ldg(qp + (long long)(i0 + i) * rs);
         a0r = fmaf(c.x, q.x, fmaf(-c.y, q.y, a0r));

@@ -27,6 +27,7 @@
 
 #include "bse_internal.cuh"
 #include "tc_direct.cuh"
+#include "tc_direct_ns.cuh"
 #include "tc_gemm.cuh"
 
 namespace {
@@ -58,6 +59,10 @@ struct SplitWS {
   int naux_pad = 0;              // M_cc row length (multiple of 16) in the fused layout
   int pairs_d = 0, nui_d = 0;    // pairs per tile; M_cc columns per ring item
   CUtensorMap tmB_d, tmM_d;      // W pieces with the fused N tile; M_cc {nu, ab, (q, k1)} per item
+  // the fused kernel with T's columns in two halves (k_tc_direct_ns): N_aux in (80, 160],
+  // Nc <= 4 and pairs x Nc^2 <= 128 (a 16-column M_cc slice in 16 KB)
+  bool nsplit = false;
+  CUtensorMap tmB_dh, tmM_dh;    // W pieces with 80-row boxes; M_cc with 16-column boxes
   // FP32 per-k stage
   float2 *PHQ = nullptr;         // [nk][n_RW]  w_R e^{-i q.R}
   float2 *PHK = nullptr;         // [nk][n_RC]  e^{+i k.R}
@@ -1639,6 +1644,17 @@ bse_status launch_direct_t(bse_ctx *c, SplitWS *w, const tcd::DArgs &a, int prof
   G.tile0[0] = 0;
   G.tile0[1] = total;
   G.n = 1;
+  if constexpr (BN == 160 && !MF && NC <= 4) {
+    if (w->nsplit) {  // T's columns in two halves, the epilogue of one under the MMAs of the next
+      G.B[0] = w->tmB_dh;
+      G.M[0] = w->tmM_dh;
+      bse_prof_begin(c, prof_id);
+      tcd::k_tc_direct_ns<NP, NC, TF><<<ctas, tcd::NS_THREADS, tcd::NsCfg<NP>::SMEM, c->stream>>>(G);
+      bse_prof_end(c, prof_id);
+      bse_count_launch();
+      return bse_check_launch(c, "tc_direct_ns");
+    }
+  }
   bse_prof_begin(c, prof_id);
   tcd::k_tc_direct<NP, BN, NC, TF, 1, MF><<<ctas, tcd::THREADS, Cf::SMEM, c->stream>>>(G);
   bse_prof_end(c, prof_id);
@@ -1703,6 +1719,11 @@ void set_direct_attr() {
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 2, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 4, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   cudaFuncSetAttribute(tcd::k_tc_direct<NP, BN, 6, TF, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if constexpr (BN == 160) {
+    constexpr int sn = tcd::NsCfg<NP>::SMEM;
+    cudaFuncSetAttribute(tcd::k_tc_direct_ns<NP, 2, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sn);
+    cudaFuncSetAttribute(tcd::k_tc_direct_ns<NP, 4, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, sn);
+  }
 }
 void set_all_attrs_now() {
   set_direct_attr<1, 64>(); set_direct_attr<1, 160>();
@@ -1747,6 +1768,7 @@ bse_status split_setup(bse_ctx *c) {
       w->nui_d = 16;
     }
     w->nui_d = std::min(w->nui_d, w->naux_pad);
+    w->nsplit = w->bn_d == 160 && na > tcd::NS_HALF && c->nc <= 4 && w->pairs_d * ncc <= 128;
   }
   const size_t pb = (size_t)w->pbytes;
   const size_t per_q = (size_t)w->pp * w->rows * w->kmem * pb + (size_t)c->nk * c->nc * c->nc * w->naux_pad * 8 +
@@ -1792,6 +1814,10 @@ bse_status split_setup(bse_ctx *c) {
             (!w->fused || make_map_c64_3d(&w->tmM_d, w->Mc32, w->naux_pad, (long long)c->nc * c->nc,
                                           (long long)w->nq * c->nk, w->naux_pad, w->nui_d, c->nc * c->nc,
                                           w->pairs_d)) &&
+            (!w->nsplit ||
+             (make_map(&w->tmB_dh, w->Wp, na, na, (long long)w->pp * c->nk, w->kmem, tcd::NS_HALF, tf) &&
+              make_map_c64_3d(&w->tmM_dh, w->Mc32, w->naux_pad, (long long)c->nc * c->nc, (long long)w->nq * c->nk,
+                              w->naux_pad, tcd::NS_MC_COLS, c->nc * c->nc, w->pairs_d))) &&
             make_map(&w->tmA_x, w->Pp, na, c->dim, w->pp, w->kmem, tcg::BM, tf) &&
             make_map(&w->tmB_x, w->Xp, na, c->dim, w->pp, w->kmem, TC_BN, tf);
   if (!ok) return bse_fail(c, BSE_ECUDA, "tensor map encoding failed");

@@ -88,6 +88,59 @@ __device__ __forceinline__ bool d_self_conj(int q, int n1, int n2, int n3) {
   return (n1 - a1) % n1 == a1 && (n2 - a2) % n2 == a2 && (n3 - a3) % n3 == a3;
 }
 
+// H block (k1, k2) += -D / N_k and its mirror (k2, k1) += conj(-D / N_k) for the D columns
+// (a, b) = half Nc^2 / 2 + e of one row (k1, i, j) of a q's tile, D[e] = acc1[e] (mr, mi) tr
+// sums and acc2[e] (mr, mi) ti sums; the q = 0 diagonal sums in FP64 with E_c - E_v.  For a
+// complex128 H the D contribution is added in FP64.
+template <int NC>
+__device__ __forceinline__ void d_apply_h(const DArgs &args, const unsigned long long (&acc1)[NC * NC / 2],
+                                          const unsigned long long (&acc2)[NC * NC / 2], int row, int b, int half) {
+  constexpr int HALF = NC * NC / 2;
+  const double inv = 1.0 / ((double)args.n1 * args.n2 * args.n3);
+  const float invf = (float)inv;
+  const int nb = args.nv + NC, rpp = args.nv * args.nv;
+  const int q = args.qlist[args.b_base + b];
+  const int k1 = row / rpp, ij = row % rpp, i = ij / args.nv, j = ij % args.nv;
+  const int k2 = d_kdiff(k1, q, args.n1, args.n2, args.n3);
+  const bool mirror = !d_self_conj(q, args.n1, args.n2, args.n3);
+  const int nvc = args.nv * NC;
+#pragma unroll
+  for (int e = 0; e < HALF; e++) {
+    const int ab = half * HALF + e, a = ab / NC, bb = ab % NC;
+    const float2 x1 = tc::up2(acc1[e]), x2 = tc::up2(acc2[e]);
+    const float dr = x1.x - x2.y, di = x1.y + x2.x;
+    const int ia = i * NC + a, jb = j * NC + bb;
+    const long long ih = ((long long)k1 * nvc + ia) * args.dim + (long long)k2 * nvc + jb;
+    const long long im = ((long long)k2 * nvc + jb) * args.dim + (long long)k1 * nvc + ia;
+    if (args.H64) {
+      double2 hv = args.H64[ih];
+      hv.x -= inv * (double)dr;
+      hv.y -= inv * (double)di;
+      if (q == 0 && ia == jb) hv.x += args.eqp[(long long)k1 * nb + args.nv + a] - args.eqp[(long long)k1 * nb + i];
+      args.H64[ih] = hv;
+      if (mirror) {
+        double2 mv = args.H64[im];
+        mv.x -= inv * (double)dr;
+        mv.y += inv * (double)di;
+        args.H64[im] = mv;
+      }
+      continue;
+    }
+    float2 *hp = args.H + ih;
+    const float2 hx = *hp;
+    float2 hv = make_float2(fmaf(-invf, dr, hx.x), fmaf(-invf, di, hx.y));
+    if (q == 0 && ia == jb)
+      hv.x = (float)((double)hx.x - inv * (double)dr + args.eqp[(long long)k1 * nb + args.nv + a] -
+                     args.eqp[(long long)k1 * nb + i]);
+    *hp = hv;
+    if (mirror) {
+      float2 *hm = args.H + im;
+      const float2 mx = *hm;
+      *hm = make_float2(fmaf(-invf, dr, mx.x), fmaf(invf, di, mx.y));
+    }
+  }
+}
+
 // The work list of one launch: NG systems' q-slabs (operand, W and M_cc tensor maps and
 // arguments each), their tiles numbered consecutively, group g owning tiles tile0[g] ..
 // tile0[g + 1] - 1 (n groups in use); a single slab is the list with NG = 1.
@@ -267,9 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant_
     for (long long t = blockIdx.x; t < total; t += gridDim.x, tcount++) {
       group_of(t, g);
       const DArgs args = G.a[GI];  // a register copy: the H stores below cannot alias it
-      const double inv = 1.0 / ((double)args.n1 * args.n2 * args.n3);
-      const float invf = (float)inv;
-      const int nb = args.nv + NC;
+      const float invf = (float)(1.0 / ((double)args.n1 * args.n2 * args.n3));
       const int rpp = args.nv * args.nv;
       it += args.k_chunks;
       bool ok = !*abort_flag && tc::mbar_wait_bounded(tfull, tcount & 1, 4 * WAIT_LIMIT);
@@ -428,48 +479,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_direct(const __grid_constant_
         continue;
       }
       if (!ok || !row_ok) continue;
-      // H block (k1, k2) += -D / N_k, its mirror (k2, k1) += conj(-D / N_k); the q = 0 diagonal
-      // sums in FP64 with E_c - E_v
-      const int q = args.qlist[args.b_base + b];
-      const int k1 = row / rpp, ij = row % rpp, i = ij / args.nv, j = ij % args.nv;
-      const int k2 = d_kdiff(k1, q, args.n1, args.n2, args.n3);
-      const bool mirror = !d_self_conj(q, args.n1, args.n2, args.n3);
-      const int nvc = args.nv * NC;
-#pragma unroll
-      for (int e = 0; e < HALF; e++) {
-        const int ab = half * HALF + e, a = ab / NC, bb = ab % NC;
-        const float2 x1 = tc::up2(acc1[e]), x2 = tc::up2(acc2[e]);
-        const float dr = x1.x - x2.y, di = x1.y + x2.x;
-        const int ia = i * NC + a, jb = j * NC + bb;
-        const long long ih = ((long long)k1 * nvc + ia) * args.dim + (long long)k2 * nvc + jb;
-        const long long im = ((long long)k2 * nvc + jb) * args.dim + (long long)k1 * nvc + ia;
-        if (args.H64) {  // complex128 H: the D contribution and the diagonal added in FP64
-          double2 hv = args.H64[ih];
-          hv.x -= inv * (double)dr;
-          hv.y -= inv * (double)di;
-          if (q == 0 && ia == jb) hv.x += args.eqp[(long long)k1 * nb + args.nv + a] - args.eqp[(long long)k1 * nb + i];
-          args.H64[ih] = hv;
-          if (mirror) {
-            double2 mv = args.H64[im];
-            mv.x -= inv * (double)dr;
-            mv.y += inv * (double)di;
-            args.H64[im] = mv;
-          }
-          continue;
-        }
-        float2 *hp = args.H + ih;
-        const float2 hx = *hp;
-        float2 hv = make_float2(fmaf(-invf, dr, hx.x), fmaf(-invf, di, hx.y));
-        if (q == 0 && ia == jb)
-          hv.x = (float)((double)hx.x - inv * (double)dr + args.eqp[(long long)k1 * nb + args.nv + a] -
-                         args.eqp[(long long)k1 * nb + i]);
-        *hp = hv;
-        if (mirror) {
-          float2 *hm = args.H + im;
-          const float2 mx = *hm;
-          *hm = make_float2(fmaf(-invf, dr, mx.x), fmaf(invf, di, mx.y));
-        }
-      }
+      d_apply_h<NC>(args, acc1, acc2, row, b, half);
     }
   }
   tc::tc_fence_before();

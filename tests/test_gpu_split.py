@@ -25,6 +25,20 @@ pytestmark = pytest.mark.gpu
 BIG_AUX = CrystalSpec("bigaux", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25], [0.5, 0.5, 0.5]]),
                       (5, 6, 5), (60, 70, 55), (2, 1, 1), (2, 2, 2), 2, 2, 777, r_max=1.0)
 
+# 80 < N_aux <= 160 with Nc <= 4: the fused direct term takes T's columns in two halves, each
+# with its own tensor-memory buffer (k_tc_direct_ns).  N_aux = 97 leaves one column in the
+# second half's last 16-column slice; Nv = Nc = 2 fills a tile with 32 pairs; Nv = 6 leaves 20
+# of a tile's 128 rows unused.
+_DIAMOND = np.array([[0, 0, 0], [0.25, 0.25, 0.25]])
+COLUMN_HALVES = {
+    "half44": CrystalSpec("half44", _fcc(5.43), _DIAMOND, (5, 6), (53, 44), (2, 1, 1), (2, 2, 3), 4, 4, 5150,
+                          r_max=1.0),
+    "half22": CrystalSpec("half22", _fcc(5.43), _DIAMOND, (4, 5), (61, 38), (2, 1, 1), (3, 2, 2), 2, 2, 5151,
+                          r_max=1.0),
+    "half62": CrystalSpec("half62", _fcc(5.43), np.array([[0, 0, 0], [0.25, 0.25, 0.25], [0.5, 0.5, 0.5]]),
+                          (4, 5, 4), (40, 41, 42), (2, 1, 1), (2, 2, 2), 6, 2, 5152, r_max=1.0),
+}
+
 
 @pytest.fixture(scope="module")
 def cfg0():
@@ -201,3 +215,16 @@ def test_split_spectrum_ragged_full_length(name):
     ref = O.eps2_exact(Href, orc.dipoles(), om.cpu().numpy(), 0.1, orc.prefactor())
     rel_l2 = np.linalg.norm(eps.cpu().numpy() - ref) / np.linalg.norm(ref)
     assert rel_l2 <= 1e-4, rel_l2
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x2", "bf16x1", "tf32x2"])
+@pytest.mark.parametrize("name", list(COLUMN_HALVES))
+def test_split_column_half_direct(name, prec):
+    """The direct term in two column halves of T (every piece kind: three, two or one bf16
+    pieces, two tf32 pieces) against the oracle, with the bounds of the tiny workload."""
+    spec = COLUMN_HALVES[name]
+    assert 80 < spec.n_aux <= 160 and spec.nc <= 4
+    inp = make_inputs(spec)
+    ref = O.BSEOracle(inp).hamiltonian()
+    b, d, H, _ = gpu_hamiltonian(inp, precision=prec)
+    assert_split_close(H.cpu().numpy(), ref, prec)

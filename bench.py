@@ -36,8 +36,9 @@ MV_DRAM_BYTES_PER_TILE = (1.032827e9 + 45.723136e6) / 7875
 # DRAM bytes per transfer q of the split assembly's two slab kernels, from ncu captures of one
 # 20-q slab of the 16000-dim case (10^3 k-points, N_aux 150, Nv = Nc = 4): the projections
 # (313.4 MB read, 922.3 MB written: the M_vv bf16 pieces and M_cc) and the fused direct term
-# (1077.2 MB read, 70.9 MB written).  Both grow in proportion to the k-points per q.
-ASM_DRAM_BYTES_PER_Q_MESH10 = ((313.358848e6 + 922.320640e6) + (1077.169e6 + 70.853376e6)) / 20
+# in its column-half form (1078.0 MB read, 71.3 MB written).  Both grow in proportion to the
+# k-points per q.
+ASM_DRAM_BYTES_PER_Q_MESH10 = ((313.358848e6 + 922.320640e6) + (1077.953e6 + 71.327744e6)) / 20
 UNIT = "H elements/s"
 
 
